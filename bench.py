@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Benchmark: PU200 events/s of the Segment Linking chain on GB300.
+
+A step is one pass of the whole chain (binning, MD, LS, T3, T5, pLS, pT5,
+pT3, cross-cleaning, track candidates) over one synthetic PU200 event
+(8000 tracks + 12 jet-like tracks, 13260-module geometry). The device-timed
+`value` has the event's hits already in HBM; `e2e` goes through the C ABI
+from pinned host buffers and includes the host-to-device copy of the hits
+and seeds and the device-to-host read of the track candidates. The L2 cache
+is flushed (a 256 MiB write) between timed steps, outside the timed spans.
+
+Multi-GPU: events are independent, so N ranks run N replicas on their own
+events (weak scaling, no collective on the data path); the time is the max
+over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PU200 events/sec"
+UNIT = "events/s"
+WORKLOAD = ("PU200 ttbar-like single event: 8000 prompt tracks (beamspot sigma_z 5 cm, dN/dpT ~ pT^-3 above "
+            "0.5 GeV, |eta| < 2.4) + 12 jet-like tracks, 2% noise hits, one 3-hit pixel seed per track; "
+            "13260-module barrel+endcap geometry")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(kernel, st, n_hits, n_seeds, n_mod):
+    """Compulsory bytes of one launch: its inputs read once and outputs written once (from object counts)."""
+    c = st["counts"]
+    md, ls, t3, t5, pls, p5, p3 = (c[k] for k in ("md", "ls", "t3", "t5", "pls", "pt5", "pt3"))
+    table = {
+        "md": n_hits * 16 + n_mod * 2 * 4 + md * 44 + n_mod * 8,          # sorted hits in, MDs out
+        "ls": md * 24 + n_mod * 8 + ls * 12 + md * 8,                     # MD anchors+stubs in, LS out
+        "t3": ls * 8 + md * 24 + t3 * 20 + md * 8,                        # LS + MDs in, T3 out
+        "t5": t3 * 16 + ls * 4 + md * 16 + t5 * 56 + md * 8,              # T3 + MDs in, T5 out
+        "pt5": n_seeds * 48 + md * 16 + t5 * 16 + p5 * 28,
+        "pt3": n_seeds * 48 + md * 16 + t3 * 8 + p3 * 28,
+    }
+    return table.get(kernel)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2209_13711_gb300 as P
+    from synth import events as E, geometry as G, maps as M
+    from synth.config import DEFAULT_CUTS
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    geom = G.make_geometry(barrel_only=False)
+    maps = M.load_maps(geom)
+    ctx = P.Context(geom.module_table(), maps, cfg=DEFAULT_CUTS, capacity=P.default_capacity(1), device=local)
+    n_ev = args.steps + args.warmup
+    events = [E.pu200_event(rank * 100000 + i, geom) for i in range(n_ev)]
+    packed = [P.pack_events([e]) for e in events]
+    dev = [{k: (torch.from_numpy(v).cuda() if k not in ("hit_off", "seed_off") else v) for k, v in b.items()}
+           for b in packed]
+    pinned = [{k: (torch.from_numpy(v).pin_memory() if k not in ("hit_off", "seed_off") else v)
+               for k, v in b.items()} for b in packed]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-timed: inputs resident in HBM ---------------------------
+    for i in range(args.warmup):
+        ctx.run_packed(dev[i], stream=st.cuda_stream)
+    barrier()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    with ClockSampler(local) as clk:
+        barrier()
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            ev0[i].record(st)
+            ctx.run_packed(dev[args.warmup + i], stream=st.cuda_stream)
+            ev1[i].record(st)
+            launches += ctx.launch_count
+        barrier()
+    dev_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    stats0 = ctx.stats(0)
+    # ---- end to end through the C ABI from pinned host memory -----------
+    e2e_s = 0.0
+    h2d = d2h = 0
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        b = pinned[args.warmup + i]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.run_packed(b, stream=st.cuda_stream)
+        tc = ctx.track_candidates(0)
+        t1 = time.perf_counter()
+        e2e_s += t1 - t0
+        h2d += sum(int(v.numel() * v.element_size()) for k, v in b.items() if k not in ("hit_off", "seed_off"))
+        h2d += 8 * len(b["hit_off"])
+        d2h += 4 + tc["n"] * (4 + 4 + 40 + 12)
+    # ---- per-kernel device times (profiling pass, same workload) --------
+    ctx.set_profiling(True)
+    per_kernel = {}
+    for i in range(min(args.steps, 5)):
+        flush.fill_(i & 0xff)
+        ctx.run_packed(dev[args.warmup + i], stream=st.cuda_stream)
+        for name, ms in ctx.kernel_times():
+            per_kernel.setdefault(name, []).append(ms)
+    ctx.set_profiling(False)
+    kavg = {k: sum(v) / len(v) for k, v in per_kernel.items()}
+    top = max(kavg, key=kavg.get)
+    # timing across ranks
+    tot = torch.tensor([dev_ms, e2e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
+    dev_ms, e2e_s = float(tot[0]), float(tot[1])
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    value = ws * args.steps / (dev_ms / 1e3)
+    hbm_peak, peak_kind = _peaks()
+    b_alg = algorithmic_bytes(top, stats0, len(events[args.warmup].x), len(events[args.warmup].seeds), geom.n_mod)
+    roof = None
+    if b_alg is not None:
+        achieved = b_alg / (kavg[top] / 1e3) / 1e9
+        roof = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 5), "traffic": None, "peak_source": peak_kind,
+                "algorithmic_bytes": int(b_alg), "kernel_ms": round(kavg[top], 4)}
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "events_per_step": 1, "path": "plain, one event per launch sequence",
+                   "l2": "flushed between steps (256 MiB write, outside the timed spans)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "e2e": {"value": round(ws * args.steps / e2e_s, 2), "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+                "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "roofline": roof,
+        "kernel_ms": {k: round(v, 4) for k, v in sorted(kavg.items(), key=lambda kv: -kv[1])},
+        "objects_per_event": stats0["counts"],
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _oracle_event_seconds(seed):
+    from oracle import oracle as O
+    from synth import events as E, geometry as G, maps as M
+    from synth.config import DEFAULT_CUTS
+    geom = G.make_geometry(barrel_only=False)
+    maps = M.load_maps(geom)
+    ev = E.pu200_event(seed, geom)
+    S = O.Setup(geom.module_table(), maps, DEFAULT_CUTS, ev)
+    t0 = time.perf_counter()
+    S.run()
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args, budget_s=30.0):
+    """The FP64 oracle, as it stands, on this host's cores (one thread)."""
+    t, n = 0.0, 0
+    while n == 0 or (t < budget_s / 2 and n < 3):
+        t += _oracle_event_seconds(n)
+        n += 1
+    return {"value": round(n / t, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} PU200 event(s), seeds 0..{n - 1}, full chain, single thread, FP64",
+            "host_cpus": os.cpu_count()}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import platform
+    budget = 150.0
+    times = []
+    t_start = time.perf_counter()
+    for i in range(min(args.warmup, 1)):
+        _oracle_event_seconds(1000 + i)
+    for i in range(args.steps):
+        times.append(_oracle_event_seconds(i))
+        if time.perf_counter() - t_start > budget:
+            break
+    k = len(times)
+    value = k / sum(times)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": k,
+        "warmup": min(args.warmup, 1), "ms_per_step": round(1e3 * sum(times) / k, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "events_per_step": 1, "path": "FP64 CPU oracle, one host thread"},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{k} PU200 event(s) (timed steps capped at {budget:.0f} s)",
+                         "host": platform.machine()},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * lst.h -- C ABI of the GB300 Segment Linking (Line Segment Tracking) library.
+ *
+ * The library builds, for one event or a batch of events, the object chain
+ * of Segment Linking (arXiv:2209.13711, Section 2.1, kernel order of
+ * Fig. KernelFlow): mini-doublets (stubs) from hit pairs in one pT module,
+ * line segments between mini-doublets of connected modules (Fig.
+ * CompModules), triplets and quintuplets from segments / triplets sharing a
+ * mini-doublet (Figs. Triplet, Quintuplet, GeomReqs), pixel line segments
+ * from pixel seeds and their links to triplets and quintuplets (pT3, pT5),
+ * the cross-cleaning of Section 2.1 and the track-candidate collection. All
+ * of it runs in CUDA kernels on one GPU (sm_103a); the host side only stages
+ * inputs and launches.
+ *
+ * Conventions
+ *   Units: cm, GeV, tesla, radians. A hit index is the position of the hit in
+ *   the caller's per-event input arrays. Pixel seeds are three space points;
+ *   seed s of an event owns pixel hits 3s, 3s+1, 3s+2.
+ *   Every function returns an lst_status: 0 success, > 0 warning, < 0 error.
+ *   Nothing is thrown across the ABI.
+ *   Ownership: the caller owns every buffer it passes. Inputs must stay valid
+ *   until the call returns (host memory; the library copies them) or until
+ *   the stream reaches the work (device memory). The library copies the
+ *   geometry and keeps it until lst_destroy.
+ *   Threading: one context per host thread; a context runs one batch at a
+ *   time, and a new lst_run_batch call invalidates the previous results.
+ */
+#ifndef LST_H
+#define LST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t lst_status;
+enum {
+    LST_OK = 0,
+    LST_WARN_TRUNCATED = 1,      /* an occupancy cap dropped objects (counted in lst_stats) */
+    LST_ERR_ARG = -1,            /* a null pointer, a negative size or an out-of-range id */
+    LST_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+    LST_ERR_OOM = -3,            /* device allocation failed at creation */
+    LST_ERR_NO_GEOMETRY = -4,    /* lst_run_batch before lst_load_geometry */
+    LST_ERR_TIMEOUT = -5,        /* reserved: a bounded device wait ran out */
+    LST_ERR_CAPACITY = -6        /* the batch exceeds the context's event / hit / seed capacity */
+};
+
+/* Cut constants of the chain. The paper fixes only pt_min = 0.8 GeV (Section 2);
+ * every other value is this library's reading, filled by lst_config_default. */
+typedef struct lst_config {
+    double pt_min, k_field, b_field, z_lumi;
+    double n_md, n_ls, n_t3, n_t5, n_pt;
+    double tol_r;
+    double chi2_rphi_t5, chi2_rz_t5, chi2_rphi_pt3, chi2_rz_pt3, chi2_rphi_pt5, chi2_rz_pt5;
+    double pls_pt_tol, sig_pix;
+    double sb_eta_max;
+    int32_t sb_n_eta, sb_n_phi;
+    double dr_clean;
+} lst_config;
+
+/* Capacities, fixed at creation; all device memory is allocated once. */
+typedef struct lst_capacity {
+    int32_t max_events;          /* events per batch */
+    int32_t max_hits;            /* outer-tracker hits per batch */
+    int32_t max_seeds;           /* pixel seeds per batch */
+    int32_t md_per_event, ls_per_event, t3_per_event, t5_per_event;
+    int32_t pt3_per_event, pt5_per_event, tc_per_event;
+} lst_capacity;
+
+/* One row of the module table (the geometry of Section 2: paired-sensor pT modules). */
+typedef struct lst_module {
+    int32_t subdet;              /* 0 barrel, 1 endcap */
+    int32_t layer;               /* barrel layer 1..6 or endcap disk 1..5 */
+    float dsep;                  /* sensor separation (cm) */
+    float sig_rphi;              /* r-phi resolution (cm) */
+    float sig_long;              /* resolution along the strip: z in the barrel, r in the endcap (cm) */
+} lst_module;
+
+/* Outer-tracker hits of a batch, concatenated event after event (SoA). */
+typedef struct lst_hits {
+    const float* x;
+    const float* y;
+    const float* z;
+    const int32_t* module;       /* module id, 0 <= module < n_mod */
+    const uint8_t* side;         /* 0 lower sensor (nearer the interaction point), 1 upper */
+    int32_t n;                   /* total hits */
+} lst_hits;
+
+/* Pixel seeds of a batch: seed i has points (xyz[9i+3j .. 9i+3j+2]), j = 0, 1, 2,
+ * ordered by increasing radius. */
+typedef struct lst_seeds {
+    const float* xyz;
+    int32_t n;
+} lst_seeds;
+
+/* Per-event statistics. counts[k] and dropped[k] for k = 0 MD, 1 LS, 2 T3, 3 T5,
+ * 4 pLS (passing), 5 pT5, 6 pT3, 7 TC. */
+typedef struct lst_stats {
+    int32_t counts[8];
+    int32_t dropped[8];
+} lst_stats;
+
+typedef struct lst_ctx lst_ctx;
+
+/* Fill *cfg with the library defaults. */
+lst_status lst_config_default(lst_config* cfg);
+/* Default capacities for `max_events` events shaped like a 200-pileup event. */
+lst_status lst_capacity_default(lst_capacity* cap, int32_t max_events);
+
+/* Create a context on CUDA device `device`; cfg and cap are copied. Allocates
+ * every device buffer. On failure *out is NULL. */
+lst_status lst_create(lst_ctx** out, const lst_config* cfg, const lst_capacity* cap, int32_t device);
+void lst_destroy(lst_ctx* ctx);
+
+/* Copy the geometry (host arrays) to the device: n_mod module rows, the
+ * module connectivity map as CSR (conn_offsets[n_mod + 1], conn_targets: for
+ * each module the modules of the next layer a pT >= pt_min helix can reach,
+ * Fig. CompModules) and the pixel superbin map as CSR (sb_offsets[n_sb + 1],
+ * sb_targets: modules a seed of that superbin can link to). n_sb must equal
+ * sb_n_eta * sb_n_phi * 2. Synchronous. */
+lst_status lst_load_geometry(lst_ctx* ctx, const lst_module* modules, int32_t n_mod,
+                             const int32_t* conn_offsets, const int32_t* conn_targets,
+                             const int32_t* sb_offsets, const int32_t* sb_targets, int32_t n_sb);
+
+/* Enqueue the whole chain for a batch of n_events events on `cuda_stream`
+ * (a cudaStream_t; NULL for the legacy default stream). hit_offsets and
+ * seed_offsets are HOST arrays of n_events + 1 prefix offsets into the
+ * concatenated hits and seeds. mem_is_device = 0: hits and seeds are host
+ * pointers and are copied (pinned host memory makes the copy asynchronous);
+ * 1: they are device pointers read in place. Returns when the work is
+ * enqueued; results are read with lst_get_track_candidates / lst_get_objects. */
+lst_status lst_run_batch(lst_ctx* ctx, const lst_hits* hits, const int32_t* hit_offsets,
+                         const lst_seeds* seeds, const int32_t* seed_offsets, int32_t n_events,
+                         int32_t mem_is_device, void* cuda_stream);
+
+/* One event: lst_run_batch with n_events = 1. */
+lst_status lst_run_event(lst_ctx* ctx, const lst_hits* hits, const lst_seeds* seeds, int32_t mem_is_device,
+                         void* cuda_stream);
+
+/* Wait for the batch and copy the track candidates of event `event` (0-based
+ * in the last batch) into caller-owned arrays (HOST memory): type[i] (0 pT5,
+ * 1 pT3, 2 T5, 3 pLS), seed[i] (pixel seed index in the event, -1 for T5),
+ * hits[10 i .. 10 i + 9] (outer-tracker hit indices in the event, -1 padded),
+ * pt_eta_phi[3 i .. 3 i + 2]. Any output pointer may be NULL. At most
+ * `capacity` rows are written; *n_out receives the true count and
+ * LST_WARN_TRUNCATED is returned when it exceeds capacity. Candidate order is
+ * unspecified. */
+lst_status lst_get_track_candidates(lst_ctx* ctx, int32_t event, int32_t capacity, int32_t* n_out,
+                                    int32_t* type, int32_t* seed, int32_t* hits, float* pt_eta_phi);
+
+/* Wait for the batch and copy one intermediate collection of event `event`
+ * (for parity tests). kind: 0 MD, 1 LS, 2 T3, 3 T5, 4 pLS, 5 pT5, 6 pT3.
+ * Rows are ints[ni * i ..] and floats[nf * i ..] (host memory) with
+ *   MD : ints {lower hit, upper hit, module}              floats {dphi, dlong}
+ *   LS : ints {inner MD row, outer MD row}                floats {dphi}
+ *   T3 : ints {inner LS row, outer LS row}                floats {beta, kappa, sigk}
+ *   T5 : ints {inner T3 row, outer T3 row}                floats {kappa, chi2_rphi, chi2_rz, eta, phi0, pt, score}
+ *   pLS: ints {seed, pass, superbin}                      floats {kappa, sigk, eta, phi0, z0, pt}
+ *   pT5: ints {seed, T5 row}                              floats {kappa, chi2_rphi, chi2_rz, score, pt}
+ *   pT3: ints {seed, T3 row}                              floats {kappa, chi2_rphi, chi2_rz, score, pt}
+ * where "row" indexes the rows returned for the same event and kind.
+ * lst_object_columns gives ni and nf. Behaviour on capacity as above. */
+lst_status lst_object_columns(int32_t kind, int32_t* ni, int32_t* nf);
+lst_status lst_get_objects(lst_ctx* ctx, int32_t event, int32_t kind, int32_t capacity, int32_t* n_out,
+                           int32_t* ints, float* floats);
+
+/* Wait for the batch and copy the per-event statistics. */
+lst_status lst_get_stats(lst_ctx* ctx, int32_t event, lst_stats* out);
+
+/* Number of kernel launches enqueued by the last lst_run_batch. */
+int32_t lst_last_launch_count(lst_ctx* ctx);
+
+/* Profiling: when enabled, lst_run_batch records a CUDA event pair around
+ * every kernel launch (on the batch's stream). lst_get_kernel_times waits for
+ * the batch and returns, for each launch of the last batch in launch order,
+ * its name (static storage) and its device time in milliseconds; at most
+ * `capacity` entries, *n_out = the number of launches. Off by default. */
+lst_status lst_set_profiling(lst_ctx* ctx, int32_t enable);
+lst_status lst_get_kernel_times(lst_ctx* ctx, int32_t capacity, int32_t* n_out, const char** names, float* ms);
+
+/* Message of a status code (static storage). */
+const char* lst_status_str(lst_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LST_H */

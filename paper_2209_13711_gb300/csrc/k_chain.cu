@@ -1,0 +1,519 @@
+// Outer-tracker object kernels: hit binning, mini-doublets (MD), line
+// segments (LS), triplets (T3) and quintuplets (T5), in the launch order of
+// the paper's Fig. KernelFlow.
+//
+// Work decomposition: one warp per unit (an (event, module) for MDs, an inner
+// MD for LS/T3/T5). A unit evaluates all of its candidates lane-parallel,
+// compacts the passing ones in order into a shared-memory stage with
+// __ballot_sync, reserves one contiguous segment of the flat arena with a
+// single atomicAdd and writes it. The (offset, count) of every unit's
+// segment is kept, so the next stage finds "all LS whose inner MD is B" as
+// one contiguous range. Stage sizes bound the objects one unit may produce
+// (the occupancy truncation of Section 3); anything beyond is counted as
+// dropped, never written out of bounds.
+#include "lst_kernels.cuh"
+#include "lst_warp.cuh"
+
+namespace lst {
+
+// ---------------------------------------------------------------------------
+// hit binning: counting sort by (event, module, side)
+// ---------------------------------------------------------------------------
+__global__ void k_bin_count(Arena A) {
+    const int nb = 2 * A.n_mod;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n_hits; i += gridDim.x * blockDim.x) {
+        int m = A.hmod[i];
+        int s = A.hside[i];
+        if (m < 0 || m >= A.n_mod || s > 1) {
+            atomicAdd(&A.counters[16], 1);
+            continue;
+        }
+        int e = event_of(A.hit_off, A.n_ev, i);
+        atomicAdd(&A.bcnt[(size_t)e * nb + 2 * m + s], 1);
+    }
+}
+
+// One block per event: exclusive scan of the event's bucket counts into boff;
+// the counts are turned into scatter cursors (= offsets).
+__global__ void __launch_bounds__(1024) k_bin_scan(Arena A) {
+    const int nb = 2 * A.n_mod;
+    const int e = blockIdx.x;
+    int* cnt = A.bcnt + (size_t)e * nb;
+    int* off = A.boff + (size_t)e * (nb + 1);
+    __shared__ int warp_sums[32];
+    const int per = (nb + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per;
+    const int b1 = min(nb, b0 + per);
+    int local = 0;
+    for (int b = b0; b < b1; ++b) local += cnt[b];
+    // block exclusive scan of `local`
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = local;
+    for (int d = 1; d < 32; d <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    if (lane == 31) warp_sums[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int nw = (blockDim.x + 31) / 32;
+        int v = lane < nw ? warp_sums[lane] : 0;
+        int inc2 = v;
+        for (int d = 1; d < 32; d <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, inc2, d);
+            if (lane >= d) inc2 += u;
+        }
+        if (lane < nw) warp_sums[lane] = inc2 - v;
+    }
+    __syncthreads();
+    int run = warp_sums[w] + incl - local;
+    for (int b = b0; b < b1; ++b) {
+        int c = cnt[b];
+        off[b] = run;
+        cnt[b] = run;           // cursor
+        run += c;
+    }
+    if (threadIdx.x == blockDim.x - 1) off[nb] = run;
+}
+
+__global__ void k_bin_scatter(Arena A) {
+    const int nb = 2 * A.n_mod;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n_hits; i += gridDim.x * blockDim.x) {
+        int m = A.hmod[i];
+        int s = A.hside[i];
+        if (m < 0 || m >= A.n_mod || s > 1) continue;
+        int e = event_of(A.hit_off, A.n_ev, i);
+        int h0 = A.hit_off[e];
+        int pos = h0 + atomicAdd(&A.bcnt[(size_t)e * nb + 2 * m + s], 1);
+        A.sx[pos] = A.hx[i];
+        A.sy[pos] = A.hy[i];
+        A.sz[pos] = A.hz[i];
+        A.sidx[pos] = i - h0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// MD: one warp per (event, module)
+// ---------------------------------------------------------------------------
+struct MdSmem {
+    float lx[kMaxHits], ly[kMaxHits], lz[kMaxHits];
+    int li[kMaxHits];
+    float ux[kMaxHits], uy[kMaxHits], uz[kMaxHits];
+    int ui[kMaxHits];
+    int stage[kMdStage];
+};
+
+// Stage n sorted-by-bucket hits starting at global position g0 into shared
+// memory, ordered by their original index (so MD order does not depend on
+// the atomic scatter).
+__device__ __forceinline__ void stage_hits(const Arena& A, int g0, int n, float* X, float* Y, float* Z, int* I) {
+    const int lane = lane_id();
+    float rx[kMaxHits / 32], ry[kMaxHits / 32], rz[kMaxHits / 32];
+    int ri[kMaxHits / 32];
+#pragma unroll
+    for (int k = 0; k < kMaxHits / 32; ++k) {
+        int j = lane + 32 * k;
+        if (j < n) {
+            rx[k] = A.sx[g0 + j];
+            ry[k] = A.sy[g0 + j];
+            rz[k] = A.sz[g0 + j];
+            ri[k] = A.sidx[g0 + j];
+            I[j] = ri[k];
+        }
+    }
+    __syncwarp();
+    int rank[kMaxHits / 32];
+#pragma unroll
+    for (int k = 0; k < kMaxHits / 32; ++k) {
+        int j = lane + 32 * k;
+        rank[k] = 0;
+        if (j < n)
+            for (int t = 0; t < n; ++t) rank[k] += I[t] < ri[k];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < kMaxHits / 32; ++k) {
+        int j = lane + 32 * k;
+        if (j < n) {
+            X[rank[k]] = rx[k];
+            Y[rank[k]] = ry[k];
+            Z[rank[k]] = rz[k];
+            I[rank[k]] = ri[k];
+        }
+    }
+    __syncwarp();
+}
+
+size_t md_smem_bytes() { return kMdWarps * sizeof(MdSmem); }
+
+__global__ void __launch_bounds__(kMdWarps * 32) k_md(Arena A, DevCfg c) {
+    extern __shared__ __align__(16) unsigned char md_raw[];
+    MdSmem& S = reinterpret_cast<MdSmem*>(md_raw)[threadIdx.x >> 5];
+    const int lane = lane_id();
+    const int n_units = A.n_ev * A.n_mod;
+    for (int u = blockIdx.x * kMdWarps + (threadIdx.x >> 5); u < n_units; u += gridDim.x * kMdWarps) {
+        const int e = u / A.n_mod, m = u - e * A.n_mod;
+        const int* bo = A.boff + (size_t)e * (2 * A.n_mod + 1);
+        const int h0 = A.hit_off[e];
+        const int ol = bo[2 * m], ou = bo[2 * m + 1];
+        int nl = ou - ol, nu = bo[2 * m + 2] - ou;
+        int dropped = max(0, nl - kMaxHits) + max(0, nu - kMaxHits);
+        nl = min(nl, kMaxHits);
+        nu = min(nu, kMaxHits);
+        if (nl == 0 || nu == 0) {
+            if (lane == 0) {
+                A.md_moff[u] = 0;
+                A.md_mcnt[u] = 0;
+                if (dropped) atomicAdd(&A.ev_drop[e * 8 + 0], dropped);
+            }
+            continue;
+        }
+        const float4 mi = A.mod[m];
+        stage_hits(A, h0 + ol, nl, S.lx, S.ly, S.lz, S.li);
+        stage_hits(A, h0 + ou, nu, S.ux, S.uy, S.uz, S.ui);
+        const int total = nl * nu;
+        int cnt = 0;
+        for (int base = 0; base < total; base += 32) {
+            const int p = base + lane;
+            bool pass = false;
+            int code = 0;
+            if (p < total) {
+                int l = p / nu, k = p - l * nu;
+                code = (l << 16) | k;
+                Pt<float> L = hit_pt<float>(S.lx[l], S.ly[l], S.lz[l], mi);
+                Pt<float> U = hit_pt<float>(S.ux[k], S.uy[k], S.uz[k], mi);
+                float dp, dl;
+                int st = md_eval<float>(c, mi, L, U, dp, dl);
+                if (st == 2) {
+                    Pt<double> Ld = hit_pt<double>(S.lx[l], S.ly[l], S.lz[l], mi);
+                    Pt<double> Ud = hit_pt<double>(S.ux[k], S.uy[k], S.uz[k], mi);
+                    double dpd, dld;
+                    st = md_eval<double>(c, mi, Ld, Ud, dpd, dld);
+                }
+                pass = st == 1;
+            }
+            int tot;
+            int r = warp_rank(pass, tot);
+            if (pass && cnt + r < kMdStage) S.stage[cnt + r] = code;
+            cnt += tot;
+        }
+        __syncwarp();
+        int n = min(cnt, kMdStage);
+        dropped += cnt - n;
+        const int base = reserve(&A.counters[0], A.md_cap, n, dropped);
+        for (int i = lane; i < n; i += 32) {
+            int code = S.stage[i];
+            int l = code >> 16, k = code & 0xffff;
+            Pt<float> L = hit_pt<float>(S.lx[l], S.ly[l], S.lz[l], mi);
+            Pt<float> U = hit_pt<float>(S.ux[k], S.uy[k], S.uz[k], mi);
+            float dp, dl;
+            md_eval<float>(c, mi, L, U, dp, dl);
+            int o = base + i;
+            A.md_lo[o] = S.li[l];
+            A.md_up[o] = S.ui[k];
+            A.md_gmod[o] = u;
+            A.md_x[o] = S.lx[l];
+            A.md_y[o] = S.ly[l];
+            A.md_z[o] = S.lz[l];
+            A.md_dx[o] = S.ux[k] - S.lx[l];
+            A.md_dy[o] = S.uy[k] - S.ly[l];
+            A.md_dphi[o] = dp;
+            A.md_dlong[o] = dl;
+        }
+        if (lane == 0) {
+            A.md_moff[u] = base;
+            A.md_mcnt[u] = n;
+            if (n) atomicAdd(&A.ev_counts[e * 8 + 0], n);
+            if (dropped) atomicAdd(&A.ev_drop[e * 8 + 0], dropped);
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LS: one warp per inner MD A, candidates = MDs of the connected modules
+// ---------------------------------------------------------------------------
+struct LsSmem {
+    int pre[32], off[32], mod[32];
+    int stage[kLsStage];
+};
+
+__device__ __forceinline__ Pt<float> md_pt_f(const Arena& A, int i, float4 mi) {
+    return hit_pt<float>(A.md_x[i], A.md_y[i], A.md_z[i], mi);
+}
+__device__ __forceinline__ Pt<double> md_pt_d(const Arena& A, int i, float4 mi) {
+    return hit_pt<double>(A.md_x[i], A.md_y[i], A.md_z[i], mi);
+}
+__device__ __forceinline__ float4 md_mod(const Arena& A, int i) {
+    int gm = A.md_gmod[i];
+    return A.mod[gm % A.n_mod];
+}
+
+__global__ void __launch_bounds__(kLsWarps * 32) k_ls(Arena A, DevCfg c) {
+    __shared__ LsSmem sm[kLsWarps];
+    LsSmem& S = sm[threadIdx.x >> 5];
+    const int lane = lane_id();
+    const int n_md = min(A.counters[0], A.md_cap);
+    for (int i = blockIdx.x * kLsWarps + (threadIdx.x >> 5); i < n_md; i += gridDim.x * kLsWarps) {
+        const int gm = A.md_gmod[i];
+        const int e = gm / A.n_mod, m1 = gm - e * A.n_mod;
+        const float4 miA = A.mod[m1];
+        const Pt<float> P = md_pt_f(A, i, miA);
+        const float sAx = A.md_dx[i], sAy = A.md_dy[i];
+        const int c0 = A.conn_off[m1], c1 = A.conn_off[m1 + 1];
+        int cnt = 0;
+        for (int cb = c0; cb < c1; cb += 32) {
+            int j = cb + lane;
+            int off = 0, len = 0, m2 = 0;
+            if (j < c1) {
+                m2 = A.conn_tgt[j];
+                int u2 = e * A.n_mod + m2;
+                off = A.md_moff[u2];
+                len = A.md_mcnt[u2];
+            }
+            S.mod[lane] = m2;
+            for_each_flat(off, len, S.pre, S.off, [&](bool valid, int seg, int B) {
+                bool pass = false;
+                if (valid) {
+                    const float4 miB = A.mod[S.mod[seg]];
+                    Pt<float> Q = md_pt_f(A, B, miB);
+                    float dp;
+                    int st = ls_eval<float>(c, P, sAx, sAy, miA, Q, A.md_dx[B], A.md_dy[B], miB, dp);
+                    if (st == 2) {
+                        double dpd;
+                        st = ls_eval<double>(c, md_pt_d(A, i, miA), double(sAx), double(sAy), miA, md_pt_d(A, B, miB),
+                                             double(A.md_dx[B]), double(A.md_dy[B]), miB, dpd);
+                    }
+                    pass = st == 1;
+                }
+                int tot;
+                int r = warp_rank(pass, tot);
+                if (pass && cnt + r < kLsStage) S.stage[cnt + r] = B;
+                cnt += tot;
+            });
+        }
+        int n = min(cnt, kLsStage);
+        int dropped = cnt - n;
+        const int base = reserve(&A.counters[1], A.ls_cap, n, dropped);
+        for (int k = lane; k < n; k += 32) {
+            int B = S.stage[k];
+            float Bx = A.md_x[B], By = A.md_y[B];
+            int o = base + k;
+            A.ls_in[o] = i;
+            A.ls_out[o] = B;
+            A.ls_dphi[o] = atan2f(P.x * By - P.y * Bx, P.x * Bx + P.y * By);
+        }
+        if (lane == 0) {
+            A.ls_off[i] = base;
+            A.ls_cnt[i] = n;
+            if (n) atomicAdd(&A.ev_counts[e * 8 + 1], n);
+            if (dropped) atomicAdd(&A.ev_drop[e * 8 + 1], dropped);
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// T3: one warp per inner MD A; candidates = (LS1 from A) x (LS2 from LS1's outer MD)
+// ---------------------------------------------------------------------------
+struct T3Smem {
+    int pre[32], off[32], l1[32], mb[32];
+    int2 stage[kT3Stage];
+};
+
+__global__ void __launch_bounds__(kT3Warps * 32) k_t3(Arena A, DevCfg c) {
+    __shared__ T3Smem sm[kT3Warps];
+    T3Smem& S = sm[threadIdx.x >> 5];
+    const int lane = lane_id();
+    const int n_md = min(A.counters[0], A.md_cap);
+    for (int i = blockIdx.x * kT3Warps + (threadIdx.x >> 5); i < n_md; i += gridDim.x * kT3Warps) {
+        const int s0 = A.ls_off[i], s1 = s0 + A.ls_cnt[i];
+        if (s1 == s0) {
+            if (lane == 0) { A.t3_off[i] = 0; A.t3_cnt[i] = 0; }
+            continue;
+        }
+        const int e = A.md_gmod[i] / A.n_mod;
+        const float4 miA = md_mod(A, i);
+        const Pt<float> PA = md_pt_f(A, i, miA);
+        int cnt = 0;
+        for (int cb = s0; cb < s1; cb += 32) {
+            int l1 = cb + lane;
+            int off = 0, len = 0, B = 0;
+            if (l1 < s1) {
+                B = A.ls_out[l1];
+                off = A.ls_off[B];
+                len = A.ls_cnt[B];
+            }
+            S.l1[lane] = l1;
+            S.mb[lane] = B;
+            for_each_flat(off, len, S.pre, S.off, [&](bool valid, int seg, int l2) {
+                bool pass = false;
+                if (valid) {
+                    int B_ = S.mb[seg];
+                    int C_ = A.ls_out[l2];
+                    float4 miB = md_mod(A, B_), miC = md_mod(A, C_);
+                    float beta, kap, rz, sk;
+                    int st = t3_eval<float>(c, PA, md_pt_f(A, B_, miB), md_pt_f(A, C_, miC), beta, kap, rz, sk);
+                    if (st == 2) {
+                        double bd, kd, rd, sd;
+                        st = t3_eval<double>(c, md_pt_d(A, i, miA), md_pt_d(A, B_, miB), md_pt_d(A, C_, miC), bd, kd,
+                                             rd, sd);
+                    }
+                    pass = st == 1;
+                }
+                int tot;
+                int r = warp_rank(pass, tot);
+                if (pass && cnt + r < kT3Stage) S.stage[cnt + r] = make_int2(S.l1[seg], l2);
+                cnt += tot;
+            });
+        }
+        int n = min(cnt, kT3Stage);
+        int dropped = cnt - n;
+        const int base = reserve(&A.counters[2], A.t3_cap, n, dropped);
+        for (int k = lane; k < n; k += 32) {
+            int2 pr = S.stage[k];
+            int B_ = A.ls_out[pr.x], C_ = A.ls_out[pr.y];
+            float beta, kap, rz, sk;
+            t3_eval<float>(c, PA, md_pt_f(A, B_, md_mod(A, B_)), md_pt_f(A, C_, md_mod(A, C_)), beta, kap, rz, sk);
+            int o = base + k;
+            A.t3_lsin[o] = pr.x;
+            A.t3_lsout[o] = pr.y;
+            A.t3_beta[o] = beta;
+            A.t3_kappa[o] = kap;
+            A.t3_sigk[o] = sk;
+        }
+        if (lane == 0) {
+            A.t3_off[i] = base;
+            A.t3_cnt[i] = n;
+            if (n) atomicAdd(&A.ev_counts[e * 8 + 2], n);
+            if (dropped) atomicAdd(&A.ev_drop[e * 8 + 2], dropped);
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// T5: one warp per inner MD A; candidates = (T3_1 from A) x (T3_2 from T3_1's
+// outer MD). FP32 curvature prefilter (conservative), then the full test in
+// FP64 for the survivors.
+// ---------------------------------------------------------------------------
+struct T5Smem {
+    int pre[32], off[32], t1[32];
+    int2 cand[kT5Pre];
+    int2 stage[kT5Stage];      // passing (T3_1, T3_2); outputs are recomputed when written
+};
+
+__device__ __forceinline__ void t3_anchor_mds(const Arena& A, int t, int& a, int& b, int& cc) {
+    int l1 = A.t3_lsin[t], l2 = A.t3_lsout[t];
+    a = A.ls_in[l1];
+    b = A.ls_out[l1];
+    cc = A.ls_out[l2];
+}
+
+__device__ __forceinline__ bool t5_eval_pair(const Arena& A, const DevCfg& c, int2 pr, T5Out& o) {
+    int m[5];
+    t3_anchor_mds(A, pr.x, m[0], m[1], m[2]);
+    t3_anchor_mds(A, pr.y, m[2], m[3], m[4]);
+    Pt<double> P[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) P[j] = md_pt_d(A, m[j], md_mod(A, m[j]));
+    return t5_eval(c, P, o);
+}
+
+// FP64 evaluation of the collected candidates; appends passing ones to the stage
+__device__ __forceinline__ void t5_flush(const Arena& A, const DevCfg& c, T5Smem& S, int ncand, int& cnt) {
+    const int lane = lane_id();
+    for (int base = 0; base < ncand; base += 32) {
+        int q = base + lane;
+        bool pass = false;
+        int2 pr = make_int2(0, 0);
+        if (q < ncand) {
+            pr = S.cand[q];
+            T5Out o;
+            pass = t5_eval_pair(A, c, pr, o);
+        }
+        int tot;
+        int r = warp_rank(pass, tot);
+        if (pass && cnt + r < kT5Stage) S.stage[cnt + r] = pr;
+        cnt += tot;
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kT5Warps * 32) k_t5(Arena A, DevCfg c) {
+    __shared__ T5Smem sm[kT5Warps];
+    T5Smem& S = sm[threadIdx.x >> 5];
+    const int lane = lane_id();
+    const int n_md = min(A.counters[0], A.md_cap);
+    const float nk = float(c.n_t5);
+    for (int i = blockIdx.x * kT5Warps + (threadIdx.x >> 5); i < n_md; i += gridDim.x * kT5Warps) {
+        const int s0 = A.t3_off[i], s1 = s0 + A.t3_cnt[i];
+        if (s1 == s0) {
+            if (lane == 0) { A.t5_off[i] = 0; A.t5_cnt[i] = 0; }
+            continue;
+        }
+        const int e = A.md_gmod[i] / A.n_mod;
+        int cnt = 0, ncand = 0;
+        for (int cb = s0; cb < s1; cb += 32) {
+            int t1 = cb + lane;
+            int off = 0, len = 0;
+            if (t1 < s1) {
+                int C_ = A.ls_out[A.t3_lsout[t1]];
+                off = A.t3_off[C_];
+                len = A.t3_cnt[C_];
+            }
+            S.t1[lane] = t1;
+            for_each_flat(off, len, S.pre, S.off, [&](bool valid, int seg, int t2) {
+                bool pass = false;
+                int t1_ = 0;
+                if (valid) {
+                    t1_ = S.t1[seg];
+                    float k1 = A.t3_kappa[t1_], k2 = A.t3_kappa[t2];
+                    float s1_ = A.t3_sigk[t1_], s2_ = A.t3_sigk[t2];
+                    float thr = nk * sqrtf(s1_ * s1_ + s2_ * s2_);
+                    // slack covers the FP32 rounding of the stored curvatures
+                    pass = fabsf(k1 - k2) <= thr * 1.01f + 1e-5f * (fabsf(k1) + fabsf(k2)) + 1e-7f;
+                }
+                int tot;
+                int r = warp_rank(pass, tot);
+                if (pass) S.cand[ncand + r] = make_int2(t1_, t2);
+                ncand += tot;
+                if (ncand > kT5Pre - 32) {
+                    __syncwarp();
+                    t5_flush(A, c, S, ncand, cnt);
+                    ncand = 0;
+                }
+            });
+        }
+        __syncwarp();
+        if (ncand) t5_flush(A, c, S, ncand, cnt);
+        int n = min(cnt, kT5Stage);
+        int dropped = cnt - n;
+        const int base = reserve(&A.counters[3], A.t5_cap, n, dropped);
+        for (int k = lane; k < n; k += 32) {
+            int2 pr = S.stage[k];
+            T5Out s;
+            t5_eval_pair(A, c, pr, s);
+            int o = base + k;
+            A.t5_in[o] = pr.x;
+            A.t5_out[o] = pr.y;
+            A.t5_kappa[o] = s.kappa;
+            A.t5_sigk[o] = s.sigk;
+            A.t5_eta[o] = s.eta;
+            A.t5_phi[o] = s.phi0;
+            A.t5_chi2[o] = float(s.chi2_rphi);
+            A.t5_chi2z[o] = float(s.chi2_rz);
+            A.t5_score[o] = float(s.score);
+            A.t5_pt[o] = float(s.pt);
+        }
+        if (lane == 0) {
+            A.t5_off[i] = base;
+            A.t5_cnt[i] = n;
+            if (n) atomicAdd(&A.ev_counts[e * 8 + 3], n);
+            if (dropped) atomicAdd(&A.ev_drop[e * 8 + 3], dropped);
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace lst

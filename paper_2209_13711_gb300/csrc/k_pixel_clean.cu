@@ -1,0 +1,435 @@
+// Pixel-seeded objects (pLS, pT5, pT3) and the cross-cleaning that forms the
+// track-candidate collection (Section 2.1; pT5 is launched before pT3, as in
+// Fig. KernelFlow).
+#include "lst_kernels.cuh"
+#include "lst_warp.cuh"
+
+namespace lst {
+
+// ---------------------------------------------------------------------------
+// pLS: one thread per seed, FP64 (three-point circle, r-z line, superbin)
+// ---------------------------------------------------------------------------
+__global__ void k_pls(Arena A, DevCfg c) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < A.n_seeds; g += gridDim.x * blockDim.x) {
+        const float* q = A.seeds + 9 * (size_t)g;
+        Pt<double> Q[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Q[j] = pix_pt<double>(q + 3 * j, c.sig_pix);
+        Tri<double> t = tri(Q[0], Q[1], Q[2]);
+        double ka = fabs(t.kappa);
+        double s1 = arc(t.lu, ka), s2 = arc(t.lw, ka);
+        double sbar = (s1 + s2) / 3.0, zbar = (Q[0].z + Q[1].z + Q[2].z) / 3.0;
+        double Sss = sq(0.0 - sbar) + sq(s1 - sbar) + sq(s2 - sbar);
+        double Ssz = (0.0 - sbar) * (Q[0].z - zbar) + (s1 - sbar) * (Q[1].z - zbar) + (s2 - sbar) * (Q[2].z - zbar);
+        double tanl = Ssz / Sss;
+        double zc = zbar - tanl * sbar;
+        double z0 = zc - tanl * arc(Q[0].r, ka);
+        double eta = asinh(tanl);
+        double phi0 = phi0_of(Q[0], t.kappa);
+        bool pass = (ka <= 2.0 * c.a / (1.0 - c.pls_pt_tol)) && (fabs(z0) <= c.z_lumi);
+        double de = 2.0 * c.sb_eta_max / c.sb_n_eta;
+        double dp = 2.0 * kPi / c.sb_n_phi;
+        long ie = (long)floor((eta + c.sb_eta_max) / de);
+        long ip = (long)floor((phi0 + kPi) / dp);
+        ip = ip < 0 ? 0 : (ip > c.sb_n_phi - 1 ? c.sb_n_phi - 1 : ip);
+        int iq = t.kappa < 0 ? 1 : 0;
+        int sb = (ie >= 0 && ie < c.sb_n_eta) ? (int)((ie * c.sb_n_phi + ip) * 2 + iq) : -1;
+        A.pls_pass[g] = pass;
+        A.pls_sb[g] = sb;
+        A.pls_kappa[g] = t.kappa;
+        A.pls_sigk[g] = t.sigk;
+        A.pls_z0[g] = float(z0);
+        A.pls_pt[g] = float(pt_of(c, t.kappa));
+        A.pls_eta[g] = eta;
+        A.pls_phi[g] = phi0;
+        if (pass) {
+            int e = event_of(A.seed_off, A.n_ev, g);
+            atomicAdd(&A.ev_counts[e * 8 + 4], 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pT5 / pT3: one warp per passing seed; candidates = T objects whose inner
+// MD sits in a module listed under the seed's superbin.
+// ---------------------------------------------------------------------------
+struct PtStage {
+    int obj;
+    float kappa, chi2, chi2z, score, pt;
+};
+
+struct PtSmem {
+    int pre[32], off[32];
+    int cand[kPtPre];
+    PtStage stage[kPtStage];
+};
+
+template <int NT>
+__device__ __forceinline__ void pt_mds(const Arena& A, int obj, int* m) {
+    if (NT == 5) {
+        int l1 = A.t3_lsin[A.t5_in[obj]], l2 = A.t3_lsout[A.t5_in[obj]];
+        int l3 = A.t3_lsin[A.t5_out[obj]], l4 = A.t3_lsout[A.t5_out[obj]];
+        m[0] = A.ls_in[l1]; m[1] = A.ls_out[l1]; m[2] = A.ls_out[l2]; m[3] = A.ls_out[l3]; m[4] = A.ls_out[l4];
+    } else {
+        int l1 = A.t3_lsin[obj], l2 = A.t3_lsout[obj];
+        m[0] = A.ls_in[l1]; m[1] = A.ls_out[l1]; m[2] = A.ls_out[l2];
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void pt_flush(const Arena& A, const DevCfg& c, PtSmem& S, int g, int ncand, int& cnt) {
+    const int lane = lane_id();
+    const double kp = A.pls_kappa[g], sp = A.pls_sigk[g];
+    for (int base = 0; base < ncand; base += 32) {
+        int q = base + lane;
+        bool pass = false;
+        PTOut o;
+        int obj = 0;
+        if (q < ncand) {
+            obj = S.cand[q];
+            Pt<double> P[NT + 3];
+            const float* sd = A.seeds + 9 * (size_t)g;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) P[j] = pix_pt<double>(sd + 3 * j, c.sig_pix);
+            int m[NT];
+            pt_mds<NT>(A, obj, m);
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                float4 mi = A.mod[A.md_gmod[m[j]] % A.n_mod];
+                P[3 + j] = hit_pt<double>(A.md_x[m[j]], A.md_y[m[j]], A.md_z[m[j]], mi);
+            }
+            double kt, st;
+            if (NT == 5) {
+                kt = A.t5_kappa[obj];
+                st = A.t5_sigk[obj];
+            } else {
+                Tri<double> tt = tri(P[3], P[4], P[5]);
+                kt = tt.kappa;
+                st = tt.sigk;
+            }
+            pass = pt_eval<NT + 3>(c, P, kp, sp, kt, st, NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3,
+                                   NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3, o);
+        }
+        int tot;
+        int r = warp_rank(pass, tot);
+        if (pass && cnt + r < kPtStage) {
+            PtStage& s = S.stage[cnt + r];
+            s.obj = obj;
+            s.kappa = float(o.kappa);
+            s.chi2 = float(o.chi2_rphi);
+            s.chi2z = float(o.chi2_rz);
+            s.score = float(o.score);
+            s.pt = float(o.pt);
+        }
+        cnt += tot;
+    }
+    __syncwarp();
+}
+
+template <int NT>
+__device__ __forceinline__ void pt_kernel_body(Arena& A, const DevCfg& c) {
+    __shared__ PtSmem sm[kPtWarps];
+    PtSmem& S = sm[threadIdx.x >> 5];
+    const int lane = lane_id();
+    const float nk = float(c.n_pt);
+    for (int g = blockIdx.x * kPtWarps + (threadIdx.x >> 5); g < A.n_seeds; g += gridDim.x * kPtWarps) {
+        if (!A.pls_pass[g] || A.pls_sb[g] < 0) continue;
+        const int e = event_of(A.seed_off, A.n_ev, g);
+        const int sb = A.pls_sb[g];
+        const float kp = float(A.pls_kappa[g]), sp = float(A.pls_sigk[g]);
+        const int j0 = A.sb_off[sb], j1 = A.sb_off[sb + 1];
+        int cnt = 0, ncand = 0;
+        for (int cb = j0; cb < j1; cb += 32) {
+            int j = cb + lane;
+            int off = 0, len = 0;
+            if (j < j1) {
+                int u = e * A.n_mod + A.sb_tgt[j];
+                off = A.md_moff[u];
+                len = A.md_mcnt[u];
+            }
+            for_each_flat(off, len, S.pre, S.off, [&](bool valid, int seg, int md) {
+                int oo = 0, on = 0;
+                if (valid) {
+                    oo = NT == 5 ? A.t5_off[md] : A.t3_off[md];
+                    on = NT == 5 ? A.t5_cnt[md] : A.t3_cnt[md];
+                }
+                for (int k = 0; __any_sync(kFull, k < on); ++k) {
+                    bool pass = false;
+                    int obj = oo + k;
+                    if (k < on) {
+                        float kt = NT == 5 ? float(A.t5_kappa[obj]) : A.t3_kappa[obj];
+                        float st = NT == 5 ? float(A.t5_sigk[obj]) : A.t3_sigk[obj];
+                        float thr = nk * sqrtf(sp * sp + st * st);
+                        pass = fabsf(kp - kt) <= thr * 1.01f + 1e-5f * (fabsf(kp) + fabsf(kt)) + 1e-7f;
+                    }
+                    int tot;
+                    int r = warp_rank(pass, tot);
+                    if (pass) S.cand[ncand + r] = obj;
+                    ncand += tot;
+                    if (ncand > kPtPre - 32) {
+                        __syncwarp();
+                        pt_flush<NT>(A, c, S, g, ncand, cnt);
+                        ncand = 0;
+                    }
+                }
+            });
+        }
+        __syncwarp();
+        if (ncand) pt_flush<NT>(A, c, S, g, ncand, cnt);
+        int n = min(cnt, kPtStage);
+        int dropped = cnt - n;
+        const int slot = NT == 5 ? 4 : 5;
+        const int base = reserve(&A.counters[slot], NT == 5 ? A.pt5_cap : A.pt3_cap, n, dropped);
+        for (int k = lane; k < n; k += 32) {
+            const PtStage& s = S.stage[k];
+            int o = base + k;
+            if (NT == 5) {
+                A.pt5_seed[o] = g; A.pt5_obj[o] = s.obj; A.pt5_kappa[o] = s.kappa; A.pt5_chi2[o] = s.chi2;
+                A.pt5_chi2z[o] = s.chi2z; A.pt5_score[o] = s.score; A.pt5_pt[o] = s.pt;
+            } else {
+                A.pt3_seed[o] = g; A.pt3_obj[o] = s.obj; A.pt3_kappa[o] = s.kappa; A.pt3_chi2[o] = s.chi2;
+                A.pt3_chi2z[o] = s.chi2z; A.pt3_score[o] = s.score; A.pt3_pt[o] = s.pt;
+            }
+        }
+        if (lane == 0) {
+            if (n) atomicAdd(&A.ev_counts[e * 8 + (NT == 5 ? 5 : 6)], n);
+            if (dropped) atomicAdd(&A.ev_drop[e * 8 + (NT == 5 ? 5 : 6)], dropped);
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(kPtWarps * 32) k_pt5(Arena A, DevCfg c) { pt_kernel_body<5>(A, c); }
+__global__ void __launch_bounds__(kPtWarps * 32) k_pt3(Arena A, DevCfg c) { pt_kernel_body<3>(A, c); }
+
+// ---------------------------------------------------------------------------
+// cross-cleaning
+// ---------------------------------------------------------------------------
+// Categories: 0 pT5, 1 pT3, 2 T5. Hit ids of an object, local to its event:
+// outer-tracker hits keep their input index; the pixel hits of seed s are
+// n_hits(event) + 3 s + j. Global key slots: hit_off[e] + local for
+// outer-tracker hits, n_hits(batch) + 3 seed_global + j for pixel hits.
+struct ObjHits {
+    int n, e;
+    int ids[13];
+    int slots[13];
+    float score;
+};
+
+__device__ __forceinline__ void md_hits_into(const Arena& A, int md, int h0, ObjHits& o) {
+    o.ids[o.n] = A.md_lo[md];
+    o.slots[o.n++] = h0 + A.md_lo[md];
+    o.ids[o.n] = A.md_up[md];
+    o.slots[o.n++] = h0 + A.md_up[md];
+}
+
+__device__ __forceinline__ void object_hits(const Arena& A, int cat, int idx, ObjHits& o) {
+    o.n = 0;
+    int m[5];
+    int nm;
+    if (cat == 2) {
+        pt_mds<5>(A, idx, m);
+        nm = 5;
+        o.e = A.md_gmod[m[0]] / A.n_mod;
+        o.score = A.t5_score[idx];
+    } else {
+        int g = cat == 0 ? A.pt5_seed[idx] : A.pt3_seed[idx];
+        o.e = event_of(A.seed_off, A.n_ev, g);
+        int nh = A.hit_off[o.e + 1] - A.hit_off[o.e];
+        int sl = g - A.seed_off[o.e];
+        for (int j = 0; j < 3; ++j) {
+            o.ids[o.n] = nh + 3 * sl + j;
+            o.slots[o.n++] = A.n_hits + 3 * g + j;
+        }
+        if (cat == 0) { pt_mds<5>(A, A.pt5_obj[idx], m); nm = 5; o.score = A.pt5_score[idx]; }
+        else { pt_mds<3>(A, A.pt3_obj[idx], m); nm = 3; o.score = A.pt3_score[idx]; }
+    }
+    int h0 = A.hit_off[o.e];
+    for (int j = 0; j < nm; ++j) md_hits_into(A, m[j], h0, o);
+}
+
+// key = (score as FP32 bits, FNV-1a of the sorted local hit ids as 32-bit words)
+__device__ __forceinline__ unsigned long long object_key(ObjHits& o) {
+    int s[13];
+    for (int i = 0; i < o.n; ++i) s[i] = o.ids[i];
+    for (int i = 1; i < o.n; ++i) {
+        int v = s[i], j = i - 1;
+        while (j >= 0 && s[j] > v) { s[j + 1] = s[j]; --j; }
+        s[j + 1] = v;
+    }
+    unsigned h = 2166136261u;
+    for (int i = 0; i < o.n; ++i) {
+        h ^= (unsigned)s[i];
+        h *= 16777619u;
+    }
+    unsigned sb = __float_as_uint(o.score);
+    return ((unsigned long long)sb << 32) | h;
+}
+
+// pass 0: per hit, the smallest key of each category; pass 1: keep an object
+// when it holds the smallest key on every one of its hits.
+__global__ void k_clean_keys(Arena A, int pass) {
+    const int n5 = min(A.counters[4], A.pt5_cap);
+    const int n3 = min(A.counters[5], A.pt3_cap);
+    const int nt = min(A.counters[3], A.t5_cap);
+    const size_t n_keys = (size_t)A.n_hits + 3 * (size_t)A.n_seeds;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n5 + n3 + nt; f += gridDim.x * blockDim.x) {
+        int cat = f < n5 ? 0 : (f < n5 + n3 ? 1 : 2);
+        int idx = cat == 0 ? f : (cat == 1 ? f - n5 : f - n5 - n3);
+        ObjHits o;
+        object_hits(A, cat, idx, o);
+        unsigned long long key = object_key(o);
+        unsigned long long* best = A.best + cat * n_keys;
+        if (pass == 0) {
+            for (int i = 0; i < o.n; ++i) atomicMin(best + o.slots[i], key);
+        } else {
+            bool keep = true;
+            for (int i = 0; i < o.n; ++i) keep &= best[o.slots[i]] == key;
+            uint8_t* kf = cat == 0 ? A.keep_pt5 : (cat == 1 ? A.keep_pt3 : A.keep_t5);
+            kf[idx] = keep;
+        }
+    }
+}
+
+__device__ __forceinline__ void tc_append(const Arena& A, int e, int type, int seed_local, int obj, const int* m,
+                                          int nm, float pt, float eta, float phi) {
+    int k = atomicAdd(&A.tc_cnt[e], 1);
+    if (k >= A.tc_cap) {
+        atomicAdd(&A.ev_drop[e * 8 + 7], 1);
+        return;
+    }
+    size_t o = (size_t)e * A.tc_cap + k;
+    A.tc_type[o] = type;
+    A.tc_seed[o] = seed_local;
+    A.tc_obj[o] = obj;
+    int* h = A.tc_hits + 10 * o;
+    for (int j = 0; j < 5; ++j) {
+        h[2 * j] = j < nm ? A.md_lo[m[j]] : -1;
+        h[2 * j + 1] = j < nm ? A.md_up[m[j]] : -1;
+    }
+    A.tc_pt[o] = pt;
+    A.tc_eta[o] = eta;
+    A.tc_phi[o] = phi;
+}
+
+__device__ __forceinline__ void list_append(const Arena& A, int e, int list, float eta, float phi, int ref) {
+    int k = atomicAdd(&A.list_cnt[e * 2 + list], 1);
+    if (k < A.list_cap) {
+        size_t o = ((size_t)e * 2 + list) * A.list_cap + k;
+        A.list_ef[o] = make_float2(eta, phi);
+        A.list_ref[o] = ref;
+    }
+}
+
+__device__ __forceinline__ void ref_eta_phi(const Arena& A, int ref, double& eta, double& phi) {
+    int cat = ref >> 28, idx = ref & 0x0fffffff;
+    int g = -1;
+    if (cat == 0) g = A.pt5_seed[idx];
+    if (cat == 1) g = A.pt3_seed[idx];
+    if (g >= 0) { eta = A.pls_eta[g]; phi = A.pls_phi[g]; }
+    else { eta = A.t5_eta[idx]; phi = A.t5_phi[idx]; }
+}
+
+// Is (eta, phi) within dr_clean of any entry of the event's list? FP32 test
+// with an FP64 re-test inside a 1e-3 relative band around the threshold.
+__device__ __forceinline__ bool dr_close(const Arena& A, const DevCfg& c, int e, int list, double eta, double phi) {
+    int n = min(A.list_cnt[e * 2 + list], A.list_cap);
+    size_t base = ((size_t)e * 2 + list) * A.list_cap;
+    const double thr2 = c.dr_clean * c.dr_clean;
+    const float thr2f = float(thr2);
+    const float ef = float(eta), pf = float(phi);
+    const float two_pi = float(2 * kPi);
+    for (int j = 0; j < n; ++j) {
+        float2 v = A.list_ef[base + j];
+        float de = v.x - ef;
+        float dp = v.y - pf;
+        if (dp > float(kPi)) dp -= two_pi;
+        if (dp <= -float(kPi)) dp += two_pi;
+        float d2 = de * de + dp * dp;
+        if (d2 < thr2f * (1.0f - 1e-3f)) return true;
+        if (d2 <= thr2f * (1.0f + 1e-3f)) {
+            double e2, p2;
+            ref_eta_phi(A, A.list_ref[base + j], e2, p2);
+            double dd = eta - e2, dq = wrap_pi(phi - p2);
+            if (dd * dd + dq * dq < thr2) return true;
+        }
+    }
+    return false;
+}
+
+// kept pT5: mark hits and seeds, list for the eta-phi tests, track candidates
+__global__ void k_clean_pt5(Arena A) {
+    const int n5 = min(A.counters[4], A.pt5_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n5; i += gridDim.x * blockDim.x) {
+        if (!A.keep_pt5[i]) continue;
+        ObjHits o;
+        object_hits(A, 0, i, o);
+        for (int j = 3; j < o.n; ++j) atomicOr(&A.mark[o.slots[j]], 1);
+        int g = A.pt5_seed[i];
+        atomicOr(&A.seed_link[g], 1);
+        list_append(A, o.e, 0, float(A.pls_eta[g]), float(A.pls_phi[g]), (0 << 28) | i);
+        int m[5];
+        pt_mds<5>(A, A.pt5_obj[i], m);
+        tc_append(A, o.e, 0, g - A.seed_off[o.e], i, m, 5, A.pt5_pt[i], float(A.pls_eta[g]), float(A.pls_phi[g]));
+    }
+}
+
+__global__ void k_clean_pt3_cross(Arena A, DevCfg c) {
+    const int n3 = min(A.counters[5], A.pt3_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
+        if (!A.keep_pt3[i]) continue;
+        ObjHits o;
+        object_hits(A, 1, i, o);
+        int g = A.pt3_seed[i];
+        bool drop = (A.seed_link[g] & 1) != 0;
+        for (int j = 3; j < o.n && !drop; ++j) drop = (A.mark[o.slots[j]] & 1) != 0;
+        if (!drop) drop = dr_close(A, c, o.e, 0, A.pls_eta[g], A.pls_phi[g]);
+        A.keep_pt3[i] = !drop;
+    }
+}
+
+__global__ void k_clean_pt3_mark(Arena A) {
+    const int n3 = min(A.counters[5], A.pt3_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
+        if (!A.keep_pt3[i]) continue;
+        ObjHits o;
+        object_hits(A, 1, i, o);
+        for (int j = 3; j < o.n; ++j) atomicOr(&A.mark[o.slots[j]], 2);
+        int g = A.pt3_seed[i];
+        atomicOr(&A.seed_link[g], 2);
+        list_append(A, o.e, 0, float(A.pls_eta[g]), float(A.pls_phi[g]), (1 << 28) | i);
+        int m[3];
+        pt_mds<3>(A, A.pt3_obj[i], m);
+        tc_append(A, o.e, 1, g - A.seed_off[o.e], i, m, 3, A.pt3_pt[i], float(A.pls_eta[g]), float(A.pls_phi[g]));
+    }
+}
+
+__global__ void k_clean_t5(Arena A, DevCfg c) {
+    const int nt = min(A.counters[3], A.t5_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
+        if (!A.keep_t5[i]) continue;
+        ObjHits o;
+        object_hits(A, 2, i, o);
+        bool drop = false;
+        for (int j = 0; j < o.n && !drop; ++j) drop = (A.mark[o.slots[j]] & 3) != 0;
+        if (!drop) drop = dr_close(A, c, o.e, 0, A.t5_eta[i], A.t5_phi[i]);
+        A.keep_t5[i] = !drop;
+        if (drop) continue;
+        list_append(A, o.e, 1, float(A.t5_eta[i]), float(A.t5_phi[i]), (2 << 28) | i);
+        int m[5];
+        pt_mds<5>(A, i, m);
+        tc_append(A, o.e, 2, -1, i, m, 5, A.t5_pt[i], float(A.t5_eta[i]), float(A.t5_phi[i]));
+    }
+}
+
+__global__ void k_clean_pls(Arena A, DevCfg c) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < A.n_seeds; g += gridDim.x * blockDim.x) {
+        if (!A.pls_pass[g] || A.seed_link[g]) continue;
+        int e = event_of(A.seed_off, A.n_ev, g);
+        double eta = A.pls_eta[g], phi = A.pls_phi[g];
+        if (dr_close(A, c, e, 0, eta, phi) || dr_close(A, c, e, 1, eta, phi)) continue;
+        tc_append(A, e, 3, g - A.seed_off[e], g, nullptr, 0, A.pls_pt[g], float(eta), float(phi));
+    }
+}
+
+}  // namespace lst

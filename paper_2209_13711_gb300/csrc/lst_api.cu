@@ -1,0 +1,621 @@
+// C ABI of the Segment Linking library: context, device memory, launch
+// sequence and result readback. See include/lst.h for the contract.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lst.h"
+#include "lst_kernels.cuh"
+
+using namespace lst;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct Buffer {
+    void* base = nullptr;
+    size_t size = 0, used = 0;
+    template <typename T> T* take(size_t n) {
+        size_t off = (used + kAlign - 1) / kAlign * kAlign;
+        used = off + std::max<size_t>(n, 1) * sizeof(T);
+        return base ? reinterpret_cast<T*>(static_cast<char*>(base) + off) : nullptr;
+    }
+};
+
+}  // namespace
+
+struct lst_ctx {
+    int device = 0;
+    int n_sm = 0;
+    lst_config cfg{};
+    lst_capacity cap{};
+    DevCfg dc{};
+    bool geometry = false;
+    void* dev_mem = nullptr;
+    size_t dev_bytes = 0;
+    Arena A{};              // pointers into dev_mem; batch fields set per run
+    // device input staging (host-memory inputs are copied here)
+    float* in_x = nullptr;
+    float* in_y = nullptr;
+    float* in_z = nullptr;
+    int* in_mod = nullptr;
+    uint8_t* in_side = nullptr;
+    float* in_seeds = nullptr;
+    int* d_hit_off = nullptr;
+    int* d_seed_off = nullptr;
+    int* h_offsets = nullptr;   // pinned: [2 (max_events + 1)]
+    cudaEvent_t done = nullptr;
+    bool ran = false;
+    int n_ev = 0;
+    int launches = 0;
+    std::vector<int> hit_off_host, seed_off_host;
+    bool profiling = false;
+    static constexpr int kMaxProf = 64;
+    cudaEvent_t prof_ev[2 * kMaxProf] = {};
+    const char* prof_name[kMaxProf] = {};
+};
+
+#define CK(x)                                      \
+    do {                                           \
+        cudaError_t err__ = (x);                   \
+        if (err__ != cudaSuccess) return LST_ERR_CUDA; \
+    } while (0)
+
+static DevCfg make_devcfg(const lst_config& c) {
+    DevCfg d{};
+    d.a = c.k_field * c.b_field / (200.0 * c.pt_min);
+    d.z_lumi = c.z_lumi; d.n_md = c.n_md; d.n_ls = c.n_ls; d.n_t3 = c.n_t3; d.n_t5 = c.n_t5; d.n_pt = c.n_pt;
+    d.tol_r = c.tol_r;
+    d.chi2_rphi_t5 = c.chi2_rphi_t5; d.chi2_rz_t5 = c.chi2_rz_t5;
+    d.chi2_rphi_pt3 = c.chi2_rphi_pt3; d.chi2_rz_pt3 = c.chi2_rz_pt3;
+    d.chi2_rphi_pt5 = c.chi2_rphi_pt5; d.chi2_rz_pt5 = c.chi2_rz_pt5;
+    d.pls_pt_tol = c.pls_pt_tol; d.sig_pix = c.sig_pix; d.sb_eta_max = c.sb_eta_max;
+    d.sb_n_eta = c.sb_n_eta; d.sb_n_phi = c.sb_n_phi;
+    d.dr_clean = c.dr_clean; d.k_field = c.k_field; d.b_field = c.b_field;
+    return d;
+}
+
+template <typename T> static lst_status fetch(std::vector<T>& v, const T* d, size_t n) {
+    v.resize(n);
+    if (n) CK(cudaMemcpy(v.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost));
+    return LST_OK;
+}
+
+extern "C" {
+
+const char* lst_status_str(lst_status s) {
+    switch (s) {
+        case LST_OK: return "ok";
+        case LST_WARN_TRUNCATED: return "output truncated by a capacity";
+        case LST_ERR_ARG: return "invalid argument";
+        case LST_ERR_CUDA: return "CUDA runtime error";
+        case LST_ERR_OOM: return "device allocation failed";
+        case LST_ERR_NO_GEOMETRY: return "geometry not loaded";
+        case LST_ERR_TIMEOUT: return "device wait timed out";
+        case LST_ERR_CAPACITY: return "batch exceeds the context capacity";
+    }
+    return "unknown status";
+}
+
+lst_status lst_config_default(lst_config* c) {
+    if (!c) return LST_ERR_ARG;
+    *c = lst_config{};
+    c->pt_min = 0.8; c->k_field = 0.3; c->b_field = 3.8; c->z_lumi = 20.0;
+    c->n_md = 3; c->n_ls = 3; c->n_t3 = 3; c->n_t5 = 3; c->n_pt = 3; c->tol_r = 0.05;
+    c->chi2_rphi_t5 = 15; c->chi2_rz_t5 = 17; c->chi2_rphi_pt3 = 17; c->chi2_rz_pt3 = 19;
+    c->chi2_rphi_pt5 = 21; c->chi2_rz_pt5 = 23;
+    c->pls_pt_tol = 0.05; c->sig_pix = 0.001; c->sb_eta_max = 3.0; c->sb_n_eta = 120; c->sb_n_phi = 72;
+    c->dr_clean = 0.02;
+    return LST_OK;
+}
+
+lst_status lst_capacity_default(lst_capacity* c, int32_t max_events) {
+    if (!c || max_events <= 0) return LST_ERR_ARG;
+    c->max_events = max_events;
+    c->max_hits = 140000 * max_events;
+    c->max_seeds = 10000 * max_events;
+    c->md_per_event = 80000;
+    c->ls_per_event = 400000;
+    c->t3_per_event = 800000;
+    c->t5_per_event = 100000;
+    c->pt3_per_event = 40000;
+    c->pt5_per_event = 40000;
+    c->tc_per_event = 16000;
+    return LST_OK;
+}
+
+lst_status lst_create(lst_ctx** out, const lst_config* cfg, const lst_capacity* cap, int32_t device) {
+    if (!out) return LST_ERR_ARG;
+    *out = nullptr;
+    if (!cfg || !cap || cap->max_events <= 0 || cap->max_hits < 0 || cap->max_seeds < 0) return LST_ERR_ARG;
+    lst_ctx* c = new (std::nothrow) lst_ctx();
+    if (!c) return LST_ERR_OOM;
+    c->device = device;
+    c->cfg = *cfg;
+    c->cap = *cap;
+    c->dc = make_devcfg(*cfg);
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(&c->h_offsets, sizeof(int) * 2 * (cap->max_events + 1)) != cudaSuccess) {
+        delete c;
+        return LST_ERR_CUDA;
+    }
+    *out = c;
+    return LST_OK;
+}
+
+void lst_destroy(lst_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->done) {
+        cudaEventSynchronize(c->done);
+        cudaEventDestroy(c->done);
+    }
+    if (c->dev_mem) cudaFree(c->dev_mem);
+    if (c->h_offsets) cudaFreeHost(c->h_offsets);
+    for (cudaEvent_t& e : c->prof_ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+// Carve every device buffer out of one allocation (first pass with a null
+// base only measures).
+static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_mod, int n_conn, int n_sb,
+                   int n_sbt) {
+    (void)mods_unused;
+    const lst_capacity& K = c->cap;
+    const size_t E = K.max_events, H = K.max_hits, S = K.max_seeds;
+    Arena& A = c->A;
+    A.n_mod = n_mod;
+    A.n_sb = n_sb;
+    A.mod = b.take<float4>(n_mod);
+    A.conn_off = b.take<int>(n_mod + 1);
+    A.conn_tgt = b.take<int>(n_conn);
+    A.sb_off = b.take<int>(n_sb + 1);
+    A.sb_tgt = b.take<int>(n_sbt);
+    c->d_hit_off = b.take<int>(E + 1);
+    c->d_seed_off = b.take<int>(E + 1);
+    c->in_x = b.take<float>(H);
+    c->in_y = b.take<float>(H);
+    c->in_z = b.take<float>(H);
+    c->in_mod = b.take<int>(H);
+    c->in_side = b.take<uint8_t>(H);
+    c->in_seeds = b.take<float>(9 * S);
+    A.bcnt = b.take<int>(E * 2 * n_mod);
+    A.boff = b.take<int>(E * (2 * n_mod + 1));
+    A.sx = b.take<float>(H);
+    A.sy = b.take<float>(H);
+    A.sz = b.take<float>(H);
+    A.sidx = b.take<int>(H);
+    A.counters = b.take<int>(32);
+    A.ev_counts = b.take<int>(E * 8);
+    A.ev_drop = b.take<int>(E * 8);
+    const size_t MD = E * K.md_per_event;
+    A.md_cap = (int)MD;
+    A.md_lo = b.take<int>(MD); A.md_up = b.take<int>(MD); A.md_gmod = b.take<int>(MD);
+    A.md_x = b.take<float>(MD); A.md_y = b.take<float>(MD); A.md_z = b.take<float>(MD);
+    A.md_dx = b.take<float>(MD); A.md_dy = b.take<float>(MD);
+    A.md_dphi = b.take<float>(MD); A.md_dlong = b.take<float>(MD);
+    A.md_moff = b.take<int>(E * n_mod); A.md_mcnt = b.take<int>(E * n_mod);
+    const size_t LS = E * K.ls_per_event;
+    A.ls_cap = (int)LS;
+    A.ls_in = b.take<int>(LS); A.ls_out = b.take<int>(LS); A.ls_dphi = b.take<float>(LS);
+    A.ls_off = b.take<int>(MD); A.ls_cnt = b.take<int>(MD);
+    const size_t T3 = E * K.t3_per_event;
+    A.t3_cap = (int)T3;
+    A.t3_lsin = b.take<int>(T3); A.t3_lsout = b.take<int>(T3);
+    A.t3_beta = b.take<float>(T3); A.t3_kappa = b.take<float>(T3); A.t3_sigk = b.take<float>(T3);
+    A.t3_off = b.take<int>(MD); A.t3_cnt = b.take<int>(MD);
+    const size_t T5 = E * K.t5_per_event;
+    A.t5_cap = (int)T5;
+    A.t5_in = b.take<int>(T5); A.t5_out = b.take<int>(T5);
+    A.t5_kappa = b.take<double>(T5); A.t5_sigk = b.take<double>(T5);
+    A.t5_eta = b.take<double>(T5); A.t5_phi = b.take<double>(T5);
+    A.t5_chi2 = b.take<float>(T5); A.t5_chi2z = b.take<float>(T5); A.t5_score = b.take<float>(T5);
+    A.t5_pt = b.take<float>(T5);
+    A.t5_off = b.take<int>(MD); A.t5_cnt = b.take<int>(MD);
+    A.pls_pass = b.take<int>(S); A.pls_sb = b.take<int>(S);
+    A.pls_kappa = b.take<double>(S); A.pls_sigk = b.take<double>(S);
+    A.pls_eta = b.take<double>(S); A.pls_phi = b.take<double>(S);
+    A.pls_z0 = b.take<float>(S); A.pls_pt = b.take<float>(S);
+    const size_t P5 = E * K.pt5_per_event, P3 = E * K.pt3_per_event;
+    A.pt5_cap = (int)P5;
+    A.pt5_seed = b.take<int>(P5); A.pt5_obj = b.take<int>(P5); A.pt5_kappa = b.take<float>(P5);
+    A.pt5_chi2 = b.take<float>(P5); A.pt5_chi2z = b.take<float>(P5); A.pt5_score = b.take<float>(P5);
+    A.pt5_pt = b.take<float>(P5);
+    A.pt3_cap = (int)P3;
+    A.pt3_seed = b.take<int>(P3); A.pt3_obj = b.take<int>(P3); A.pt3_kappa = b.take<float>(P3);
+    A.pt3_chi2 = b.take<float>(P3); A.pt3_chi2z = b.take<float>(P3); A.pt3_score = b.take<float>(P3);
+    A.pt3_pt = b.take<float>(P3);
+    const size_t NK = H + 3 * S;
+    A.best = b.take<unsigned long long>(3 * NK);
+    A.mark = b.take<int>(NK);
+    A.keep_pt5 = b.take<uint8_t>(P5); A.keep_pt3 = b.take<uint8_t>(P3); A.keep_t5 = b.take<uint8_t>(T5);
+    A.seed_link = b.take<int>(S);
+    A.list_cap = 32768;
+    A.list_cnt = b.take<int>(E * 2);
+    A.list_ef = b.take<float2>(E * 2 * A.list_cap);
+    A.list_ref = b.take<int>(E * 2 * A.list_cap);
+    A.tc_cap = K.tc_per_event;
+    A.tc_cnt = b.take<int>(E);
+    const size_t TC = E * K.tc_per_event;
+    A.tc_type = b.take<int>(TC); A.tc_seed = b.take<int>(TC); A.tc_obj = b.take<int>(TC);
+    A.tc_hits = b.take<int>(10 * TC);
+    A.tc_pt = b.take<float>(TC); A.tc_eta = b.take<float>(TC); A.tc_phi = b.take<float>(TC);
+}
+
+lst_status lst_load_geometry(lst_ctx* c, const lst_module* mods, int32_t n_mod, const int32_t* conn_off,
+                             const int32_t* conn_tgt, const int32_t* sb_off, const int32_t* sb_tgt, int32_t n_sb) {
+    if (!c || !mods || n_mod <= 0 || !conn_off || !sb_off || n_sb <= 0) return LST_ERR_ARG;
+    if (n_sb != c->cfg.sb_n_eta * c->cfg.sb_n_phi * 2) return LST_ERR_ARG;
+    const int n_conn = conn_off[n_mod], n_sbt = sb_off[n_sb];
+    if (n_conn < 0 || n_sbt < 0 || (n_conn && !conn_tgt) || (n_sbt && !sb_tgt)) return LST_ERR_ARG;
+    for (int i = 0; i < n_conn; ++i)
+        if (conn_tgt[i] < 0 || conn_tgt[i] >= n_mod) return LST_ERR_ARG;
+    for (int i = 0; i < n_sbt; ++i)
+        if (sb_tgt[i] < 0 || sb_tgt[i] >= n_mod) return LST_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    if (c->dev_mem) {
+        cudaEventSynchronize(c->done);
+        cudaFree(c->dev_mem);
+        c->dev_mem = nullptr;
+    }
+    Buffer probe;
+    layout(c, probe, mods, n_mod, n_conn, n_sb, n_sbt);
+    if (cudaMalloc(&c->dev_mem, probe.used) != cudaSuccess) {
+        c->dev_mem = nullptr;
+        c->geometry = false;
+        return LST_ERR_OOM;
+    }
+    c->dev_bytes = probe.used;
+    Buffer real;
+    real.base = c->dev_mem;
+    real.size = probe.used;
+    layout(c, real, mods, n_mod, n_conn, n_sb, n_sbt);
+    std::vector<float4> m4(n_mod);
+    for (int i = 0; i < n_mod; ++i)
+        m4[i] = make_float4(mods[i].dsep, mods[i].sig_rphi, mods[i].sig_long, float(mods[i].subdet));
+    CK(cudaMemcpy((void*)c->A.mod, m4.data(), sizeof(float4) * n_mod, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)c->A.conn_off, conn_off, sizeof(int) * (n_mod + 1), cudaMemcpyHostToDevice));
+    if (n_conn) CK(cudaMemcpy((void*)c->A.conn_tgt, conn_tgt, sizeof(int) * n_conn, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)c->A.sb_off, sb_off, sizeof(int) * (n_sb + 1), cudaMemcpyHostToDevice));
+    if (n_sbt) CK(cudaMemcpy((void*)c->A.sb_tgt, sb_tgt, sizeof(int) * n_sbt, cudaMemcpyHostToDevice));
+    CK(cudaFuncSetAttribute(k_md, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)md_smem_bytes()));
+    c->geometry = true;
+    c->ran = false;
+    return LST_OK;
+}
+
+static int grid_for(int n, int block, int cap_blocks) {
+    int g = (n + block - 1) / block;
+    return std::max(1, std::min(g, cap_blocks));
+}
+
+lst_status lst_run_batch(lst_ctx* c, const lst_hits* hits, const int32_t* hit_off, const lst_seeds* seeds,
+                         const int32_t* seed_off, int32_t n_ev, int32_t mem_is_device, void* stream_) {
+    if (!c) return LST_ERR_ARG;
+    if (!c->geometry) return LST_ERR_NO_GEOMETRY;
+    if (!hits || !hit_off || !seeds || !seed_off || n_ev <= 0) return LST_ERR_ARG;
+    if (n_ev > c->cap.max_events || hits->n > c->cap.max_hits || seeds->n > c->cap.max_seeds) return LST_ERR_CAPACITY;
+    if (hits->n < 0 || seeds->n < 0 || hit_off[0] != 0 || seed_off[0] != 0 || hit_off[n_ev] != hits->n ||
+        seed_off[n_ev] != seeds->n)
+        return LST_ERR_ARG;
+    for (int e = 0; e < n_ev; ++e)
+        if (hit_off[e + 1] < hit_off[e] || seed_off[e + 1] < seed_off[e]) return LST_ERR_ARG;
+    if ((hits->n && (!hits->x || !hits->y || !hits->z || !hits->module || !hits->side)) || (seeds->n && !seeds->xyz))
+        return LST_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream_);
+    if (c->ran) CK(cudaEventSynchronize(c->done));   // the pinned staging is reused
+    Arena& A = c->A;
+    A.n_ev = n_ev;
+    A.n_hits = hits->n;
+    A.n_seeds = seeds->n;
+    c->n_ev = n_ev;
+    c->hit_off_host.assign(hit_off, hit_off + n_ev + 1);
+    c->seed_off_host.assign(seed_off, seed_off + n_ev + 1);
+    std::memcpy(c->h_offsets, hit_off, sizeof(int) * (n_ev + 1));
+    std::memcpy(c->h_offsets + n_ev + 1, seed_off, sizeof(int) * (n_ev + 1));
+    CK(cudaMemcpyAsync(c->d_hit_off, c->h_offsets, sizeof(int) * (n_ev + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_seed_off, c->h_offsets + n_ev + 1, sizeof(int) * (n_ev + 1), cudaMemcpyHostToDevice, st));
+    A.hit_off = c->d_hit_off;
+    A.seed_off = c->d_seed_off;
+    const size_t H = hits->n, S = seeds->n;
+    if (mem_is_device) {
+        A.hx = hits->x; A.hy = hits->y; A.hz = hits->z; A.hmod = hits->module; A.hside = hits->side;
+        A.seeds = seeds->xyz;
+    } else {
+        if (H) {
+            CK(cudaMemcpyAsync(c->in_x, hits->x, 4 * H, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(c->in_y, hits->y, 4 * H, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(c->in_z, hits->z, 4 * H, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(c->in_mod, hits->module, 4 * H, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(c->in_side, hits->side, H, cudaMemcpyHostToDevice, st));
+        }
+        if (S) CK(cudaMemcpyAsync(c->in_seeds, seeds->xyz, 36 * S, cudaMemcpyHostToDevice, st));
+        A.hx = c->in_x; A.hy = c->in_y; A.hz = c->in_z; A.hmod = c->in_mod; A.hside = c->in_side;
+        A.seeds = c->in_seeds;
+    }
+    const size_t nb = (size_t)n_ev * 2 * A.n_mod;
+    const size_t NK = H + 3 * S;
+    CK(cudaMemsetAsync(A.counters, 0, sizeof(int) * 32, st));
+    CK(cudaMemsetAsync(A.ev_counts, 0, sizeof(int) * 8 * n_ev, st));
+    CK(cudaMemsetAsync(A.ev_drop, 0, sizeof(int) * 8 * n_ev, st));
+    CK(cudaMemsetAsync(A.bcnt, 0, sizeof(int) * nb, st));
+    CK(cudaMemsetAsync(A.best, 0xff, sizeof(unsigned long long) * 3 * NK, st));
+    CK(cudaMemsetAsync(A.mark, 0, sizeof(int) * std::max<size_t>(NK, 1), st));
+    CK(cudaMemsetAsync(A.seed_link, 0, sizeof(int) * std::max<size_t>(S, 1), st));
+    CK(cudaMemsetAsync(A.list_cnt, 0, sizeof(int) * 2 * n_ev, st));
+    CK(cudaMemsetAsync(A.tc_cnt, 0, sizeof(int) * n_ev, st));
+    // The best-key arrays are laid out for the context's capacity; index them
+    // with this batch's key count.
+    const int nsm = c->n_sm;
+    const DevCfg& dc = c->dc;
+    int L = 0;
+    // each launch is bracketed by a CUDA event pair when profiling is on
+#define LAUNCH(NAME, ...)                                                              \
+    do {                                                                               \
+        if (c->profiling && L < lst_ctx::kMaxProf) {                                   \
+            c->prof_name[L] = NAME;                                                    \
+            cudaEventRecord(c->prof_ev[2 * L], st);                                    \
+        }                                                                              \
+        __VA_ARGS__;                                                                   \
+        if (c->profiling && L < lst_ctx::kMaxProf) cudaEventRecord(c->prof_ev[2 * L + 1], st); \
+        ++L;                                                                           \
+    } while (0)
+    LAUNCH("bin_count", k_bin_count<<<grid_for((int)H, 256, nsm * 8), 256, 0, st>>>(A));
+    LAUNCH("bin_scan", k_bin_scan<<<n_ev, 1024, 0, st>>>(A));
+    LAUNCH("bin_scatter", k_bin_scatter<<<grid_for((int)H, 256, nsm * 8), 256, 0, st>>>(A));
+    LAUNCH("md", k_md<<<nsm * 4, kMdWarps * 32, md_smem_bytes(), st>>>(A, dc));
+    LAUNCH("ls", k_ls<<<nsm * 8, kLsWarps * 32, 0, st>>>(A, dc));
+    LAUNCH("t3", k_t3<<<nsm * 8, kT3Warps * 32, 0, st>>>(A, dc));
+    LAUNCH("t5", k_t5<<<nsm * 6, kT5Warps * 32, 0, st>>>(A, dc));
+    LAUNCH("pls", k_pls<<<grid_for((int)S, 128, nsm * 4), 128, 0, st>>>(A, dc));
+    LAUNCH("pt5", k_pt5<<<nsm * 8, kPtWarps * 32, 0, st>>>(A, dc));
+    LAUNCH("pt3", k_pt3<<<nsm * 8, kPtWarps * 32, 0, st>>>(A, dc));
+    LAUNCH("clean_keys", k_clean_keys<<<nsm * 4, 256, 0, st>>>(A, 0));
+    LAUNCH("clean_keep", k_clean_keys<<<nsm * 4, 256, 0, st>>>(A, 1));
+    LAUNCH("clean_pt5", k_clean_pt5<<<nsm * 2, 256, 0, st>>>(A));
+    LAUNCH("clean_pt3_cross", k_clean_pt3_cross<<<nsm * 2, 256, 0, st>>>(A, dc));
+    LAUNCH("clean_pt3_mark", k_clean_pt3_mark<<<nsm * 2, 256, 0, st>>>(A));
+    LAUNCH("clean_t5", k_clean_t5<<<nsm * 4, 256, 0, st>>>(A, dc));
+    LAUNCH("clean_pls", k_clean_pls<<<grid_for((int)S, 128, nsm * 4), 128, 0, st>>>(A, dc));
+#undef LAUNCH
+    c->launches = L;
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(c->done, st));
+    c->ran = true;
+    return LST_OK;
+}
+
+lst_status lst_run_event(lst_ctx* c, const lst_hits* hits, const lst_seeds* seeds, int32_t mem_is_device,
+                         void* stream) {
+    if (!hits || !seeds) return LST_ERR_ARG;
+    int32_t ho[2] = {0, hits->n}, so[2] = {0, seeds->n};
+    return lst_run_batch(c, hits, ho, seeds, so, 1, mem_is_device, stream);
+}
+
+int32_t lst_last_launch_count(lst_ctx* c) { return c ? c->launches : 0; }
+
+lst_status lst_set_profiling(lst_ctx* c, int32_t enable) {
+    if (!c) return LST_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    if (enable && !c->prof_ev[0])
+        for (cudaEvent_t& e : c->prof_ev) CK(cudaEventCreate(&e));
+    if (c->ran) CK(cudaEventSynchronize(c->done));
+    c->profiling = enable != 0;
+    return LST_OK;
+}
+
+lst_status lst_get_kernel_times(lst_ctx* c, int32_t capacity, int32_t* n_out, const char** names, float* ms) {
+    if (!c || capacity < 0) return LST_ERR_ARG;
+    if (!c->ran || !c->profiling) return LST_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cudaEventSynchronize(c->done));
+    const int n = std::min(c->launches, (int)lst_ctx::kMaxProf);
+    if (n_out) *n_out = n;
+    for (int i = 0; i < std::min(n, (int)capacity); ++i) {
+        if (names) names[i] = c->prof_name[i];
+        if (ms) CK(cudaEventElapsedTime(ms + i, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]));
+    }
+    return n > capacity ? LST_WARN_TRUNCATED : LST_OK;
+}
+
+static lst_status wait_batch(lst_ctx* c, int32_t event) {
+    if (!c) return LST_ERR_ARG;
+    if (!c->ran) return LST_ERR_ARG;
+    if (event < 0 || event >= c->n_ev) return LST_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cudaEventSynchronize(c->done));
+    CK(cudaGetLastError());
+    return LST_OK;
+}
+
+
+#define FETCH(v, d, n)                          \
+    do {                                        \
+        lst_status s__ = fetch(v, d, n);        \
+        if (s__ != LST_OK) return s__;          \
+    } while (0)
+
+lst_status lst_get_stats(lst_ctx* c, int32_t event, lst_stats* out) {
+    lst_status s = wait_batch(c, event);
+    if (s != LST_OK) return s;
+    if (!out) return LST_ERR_ARG;
+    int cnt[8], drop[8], tc = 0;
+    CK(cudaMemcpy(cnt, c->A.ev_counts + 8 * event, sizeof cnt, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(drop, c->A.ev_drop + 8 * event, sizeof drop, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&tc, c->A.tc_cnt + event, sizeof(int), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 8; ++k) { out->counts[k] = cnt[k]; out->dropped[k] = drop[k]; }
+    out->counts[7] = std::min(tc, c->A.tc_cap);
+    return LST_OK;
+}
+
+lst_status lst_get_track_candidates(lst_ctx* c, int32_t event, int32_t capacity, int32_t* n_out, int32_t* type,
+                                    int32_t* seed, int32_t* hits, float* pet) {
+    lst_status s = wait_batch(c, event);
+    if (s != LST_OK) return s;
+    if (capacity < 0) return LST_ERR_ARG;
+    int n = 0;
+    CK(cudaMemcpy(&n, c->A.tc_cnt + event, sizeof(int), cudaMemcpyDeviceToHost));
+    n = std::min(n, c->A.tc_cap);
+    if (n_out) *n_out = n;
+    const int k = std::min(n, (int)capacity);
+    const size_t o = (size_t)event * c->A.tc_cap;
+    if (k > 0) {
+        if (type) CK(cudaMemcpy(type, c->A.tc_type + o, 4 * k, cudaMemcpyDeviceToHost));
+        if (seed) CK(cudaMemcpy(seed, c->A.tc_seed + o, 4 * k, cudaMemcpyDeviceToHost));
+        if (hits) CK(cudaMemcpy(hits, c->A.tc_hits + 10 * o, 40 * (size_t)k, cudaMemcpyDeviceToHost));
+        if (pet) {
+            std::vector<float> a, b2, d;
+            FETCH(a, c->A.tc_pt + o, k);
+            FETCH(b2, c->A.tc_eta + o, k);
+            FETCH(d, c->A.tc_phi + o, k);
+            for (int i = 0; i < k; ++i) { pet[3 * i] = a[i]; pet[3 * i + 1] = b2[i]; pet[3 * i + 2] = d[i]; }
+        }
+    }
+    return n > capacity ? LST_WARN_TRUNCATED : LST_OK;
+}
+
+lst_status lst_object_columns(int32_t kind, int32_t* ni, int32_t* nf) {
+    static const int NI[] = {3, 2, 2, 2, 3, 2, 2};
+    static const int NF[] = {2, 1, 3, 7, 6, 5, 5};
+    if (kind < 0 || kind > 6 || !ni || !nf) return LST_ERR_ARG;
+    *ni = NI[kind];
+    *nf = NF[kind];
+    return LST_OK;
+}
+
+lst_status lst_get_objects(lst_ctx* c, int32_t event, int32_t kind, int32_t capacity, int32_t* n_out, int32_t* I,
+                           float* F) {
+    lst_status s = wait_batch(c, event);
+    if (s != LST_OK) return s;
+    if (kind < 0 || kind > 6 || capacity < 0) return LST_ERR_ARG;
+    const Arena& A = c->A;
+    int cnt[32];
+    CK(cudaMemcpy(cnt, A.counters, sizeof cnt, cudaMemcpyDeviceToHost));
+    const int n_md = std::min(cnt[0], A.md_cap), n_ls = std::min(cnt[1], A.ls_cap);
+    const int n_t3 = std::min(cnt[2], A.t3_cap), n_t5 = std::min(cnt[3], A.t5_cap);
+    const int n_p5 = std::min(cnt[4], A.pt5_cap), n_p3 = std::min(cnt[5], A.pt3_cap);
+    std::vector<int> iv;        // rows: ints
+    std::vector<float> fv;      // rows: floats
+    int ni = 0, nf = 0;
+    lst_object_columns(kind, &ni, &nf);
+    // MD rows of this event (and their global -> row map) are needed by all kinds but pLS
+    std::vector<int> md_row, ls_row, t3_row, t5_row;
+    std::vector<int> gmod;
+    FETCH(gmod, A.md_gmod, n_md);
+    md_row.assign(n_md, -1);
+    int r = 0;
+    for (int i = 0; i < n_md; ++i)
+        if (gmod[i] / A.n_mod == event) md_row[i] = r++;
+    const int s0 = c->seed_off_host[event], s1 = c->seed_off_host[event + 1];
+    if (kind == 0) {
+        std::vector<int> lo, up;
+        std::vector<float> dp, dl;
+        FETCH(lo, A.md_lo, n_md); FETCH(up, A.md_up, n_md); FETCH(dp, A.md_dphi, n_md); FETCH(dl, A.md_dlong, n_md);
+        for (int i = 0; i < n_md; ++i)
+            if (md_row[i] >= 0) {
+                iv.insert(iv.end(), {lo[i], up[i], gmod[i] % A.n_mod});
+                fv.insert(fv.end(), {dp[i], dl[i]});
+            }
+    }
+    std::vector<int> li, lo2;
+    if (kind >= 1 && kind != 4) {
+        FETCH(li, A.ls_in, n_ls);
+        FETCH(lo2, A.ls_out, n_ls);
+        ls_row.assign(n_ls, -1);
+        r = 0;
+        for (int i = 0; i < n_ls; ++i)
+            if (md_row[li[i]] >= 0) ls_row[i] = r++;
+    }
+    if (kind == 1) {
+        std::vector<float> dp;
+        FETCH(dp, A.ls_dphi, n_ls);
+        for (int i = 0; i < n_ls; ++i)
+            if (ls_row[i] >= 0) {
+                iv.insert(iv.end(), {md_row[li[i]], md_row[lo2[i]]});
+                fv.push_back(dp[i]);
+            }
+    }
+    std::vector<int> t3i, t3o;
+    if (kind == 2 || kind == 3 || kind == 5 || kind == 6) {
+        FETCH(t3i, A.t3_lsin, n_t3);
+        FETCH(t3o, A.t3_lsout, n_t3);
+        t3_row.assign(n_t3, -1);
+        r = 0;
+        for (int i = 0; i < n_t3; ++i)
+            if (ls_row[t3i[i]] >= 0) t3_row[i] = r++;
+    }
+    if (kind == 2) {
+        std::vector<float> b, k, sk;
+        FETCH(b, A.t3_beta, n_t3); FETCH(k, A.t3_kappa, n_t3); FETCH(sk, A.t3_sigk, n_t3);
+        for (int i = 0; i < n_t3; ++i)
+            if (t3_row[i] >= 0) {
+                iv.insert(iv.end(), {ls_row[t3i[i]], ls_row[t3o[i]]});
+                fv.insert(fv.end(), {b[i], k[i], sk[i]});
+            }
+    }
+    std::vector<int> t5i, t5o;
+    if (kind == 3 || kind == 5) {
+        FETCH(t5i, A.t5_in, n_t5);
+        FETCH(t5o, A.t5_out, n_t5);
+        t5_row.assign(n_t5, -1);
+        r = 0;
+        for (int i = 0; i < n_t5; ++i)
+            if (t3_row[t5i[i]] >= 0) t5_row[i] = r++;
+    }
+    if (kind == 3) {
+        std::vector<double> k, et, ph;
+        std::vector<float> c2, cz, sc, pt;
+        FETCH(k, A.t5_kappa, n_t5); FETCH(et, A.t5_eta, n_t5); FETCH(ph, A.t5_phi, n_t5);
+        FETCH(c2, A.t5_chi2, n_t5); FETCH(cz, A.t5_chi2z, n_t5); FETCH(sc, A.t5_score, n_t5); FETCH(pt, A.t5_pt, n_t5);
+        for (int i = 0; i < n_t5; ++i)
+            if (t5_row[i] >= 0) {
+                iv.insert(iv.end(), {t3_row[t5i[i]], t3_row[t5o[i]]});
+                fv.insert(fv.end(), {float(k[i]), c2[i], cz[i], float(et[i]), float(ph[i]), pt[i], sc[i]});
+            }
+    }
+    if (kind == 4) {
+        int n = s1 - s0;
+        std::vector<int> ps, sb;
+        std::vector<double> k, sk, et, ph;
+        std::vector<float> z0, pt;
+        FETCH(ps, A.pls_pass + s0, n); FETCH(sb, A.pls_sb + s0, n);
+        FETCH(k, A.pls_kappa + s0, n); FETCH(sk, A.pls_sigk + s0, n); FETCH(et, A.pls_eta + s0, n);
+        FETCH(ph, A.pls_phi + s0, n); FETCH(z0, A.pls_z0 + s0, n); FETCH(pt, A.pls_pt + s0, n);
+        for (int i = 0; i < n; ++i) {
+            iv.insert(iv.end(), {i, ps[i], sb[i]});
+            fv.insert(fv.end(), {float(k[i]), float(sk[i]), float(et[i]), float(ph[i]), z0[i], pt[i]});
+        }
+    }
+    if (kind == 5 || kind == 6) {
+        const int n = kind == 5 ? n_p5 : n_p3;
+        std::vector<int> sd, ob;
+        std::vector<float> k, c2, cz, sc, pt;
+        FETCH(sd, kind == 5 ? A.pt5_seed : A.pt3_seed, n); FETCH(ob, kind == 5 ? A.pt5_obj : A.pt3_obj, n);
+        FETCH(k, kind == 5 ? A.pt5_kappa : A.pt3_kappa, n); FETCH(c2, kind == 5 ? A.pt5_chi2 : A.pt3_chi2, n);
+        FETCH(cz, kind == 5 ? A.pt5_chi2z : A.pt3_chi2z, n); FETCH(sc, kind == 5 ? A.pt5_score : A.pt3_score, n);
+        FETCH(pt, kind == 5 ? A.pt5_pt : A.pt3_pt, n);
+        for (int i = 0; i < n; ++i)
+            if (sd[i] >= s0 && sd[i] < s1) {
+                iv.insert(iv.end(), {sd[i] - s0, kind == 5 ? t5_row[ob[i]] : t3_row[ob[i]]});
+                fv.insert(fv.end(), {k[i], c2[i], cz[i], sc[i], pt[i]});
+            }
+    }
+    const int rows = ni ? (int)(iv.size() / ni) : 0;
+    if (n_out) *n_out = rows;
+    const int k = std::min(rows, (int)capacity);
+    if (I && k) std::memcpy(I, iv.data(), sizeof(int) * ni * (size_t)k);
+    if (F && k) std::memcpy(F, fv.data(), sizeof(float) * nf * (size_t)k);
+    return rows > capacity ? LST_WARN_TRUNCATED : LST_OK;
+}
+
+}  // extern "C"

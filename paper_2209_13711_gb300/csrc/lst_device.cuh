@@ -1,0 +1,559 @@
+// Device-side types and cut arithmetic of the Segment Linking chain.
+//
+// Every candidate test is written once as a template over the arithmetic
+// type T. The float instantiation is the fast path: each cut "v <= thr" is
+// decided in FP32 unless v lies within kBand * |thr| of its threshold, in
+// which case the candidate is re-evaluated with T = double and that decision
+// stands (a filtered predicate). The double instantiation decides every cut
+// exactly as written. Quantities whose FP32 rounding is too coarse for a
+// 1e-5 relative agreement (circle-fit residuals of 26 um against 100 cm
+// coordinates) are only ever computed in double.
+//
+// The cut formulas are this library's reading of Section 2.1 of the paper
+// (which gives the cut concepts, not formulas):
+//   MD  (Section 2, Fig. pTModule): position-angle change between the two
+//       sensors bounded by a pT_min helix, and the hits' z (barrel) or r
+//       (endcap) consistent with a track from the luminous region.
+//   LS  (Fig. CompModules): r-z pointing to |z0| <= z_lumi, position-angle
+//       change and stub-vs-segment angles bounded by a pT_min helix.
+//   T3  (Figs. Triplet, GeomReqs): relative angle beta of the two segments
+//       bounded by a pT_min helix, r-z residual of the three anchors.
+//   T5  (Fig. Quintuplet): inner/outer triplet curvature agreement, circle
+//       fit chi2 and curvature, r-z line chi2.
+//   pLS, pT3, pT5 (Section 2.1): seed curvature and z0 cuts, superbin,
+//       pLS/T-object curvature agreement, joint circle and r-z fits.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lst {
+
+constexpr float kBand = 2e-3f;   // relative width of the FP32 undecided band around a threshold
+constexpr double kPi = 3.14159265358979323846;
+
+// Cut constants as seen by the kernels (derived on the host from lst_config).
+struct DevCfg {
+    double a;              // 1 / (2 R_min), R_min = 100 pT_min / (k B) cm
+    double z_lumi, n_md, n_ls, n_t3, n_t5, n_pt, tol_r;
+    double chi2_rphi_t5, chi2_rz_t5, chi2_rphi_pt3, chi2_rz_pt3, chi2_rphi_pt5, chi2_rz_pt5;
+    double pls_pt_tol, sig_pix, sb_eta_max;
+    int sb_n_eta, sb_n_phi;
+    double dr_clean, k_field, b_field;
+};
+
+// Device buffers of one context (all preallocated; flat object arenas with
+// per-unit segments).
+struct Arena {
+    // geometry
+    int n_mod, n_sb;
+    const float4* mod;            // {dsep, sig_rphi, sig_long, subdet}
+    const int* conn_off;
+    const int* conn_tgt;
+    const int* sb_off;
+    const int* sb_tgt;
+    // batch
+    int n_ev, n_hits, n_seeds;
+    const int* hit_off;           // [n_ev + 1]
+    const int* seed_off;          // [n_ev + 1]
+    const float* hx;
+    const float* hy;
+    const float* hz;
+    const int* hmod;
+    const uint8_t* hside;
+    const float* seeds;           // [n_seeds][9]
+    // hit binning: bucket (e, module, side) = e * 2 n_mod + 2 module + side
+    int* bcnt;                    // [n_ev * 2 n_mod]: counts, then scatter cursors
+    int* boff;                    // [n_ev * (2 n_mod + 1)]: offsets relative to hit_off[e]
+    float* sx;
+    float* sy;
+    float* sz;
+    int* sidx;                    // original hit index within the event
+    // counters: [0] MD [1] LS [2] T3 [3] T5 [4] pT5 [5] pT3, [8..15] dropped per kind, [16] bad hits
+    int* counters;
+    int* ev_counts;               // [n_ev][8]
+    int* ev_drop;                 // [n_ev][8]
+    // MD
+    int md_cap;
+    int* md_lo;
+    int* md_up;
+    int* md_gmod;                 // e * n_mod + module
+    float* md_x;
+    float* md_y;
+    float* md_z;
+    float* md_dx;
+    float* md_dy;
+    float* md_dphi;
+    float* md_dlong;
+    int* md_moff;                 // [n_ev * n_mod]
+    int* md_mcnt;
+    // LS
+    int ls_cap;
+    int* ls_in;
+    int* ls_out;
+    float* ls_dphi;
+    int* ls_off;                  // [md_cap] segment of LS whose inner MD is this MD
+    int* ls_cnt;
+    // T3
+    int t3_cap;
+    int* t3_lsin;
+    int* t3_lsout;
+    float* t3_beta;
+    float* t3_kappa;
+    float* t3_sigk;
+    int* t3_off;                  // [md_cap] by inner MD
+    int* t3_cnt;
+    // T5
+    int t5_cap;
+    int* t5_in;
+    int* t5_out;
+    double* t5_kappa;
+    float* t5_chi2;
+    float* t5_chi2z;
+    float* t5_score;
+    float* t5_pt;
+    double* t5_sigk;
+    double* t5_eta;
+    double* t5_phi;
+    int* t5_off;                  // [md_cap] by inner MD
+    int* t5_cnt;
+    // pLS, per seed
+    int* pls_pass;
+    int* pls_sb;
+    double* pls_kappa;
+    double* pls_sigk;
+    float* pls_z0;
+    float* pls_pt;
+    double* pls_eta;
+    double* pls_phi;
+    // pT5 / pT3
+    int pt5_cap;
+    int* pt5_seed;
+    int* pt5_obj;
+    float* pt5_kappa;
+    float* pt5_chi2;
+    float* pt5_chi2z;
+    float* pt5_score;
+    float* pt5_pt;
+    int pt3_cap;
+    int* pt3_seed;
+    int* pt3_obj;
+    float* pt3_kappa;
+    float* pt3_chi2;
+    float* pt3_chi2z;
+    float* pt3_score;
+    float* pt3_pt;
+    // cleaning
+    unsigned long long* best;     // [3][n_keys]: n_keys = n_hits + 3 n_seeds
+    int* mark;                    // [n_keys] bit 0: used by a kept pT5, bit 1: by a kept pT3
+    uint8_t* keep_pt5;
+    uint8_t* keep_pt3;
+    uint8_t* keep_t5;
+    int* seed_link;               // [n_seeds]
+    int list_cap;                 // per event
+    int* list_cnt;                // [n_ev][2]: list 0 = kept pT5 + pT3, list 1 = kept T5
+    float2* list_ef;              // [n_ev][2][list_cap] (eta, phi) float
+    int* list_ref;                // [n_ev][2][list_cap] (category << 28) | index
+    // track candidates, per-event slabs
+    int tc_cap;
+    int* tc_cnt;                  // [n_ev]
+    int* tc_type;
+    int* tc_seed;
+    int* tc_obj;
+    int* tc_hits;                 // [n_ev * tc_cap][10]
+    float* tc_pt;
+    float* tc_eta;
+    float* tc_phi;
+};
+
+// ---------------------------------------------------------------------------
+// arithmetic helpers (float and double overloads)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float m_sqrt(float v) { return sqrtf(v); }
+__device__ __forceinline__ double m_sqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ float m_asin(float v) { return asinf(v); }
+__device__ __forceinline__ double m_asin(double v) { return asin(v); }
+__device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float m_hypot(float a, float b) { return hypotf(a, b); }
+__device__ __forceinline__ double m_hypot(double a, double b) { return hypot(a, b); }
+__device__ __forceinline__ float m_abs(float v) { return fabsf(v); }
+__device__ __forceinline__ double m_abs(double v) { return fabs(v); }
+__device__ __forceinline__ float m_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double m_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float m_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double m_min(double a, double b) { return fmin(a, b); }
+
+template <typename T> __device__ __forceinline__ T sq(T v) { return v * v; }
+template <typename T> __device__ __forceinline__ T asinc(T v) { return m_asin(m_min(T(1), m_max(T(0), v))); }
+// transverse arc length of a chord c on a circle of curvature k
+template <typename T> __device__ __forceinline__ T arc(T c, T k) {
+    return k > T(0) ? T(2) * m_asin(m_min(T(1), c * k / T(2))) / k : c;
+}
+// angle in (-pi, pi]; loop-free (a non-finite input gives NaN)
+__device__ __forceinline__ double wrap_pi(double p) {
+    double q = p - 2 * kPi * rint(p / (2 * kPi));
+    if (q <= -kPi) q += 2 * kPi;
+    if (q > kPi) q -= 2 * kPi;
+    return q;
+}
+
+// Filtered cut bookkeeping: state 1 accept, 0 reject, 2 undecided (FP32 only).
+template <typename T> struct Cuts {
+    bool fail = false;
+    bool near = false;
+    __device__ __forceinline__ void operator()(T v, T thr) {
+        if (sizeof(T) == 4) {
+            T band = T(kBand) * m_abs(thr);
+            if (m_abs(v - thr) <= band) near = true;
+            else if (!(v <= thr)) fail = true;        // also rejects NaN
+        } else {
+            if (!(v <= thr)) fail = true;
+        }
+    }
+    __device__ __forceinline__ int state() const { return fail ? 0 : (near ? 2 : 1); }
+};
+
+// A measured point with its resolutions (along phi-hat, z, r-hat).
+template <typename T> struct Pt {
+    T x, y, z, r, srphi, sz, sr;
+};
+
+template <typename T> __device__ __forceinline__ Pt<T> hit_pt(float x, float y, float z, float4 mi) {
+    Pt<T> p;
+    p.x = T(x); p.y = T(y); p.z = T(z);
+    p.r = m_hypot(p.x, p.y);
+    p.srphi = T(mi.y);
+    bool barrel = mi.w < 0.5f;
+    p.sz = barrel ? T(mi.z) : T(0);
+    p.sr = barrel ? T(0) : T(mi.z);
+    return p;
+}
+
+template <typename T> __device__ __forceinline__ Pt<T> pix_pt(const float* q, double sig_pix) {
+    Pt<T> p;
+    p.x = T(q[0]); p.y = T(q[1]); p.z = T(q[2]);
+    p.r = m_hypot(p.x, p.y);
+    p.srphi = T(sig_pix); p.sz = T(sig_pix); p.sr = T(0);
+    return p;
+}
+
+// error of P perpendicular to a chord of unit direction (cx, cy)
+template <typename T> __device__ __forceinline__ T sigma_perp(const Pt<T>& P, T cx, T cy) {
+    T rx = P.x / P.r, ry = P.y / P.r;
+    T along = cx * rx + cy * ry;
+    T across = m_abs(cx * ry - cy * rx);
+    return m_sqrt(sq(P.srphi * along) + sq(P.sr * across));
+}
+
+// ---------------------------------------------------------------------------
+// MD: lower hit L, upper hit U of one module (mi = module row)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ int md_eval(const DevCfg& c, float4 mi, const Pt<T>& L, const Pt<T>& U, T& dphi_o,
+                                       T& dlong_o) {
+    const T a = T(c.a);
+    T dx = U.x - L.x, dy = U.y - L.y, dz = U.z - L.z;
+    T rL = L.r;
+    T dsep = T(mi.x), srphi = T(mi.y), sl = T(mi.z);
+    T dphi = m_atan2(L.x * dy - L.y * dx, L.x * U.x + L.y * U.y);
+    T dlong, thr_phi, thr_long;
+    const T rt2 = T(1.4142135623730951);
+    if (mi.w < 0.5f) {
+        thr_phi = asinc((rL + dsep) * a) - asinc(rL * a) + T(c.n_md) * rt2 * srphi / rL;
+        dlong = dz - dsep * L.z / rL;
+        thr_long = T(c.n_md) * rt2 * sl + dsep * T(c.z_lumi) / rL;
+    } else {
+        T az = m_abs(L.z);
+        // r_U - r_L from the exact coordinate differences (no cancellation)
+        T dr = (dx * (U.x + L.x) + dy * (U.y + L.y)) / (U.r + rL);
+        dlong = dr - dsep * rL / az;
+        thr_long = T(c.n_md) * rt2 * sl;
+        T ds_max = T(1.2) * dsep * (rL + T(c.n_md) * sl) / (az - T(c.z_lumi));
+        thr_phi = a * ds_max + T(c.n_md) * rt2 * srphi / rL;
+    }
+    Cuts<T> cut;
+    cut(m_abs(dphi), thr_phi);
+    if (!cut.fail) cut(m_abs(dlong), thr_long);
+    dphi_o = dphi;
+    dlong_o = dlong;
+    return cut.state();
+}
+
+// ---------------------------------------------------------------------------
+// LS between MD A (anchor PA, stub sA, module mA) and MD B
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ int ls_eval(const DevCfg& c, const Pt<T>& P, T sAx, T sAy, float4 mA, const Pt<T>& Q,
+                                       T sBx, T sBy, float4 mB, T& dphi_o) {
+    const T a = T(c.a);
+    const T n = T(c.n_ls);
+    Cuts<T> cut;
+    T num = P.z * Q.r - Q.z * P.r;
+    T den = Q.r - P.r;
+    T sig_num = m_sqrt(sq(Q.r * P.sz) + sq(P.r * Q.sz) + sq(Q.z * P.sr) + sq(P.z * Q.sr));
+    cut(m_abs(num), T(c.z_lumi) * m_abs(den) + n * sig_num);
+    T dphi = m_atan2(P.x * Q.y - P.y * Q.x, P.x * Q.x + P.y * Q.y);
+    dphi_o = dphi;
+    if (cut.fail) return 0;
+    T lo = asinc(m_max(T(0), P.r - n * P.sr) * a);
+    T thr_phi = asinc((Q.r + n * Q.sr) * a) - lo + n * m_sqrt(sq(P.srphi / P.r) + sq(Q.srphi / Q.r));
+    cut(m_abs(dphi), thr_phi);
+    if (cut.fail) return 0;
+    T ux = Q.x - P.x, uy = Q.y - P.y;
+    T lu = m_hypot(ux, uy);
+    T base = asinc((Q.r + T(mB.x) + n * Q.sr) * a) - lo;
+    T rt2 = T(1.4142135623730951);
+    if (mA.w < 0.5f) {
+        T ls_ = m_hypot(sAx, sAy);
+        T al = m_atan2(sAx * uy - sAy * ux, sAx * ux + sAy * uy);
+        cut(m_abs(al), base + n * (rt2 * P.srphi / ls_ + (P.sr + Q.sr) / lu));
+        if (cut.fail) return 0;
+    }
+    if (mB.w < 0.5f) {
+        T ls_ = m_hypot(sBx, sBy);
+        T al = m_atan2(sBx * uy - sBy * ux, sBx * ux + sBy * uy);
+        cut(m_abs(al), base + n * (rt2 * Q.srphi / ls_ + (P.sr + Q.sr) / lu));
+    }
+    return cut.state();
+}
+
+// ---------------------------------------------------------------------------
+// three-point quantities
+// ---------------------------------------------------------------------------
+template <typename T> struct Tri {
+    T lu, lv, lw, beta, sig_beta, kappa, sigk;
+};
+
+template <typename T> __device__ __forceinline__ Tri<T> tri(const Pt<T>& A, const Pt<T>& B, const Pt<T>& C) {
+    Tri<T> t;
+    T ux = B.x - A.x, uy = B.y - A.y;
+    T vx = C.x - B.x, vy = C.y - B.y;
+    T wx = C.x - A.x, wy = C.y - A.y;
+    t.lu = m_hypot(ux, uy);
+    t.lv = m_hypot(vx, vy);
+    t.lw = m_hypot(wx, wy);
+    t.beta = m_atan2(ux * vy - uy * vx, ux * vx + uy * vy);
+    T iu = T(1) / t.lu, iv = T(1) / t.lv;
+    T sAu = sigma_perp(A, ux * iu, uy * iu);
+    T sBu = sigma_perp(B, ux * iu, uy * iu);
+    T sBv = sigma_perp(B, vx * iv, vy * iv);
+    T sCv = sigma_perp(C, vx * iv, vy * iv);
+    t.sig_beta = m_sqrt(sq(sAu * iu) + sq(sBu * iu + sBv * iv) + sq(sCv * iv));
+    t.kappa = T(2) * (ux * wy - uy * wx) / (t.lu * t.lv * t.lw);
+    t.sigk = T(2) * t.sig_beta / (t.lu + t.lv);
+    return t;
+}
+
+template <typename T>
+__device__ __forceinline__ int t3_eval(const DevCfg& c, const Pt<T>& A, const Pt<T>& B, const Pt<T>& C, T& beta_o,
+                                       T& kappa_o, T& rz_o, T& sigk_o) {
+    const T a = T(c.a);
+    Tri<T> t = tri(A, B, C);
+    Cuts<T> cut;
+    beta_o = t.beta;
+    kappa_o = t.kappa;
+    sigk_o = t.sigk;
+    cut(m_abs(t.beta), asinc(t.lu * a) + asinc(t.lv * a) + T(c.n_t3) * t.sig_beta);
+    T ka = m_abs(t.kappa);
+    T sB = arc(t.lu, ka), sC = arc(t.lw, ka);
+    T d = (B.z - A.z) * sC - (C.z - A.z) * sB;
+    rz_o = d;
+    if (cut.fail) return 0;
+    T sig_d = m_sqrt(sq((sB - sC) * A.sz) + sq(sC * B.sz) + sq(sB * C.sz) + sq((C.z - B.z) * A.sr) +
+                     sq((C.z - A.z) * B.sr) + sq((B.z - A.z) * C.sr));
+    cut(m_abs(d), T(c.n_t3) * sig_d);
+    return cut.state();
+}
+
+// ---------------------------------------------------------------------------
+// circle fit in the chord frame + r-z line fit (double only)
+// ---------------------------------------------------------------------------
+struct Fit {
+    double kappa, chi2_rphi, chi2_rz, tanl;
+};
+
+__device__ inline bool solve3(double M[3][3], double b[3], double x[3]) {
+    double A[3][4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) A[i][j] = M[i][j];
+        A[i][3] = b[i];
+    }
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 3; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (A[piv][col] == 0.0) return false;
+        if (piv != col)
+            for (int j = 0; j < 4; ++j) {
+                double tmp = A[piv][j];
+                A[piv][j] = A[col][j];
+                A[col][j] = tmp;
+            }
+        for (int r = col + 1; r < 3; ++r) {
+            double f = A[r][col] / A[col][col];
+            for (int j = col; j < 4; ++j) A[r][j] -= f * A[col][j];
+        }
+    }
+    for (int i = 2; i >= 0; --i) {
+        double s = A[i][3];
+        for (int j = i + 1; j < 3; ++j) s -= A[i][j] * x[j];
+        x[i] = s / A[i][i];
+    }
+    return true;
+}
+
+template <int N> __device__ inline Fit fit_track(const Pt<double>* P) {
+    Fit f;
+    const Pt<double>& O = P[N / 2];
+    double ex = P[N - 1].x - P[0].x, ey = P[N - 1].y - P[0].y;
+    double le = hypot(ex, ey);
+    double xx = ex / le, xy = ey / le;
+    double yx = -xy, yy = xx;
+    double xi[N], et[N], rho2[N];
+    double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, b[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        double dx = P[i].x - O.x, dy = P[i].y - O.y;
+        xi[i] = dx * xx + dy * xy;
+        et[i] = dx * yx + dy * yy;
+        rho2[i] = xi[i] * xi[i] + et[i] * et[i];
+        double row[3] = {rho2[i], xi[i], 1.0};
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) M[p][q] += row[p] * row[q];
+            b[p] += row[p] * et[i];
+        }
+    }
+    double sol[3] = {0, 0, 0};
+    if (!solve3(M, b, sol)) {
+        f.kappa = 1e30; f.chi2_rphi = 1e30; f.chi2_rz = 1e30; f.tanl = 0;
+        return f;
+    }
+    double gg = sol[0], hh = sol[1], kk = sol[2];
+    double S = sqrt(fmax(0.0, 1.0 + hh * hh - 4.0 * gg * kk));
+    f.kappa = 2.0 * gg / S;
+    double chi2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        double u = gg * rho2[i] + hh * xi[i] + kk - et[i];
+        double e = 2.0 * u / (S + sqrt(fmax(0.0, S * S + 4.0 * gg * u)));
+        double nlx = 2.0 * gg * xi[i] + hh, nly = 2.0 * gg * et[i] - 1.0;
+        double nx = nlx * xx + nly * yx, ny = nlx * xy + nly * yy;
+        double nn = hypot(nx, ny);
+        nx /= nn;
+        ny /= nn;
+        double rx = P[i].x / P[i].r, ry = P[i].y / P[i].r;
+        double n_phi = -nx * ry + ny * rx;
+        double n_r = nx * rx + ny * ry;
+        double s2 = fmax(sq(P[i].srphi * n_phi) + sq(P[i].sr * n_r), sq(0.01 * P[i].srphi));
+        chi2 += e * e / s2;
+    }
+    f.chi2_rphi = chi2;
+    double ka = fabs(f.kappa);
+    double s[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) s[i] = arc(hypot(P[i].x - P[0].x, P[i].y - P[0].y), ka);
+    double t_hat = (P[N - 1].z - P[0].z) / s[N - 1];
+    double w[N], W = 0, Ws = 0, Wz = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        w[i] = 1.0 / fmax(1e-12, sq(P[i].sz) + sq(t_hat * P[i].sr));
+        W += w[i];
+        Ws += w[i] * s[i];
+        Wz += w[i] * P[i].z;
+    }
+    double sbar = Ws / W, zbar = Wz / W, Sss = 0, Ssz = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        Sss += w[i] * sq(s[i] - sbar);
+        Ssz += w[i] * (s[i] - sbar) * (P[i].z - zbar);
+    }
+    double t = Ssz / Sss, c0 = zbar - t * sbar, chi2z = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) chi2z += w[i] * sq(P[i].z - c0 - t * s[i]);
+    f.chi2_rz = chi2z;
+    f.tanl = t;
+    return f;
+}
+
+__device__ __forceinline__ double phi0_of(const Pt<double>& P, double kappa) {
+    double s = kappa < 0 ? -1.0 : 1.0;
+    return wrap_pi(atan2(P.y, P.x) - s * asinc(P.r * fabs(kappa) / 2.0));
+}
+
+__device__ __forceinline__ double pt_of(const DevCfg& c, double kappa) {
+    double ka = fabs(kappa);
+    return ka > 0 ? c.k_field * c.b_field / (100.0 * ka) : 1e30;
+}
+
+// T5 on anchors P[0..4]; outputs in double
+struct T5Out {
+    double kappa, chi2_rphi, chi2_rz, eta, phi0, pt, score, sigk;
+};
+
+__device__ inline bool t5_eval(const DevCfg& c, const Pt<double>* P, T5Out& o) {
+    Tri<double> ti = tri(P[0], P[1], P[2]);
+    Tri<double> to = tri(P[2], P[3], P[4]);
+    o.sigk = 0.5 * sqrt(sq(ti.sigk) + sq(to.sigk));
+    if (!(fabs(ti.kappa - to.kappa) <= c.n_t5 * sqrt(sq(ti.sigk) + sq(to.sigk)))) return false;
+    Fit f = fit_track<5>(P);
+    o.kappa = f.kappa;
+    o.chi2_rphi = f.chi2_rphi;
+    o.chi2_rz = f.chi2_rz;
+    o.eta = asinh(f.tanl);
+    o.phi0 = phi0_of(P[0], f.kappa);
+    o.pt = pt_of(c, f.kappa);
+    o.score = f.chi2_rphi + f.chi2_rz;
+    if (!(fabs(f.kappa) <= (1.0 + c.tol_r) * 2.0 * c.a)) return false;
+    if (!(f.chi2_rphi <= c.chi2_rphi_t5)) return false;
+    if (!(f.chi2_rz <= c.chi2_rz_t5)) return false;
+    return true;
+}
+
+struct PTOut {
+    double kappa, chi2_rphi, chi2_rz, score, pt;
+};
+
+template <int N>
+__device__ inline bool pt_eval(const DevCfg& c, const Pt<double>* P, double kp, double sp, double kt, double st,
+                               double chi2_rphi_max, double chi2_rz_max, PTOut& o) {
+    if (!(fabs(kp - kt) <= c.n_pt * sqrt(sq(sp) + sq(st)))) return false;
+    Fit f = fit_track<N>(P);
+    o.kappa = f.kappa;
+    o.chi2_rphi = f.chi2_rphi;
+    o.chi2_rz = f.chi2_rz;
+    o.score = f.chi2_rphi + f.chi2_rz;
+    o.pt = pt_of(c, f.kappa);
+    if (!(fabs(f.kappa) <= (1.0 + c.tol_r) * 2.0 * c.a)) return false;
+    if (!(f.chi2_rphi <= chi2_rphi_max)) return false;
+    if (!(f.chi2_rz <= chi2_rz_max)) return false;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// small device utilities
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int event_of(const int* off, int n_ev, int i) {
+    int lo = 0, hi = n_ev;            // off[lo] <= i < off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// exclusive prefix of `flag` across the warp, and the warp total
+__device__ __forceinline__ int warp_rank(bool flag, int& total) {
+    unsigned m = __ballot_sync(0xffffffffu, flag);
+    total = __popc(m);
+    return __popc(m & ((1u << lane_id()) - 1u));
+}
+
+}  // namespace lst

@@ -1,0 +1,44 @@
+// Kernel declarations and per-unit occupancy bounds of the device chain.
+#pragma once
+
+#include "lst_device.cuh"
+
+namespace lst {
+
+// Per-unit stage sizes: the most objects one unit may produce (occupancy
+// truncation); excess objects are counted as dropped.
+constexpr int kMaxHits = 256;     // hits per sensor of one module
+constexpr int kMdStage = 1024;    // MDs per module
+constexpr int kLsStage = 256;     // LS per inner MD
+constexpr int kT3Stage = 512;     // T3 per inner MD
+constexpr int kT5Pre = 256;       // FP32-prefiltered T5 candidates held before an FP64 pass
+constexpr int kT5Stage = 1024;    // T5 per inner MD
+constexpr int kPtPre = 128;       // prefiltered pT3/pT5 candidates held before an FP64 pass
+constexpr int kPtStage = 96;      // pT3/pT5 per pixel seed
+
+constexpr int kMdWarps = 4;
+constexpr int kLsWarps = 8;
+constexpr int kT3Warps = 8;
+constexpr int kT5Warps = 4;
+constexpr int kPtWarps = 4;
+
+__global__ void k_bin_count(Arena A);
+__global__ void k_bin_scan(Arena A);
+__global__ void k_bin_scatter(Arena A);
+__global__ void k_md(Arena A, DevCfg c);
+__global__ void k_ls(Arena A, DevCfg c);
+__global__ void k_t3(Arena A, DevCfg c);
+__global__ void k_t5(Arena A, DevCfg c);
+__global__ void k_pls(Arena A, DevCfg c);
+__global__ void k_pt5(Arena A, DevCfg c);
+__global__ void k_pt3(Arena A, DevCfg c);
+__global__ void k_clean_keys(Arena A, int pass);
+__global__ void k_clean_pt5(Arena A);
+__global__ void k_clean_pt3_cross(Arena A, DevCfg c);
+__global__ void k_clean_pt3_mark(Arena A);
+__global__ void k_clean_t5(Arena A, DevCfg c);
+__global__ void k_clean_pls(Arena A, DevCfg c);
+
+size_t md_smem_bytes();
+
+}  // namespace lst

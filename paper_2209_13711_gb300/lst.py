@@ -1,0 +1,251 @@
+"""Python binding of the C ABI in include/lst.h (argument marshalling only).
+
+Every step of the chain runs in the CUDA kernels of liblst.so; this module
+packs arrays, passes pointers and unpacks results. Inputs are numpy arrays
+(host memory: the library copies them) or CUDA torch tensors (device memory:
+read in place). Importing this module without a built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblst.so")
+
+KIND_NAMES = ("md", "ls", "t3", "t5", "pls", "pt5", "pt3")
+COLUMNS = {
+    "md": (["lo", "up", "mod"], ["dphi", "dlong"]),
+    "ls": (["md_in", "md_out"], ["dphi"]),
+    "t3": (["ls_in", "ls_out"], ["beta", "kappa", "sigk"]),
+    "t5": (["t3_in", "t3_out"], ["kappa", "chi2_rphi", "chi2_rz", "eta", "phi0", "pt", "score"]),
+    "pls": (["seed", "pass", "sb"], ["kappa", "sigk", "eta", "phi0", "z0", "pt"]),
+    "pt5": (["seed", "t5"], ["kappa", "chi2_rphi", "chi2_rz", "score", "pt"]),
+    "pt3": (["seed", "t3"], ["kappa", "chi2_rphi", "chi2_rz", "score", "pt"]),
+}
+STAT_NAMES = ("md", "ls", "t3", "t5", "pls", "pt5", "pt3", "tc")
+
+
+class LstConfig(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "pt_min", "k_field", "b_field", "z_lumi", "n_md", "n_ls", "n_t3", "n_t5", "n_pt", "tol_r",
+        "chi2_rphi_t5", "chi2_rz_t5", "chi2_rphi_pt3", "chi2_rz_pt3", "chi2_rphi_pt5", "chi2_rz_pt5",
+        "pls_pt_tol", "sig_pix", "sb_eta_max")] + \
+        [("sb_n_eta", C.c_int32), ("sb_n_phi", C.c_int32), ("dr_clean", C.c_double)]
+
+
+class LstCapacity(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in (
+        "max_events", "max_hits", "max_seeds", "md_per_event", "ls_per_event", "t3_per_event", "t5_per_event",
+        "pt3_per_event", "pt5_per_event", "tc_per_event")]
+
+
+class LstModule(C.Structure):
+    _fields_ = [("subdet", C.c_int32), ("layer", C.c_int32), ("dsep", C.c_float), ("sig_rphi", C.c_float),
+                ("sig_long", C.c_float)]
+
+
+class LstHits(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("module", C.c_void_p),
+                ("side", C.c_void_p), ("n", C.c_int32)]
+
+
+class LstSeeds(C.Structure):
+    _fields_ = [("xyz", C.c_void_p), ("n", C.c_int32)]
+
+
+class LstStats(C.Structure):
+    _fields_ = [("counts", C.c_int32 * 8), ("dropped", C.c_int32 * 8)]
+
+
+class LstError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def library():
+    """Load liblst.so (built in-tree by build.py); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LstError(f"liblst.so is not built ({LIB_PATH}); run paper_2209_13711_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, p = C.c_void_p, C.c_int32, C.POINTER
+        L.lst_status_str.restype = C.c_char_p
+        L.lst_status_str.argtypes = [i32]
+        L.lst_config_default.argtypes = [vp]
+        L.lst_capacity_default.argtypes = [vp, i32]
+        L.lst_create.argtypes = [p(vp), vp, vp, i32]
+        L.lst_destroy.argtypes = [vp]
+        L.lst_destroy.restype = None
+        L.lst_load_geometry.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32]
+        L.lst_run_batch.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp]
+        L.lst_run_event.argtypes = [vp, vp, vp, i32, vp]
+        L.lst_get_track_candidates.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
+        L.lst_object_columns.argtypes = [i32, vp, vp]
+        L.lst_get_objects.argtypes = [vp, i32, i32, i32, vp, vp, vp]
+        L.lst_get_stats.argtypes = [vp, i32, vp]
+        L.lst_last_launch_count.argtypes = [vp]
+        L.lst_set_profiling.argtypes = [vp, i32]
+        L.lst_get_kernel_times.argtypes = [vp, i32, vp, vp, vp]
+        for f in ("lst_config_default", "lst_capacity_default", "lst_create", "lst_load_geometry", "lst_run_batch",
+                  "lst_run_event", "lst_get_track_candidates", "lst_object_columns", "lst_get_objects",
+                  "lst_get_stats", "lst_last_launch_count", "lst_set_profiling", "lst_get_kernel_times"):
+            getattr(L, f).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status < 0:
+        raise LstError(f"lst error {status}: {library().lst_status_str(status).decode()}")
+    return status
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def default_config(overrides=None):
+    c = LstConfig()
+    _check(library().lst_config_default(C.byref(c)))
+    for k, v in (overrides or {}).items():
+        if any(k == f for f, _ in LstConfig._fields_):
+            setattr(c, k, v)
+    return c
+
+
+def default_capacity(max_events=1, **overrides):
+    k = LstCapacity()
+    _check(library().lst_capacity_default(C.byref(k), int(max_events)))
+    for n, v in overrides.items():
+        setattr(k, n, int(v))
+    return k
+
+
+def pack_events(events):
+    """Concatenate per-event arrays (numpy) into one batch."""
+    hit_off = np.zeros(len(events) + 1, np.int32)
+    seed_off = np.zeros(len(events) + 1, np.int32)
+    for i, ev in enumerate(events):
+        hit_off[i + 1] = hit_off[i] + len(ev.x)
+        seed_off[i + 1] = seed_off[i] + len(ev.seeds)
+    cat = lambda name, dt: np.ascontiguousarray(np.concatenate([np.asarray(getattr(e, name), dt).ravel()
+                                                                 for e in events]) if events else np.zeros(0, dt))
+    return dict(x=cat("x", np.float32), y=cat("y", np.float32), z=cat("z", np.float32),
+                module=cat("module", np.int32), side=cat("side", np.uint8), seeds=cat("seeds", np.float32),
+                hit_off=hit_off, seed_off=seed_off)
+
+
+class Context:
+    """One library context: geometry resident on the device, one batch at a time."""
+
+    def __init__(self, module_table, maps, cfg=None, capacity=None, device=0):
+        L = library()
+        self._cfg = cfg if isinstance(cfg, LstConfig) else default_config(cfg)
+        self._cap = capacity if capacity is not None else default_capacity(1)
+        h = C.c_void_p()
+        _check(L.lst_create(C.byref(h), C.byref(self._cfg), C.byref(self._cap), int(device)))
+        self._h = h
+        n_mod = len(module_table["subdet"])
+        mods = (LstModule * n_mod)()
+        for i in range(n_mod):
+            mods[i] = LstModule(int(module_table["subdet"][i]), int(module_table["layer"][i]),
+                                float(module_table["dsep"][i]), float(module_table["sig_rphi"][i]),
+                                float(module_table["sig_long"][i]))
+        co, ct, so, st = [np.ascontiguousarray(a, np.int32) for a in maps]
+        _check(L.lst_load_geometry(self._h, mods, n_mod, _ptr(co), _ptr(ct), _ptr(so), _ptr(st), len(so) - 1))
+        self.n_events = 0
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            library().lst_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def capacity(self):
+        return self._cap
+
+    # -- running ----------------------------------------------------------
+    def run_packed(self, b, stream=None):
+        """b: dict from pack_events (numpy) or the same keys as CUDA torch tensors
+        (hit_off / seed_off stay numpy: they are host arrays)."""
+        dev = hasattr(b["x"], "is_cuda") and b["x"].is_cuda
+        hits = LstHits(_ptr(b["x"]), _ptr(b["y"]), _ptr(b["z"]), _ptr(b["module"]), _ptr(b["side"]),
+                       int(b["hit_off"][-1]))
+        seeds = LstSeeds(_ptr(b["seeds"]), int(b["seed_off"][-1]))
+        ho = np.ascontiguousarray(b["hit_off"], np.int32)
+        so = np.ascontiguousarray(b["seed_off"], np.int32)
+        self._keep = (b, ho, so)          # the library may read host inputs until the call returns
+        s = C.c_void_p(stream) if stream is not None else None
+        _check(library().lst_run_batch(self._h, C.byref(hits), _ptr(ho), C.byref(seeds), _ptr(so), len(ho) - 1,
+                                       1 if dev else 0, s))
+        self.n_events = len(ho) - 1
+
+    def run(self, events, stream=None):
+        self.run_packed(pack_events(list(events)), stream)
+
+    @property
+    def launch_count(self):
+        return library().lst_last_launch_count(self._h)
+
+    def set_profiling(self, on=True):
+        _check(library().lst_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_times(self):
+        """[(name, ms)] of every launch of the last batch (profiling must be on)."""
+        L = library()
+        n = C.c_int32(0)
+        names = (C.c_char_p * 64)()
+        ms = np.zeros(64, np.float32)
+        _check(L.lst_get_kernel_times(self._h, 64, C.byref(n), names, _ptr(ms)))
+        return [(names[i].decode(), float(ms[i])) for i in range(n.value)]
+
+    # -- results ----------------------------------------------------------
+    def stats(self, event=0):
+        s = LstStats()
+        _check(library().lst_get_stats(self._h, int(event), C.byref(s)))
+        return dict(counts=dict(zip(STAT_NAMES, list(s.counts))), dropped=dict(zip(STAT_NAMES, list(s.dropped))))
+
+    def track_candidates(self, event=0):
+        L = library()
+        n = C.c_int32(0)
+        _check(L.lst_get_track_candidates(self._h, int(event), 0, C.byref(n), None, None, None, None))
+        k = n.value
+        t = np.zeros(k, np.int32)
+        sd = np.zeros(k, np.int32)
+        h = np.zeros((k, 10), np.int32)
+        f = np.zeros((k, 3), np.float32)
+        _check(L.lst_get_track_candidates(self._h, int(event), k, C.byref(n), _ptr(t), _ptr(sd), _ptr(h), _ptr(f)))
+        return dict(n=k, type=t, seed=sd, hits=h, pt=f[:, 0], eta=f[:, 1], phi0=f[:, 2])
+
+    def objects(self, kind, event=0):
+        L = library()
+        code = KIND_NAMES.index(kind)
+        ni, nf = C.c_int32(), C.c_int32()
+        _check(L.lst_object_columns(code, C.byref(ni), C.byref(nf)))
+        n = C.c_int32(0)
+        _check(L.lst_get_objects(self._h, int(event), code, 0, C.byref(n), None, None))
+        I = np.zeros((n.value, ni.value), np.int32)
+        F = np.zeros((n.value, nf.value), np.float32)
+        _check(L.lst_get_objects(self._h, int(event), code, n.value, C.byref(n), _ptr(I), _ptr(F)))
+        icol, fcol = COLUMNS[kind]
+        rec = {c: I[:, j] for j, c in enumerate(icol)}
+        rec.update({c: F[:, j] for j, c in enumerate(fcol)})
+        rec["n"] = n.value
+        return rec

@@ -1,0 +1,26 @@
+"""Shared set-up of the GPU tests: contexts, oracle runs, result dicts."""
+import numpy as np
+
+from oracle import oracle as O
+from synth import geometry as G
+from synth import maps as M
+from synth.config import DEFAULT_CUTS
+
+A_HALF = DEFAULT_CUTS["k_field"] * DEFAULT_CUTS["b_field"] / (200.0 * DEFAULT_CUTS["pt_min"])
+
+
+def make_context(geom, maps, max_events=1, **cap):
+    import paper_2209_13711_gb300 as P
+    cap_ = P.default_capacity(max_events, **cap)
+    return P.Context(geom.module_table(), maps, cfg=DEFAULT_CUTS, capacity=cap_)
+
+
+def gpu_result(ctx, event=0):
+    out = {k: ctx.objects(k, event) for k in ("md", "ls", "t3", "t5", "pls", "pt5", "pt3")}
+    out["tc"] = ctx.track_candidates(event)
+    out["stats"] = ctx.stats(event)
+    return out
+
+
+def oracle_result(geom, maps, ev):
+    return O.Setup(geom.module_table(), maps, DEFAULT_CUTS, ev).run()

@@ -1,0 +1,48 @@
+"""CPU checks of the C ABI: the library loads and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lst.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lst_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("lst_load_geometry", "lst_run_event", "lst_run_batch", "lst_get_track_candidates", "lst_create",
+              "lst_destroy", "lst_get_objects", "lst_get_stats"):
+        assert n in names
+
+
+def test_library_exports_every_symbol():
+    from paper_2209_13711_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
+def test_config_defaults_match_input_constants():
+    from paper_2209_13711_gb300 import lst
+    from synth.config import DEFAULT_CUTS
+    c = lst.default_config()
+    for f, _ in lst.LstConfig._fields_:
+        assert getattr(c, f) == pytest.approx(DEFAULT_CUTS[f]), f
+
+
+def test_argument_errors_without_device():
+    from paper_2209_13711_gb300 import lst
+    L = lst.library()
+    assert L.lst_create(None, None, None, 0) == -1
+    assert L.lst_config_default(None) == -1
+    assert L.lst_capacity_default(None, 1) == -1
+    ni, nf = ctypes.c_int32(), ctypes.c_int32()
+    assert L.lst_object_columns(7, ctypes.byref(ni), ctypes.byref(nf)) == -1
+    assert L.lst_object_columns(3, ctypes.byref(ni), ctypes.byref(nf)) == 0 and (ni.value, nf.value) == (2, 7)
+    assert L.lst_status_str(-6) == b"batch exceeds the context capacity"

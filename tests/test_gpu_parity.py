@@ -1,0 +1,147 @@
+"""Device chain vs FP64 oracle, element by element, through the C ABI (GPU)."""
+import numpy as np
+import pytest
+
+from synth import events as E
+from synth.config import DEFAULT_CUTS
+from tests.gpu_common import A_HALF, gpu_result, make_context, oracle_result
+from tests.parity import chain_tuples, compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx_barrel(geom_barrel, maps_barrel):
+    return make_context(geom_barrel, maps_barrel, max_events=8)
+
+
+@pytest.fixture(scope="module")
+def ctx_full(geom_full, maps_full):
+    return make_context(geom_full, maps_full, max_events=4)
+
+
+def _no_drops(res):
+    assert all(v == 0 for v in res["stats"]["dropped"].values()), res["stats"]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_tiny_event_parity(ctx_barrel, geom_barrel, maps_barrel, seed):
+    ev = E.tiny_event(seed, geom_barrel)
+    ctx_barrel.run([ev])
+    g = gpu_result(ctx_barrel)
+    _no_drops(g)
+    o = oracle_result(geom_barrel, maps_barrel, ev)
+    s = compare(g, o, A_HALF, DEFAULT_CUTS)
+    assert s["tc"][0] >= 8
+
+
+@pytest.mark.parametrize("pu,seed", [(25, 1), (60, 2)])
+def test_pileup_event_parity(ctx_full, geom_full, maps_full, pu, seed):
+    ev = E.pileup_event(pu, seed, geom_full)
+    ctx_full.run([ev])
+    g = gpu_result(ctx_full)
+    _no_drops(g)
+    o = oracle_result(geom_full, maps_full, ev)
+    compare(g, o, A_HALF, DEFAULT_CUTS)
+
+
+def test_pu200_event_parity(ctx_full, geom_full, maps_full):
+    """Full-size PU200 event (the benchmark's workload), every object level."""
+    ev = E.pu200_event(0, geom_full)
+    ctx_full.run([ev])
+    g = gpu_result(ctx_full)
+    _no_drops(g)
+    o = oracle_result(geom_full, maps_full, ev)
+    s = compare(g, o, A_HALF, DEFAULT_CUTS)
+    assert s["t5"][0] > 10000 and s["tc"][0] > 2000
+
+
+def _all_tuples(ctx, event):
+    g = gpu_result(ctx, event)
+    T = chain_tuples(g)
+    tc = {(int(t), int(s), tuple(sorted(h[h >= 0].tolist())))
+          for t, s, h in zip(g["tc"]["type"], g["tc"]["seed"], g["tc"]["hits"])}
+    return {k: set(v) for k, v in T.items()}, tc
+
+
+def test_batch_equals_single_events(ctx_full, geom_full):
+    evs = [E.pileup_event(pu, 40 + i, geom_full) for i, pu in enumerate((10, 50, 3, 80))]
+    ctx_full.run(evs)
+    batched = [_all_tuples(ctx_full, i) for i in range(len(evs))]
+    for i, ev in enumerate(evs):
+        ctx_full.run([ev])
+        assert _all_tuples(ctx_full, 0) == batched[i]
+
+
+def test_empty_and_seedless_events(ctx_barrel, geom_barrel, maps_barrel):
+    empty = E.Event(x=np.zeros(0, np.float32), y=np.zeros(0, np.float32), z=np.zeros(0, np.float32),
+                    module=np.zeros(0, np.int32), side=np.zeros(0, np.uint8), pid=np.zeros(0, np.int32),
+                    seeds=np.zeros((0, 3, 3), np.float32), seed_pid=np.zeros(0, np.int32), tracks=None)
+    ev = E.tiny_event(3, geom_barrel)
+    seedless = E.Event(x=ev.x, y=ev.y, z=ev.z, module=ev.module, side=ev.side, pid=ev.pid,
+                       seeds=np.zeros((0, 3, 3), np.float32), seed_pid=np.zeros(0, np.int32), tracks=ev.tracks)
+    ctx_barrel.run([empty, seedless, empty])
+    for i in (0, 2):
+        g = gpu_result(ctx_barrel, i)
+        assert g["tc"]["n"] == 0 and g["md"]["n"] == 0 and g["pls"]["n"] == 0
+    g = gpu_result(ctx_barrel, 1)
+    o = oracle_result(geom_barrel, maps_barrel, seedless)
+    compare(g, o, A_HALF, DEFAULT_CUTS)
+    assert set(g["tc"]["type"].tolist()) <= {2}
+
+
+def test_device_resident_input(ctx_barrel, geom_barrel):
+    torch = pytest.importorskip("torch")
+    import paper_2209_13711_gb300 as P
+    evs = [E.tiny_event(s, geom_barrel) for s in (5, 6)]
+    b = P.pack_events(evs)
+    ctx_barrel.run_packed(b)
+    host = [_all_tuples(ctx_barrel, i) for i in range(2)]
+    bd = {k: (torch.from_numpy(v).cuda() if k not in ("hit_off", "seed_off") else v) for k, v in b.items()}
+    ctx_barrel.run_packed(bd, stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert [_all_tuples(ctx_barrel, i) for i in range(2)] == host
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_noiseless_tracks_one_pt5_each(ctx_barrel, geom_barrel, seed):
+    """Noiseless prompt tracks: one candidate per track, a pT5 for every fully contained one."""
+    ev = E.tiny_event(seed, geom_barrel, smear=False)
+    ctx_barrel.run([ev])
+    tc = ctx_barrel.track_candidates(0)
+    contained = {t for t in range(ev.tracks.n)
+                 if len(ev.module[(ev.pid == t) & (ev.side == 0)]) == 6 and
+                 sorted(ev.module[(ev.pid == t) & (ev.side == 0)]) == sorted(ev.module[(ev.pid == t) & (ev.side == 1)])}
+    pids = []
+    for i in range(tc["n"]):
+        h = tc["hits"][i]
+        p = set(ev.pid[h[h >= 0]].tolist())
+        assert len(p) == 1
+        pid = p.pop()
+        if pid in contained:
+            assert tc["type"][i] == 0
+        pids.append(pid)
+    assert len(pids) == len(set(pids)) and contained <= set(pids)
+
+
+def test_capacity_errors(ctx_barrel, geom_barrel):
+    import paper_2209_13711_gb300 as P
+    evs = [E.tiny_event(0, geom_barrel)] * 9            # context holds 8 events
+    with pytest.raises(P.LstError):
+        ctx_barrel.run(evs)
+    bad = E.tiny_event(1, geom_barrel)
+    b = P.pack_events([bad])
+    b["seed_off"] = np.array([0, -1], np.int32)          # negative seed count
+    with pytest.raises(P.LstError):
+        ctx_barrel.run_packed(b)
+
+
+def test_truncation_is_counted(geom_full, maps_full):
+    ctx = make_context(geom_full, maps_full, max_events=1, ls_per_event=2000)
+    ev = E.pileup_event(40, 7, geom_full)
+    ctx.run([ev])
+    st = ctx.stats(0)
+    assert st["dropped"]["ls"] > 0 and st["counts"]["ls"] <= 2000
+    tc = ctx.track_candidates(0)
+    assert tc["n"] >= 0
+    ctx.close()
