@@ -158,75 +158,102 @@ def _obj_info(r, T, cat, i):
 
 
 def compare_tc(gpu, orc, G, O, M, cuts):
-    def tc_set(tc):
+    """Track candidates, minus those whose cleaning decision may depend on arithmetic inside a margin.
+
+    Cleaning order: duplicates inside a category (pT5, pT3, T5), then pT3 vs
+    kept pT5, T5 vs kept pT5/pT3, unlinked pLS vs all kept. An object whose
+    existence is uncertain (margin at object level, on either side) may change
+    the dedup decision of same-category objects sharing a hit with it; an
+    object whose keep decision is uncertain may change the decisions of
+    later-category objects that share a hit, sit within dr_clean (1e-4
+    widened) or use its seed.
+    """
+    thr2 = (cuts["dr_clean"] * (1 + 1e-4)) ** 2
+    cats = ("pt5", "pt3", "t5", "pls")
+    # universe: (cat, key) -> (hits, eta, phi, seed)
+    U = {}
+    for r, T in ((gpu, G), (orc, O)):
+        for c, key in enumerate(cats):
+            n = r["pls"]["n"] if key == "pls" else len(T[key])
+            for i in range(n):
+                h, e, p = _obj_info(r, T, c, i)
+                k = i if key == "pls" else T[key][i]
+                seed = i if key == "pls" else (T[key][i][0] if c < 2 else -1)
+                U.setdefault((c, k), (h, e, p, seed))
+    keys = list(U)
+    kidx = {k: j for j, k in enumerate(keys)}
+    cat = np.array([k[0] for k in keys])
+    eta = np.array([U[k][1] for k in keys])
+    phi = np.array([U[k][2] for k in keys])
+    seed = np.array([U[k][3] for k in keys])
+    hit_of = {}
+    for j, k in enumerate(keys):
+        for h in U[k][0]:
+            hit_of.setdefault(h, []).append(j)
+    exist_unc = set()
+    for c, key in enumerate(cats[:3]):
+        ex = getattr(M, "ex_" + key)
+        for T in (G, O):
+            for t in T[key]:
+                if ex(t):
+                    exist_unc.add(kidx[(c, t)])
+    for s_ in M.pls:
+        exist_unc.add(kidx[(3, s_)])
+    dec = np.zeros(len(keys), bool)
+    for j in exist_unc:
+        dec[j] = True
+        for h in U[keys[j]][0]:                       # same-category dedup partners
+            for j2 in hit_of[h]:
+                if cat[j2] == cat[j]:
+                    dec[j2] = True
+    for c1, i1, c2, i2 in orc["m_clean"]:
+        k1 = (int(c1), int(i1) if c1 == 3 else O[cats[c1]][i1])
+        dec[kidx[k1]] = True
+        if c1 == c2:
+            dec[kidx[(int(c2), O[cats[c2]][i2])]] = True
+    # decisions flow downward in category order
+    for c in (0, 1, 2):
+        src = np.nonzero(dec & (cat == c))[0]
+        if len(src) == 0:
+            continue
+        lower = cat > c
+        for j in src:
+            h, e, p, sd = U[keys[j]]
+            for hh in h:
+                for j2 in hit_of[hh]:
+                    if cat[j2] > c:
+                        dec[j2] = True
+            de = eta - e
+            dp = np.remainder(phi - p + np.pi, 2 * np.pi) - np.pi
+            dec |= lower & ((de * de + dp * dp) < thr2)
+            if sd >= 0:
+                dec |= lower & (cat == 3) & (seed == sd)
+
+    def tc_items(r):
+        tc = r["tc"]
         out = {}
         for i in range(tc["n"]):
-            hs = tuple(sorted(int(h) for h in (tc["hits"][i] if "hits" in tc else
-                                               [tc[f"h{j}"][i] for j in range(10)]) if h >= 0))
-            out[(int(tc["type"][i]), int(tc["seed"][i]), hs)] = i
+            hs = [int(h) for h in (tc["hits"][i] if "hits" in tc else [tc[f"h{j}"][i] for j in range(10)]) if h >= 0]
+            out[(int(tc["type"][i]), int(tc["seed"][i]), tuple(sorted(hs)))] = i
         return out
 
-    g_tc, o_tc = tc_set(gpu["tc"]), tc_set(orc["tc"])
-    # tainted seeds: margin objects on either side and near-threshold cleaning comparisons
-    tainted = []
-    for side, r, T in (("g", gpu, G), ("o", orc, O)):
-        for i, t in enumerate(T["pt5"]):
-            if M.ex_pt5(t):
-                tainted.append(_obj_info(r, T, 0, i))
-        for i, t in enumerate(T["pt3"]):
-            if M.ex_pt3(t):
-                tainted.append(_obj_info(r, T, 1, i))
-        for i, t in enumerate(T["t5"]):
-            if M.ex_t5(t):
-                tainted.append(_obj_info(r, T, 2, i))
-        for s in M.pls:
-            tainted.append(_obj_info(r, T, 3, s))
-    for c1, i1, c2, i2 in orc["m_clean"]:
-        tainted.append(_obj_info(orc, O, int(c1), int(i1)))
-        tainted.append(_obj_info(orc, O, int(c2), int(i2)))
-    if tainted:
-        # candidate universe: every cleaning candidate on both sides
-        cands = []
-        for r, T in ((gpu, G), (orc, O)):
-            for cat, key in ((0, "pt5"), (1, "pt3"), (2, "t5")):
-                for i in range(len(T[key])):
-                    cands.append(_obj_info(r, T, cat, i))
-            for s in range(r["pls"]["n"]):
-                cands.append(_obj_info(r, T, 3, s))
-        thr = cuts["dr_clean"] * (1 + 1e-4)
-        taint_hits = set()
-        taint_dirs = []
-        for h, e, p in tainted:
-            taint_hits |= h
-            taint_dirs.append((e, p))
-        for _ in range(5):                # depth of the cleaning's dependency chain
-            new_hits, new_dirs = set(), []
-            for h, e, p in cands:
-                if h <= taint_hits:
-                    continue
-                near = bool(h & taint_hits) or any(
-                    (e - e2) ** 2 + math.remainder(p - p2, 2 * math.pi) ** 2 < thr * thr for e2, p2 in taint_dirs)
-                if near:
-                    new_hits |= h
-                    new_dirs.append((e, p))
-            if not (new_hits - taint_hits):
-                break
-            taint_hits |= new_hits
-            taint_dirs += new_dirs
-    else:
-        taint_hits = set()
+    # map each candidate to its object through the hit set + seed
+    by_sig = {}
+    for j, k in enumerate(keys):
+        h, e, p, sd = U[k]
+        ot = tuple(sorted(x for x in h if not isinstance(x, tuple)))
+        by_sig[(int(cat[j]), int(sd) if cat[j] != 2 else -1, ot)] = j
+    g_tc, o_tc = tc_items(gpu), tc_items(orc)
 
-    def ok(key):
-        typ, seed, hs = key
-        hits = set(hs) | ({("p", seed)} if seed >= 0 and typ != 2 else set())
-        return not (hits & taint_hits)
+    def ok(t):
+        j = by_sig.get(t)
+        return j is not None and not dec[j]
 
-    g = {k for k in g_tc if ok(k)}
-    o = {k for k in o_tc if ok(k)}
+    g = {t for t in g_tc if ok(t)}
+    o = {t for t in o_tc if ok(t)}
     assert g == o, f"tc: {len(g - o)} GPU-only {sorted(g - o)[:2]}, {len(o - g)} oracle-only {sorted(o - g)[:2]}"
-    # kinematics of matched candidates
-    for k in g:
-        i, j = g_tc[k], o_tc[k]
+    for t in g:
+        i, j = g_tc[t], o_tc[t]
         assert close(gpu["tc"]["eta"][i], orc["tc"]["eta"][j], 1.0)
         assert close(gpu["tc"]["phi0"][i], orc["tc"]["phi0"][j], math.pi)
         assert close(gpu["tc"]["pt"][i], orc["tc"]["pt"][j], 0.0)
