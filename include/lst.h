@@ -179,6 +179,36 @@ int32_t lst_last_launch_count(lst_ctx* ctx);
 lst_status lst_set_profiling(lst_ctx* ctx, int32_t enable);
 lst_status lst_get_kernel_times(lst_ctx* ctx, int32_t capacity, int32_t* n_out, const char** names, float* ms);
 
+/* Allocation-free mini-doublet builder (the paper has no counterpart; this
+ * is a library service). For callers that cannot allocate device memory: a
+ * host framework that owns the device budget through its own pool and forbids
+ * its plugins from calling cudaMalloc, or a latency-critical loop that must
+ * not pay for an allocation. It runs the hit binning and mini-doublet kernels
+ * of lst_run_batch on one event and allocates nothing: its scratch (bucket
+ * counters, sorted hits, module table in device layout, MD anchors) lives in
+ * one file-scope device array of about 7.3 MB that every device loading the
+ * library keeps until the process exits.
+ *   All pointers except cfg are DEVICE memory owned by the caller: modules
+ *   (n_mod rows), the event's hits (x, y, z, module, side; n_hits), and the
+ *   outputs md_lower / md_upper (hit indices), md_module, md_dphi, md_dlong
+ *   with room for md_capacity rows, md_count (one int: rows written) and
+ *   md_dropped (one int, may be NULL: MDs lost to the per-module bounds or to
+ *   md_capacity). Rows match lst_get_objects(kind = 0) of the same event as a
+ *   set (their order may differ).
+ *   Limits: n_hits <= 262144, n_mod <= 16384, md_capacity <= 131072; larger
+ *   sizes return LST_ERR_CAPACITY before any work is enqueued.
+ *   The first call on a device looks up the array's device address (on the
+ *   current device); make that first call before any stream capture. Every
+ *   call reuses the same array and clears what must start at zero; calls that
+ *   overlap on the GPU race on it and must be serialized by the caller.
+ *   Asynchronous on cuda_stream (NULL: legacy default stream). */
+lst_status lst_build_mini_doublets_static(const lst_config* cfg, const lst_module* modules, int32_t n_mod,
+                                          const float* x, const float* y, const float* z, const int32_t* module,
+                                          const uint8_t* side, int32_t n_hits, int32_t md_capacity,
+                                          int32_t* md_lower, int32_t* md_upper, int32_t* md_module, float* md_dphi,
+                                          float* md_dlong, int32_t* md_count, int32_t* md_dropped,
+                                          void* cuda_stream);
+
 /* Message of a status code (static storage). */
 const char* lst_status_str(lst_status s);
 
