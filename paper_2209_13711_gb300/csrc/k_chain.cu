@@ -420,14 +420,39 @@ __device__ __forceinline__ bool t5_eval_pair(const Arena& A, const DevCfg& c, in
     return t5_eval(c, P, o);
 }
 
-// FP64 evaluation of the collected candidates; appends passing ones to the stage
+__device__ __forceinline__ bool t5_prefit_f32(const Arena& A, const DevCfg& c, int2 pr) {
+    int m[5];
+    t3_anchor_mds(A, pr.x, m[0], m[1], m[2]);
+    t3_anchor_mds(A, pr.y, m[2], m[3], m[4]);
+    Pt<float> P[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) P[j] = md_pt_f(A, m[j], md_mod(A, m[j]));
+    float k, c2, cz;
+    fit_track_f32<5>(P, k, c2, cz);
+    return fit_may_pass(c, k, c2, cz, float(c.chi2_rphi_t5), float(c.chi2_rz_t5));
+}
+
+// Collected candidates: FP32 fit prefilter (compacted in place), then the
+// FP64 test; passing pairs are appended to the stage.
 __device__ __forceinline__ void t5_flush(const Arena& A, const DevCfg& c, T5Smem& S, int ncand, int& cnt) {
     const int lane = lane_id();
+    int n2 = 0;
     for (int base = 0; base < ncand; base += 32) {
+        int q = base + lane;
+        int2 pr = q < ncand ? S.cand[q] : make_int2(0, 0);
+        bool keep = q < ncand && t5_prefit_f32(A, c, pr);
+        __syncwarp();
+        int tot;
+        int r = warp_rank(keep, tot);
+        if (keep) S.cand[n2 + r] = pr;        // n2 + r <= q: in-place compaction is safe
+        n2 += tot;
+    }
+    __syncwarp();
+    for (int base = 0; base < n2; base += 32) {
         int q = base + lane;
         bool pass = false;
         int2 pr = make_int2(0, 0);
-        if (q < ncand) {
+        if (q < n2) {
             pr = S.cand[q];
             T5Out o;
             pass = t5_eval_pair(A, c, pr, o);

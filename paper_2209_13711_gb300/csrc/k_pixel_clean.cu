@@ -77,9 +77,42 @@ __device__ __forceinline__ void pt_mds(const Arena& A, int obj, int* m) {
 }
 
 template <int NT>
+__device__ __forceinline__ bool pt_prefit_f32(const Arena& A, const DevCfg& c, int g, int obj) {
+    Pt<float> P[NT + 3];
+    const float* sd = A.seeds + 9 * (size_t)g;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) P[j] = pix_pt<float>(sd + 3 * j, c.sig_pix);
+    int m[NT];
+    pt_mds<NT>(A, obj, m);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        float4 mi = A.mod[A.md_gmod[m[j]] % A.n_mod];
+        P[3 + j] = hit_pt<float>(A.md_x[m[j]], A.md_y[m[j]], A.md_z[m[j]], mi);
+    }
+    float k, c2, cz;
+    fit_track_f32<NT + 3>(P, k, c2, cz);
+    return fit_may_pass(c, k, c2, cz, float(NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3),
+                        float(NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3));
+}
+
+template <int NT>
 __device__ __forceinline__ void pt_flush(const Arena& A, const DevCfg& c, PtSmem& S, int g, int ncand, int& cnt) {
     const int lane = lane_id();
     const double kp = A.pls_kappa[g], sp = A.pls_sigk[g];
+    // FP32 fit prefilter, compacted in place (the write index never passes the read index)
+    int n2 = 0;
+    for (int base = 0; base < ncand; base += 32) {
+        int q = base + lane;
+        int obj = q < ncand ? S.cand[q] : 0;
+        bool keep = q < ncand && pt_prefit_f32<NT>(A, c, g, obj);
+        __syncwarp();
+        int tot;
+        int r = warp_rank(keep, tot);
+        if (keep) S.cand[n2 + r] = obj;
+        n2 += tot;
+    }
+    __syncwarp();
+    ncand = n2;
     for (int base = 0; base < ncand; base += 32) {
         int q = base + lane;
         bool pass = false;

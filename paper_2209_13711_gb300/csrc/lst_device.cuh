@@ -481,6 +481,86 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P) {
     return f;
 }
 
+// FP32 twin of fit_track, used only as a conservative prefilter before the
+// FP64 fit: same frame and residual definitions, with the normal equations
+// centred (2x2 solve) for conditioning in single precision.
+template <int N> __device__ inline void fit_track_f32(const Pt<float>* P, float& kappa, float& chi2, float& chi2z) {
+    const Pt<float>& O = P[N / 2];
+    float ex = P[N - 1].x - P[0].x, ey = P[N - 1].y - P[0].y;
+    float il = 1.0f / hypotf(ex, ey);
+    float xx = ex * il, xy = ey * il, yx = -xy, yy = xx;
+    float xi[N], et[N], rho2[N];
+    float mr = 0.f, mx = 0.f, me = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        float dx = P[i].x - O.x, dy = P[i].y - O.y;
+        xi[i] = dx * xx + dy * xy;
+        et[i] = dx * yx + dy * yy;
+        rho2[i] = xi[i] * xi[i] + et[i] * et[i];
+        mr += rho2[i]; mx += xi[i]; me += et[i];
+    }
+    mr *= 1.0f / N; mx *= 1.0f / N; me *= 1.0f / N;
+    float saa = 0.f, sab = 0.f, sbb = 0.f, sac = 0.f, sbc = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        float a = rho2[i] - mr, b = xi[i] - mx, cc = et[i] - me;
+        saa += a * a; sab += a * b; sbb += b * b; sac += a * cc; sbc += b * cc;
+    }
+    float det = saa * sbb - sab * sab;
+    if (!(det > 0.f)) { kappa = 1e30f; chi2 = 1e30f; chi2z = 1e30f; return; }
+    float gg = (sac * sbb - sab * sbc) / det;
+    float hh = (saa * sbc - sab * sac) / det;
+    float kk = me - gg * mr - hh * mx;
+    float S = sqrtf(fmaxf(0.f, 1.f + hh * hh - 4.f * gg * kk));
+    kappa = 2.f * gg / S;
+    float c2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        float u = gg * rho2[i] + hh * xi[i] + kk - et[i];
+        float e = 2.f * u / (S + sqrtf(fmaxf(0.f, S * S + 4.f * gg * u)));
+        float nlx = 2.f * gg * xi[i] + hh, nly = 2.f * gg * et[i] - 1.f;
+        float nx = nlx * xx + nly * yx, ny = nlx * xy + nly * yy;
+        float inn = 1.0f / hypotf(nx, ny);
+        nx *= inn; ny *= inn;
+        float ir = 1.0f / P[i].r;
+        float rx = P[i].x * ir, ry = P[i].y * ir;
+        float n_phi = -nx * ry + ny * rx, n_r = nx * rx + ny * ry;
+        float s2 = fmaxf(sq(P[i].srphi * n_phi) + sq(P[i].sr * n_r), sq(0.01f * P[i].srphi));
+        c2 += e * e / s2;
+    }
+    chi2 = c2;
+    float ka = fabsf(kappa);
+    float s[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) s[i] = arc(hypotf(P[i].x - P[0].x, P[i].y - P[0].y), ka);
+    float t_hat = (P[N - 1].z - P[0].z) / s[N - 1];
+    float w[N], W = 0.f, Ws = 0.f, Wz = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        w[i] = 1.0f / fmaxf(1e-12f, sq(P[i].sz) + sq(t_hat * P[i].sr));
+        W += w[i]; Ws += w[i] * s[i]; Wz += w[i] * P[i].z;
+    }
+    float sbar = Ws / W, zbar = Wz / W, Sss = 0.f, Ssz = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        Sss += w[i] * sq(s[i] - sbar);
+        Ssz += w[i] * (s[i] - sbar) * (P[i].z - zbar);
+    }
+    float t = Ssz / Sss, c0 = zbar - t * sbar, cz = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) cz += w[i] * sq(P[i].z - c0 - t * s[i]);
+    chi2z = cz;
+}
+
+// Conservative FP32 verdict on the fit cuts: false only when every cut fails
+// by far more than FP32 rounding can explain.
+__device__ __forceinline__ bool fit_may_pass(const DevCfg& c, float kappa, float chi2, float chi2z, float chi2_max,
+                                             float chi2z_max) {
+    float kmax = float((1.0 + c.tol_r) * 2.0 * c.a);
+    return fabsf(kappa) <= kmax * 1.01f + 1e-5f && chi2 <= 1.25f * chi2_max + 2.f &&
+           chi2z <= 1.25f * chi2z_max + 2.f;
+}
+
 __device__ __forceinline__ double phi0_of(const Pt<double>& P, double kappa) {
     double s = kappa < 0 ? -1.0 : 1.0;
     return wrap_pi(atan2(P.y, P.x) - s * asinc(P.r * fabs(kappa) / 2.0));
