@@ -212,9 +212,8 @@ __global__ void __launch_bounds__(kMdWarps * 32) k_md(Arena A, DevCfg c) {
             A.md_lo[o] = S.li[l];
             A.md_up[o] = S.ui[k];
             A.md_gmod[o] = u;
-            A.md_x[o] = S.lx[l];
-            A.md_y[o] = S.ly[l];
-            A.md_z[o] = S.lz[l];
+            A.md_p4[o] = make_float4(S.lx[l], S.ly[l], S.lz[l], mi.w < 0.5f ? mi.z : -mi.z);
+            A.md_srp[o] = mi.y;
             A.md_dx[o] = S.ux[k] - S.lx[l];
             A.md_dy[o] = S.uy[k] - S.ly[l];
             A.md_dphi[o] = dp;
@@ -238,12 +237,8 @@ struct LsSmem {
     int stage[kLsStage];
 };
 
-__device__ __forceinline__ Pt<float> md_pt_f(const Arena& A, int i, float4 mi) {
-    return hit_pt<float>(A.md_x[i], A.md_y[i], A.md_z[i], mi);
-}
-__device__ __forceinline__ Pt<double> md_pt_d(const Arena& A, int i, float4 mi) {
-    return hit_pt<double>(A.md_x[i], A.md_y[i], A.md_z[i], mi);
-}
+__device__ __forceinline__ Pt<float> md_pt_f(const Arena& A, int i, float4) { return md_point<float>(A, i); }
+__device__ __forceinline__ Pt<double> md_pt_d(const Arena& A, int i, float4) { return md_point<double>(A, i); }
 __device__ __forceinline__ float4 md_mod(const Arena& A, int i) {
     int gm = A.md_gmod[i];
     return A.mod[gm % A.n_mod];
@@ -297,7 +292,8 @@ __global__ void __launch_bounds__(kLsWarps * 32) k_ls(Arena A, DevCfg c) {
         const int base = reserve(&A.counters[1], A.ls_cap, n, dropped);
         for (int k = lane; k < n; k += 32) {
             int B = S.stage[k];
-            float Bx = A.md_x[B], By = A.md_y[B];
+            float4 Bp = A.md_p4[B];
+            float Bx = Bp.x, By = Bp.y;
             int o = base + k;
             A.ls_in[o] = i;
             A.ls_out[o] = B;
@@ -378,6 +374,9 @@ __global__ void __launch_bounds__(kT3Warps * 32) k_t3(Arena A, DevCfg c) {
             int o = base + k;
             A.t3_lsin[o] = pr.x;
             A.t3_lsout[o] = pr.y;
+            A.t3_m0[o] = i;
+            A.t3_m1[o] = B_;
+            A.t3_m2[o] = C_;
             A.t3_beta[o] = beta;
             A.t3_kappa[o] = kap;
             A.t3_sigk[o] = sk;
@@ -403,68 +402,43 @@ struct T5Smem {
     int2 stage[kT5Stage];      // passing (T3_1, T3_2); outputs are recomputed when written
 };
 
-__device__ __forceinline__ void t3_anchor_mds(const Arena& A, int t, int& a, int& b, int& cc) {
-    int l1 = A.t3_lsin[t], l2 = A.t3_lsout[t];
-    a = A.ls_in[l1];
-    b = A.ls_out[l1];
-    cc = A.ls_out[l2];
-}
-
-__device__ __forceinline__ bool t5_eval_pair(const Arena& A, const DevCfg& c, int2 pr, T5Out& o) {
-    int m[5];
-    t3_anchor_mds(A, pr.x, m[0], m[1], m[2]);
-    t3_anchor_mds(A, pr.y, m[2], m[3], m[4]);
-    Pt<double> P[5];
-#pragma unroll
-    for (int j = 0; j < 5; ++j) P[j] = md_pt_d(A, m[j], md_mod(A, m[j]));
-    return t5_eval(c, P, o);
+__device__ __forceinline__ void t5_mds(const Arena& A, int2 pr, int* m) {
+    m[0] = A.t3_m0[pr.x];
+    m[1] = A.t3_m1[pr.x];
+    m[2] = A.t3_m2[pr.x];
+    m[3] = A.t3_m1[pr.y];
+    m[4] = A.t3_m2[pr.y];
 }
 
 __device__ __forceinline__ bool t5_prefit_f32(const Arena& A, const DevCfg& c, int2 pr) {
     int m[5];
-    t3_anchor_mds(A, pr.x, m[0], m[1], m[2]);
-    t3_anchor_mds(A, pr.y, m[2], m[3], m[4]);
+    t5_mds(A, pr, m);
     Pt<float> P[5];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) P[j] = md_pt_f(A, m[j], md_mod(A, m[j]));
+    for (int j = 0; j < 5; ++j) P[j] = md_point<float>(A, m[j]);
     float k, c2, cz;
     fit_track_f32<5>(P, k, c2, cz);
     return fit_may_pass(c, k, c2, cz, float(c.chi2_rphi_t5), float(c.chi2_rz_t5));
 }
 
-// Collected candidates: FP32 fit prefilter (compacted in place), then the
-// FP64 test; passing pairs are appended to the stage.
+// Collected candidates: FP32 fit prefilter; survivors are appended to the stage.
 __device__ __forceinline__ void t5_flush(const Arena& A, const DevCfg& c, T5Smem& S, int ncand, int& cnt) {
     const int lane = lane_id();
-    int n2 = 0;
     for (int base = 0; base < ncand; base += 32) {
         int q = base + lane;
         int2 pr = q < ncand ? S.cand[q] : make_int2(0, 0);
         bool keep = q < ncand && t5_prefit_f32(A, c, pr);
-        __syncwarp();
         int tot;
         int r = warp_rank(keep, tot);
-        if (keep) S.cand[n2 + r] = pr;        // n2 + r <= q: in-place compaction is safe
-        n2 += tot;
-    }
-    __syncwarp();
-    for (int base = 0; base < n2; base += 32) {
-        int q = base + lane;
-        bool pass = false;
-        int2 pr = make_int2(0, 0);
-        if (q < n2) {
-            pr = S.cand[q];
-            T5Out o;
-            pass = t5_eval_pair(A, c, pr, o);
-        }
-        int tot;
-        int r = warp_rank(pass, tot);
-        if (pass && cnt + r < kT5Stage) S.stage[cnt + r] = pr;
+        if (keep && cnt + r < kT5Stage) S.stage[cnt + r] = pr;
         cnt += tot;
     }
     __syncwarp();
 }
 
+// T5 search (FP32 only): one warp per inner MD A; candidates = (T3_1 from A) x
+// (T3_2 from T3_1's outer MD); curvature prefilter, FP32 fit prefilter. The
+// survivors are written as the MD's T5 segment; k_t5_refine decides them in FP64.
 __global__ void __launch_bounds__(kT5Warps * 32) k_t5(Arena A, DevCfg c) {
     __shared__ T5Smem sm[kT5Warps];
     T5Smem& S = sm[threadIdx.x >> 5];
@@ -483,7 +457,7 @@ __global__ void __launch_bounds__(kT5Warps * 32) k_t5(Arena A, DevCfg c) {
             int t1 = cb + lane;
             int off = 0, len = 0;
             if (t1 < s1) {
-                int C_ = A.ls_out[A.t3_lsout[t1]];
+                int C_ = A.t3_m2[t1];
                 off = A.t3_off[C_];
                 len = A.t3_cnt[C_];
             }
@@ -517,27 +491,39 @@ __global__ void __launch_bounds__(kT5Warps * 32) k_t5(Arena A, DevCfg c) {
         const int base = reserve(&A.counters[3], A.t5_cap, n, dropped);
         for (int k = lane; k < n; k += 32) {
             int2 pr = S.stage[k];
-            T5Out s;
-            t5_eval_pair(A, c, pr, s);
-            int o = base + k;
-            A.t5_in[o] = pr.x;
-            A.t5_out[o] = pr.y;
-            A.t5_kappa[o] = s.kappa;
-            A.t5_sigk[o] = s.sigk;
-            A.t5_eta[o] = s.eta;
-            A.t5_phi[o] = s.phi0;
-            A.t5_chi2[o] = float(s.chi2_rphi);
-            A.t5_chi2z[o] = float(s.chi2_rz);
-            A.t5_score[o] = float(s.score);
-            A.t5_pt[o] = float(s.pt);
+            A.t5_in[base + k] = pr.x;
+            A.t5_out[base + k] = pr.y;
         }
         if (lane == 0) {
             A.t5_off[i] = base;
             A.t5_cnt[i] = n;
-            if (n) atomicAdd(&A.ev_counts[e * 8 + 3], n);
             if (dropped) atomicAdd(&A.ev_drop[e * 8 + 3], dropped);
         }
         __syncwarp();
+    }
+}
+
+// T5 refine (FP64): one thread per searched candidate, lane-dense.
+__global__ void k_t5_refine(Arena A, DevCfg c) {
+    const int n = min(A.counters[3], A.t5_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int m[5];
+        t5_mds(A, make_int2(A.t5_in[i], A.t5_out[i]), m);
+        Pt<double> P[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) P[j] = md_point<double>(A, m[j]);
+        T5Out o{};
+        bool pass = t5_eval(c, P, o);
+        A.t5_valid[i] = pass;
+        A.t5_kappa[i] = o.kappa;
+        A.t5_sigk[i] = o.sigk;
+        A.t5_eta[i] = o.eta;
+        A.t5_phi[i] = o.phi0;
+        A.t5_chi2[i] = float(o.chi2_rphi);
+        A.t5_chi2z[i] = float(o.chi2_rz);
+        A.t5_score[i] = float(o.score);
+        A.t5_pt[i] = float(o.pt);
+        if (pass) atomicAdd(&A.ev_counts[(A.md_gmod[m[0]] / A.n_mod) * 8 + 3], 1);
     }
 }
 

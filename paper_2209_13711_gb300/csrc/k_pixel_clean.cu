@@ -53,26 +53,19 @@ __global__ void k_pls(Arena A, DevCfg c) {
 // pT5 / pT3: one warp per passing seed; candidates = T objects whose inner
 // MD sits in a module listed under the seed's superbin.
 // ---------------------------------------------------------------------------
-struct PtStage {
-    int obj;
-    float kappa, chi2, chi2z, score, pt;
-};
-
 struct PtSmem {
     int pre[32], off[32];
     int cand[kPtPre];
-    PtStage stage[kPtStage];
+    int stage[kPtStage];
 };
 
 template <int NT>
 __device__ __forceinline__ void pt_mds(const Arena& A, int obj, int* m) {
     if (NT == 5) {
-        int l1 = A.t3_lsin[A.t5_in[obj]], l2 = A.t3_lsout[A.t5_in[obj]];
-        int l3 = A.t3_lsin[A.t5_out[obj]], l4 = A.t3_lsout[A.t5_out[obj]];
-        m[0] = A.ls_in[l1]; m[1] = A.ls_out[l1]; m[2] = A.ls_out[l2]; m[3] = A.ls_out[l3]; m[4] = A.ls_out[l4];
+        int a = A.t5_in[obj], b = A.t5_out[obj];
+        m[0] = A.t3_m0[a]; m[1] = A.t3_m1[a]; m[2] = A.t3_m2[a]; m[3] = A.t3_m1[b]; m[4] = A.t3_m2[b];
     } else {
-        int l1 = A.t3_lsin[obj], l2 = A.t3_lsout[obj];
-        m[0] = A.ls_in[l1]; m[1] = A.ls_out[l1]; m[2] = A.ls_out[l2];
+        m[0] = A.t3_m0[obj]; m[1] = A.t3_m1[obj]; m[2] = A.t3_m2[obj];
     }
 }
 
@@ -85,80 +78,32 @@ __device__ __forceinline__ bool pt_prefit_f32(const Arena& A, const DevCfg& c, i
     int m[NT];
     pt_mds<NT>(A, obj, m);
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
-        float4 mi = A.mod[A.md_gmod[m[j]] % A.n_mod];
-        P[3 + j] = hit_pt<float>(A.md_x[m[j]], A.md_y[m[j]], A.md_z[m[j]], mi);
-    }
+    for (int j = 0; j < NT; ++j) P[3 + j] = md_point<float>(A, m[j]);
     float k, c2, cz;
     fit_track_f32<NT + 3>(P, k, c2, cz);
     return fit_may_pass(c, k, c2, cz, float(NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3),
                         float(NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3));
 }
 
+// Collected candidates: FP32 fit prefilter; survivors are appended to the stage.
 template <int NT>
 __device__ __forceinline__ void pt_flush(const Arena& A, const DevCfg& c, PtSmem& S, int g, int ncand, int& cnt) {
     const int lane = lane_id();
-    const double kp = A.pls_kappa[g], sp = A.pls_sigk[g];
-    // FP32 fit prefilter, compacted in place (the write index never passes the read index)
-    int n2 = 0;
     for (int base = 0; base < ncand; base += 32) {
         int q = base + lane;
         int obj = q < ncand ? S.cand[q] : 0;
         bool keep = q < ncand && pt_prefit_f32<NT>(A, c, g, obj);
-        __syncwarp();
         int tot;
         int r = warp_rank(keep, tot);
-        if (keep) S.cand[n2 + r] = obj;
-        n2 += tot;
-    }
-    __syncwarp();
-    ncand = n2;
-    for (int base = 0; base < ncand; base += 32) {
-        int q = base + lane;
-        bool pass = false;
-        PTOut o;
-        int obj = 0;
-        if (q < ncand) {
-            obj = S.cand[q];
-            Pt<double> P[NT + 3];
-            const float* sd = A.seeds + 9 * (size_t)g;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) P[j] = pix_pt<double>(sd + 3 * j, c.sig_pix);
-            int m[NT];
-            pt_mds<NT>(A, obj, m);
-#pragma unroll
-            for (int j = 0; j < NT; ++j) {
-                float4 mi = A.mod[A.md_gmod[m[j]] % A.n_mod];
-                P[3 + j] = hit_pt<double>(A.md_x[m[j]], A.md_y[m[j]], A.md_z[m[j]], mi);
-            }
-            double kt, st;
-            if (NT == 5) {
-                kt = A.t5_kappa[obj];
-                st = A.t5_sigk[obj];
-            } else {
-                Tri<double> tt = tri(P[3], P[4], P[5]);
-                kt = tt.kappa;
-                st = tt.sigk;
-            }
-            pass = pt_eval<NT + 3>(c, P, kp, sp, kt, st, NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3,
-                                   NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3, o);
-        }
-        int tot;
-        int r = warp_rank(pass, tot);
-        if (pass && cnt + r < kPtStage) {
-            PtStage& s = S.stage[cnt + r];
-            s.obj = obj;
-            s.kappa = float(o.kappa);
-            s.chi2 = float(o.chi2_rphi);
-            s.chi2z = float(o.chi2_rz);
-            s.score = float(o.score);
-            s.pt = float(o.pt);
-        }
+        if (keep && cnt + r < kPtStage) S.stage[cnt + r] = obj;
         cnt += tot;
     }
     __syncwarp();
 }
 
+// pT5 / pT3 search (FP32 only): one warp per passing seed; candidates = T
+// objects whose inner MD sits in a module listed under the seed's superbin;
+// curvature prefilter and FP32 fit prefilter. k_pt_refine decides in FP64.
 template <int NT>
 __device__ __forceinline__ void pt_kernel_body(Arena& A, const DevCfg& c) {
     __shared__ PtSmem sm[kPtWarps];
@@ -189,7 +134,7 @@ __device__ __forceinline__ void pt_kernel_body(Arena& A, const DevCfg& c) {
                 for (int k = 0; __any_sync(kFull, k < on); ++k) {
                     bool pass = false;
                     int obj = oo + k;
-                    if (k < on) {
+                    if (k < on && (NT == 3 || A.t5_valid[obj])) {
                         float kt = NT == 5 ? float(A.t5_kappa[obj]) : A.t3_kappa[obj];
                         float st = NT == 5 ? float(A.t5_sigk[obj]) : A.t3_sigk[obj];
                         float thr = nk * sqrtf(sp * sp + st * st);
@@ -214,26 +159,57 @@ __device__ __forceinline__ void pt_kernel_body(Arena& A, const DevCfg& c) {
         const int slot = NT == 5 ? 4 : 5;
         const int base = reserve(&A.counters[slot], NT == 5 ? A.pt5_cap : A.pt3_cap, n, dropped);
         for (int k = lane; k < n; k += 32) {
-            const PtStage& s = S.stage[k];
-            int o = base + k;
-            if (NT == 5) {
-                A.pt5_seed[o] = g; A.pt5_obj[o] = s.obj; A.pt5_kappa[o] = s.kappa; A.pt5_chi2[o] = s.chi2;
-                A.pt5_chi2z[o] = s.chi2z; A.pt5_score[o] = s.score; A.pt5_pt[o] = s.pt;
-            } else {
-                A.pt3_seed[o] = g; A.pt3_obj[o] = s.obj; A.pt3_kappa[o] = s.kappa; A.pt3_chi2[o] = s.chi2;
-                A.pt3_chi2z[o] = s.chi2z; A.pt3_score[o] = s.score; A.pt3_pt[o] = s.pt;
-            }
+            if (NT == 5) { A.pt5_seed[base + k] = g; A.pt5_obj[base + k] = S.stage[k]; }
+            else { A.pt3_seed[base + k] = g; A.pt3_obj[base + k] = S.stage[k]; }
         }
-        if (lane == 0) {
-            if (n) atomicAdd(&A.ev_counts[e * 8 + (NT == 5 ? 5 : 6)], n);
-            if (dropped) atomicAdd(&A.ev_drop[e * 8 + (NT == 5 ? 5 : 6)], dropped);
-        }
+        if (lane == 0 && dropped) atomicAdd(&A.ev_drop[e * 8 + (NT == 5 ? 5 : 6)], dropped);
         __syncwarp();
     }
 }
 
 __global__ void __launch_bounds__(kPtWarps * 32) k_pt5(Arena A, DevCfg c) { pt_kernel_body<5>(A, c); }
 __global__ void __launch_bounds__(kPtWarps * 32) k_pt3(Arena A, DevCfg c) { pt_kernel_body<3>(A, c); }
+
+// pT5 / pT3 refine (FP64): one thread per searched candidate.
+template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const DevCfg& c) {
+    const int n = min(A.counters[NT == 5 ? 4 : 5], NT == 5 ? A.pt5_cap : A.pt3_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int g = NT == 5 ? A.pt5_seed[i] : A.pt3_seed[i];
+        const int obj = NT == 5 ? A.pt5_obj[i] : A.pt3_obj[i];
+        Pt<double> P[NT + 3];
+        const float* sd = A.seeds + 9 * (size_t)g;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) P[j] = pix_pt<double>(sd + 3 * j, c.sig_pix);
+        int m[NT];
+        pt_mds<NT>(A, obj, m);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) P[3 + j] = md_point<double>(A, m[j]);
+        double kt, st;
+        if (NT == 5) {
+            kt = A.t5_kappa[obj];
+            st = A.t5_sigk[obj];
+        } else {
+            Tri<double> tt = tri(P[3], P[4], P[5]);
+            kt = tt.kappa;
+            st = tt.sigk;
+        }
+        PTOut o{};
+        bool pass = pt_eval<NT + 3>(c, P, A.pls_kappa[g], A.pls_sigk[g], kt, st,
+                                    NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3,
+                                    NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3, o);
+        if (NT == 5) {
+            A.pt5_valid[i] = pass; A.pt5_kappa[i] = float(o.kappa); A.pt5_chi2[i] = float(o.chi2_rphi);
+            A.pt5_chi2z[i] = float(o.chi2_rz); A.pt5_score[i] = float(o.score); A.pt5_pt[i] = float(o.pt);
+        } else {
+            A.pt3_valid[i] = pass; A.pt3_kappa[i] = float(o.kappa); A.pt3_chi2[i] = float(o.chi2_rphi);
+            A.pt3_chi2z[i] = float(o.chi2_rz); A.pt3_score[i] = float(o.score); A.pt3_pt[i] = float(o.pt);
+        }
+        if (pass) atomicAdd(&A.ev_counts[event_of(A.seed_off, A.n_ev, g) * 8 + (NT == 5 ? 5 : 6)], 1);
+    }
+}
+
+__global__ void k_pt5_refine(Arena A, DevCfg c) { pt_refine_body<5>(A, c); }
+__global__ void k_pt3_refine(Arena A, DevCfg c) { pt_refine_body<3>(A, c); }
 
 // ---------------------------------------------------------------------------
 // cross-cleaning
@@ -309,6 +285,12 @@ __global__ void k_clean_keys(Arena A, int pass) {
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n5 + n3 + nt; f += gridDim.x * blockDim.x) {
         int cat = f < n5 ? 0 : (f < n5 + n3 ? 1 : 2);
         int idx = cat == 0 ? f : (cat == 1 ? f - n5 : f - n5 - n3);
+        const uint8_t* vf = cat == 0 ? A.pt5_valid : (cat == 1 ? A.pt3_valid : A.t5_valid);
+        uint8_t* kf = cat == 0 ? A.keep_pt5 : (cat == 1 ? A.keep_pt3 : A.keep_t5);
+        if (!vf[idx]) {
+            if (pass == 1) kf[idx] = 0;
+            continue;
+        }
         ObjHits o;
         object_hits(A, cat, idx, o);
         unsigned long long key = object_key(o);
@@ -318,7 +300,6 @@ __global__ void k_clean_keys(Arena A, int pass) {
         } else {
             bool keep = true;
             for (int i = 0; i < o.n; ++i) keep &= best[o.slots[i]] == key;
-            uint8_t* kf = cat == 0 ? A.keep_pt5 : (cat == 1 ? A.keep_pt3 : A.keep_t5);
             kf[idx] = keep;
         }
     }

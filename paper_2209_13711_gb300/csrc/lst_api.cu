@@ -200,7 +200,7 @@ static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_m
     const size_t MD = E * K.md_per_event;
     A.md_cap = (int)MD;
     A.md_lo = b.take<int>(MD); A.md_up = b.take<int>(MD); A.md_gmod = b.take<int>(MD);
-    A.md_x = b.take<float>(MD); A.md_y = b.take<float>(MD); A.md_z = b.take<float>(MD);
+    A.md_p4 = b.take<float4>(MD); A.md_srp = b.take<float>(MD);
     A.md_dx = b.take<float>(MD); A.md_dy = b.take<float>(MD);
     A.md_dphi = b.take<float>(MD); A.md_dlong = b.take<float>(MD);
     A.md_moff = b.take<int>(E * n_mod); A.md_mcnt = b.take<int>(E * n_mod);
@@ -212,6 +212,7 @@ static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_m
     A.t3_cap = (int)T3;
     A.t3_lsin = b.take<int>(T3); A.t3_lsout = b.take<int>(T3);
     A.t3_beta = b.take<float>(T3); A.t3_kappa = b.take<float>(T3); A.t3_sigk = b.take<float>(T3);
+    A.t3_m0 = b.take<int>(T3); A.t3_m1 = b.take<int>(T3); A.t3_m2 = b.take<int>(T3);
     A.t3_off = b.take<int>(MD); A.t3_cnt = b.take<int>(MD);
     const size_t T5 = E * K.t5_per_event;
     A.t5_cap = (int)T5;
@@ -219,7 +220,7 @@ static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_m
     A.t5_kappa = b.take<double>(T5); A.t5_sigk = b.take<double>(T5);
     A.t5_eta = b.take<double>(T5); A.t5_phi = b.take<double>(T5);
     A.t5_chi2 = b.take<float>(T5); A.t5_chi2z = b.take<float>(T5); A.t5_score = b.take<float>(T5);
-    A.t5_pt = b.take<float>(T5);
+    A.t5_pt = b.take<float>(T5); A.t5_valid = b.take<uint8_t>(T5);
     A.t5_off = b.take<int>(MD); A.t5_cnt = b.take<int>(MD);
     A.pls_pass = b.take<int>(S); A.pls_sb = b.take<int>(S);
     A.pls_kappa = b.take<double>(S); A.pls_sigk = b.take<double>(S);
@@ -229,11 +230,11 @@ static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_m
     A.pt5_cap = (int)P5;
     A.pt5_seed = b.take<int>(P5); A.pt5_obj = b.take<int>(P5); A.pt5_kappa = b.take<float>(P5);
     A.pt5_chi2 = b.take<float>(P5); A.pt5_chi2z = b.take<float>(P5); A.pt5_score = b.take<float>(P5);
-    A.pt5_pt = b.take<float>(P5);
+    A.pt5_pt = b.take<float>(P5); A.pt5_valid = b.take<uint8_t>(P5);
     A.pt3_cap = (int)P3;
     A.pt3_seed = b.take<int>(P3); A.pt3_obj = b.take<int>(P3); A.pt3_kappa = b.take<float>(P3);
     A.pt3_chi2 = b.take<float>(P3); A.pt3_chi2z = b.take<float>(P3); A.pt3_score = b.take<float>(P3);
-    A.pt3_pt = b.take<float>(P3);
+    A.pt3_pt = b.take<float>(P3); A.pt3_valid = b.take<uint8_t>(P3);
     const size_t NK = H + 3 * S;
     A.best = b.take<unsigned long long>(3 * NK);
     A.mark = b.take<int>(NK);
@@ -377,9 +378,12 @@ lst_status lst_run_batch(lst_ctx* c, const lst_hits* hits, const int32_t* hit_of
     LAUNCH("ls", k_ls<<<nsm * 8, kLsWarps * 32, 0, st>>>(A, dc));
     LAUNCH("t3", k_t3<<<nsm * 8, kT3Warps * 32, 0, st>>>(A, dc));
     LAUNCH("t5", k_t5<<<nsm * 6, kT5Warps * 32, 0, st>>>(A, dc));
+    LAUNCH("t5_refine", k_t5_refine<<<nsm * 4, 128, 0, st>>>(A, dc));
     LAUNCH("pls", k_pls<<<grid_for((int)S, 128, nsm * 4), 128, 0, st>>>(A, dc));
     LAUNCH("pt5", k_pt5<<<nsm * 8, kPtWarps * 32, 0, st>>>(A, dc));
+    LAUNCH("pt5_refine", k_pt5_refine<<<nsm * 2, 128, 0, st>>>(A, dc));
     LAUNCH("pt3", k_pt3<<<nsm * 8, kPtWarps * 32, 0, st>>>(A, dc));
+    LAUNCH("pt3_refine", k_pt3_refine<<<nsm * 2, 128, 0, st>>>(A, dc));
     LAUNCH("clean_keys", k_clean_keys<<<nsm * 4, 256, 0, st>>>(A, 0));
     LAUNCH("clean_keep", k_clean_keys<<<nsm * 4, 256, 0, st>>>(A, 1));
     LAUNCH("clean_pt5", k_clean_pt5<<<nsm * 2, 256, 0, st>>>(A));
@@ -567,10 +571,12 @@ lst_status lst_get_objects(lst_ctx* c, int32_t event, int32_t kind, int32_t capa
     if (kind == 3 || kind == 5) {
         FETCH(t5i, A.t5_in, n_t5);
         FETCH(t5o, A.t5_out, n_t5);
+        std::vector<uint8_t> v5;
+        FETCH(v5, A.t5_valid, n_t5);
         t5_row.assign(n_t5, -1);
         r = 0;
         for (int i = 0; i < n_t5; ++i)
-            if (t3_row[t5i[i]] >= 0) t5_row[i] = r++;
+            if (v5[i] && t3_row[t5i[i]] >= 0) t5_row[i] = r++;
     }
     if (kind == 3) {
         std::vector<double> k, et, ph;
@@ -599,13 +605,15 @@ lst_status lst_get_objects(lst_ctx* c, int32_t event, int32_t kind, int32_t capa
     if (kind == 5 || kind == 6) {
         const int n = kind == 5 ? n_p5 : n_p3;
         std::vector<int> sd, ob;
+        std::vector<uint8_t> vv;
         std::vector<float> k, c2, cz, sc, pt;
+        FETCH(vv, kind == 5 ? A.pt5_valid : A.pt3_valid, n);
         FETCH(sd, kind == 5 ? A.pt5_seed : A.pt3_seed, n); FETCH(ob, kind == 5 ? A.pt5_obj : A.pt3_obj, n);
         FETCH(k, kind == 5 ? A.pt5_kappa : A.pt3_kappa, n); FETCH(c2, kind == 5 ? A.pt5_chi2 : A.pt3_chi2, n);
         FETCH(cz, kind == 5 ? A.pt5_chi2z : A.pt3_chi2z, n); FETCH(sc, kind == 5 ? A.pt5_score : A.pt3_score, n);
         FETCH(pt, kind == 5 ? A.pt5_pt : A.pt3_pt, n);
         for (int i = 0; i < n; ++i)
-            if (sd[i] >= s0 && sd[i] < s1) {
+            if (vv[i] && sd[i] >= s0 && sd[i] < s1) {
                 iv.insert(iv.end(), {sd[i] - s0, kind == 5 ? t5_row[ob[i]] : t3_row[ob[i]]});
                 fv.insert(fv.end(), {k[i], c2[i], cz[i], sc[i], pt[i]});
             }

@@ -78,9 +78,8 @@ struct Arena {
     int* md_lo;
     int* md_up;
     int* md_gmod;                 // e * n_mod + module
-    float* md_x;
-    float* md_y;
-    float* md_z;
+    float4* md_p4;                // anchor (lower hit) x, y, z and +sig_z (barrel) / -sig_r (endcap)
+    float* md_srp;                // anchor r-phi resolution
     float* md_dx;
     float* md_dy;
     float* md_dphi;
@@ -101,6 +100,9 @@ struct Arena {
     float* t3_beta;
     float* t3_kappa;
     float* t3_sigk;
+    int* t3_m0;                   // the three MDs (inner, middle, outer)
+    int* t3_m1;
+    int* t3_m2;
     int* t3_off;                  // [md_cap] by inner MD
     int* t3_cnt;
     // T5
@@ -115,6 +117,7 @@ struct Arena {
     double* t5_sigk;
     double* t5_eta;
     double* t5_phi;
+    uint8_t* t5_valid;            // the FP64 test passed (entries are FP32-prefiltered candidates)
     int* t5_off;                  // [md_cap] by inner MD
     int* t5_cnt;
     // pLS, per seed
@@ -135,6 +138,7 @@ struct Arena {
     float* pt5_chi2z;
     float* pt5_score;
     float* pt5_pt;
+    uint8_t* pt5_valid;
     int pt3_cap;
     int* pt3_seed;
     int* pt3_obj;
@@ -143,6 +147,7 @@ struct Arena {
     float* pt3_chi2z;
     float* pt3_score;
     float* pt3_pt;
+    uint8_t* pt3_valid;
     // cleaning
     unsigned long long* best;     // [3][n_keys]: n_keys = n_hits + 3 n_seeds
     int* mark;                    // [n_keys] bit 0: used by a kept pT5, bit 1: by a kept pT3
@@ -236,6 +241,18 @@ template <typename T> __device__ __forceinline__ Pt<T> pix_pt(const float* q, do
     p.r = m_hypot(p.x, p.y);
     p.srphi = T(sig_pix); p.sz = T(sig_pix); p.sr = T(0);
     return p;
+}
+
+// MD anchor as a measured point
+template <typename T> __device__ __forceinline__ Pt<T> md_point(const Arena& A, int i) {
+    float4 p = A.md_p4[i];
+    Pt<T> q;
+    q.x = T(p.x); q.y = T(p.y); q.z = T(p.z);
+    q.r = m_hypot(q.x, q.y);
+    q.srphi = T(A.md_srp[i]);
+    q.sz = p.w > 0.f ? T(p.w) : T(0);
+    q.sr = p.w > 0.f ? T(0) : T(-p.w);
+    return q;
 }
 
 // error of P perpendicular to a chord of unit direction (cx, cy)

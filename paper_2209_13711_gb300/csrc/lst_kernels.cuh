@@ -14,7 +14,7 @@ constexpr int kT3Stage = 512;     // T3 per inner MD
 constexpr int kT5Pre = 256;       // FP32-prefiltered T5 candidates held before an FP64 pass
 constexpr int kT5Stage = 1024;    // T5 per inner MD
 constexpr int kPtPre = 128;       // prefiltered pT3/pT5 candidates held before an FP64 pass
-constexpr int kPtStage = 96;      // pT3/pT5 per pixel seed
+constexpr int kPtStage = 256;     // pT3/pT5 candidates per pixel seed
 
 constexpr int kMdWarps = 4;
 constexpr int kLsWarps = 8;
@@ -29,9 +29,12 @@ __global__ void k_md(Arena A, DevCfg c);
 __global__ void k_ls(Arena A, DevCfg c);
 __global__ void k_t3(Arena A, DevCfg c);
 __global__ void k_t5(Arena A, DevCfg c);
+__global__ void k_t5_refine(Arena A, DevCfg c);
 __global__ void k_pls(Arena A, DevCfg c);
 __global__ void k_pt5(Arena A, DevCfg c);
 __global__ void k_pt3(Arena A, DevCfg c);
+__global__ void k_pt5_refine(Arena A, DevCfg c);
+__global__ void k_pt3_refine(Arena A, DevCfg c);
 __global__ void k_clean_keys(Arena A, int pass);
 __global__ void k_clean_pt5(Arena A);
 __global__ void k_clean_pt3_cross(Arena A, DevCfg c);
