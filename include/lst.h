@@ -209,6 +209,13 @@ lst_status lst_build_mini_doublets_static(const lst_config* cfg, const lst_modul
                                           float* md_dlong, int32_t* md_count, int32_t* md_dropped,
                                           void* cuda_stream);
 
+/* Wait for the batch and copy the batch-wide device counters: [0..5] objects
+ * reserved (MD, LS, T3, T5 candidates, pT5 candidates, pT3 candidates), [16]
+ * hits with an invalid module or side, [20] inner MDs whose T5 candidates
+ * overflowed the per-unit stage and were written by the overflow pass. At most
+ * n (<= 32) values. */
+lst_status lst_get_counters(lst_ctx* ctx, int32_t* out, int32_t n);
+
 /* Message of a status code (static storage). */
 const char* lst_status_str(lst_status s);
 

@@ -19,16 +19,38 @@ namespace lst {
 // ---------------------------------------------------------------------------
 // hit binning: counting sort by (event, module, side)
 // ---------------------------------------------------------------------------
+// Zero the per-batch counters and lists; the key arrays start at all ones.
+__global__ void k_reset(Arena A) {
+    const BatchDesc B = *A.bd;
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    const size_t n_keys = (size_t)B.n_hits + 3 * (size_t)B.n_seeds;
+    for (size_t i = t; i < 3 * n_keys; i += stride) A.best[i] = ~0ull;
+    for (size_t i = t; i < n_keys; i += stride) A.mark[i] = 0;
+    for (size_t i = t; i < (size_t)B.n_ev * 2 * A.n_mod; i += stride) A.bcnt[i] = 0;
+    for (size_t i = t; i < (size_t)B.n_seeds; i += stride) A.seed_link[i] = 0;
+    for (size_t i = t; i < (size_t)B.n_ev * 8; i += stride) {
+        A.ev_counts[i] = 0;
+        A.ev_drop[i] = 0;
+    }
+    for (size_t i = t; i < (size_t)B.n_ev; i += stride) {
+        A.list_cnt[2 * i] = 0;
+        A.list_cnt[2 * i + 1] = 0;
+        A.tc_cnt[i] = 0;
+    }
+    if (t < 32) A.counters[t] = 0;
+}
+
 __global__ void k_bin_count(Arena A) {
     const int nb = 2 * A.n_mod;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n_hits; i += gridDim.x * blockDim.x) {
-        int m = A.hmod[i];
-        int s = A.hside[i];
+    const BatchDesc B = *A.bd;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n_hits; i += gridDim.x * blockDim.x) {
+        int m = B.hmod[i];
+        int s = B.hside[i];
         if (m < 0 || m >= A.n_mod || s > 1) {
             atomicAdd(&A.counters[16], 1);
             continue;
         }
-        int e = event_of(A.hit_off, A.n_ev, i);
+        int e = event_of(A.hit_off, B.n_ev, i);
         atomicAdd(&A.bcnt[(size_t)e * nb + 2 * m + s], 1);
     }
 }
@@ -38,6 +60,7 @@ __global__ void k_bin_count(Arena A) {
 __global__ void __launch_bounds__(1024) k_bin_scan(Arena A) {
     const int nb = 2 * A.n_mod;
     const int e = blockIdx.x;
+    if (e >= A.bd->n_ev) return;
     int* cnt = A.bcnt + (size_t)e * nb;
     int* off = A.boff + (size_t)e * (nb + 1);
     __shared__ int warp_sums[32];
@@ -78,16 +101,17 @@ __global__ void __launch_bounds__(1024) k_bin_scan(Arena A) {
 
 __global__ void k_bin_scatter(Arena A) {
     const int nb = 2 * A.n_mod;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n_hits; i += gridDim.x * blockDim.x) {
-        int m = A.hmod[i];
-        int s = A.hside[i];
+    const BatchDesc B = *A.bd;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n_hits; i += gridDim.x * blockDim.x) {
+        int m = B.hmod[i];
+        int s = B.hside[i];
         if (m < 0 || m >= A.n_mod || s > 1) continue;
-        int e = event_of(A.hit_off, A.n_ev, i);
+        int e = event_of(A.hit_off, B.n_ev, i);
         int h0 = A.hit_off[e];
         int pos = h0 + atomicAdd(&A.bcnt[(size_t)e * nb + 2 * m + s], 1);
-        A.sx[pos] = A.hx[i];
-        A.sy[pos] = A.hy[i];
-        A.sz[pos] = A.hz[i];
+        A.sx[pos] = B.hx[i];
+        A.sy[pos] = B.hy[i];
+        A.sz[pos] = B.hz[i];
         A.sidx[pos] = i - h0;
     }
 }
@@ -150,7 +174,7 @@ __global__ void __launch_bounds__(kMdWarps * 32) k_md(Arena A, DevCfg c) {
     extern __shared__ __align__(16) unsigned char md_raw[];
     MdSmem& S = reinterpret_cast<MdSmem*>(md_raw)[threadIdx.x >> 5];
     const int lane = lane_id();
-    const int n_units = A.n_ev * A.n_mod;
+    const int n_units = A.bd->n_ev * A.n_mod;
     for (int u = blockIdx.x * kMdWarps + (threadIdx.x >> 5); u < n_units; u += gridDim.x * kMdWarps) {
         const int e = u / A.n_mod, m = u - e * A.n_mod;
         const int* bo = A.boff + (size_t)e * (2 * A.n_mod + 1);
@@ -421,8 +445,10 @@ __device__ __forceinline__ bool t5_prefit_f32(const Arena& A, const DevCfg& c, i
     return fit_may_pass(c, k, c2, cz, float(c.chi2_rphi_t5), float(c.chi2_rz_t5));
 }
 
-// Collected candidates: FP32 fit prefilter; survivors are appended to the stage.
-__device__ __forceinline__ void t5_flush(const Arena& A, const DevCfg& c, T5Smem& S, int ncand, int& cnt) {
+// Collected candidates: FP32 fit prefilter; every group of 32 verdicts is
+// handed to the sink in candidate order (the sink places the survivors).
+template <typename Sink>
+__device__ __forceinline__ void t5_flush(const Arena& A, const DevCfg& c, T5Smem& S, int ncand, Sink& sink) {
     const int lane = lane_id();
     for (int base = 0; base < ncand; base += 32) {
         int q = base + lane;
@@ -430,64 +456,85 @@ __device__ __forceinline__ void t5_flush(const Arena& A, const DevCfg& c, T5Smem
         bool keep = q < ncand && t5_prefit_f32(A, c, pr);
         int tot;
         int r = warp_rank(keep, tot);
-        if (keep && cnt + r < kT5Stage) S.stage[cnt + r] = pr;
-        cnt += tot;
+        sink(keep, pr, r, tot);
     }
     __syncwarp();
 }
 
-// T5 search (FP32 only): one warp per inner MD A; candidates = (T3_1 from A) x
-// (T3_2 from T3_1's outer MD); curvature prefilter, FP32 fit prefilter. The
-// survivors are written as the MD's T5 segment; k_t5_refine decides them in FP64.
+// All candidates of inner MD i in a fixed order: (T3_1 from i) x (T3_2 from
+// T3_1's outer MD), curvature prefilter, FP32 fit prefilter, then the sink.
+template <typename Sink>
+__device__ __forceinline__ void t5_enumerate(const Arena& A, const DevCfg& c, T5Smem& S, int i, Sink& sink) {
+    const int lane = lane_id();
+    const float nk = float(c.n_t5);
+    const int s0 = A.t3_off[i], s1 = s0 + A.t3_cnt[i];
+    int ncand = 0;
+    for (int cb = s0; cb < s1; cb += 32) {
+        int t1 = cb + lane;
+        int off = 0, len = 0;
+        if (t1 < s1) {
+            int C_ = A.t3_m2[t1];
+            off = A.t3_off[C_];
+            len = A.t3_cnt[C_];
+        }
+        S.t1[lane] = t1;
+        for_each_flat(off, len, S.pre, S.off, [&](bool valid, int seg, int t2) {
+            bool pass = false;
+            int t1_ = 0;
+            if (valid) {
+                t1_ = S.t1[seg];
+                float k1 = A.t3_kappa[t1_], k2 = A.t3_kappa[t2];
+                float s1_ = A.t3_sigk[t1_], s2_ = A.t3_sigk[t2];
+                float thr = nk * sqrtf(s1_ * s1_ + s2_ * s2_);
+                // slack covers the FP32 rounding of the stored curvatures
+                pass = fabsf(k1 - k2) <= thr * 1.01f + 1e-5f * (fabsf(k1) + fabsf(k2)) + 1e-7f;
+            }
+            int tot;
+            int r = warp_rank(pass, tot);
+            if (pass) S.cand[ncand + r] = make_int2(t1_, t2);
+            ncand += tot;
+            if (ncand > kT5Pre - 32) {
+                __syncwarp();
+                t5_flush(A, c, S, ncand, sink);
+                ncand = 0;
+            }
+        });
+    }
+    __syncwarp();
+    if (ncand) t5_flush(A, c, S, ncand, sink);
+}
+
+// T5 search (FP32 only): one warp per inner MD. The survivors are written as
+// the MD's T5 segment; k_t5_refine decides them in FP64. A unit with more
+// survivors than the stage holds is queued for k_t5_overflow.
 __global__ void __launch_bounds__(kT5Warps * 32) k_t5(Arena A, DevCfg c) {
     __shared__ T5Smem sm[kT5Warps];
     T5Smem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
     const int n_md = min(A.counters[0], A.md_cap);
-    const float nk = float(c.n_t5);
     for (int i = blockIdx.x * kT5Warps + (threadIdx.x >> 5); i < n_md; i += gridDim.x * kT5Warps) {
-        const int s0 = A.t3_off[i], s1 = s0 + A.t3_cnt[i];
-        if (s1 == s0) {
+        if (A.t3_cnt[i] == 0) {
             if (lane == 0) { A.t5_off[i] = 0; A.t5_cnt[i] = 0; }
             continue;
         }
-        const int e = A.md_gmod[i] / A.n_mod;
-        int cnt = 0, ncand = 0;
-        for (int cb = s0; cb < s1; cb += 32) {
-            int t1 = cb + lane;
-            int off = 0, len = 0;
-            if (t1 < s1) {
-                int C_ = A.t3_m2[t1];
-                off = A.t3_off[C_];
-                len = A.t3_cnt[C_];
+        int cnt = 0;
+        auto sink = [&](bool keep, int2 pr, int r, int tot) {
+            if (keep && cnt + r < kT5Stage) S.stage[cnt + r] = pr;
+            cnt += tot;
+        };
+        t5_enumerate(A, c, S, i, sink);
+        if (cnt > kT5Stage) {
+            if (lane == 0) {
+                A.t5_off[i] = 0;
+                A.t5_cnt[i] = 0;
+                int k = atomicAdd(&A.counters[20], 1);
+                if (k < A.ovf_cap) A.ovf_list[k] = i;
+                else atomicAdd(&A.ev_drop[(A.md_gmod[i] / A.n_mod) * 8 + 3], cnt);
             }
-            S.t1[lane] = t1;
-            for_each_flat(off, len, S.pre, S.off, [&](bool valid, int seg, int t2) {
-                bool pass = false;
-                int t1_ = 0;
-                if (valid) {
-                    t1_ = S.t1[seg];
-                    float k1 = A.t3_kappa[t1_], k2 = A.t3_kappa[t2];
-                    float s1_ = A.t3_sigk[t1_], s2_ = A.t3_sigk[t2];
-                    float thr = nk * sqrtf(s1_ * s1_ + s2_ * s2_);
-                    // slack covers the FP32 rounding of the stored curvatures
-                    pass = fabsf(k1 - k2) <= thr * 1.01f + 1e-5f * (fabsf(k1) + fabsf(k2)) + 1e-7f;
-                }
-                int tot;
-                int r = warp_rank(pass, tot);
-                if (pass) S.cand[ncand + r] = make_int2(t1_, t2);
-                ncand += tot;
-                if (ncand > kT5Pre - 32) {
-                    __syncwarp();
-                    t5_flush(A, c, S, ncand, cnt);
-                    ncand = 0;
-                }
-            });
+            __syncwarp();
+            continue;
         }
-        __syncwarp();
-        if (ncand) t5_flush(A, c, S, ncand, cnt);
-        int n = min(cnt, kT5Stage);
-        int dropped = cnt - n;
+        int n = cnt, dropped = 0;
         const int base = reserve(&A.counters[3], A.t5_cap, n, dropped);
         for (int k = lane; k < n; k += 32) {
             int2 pr = S.stage[k];
@@ -497,7 +544,39 @@ __global__ void __launch_bounds__(kT5Warps * 32) k_t5(Arena A, DevCfg c) {
         if (lane == 0) {
             A.t5_off[i] = base;
             A.t5_cnt[i] = n;
-            if (dropped) atomicAdd(&A.ev_drop[e * 8 + 3], dropped);
+            if (dropped) atomicAdd(&A.ev_drop[(A.md_gmod[i] / A.n_mod) * 8 + 3], dropped);
+        }
+        __syncwarp();
+    }
+}
+
+// Units whose survivors overflowed the stage: count, reserve, then enumerate
+// again writing straight to the arena in the same order.
+__global__ void __launch_bounds__(kT5Warps * 32) k_t5_overflow(Arena A, DevCfg c) {
+    __shared__ T5Smem sm[kT5Warps];
+    T5Smem& S = sm[threadIdx.x >> 5];
+    const int lane = lane_id();
+    const int n_ovf = min(A.counters[20], A.ovf_cap);
+    for (int k = blockIdx.x * kT5Warps + (threadIdx.x >> 5); k < n_ovf; k += gridDim.x * kT5Warps) {
+        const int i = A.ovf_list[k];
+        int cnt = 0;
+        auto count = [&](bool, int2, int, int tot) { cnt += tot; };
+        t5_enumerate(A, c, S, i, count);
+        int n = cnt, dropped = 0;
+        const int base = reserve(&A.counters[3], A.t5_cap, n, dropped);
+        int w = 0;
+        auto write = [&](bool keep, int2 pr, int r, int tot) {
+            if (keep && w + r < n) {
+                A.t5_in[base + w + r] = pr.x;
+                A.t5_out[base + w + r] = pr.y;
+            }
+            w += tot;
+        };
+        t5_enumerate(A, c, S, i, write);
+        if (lane == 0) {
+            A.t5_off[i] = base;
+            A.t5_cnt[i] = n;
+            if (dropped) atomicAdd(&A.ev_drop[(A.md_gmod[i] / A.n_mod) * 8 + 3], dropped);
         }
         __syncwarp();
     }

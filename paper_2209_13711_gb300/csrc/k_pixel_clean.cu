@@ -10,8 +10,9 @@ namespace lst {
 // pLS: one thread per seed, FP64 (three-point circle, r-z line, superbin)
 // ---------------------------------------------------------------------------
 __global__ void k_pls(Arena A, DevCfg c) {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < A.n_seeds; g += gridDim.x * blockDim.x) {
-        const float* q = A.seeds + 9 * (size_t)g;
+    const BatchDesc B = *A.bd;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < B.n_seeds; g += gridDim.x * blockDim.x) {
+        const float* q = B.seeds + 9 * (size_t)g;
         Pt<double> Q[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) Q[j] = pix_pt<double>(q + 3 * j, c.sig_pix);
@@ -43,7 +44,7 @@ __global__ void k_pls(Arena A, DevCfg c) {
         A.pls_eta[g] = eta;
         A.pls_phi[g] = phi0;
         if (pass) {
-            int e = event_of(A.seed_off, A.n_ev, g);
+            int e = event_of(A.seed_off, B.n_ev, g);
             atomicAdd(&A.ev_counts[e * 8 + 4], 1);
         }
     }
@@ -72,7 +73,7 @@ __device__ __forceinline__ void pt_mds(const Arena& A, int obj, int* m) {
 template <int NT>
 __device__ __forceinline__ bool pt_prefit_f32(const Arena& A, const DevCfg& c, int g, int obj) {
     Pt<float> P[NT + 3];
-    const float* sd = A.seeds + 9 * (size_t)g;
+    const float* sd = A.bd->seeds + 9 * (size_t)g;
 #pragma unroll
     for (int j = 0; j < 3; ++j) P[j] = pix_pt<float>(sd + 3 * j, c.sig_pix);
     int m[NT];
@@ -110,9 +111,10 @@ __device__ __forceinline__ void pt_kernel_body(Arena& A, const DevCfg& c) {
     PtSmem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
     const float nk = float(c.n_pt);
-    for (int g = blockIdx.x * kPtWarps + (threadIdx.x >> 5); g < A.n_seeds; g += gridDim.x * kPtWarps) {
+    const int n_ev = A.bd->n_ev, n_seeds = A.bd->n_seeds;
+    for (int g = blockIdx.x * kPtWarps + (threadIdx.x >> 5); g < n_seeds; g += gridDim.x * kPtWarps) {
         if (!A.pls_pass[g] || A.pls_sb[g] < 0) continue;
-        const int e = event_of(A.seed_off, A.n_ev, g);
+        const int e = event_of(A.seed_off, n_ev, g);
         const int sb = A.pls_sb[g];
         const float kp = float(A.pls_kappa[g]), sp = float(A.pls_sigk[g]);
         const int j0 = A.sb_off[sb], j1 = A.sb_off[sb + 1];
@@ -177,7 +179,7 @@ template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const
         const int g = NT == 5 ? A.pt5_seed[i] : A.pt3_seed[i];
         const int obj = NT == 5 ? A.pt5_obj[i] : A.pt3_obj[i];
         Pt<double> P[NT + 3];
-        const float* sd = A.seeds + 9 * (size_t)g;
+        const float* sd = A.bd->seeds + 9 * (size_t)g;
 #pragma unroll
         for (int j = 0; j < 3; ++j) P[j] = pix_pt<double>(sd + 3 * j, c.sig_pix);
         int m[NT];
@@ -204,7 +206,7 @@ template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const
             A.pt3_valid[i] = pass; A.pt3_kappa[i] = float(o.kappa); A.pt3_chi2[i] = float(o.chi2_rphi);
             A.pt3_chi2z[i] = float(o.chi2_rz); A.pt3_score[i] = float(o.score); A.pt3_pt[i] = float(o.pt);
         }
-        if (pass) atomicAdd(&A.ev_counts[event_of(A.seed_off, A.n_ev, g) * 8 + (NT == 5 ? 5 : 6)], 1);
+        if (pass) atomicAdd(&A.ev_counts[event_of(A.seed_off, A.bd->n_ev, g) * 8 + (NT == 5 ? 5 : 6)], 1);
     }
 }
 
@@ -243,12 +245,12 @@ __device__ __forceinline__ void object_hits(const Arena& A, int cat, int idx, Ob
         o.score = A.t5_score[idx];
     } else {
         int g = cat == 0 ? A.pt5_seed[idx] : A.pt3_seed[idx];
-        o.e = event_of(A.seed_off, A.n_ev, g);
+        o.e = event_of(A.seed_off, A.bd->n_ev, g);
         int nh = A.hit_off[o.e + 1] - A.hit_off[o.e];
         int sl = g - A.seed_off[o.e];
         for (int j = 0; j < 3; ++j) {
             o.ids[o.n] = nh + 3 * sl + j;
-            o.slots[o.n++] = A.n_hits + 3 * g + j;
+            o.slots[o.n++] = A.bd->n_hits + 3 * g + j;
         }
         if (cat == 0) { pt_mds<5>(A, A.pt5_obj[idx], m); nm = 5; o.score = A.pt5_score[idx]; }
         else { pt_mds<3>(A, A.pt3_obj[idx], m); nm = 3; o.score = A.pt3_score[idx]; }
@@ -281,7 +283,7 @@ __global__ void k_clean_keys(Arena A, int pass) {
     const int n5 = min(A.counters[4], A.pt5_cap);
     const int n3 = min(A.counters[5], A.pt3_cap);
     const int nt = min(A.counters[3], A.t5_cap);
-    const size_t n_keys = (size_t)A.n_hits + 3 * (size_t)A.n_seeds;
+    const size_t n_keys = (size_t)A.bd->n_hits + 3 * (size_t)A.bd->n_seeds;
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n5 + n3 + nt; f += gridDim.x * blockDim.x) {
         int cat = f < n5 ? 0 : (f < n5 + n3 ? 1 : 2);
         int idx = cat == 0 ? f : (cat == 1 ? f - n5 : f - n5 - n3);
@@ -344,31 +346,47 @@ __device__ __forceinline__ void ref_eta_phi(const Arena& A, int ref, double& eta
     else { eta = A.t5_eta[idx]; phi = A.t5_phi[idx]; }
 }
 
-// Is (eta, phi) within dr_clean of any entry of the event's list? FP32 test
-// with an FP64 re-test inside a 1e-3 relative band around the threshold.
-__device__ __forceinline__ bool dr_close(const Arena& A, const DevCfg& c, int e, int list, double eta, double phi) {
-    int n = min(A.list_cnt[e * 2 + list], A.list_cap);
-    size_t base = ((size_t)e * 2 + list) * A.list_cap;
+// Is (eta, phi) within dr_clean of any entry of the event's list? Called by
+// all 32 lanes of a warp with the same query; the lanes stride over the list.
+// FP32 test with an FP64 re-test inside a 1e-3 relative band around the
+// threshold.
+__device__ __forceinline__ bool dr_close_warp(const Arena& A, const DevCfg& c, int e, int list, double eta,
+                                              double phi) {
+    const int n = min(A.list_cnt[e * 2 + list], A.list_cap);
+    const size_t base = ((size_t)e * 2 + list) * A.list_cap;
     const double thr2 = c.dr_clean * c.dr_clean;
     const float thr2f = float(thr2);
     const float ef = float(eta), pf = float(phi);
     const float two_pi = float(2 * kPi);
-    for (int j = 0; j < n; ++j) {
-        float2 v = A.list_ef[base + j];
-        float de = v.x - ef;
-        float dp = v.y - pf;
-        if (dp > float(kPi)) dp -= two_pi;
-        if (dp <= -float(kPi)) dp += two_pi;
-        float d2 = de * de + dp * dp;
-        if (d2 < thr2f * (1.0f - 1e-3f)) return true;
-        if (d2 <= thr2f * (1.0f + 1e-3f)) {
-            double e2, p2;
-            ref_eta_phi(A, A.list_ref[base + j], e2, p2);
-            double dd = eta - e2, dq = wrap_pi(phi - p2);
-            if (dd * dd + dq * dq < thr2) return true;
+    for (int j0 = 0; j0 < n; j0 += 32) {
+        const int j = j0 + lane_id();
+        bool hit = false;
+        if (j < n) {
+            float2 v = A.list_ef[base + j];
+            float de = v.x - ef;
+            float dp = v.y - pf;
+            if (dp > float(kPi)) dp -= two_pi;
+            if (dp <= -float(kPi)) dp += two_pi;
+            float d2 = de * de + dp * dp;
+            if (d2 < thr2f * (1.0f - 1e-3f)) {
+                hit = true;
+            } else if (d2 <= thr2f * (1.0f + 1e-3f)) {
+                double e2, p2;
+                ref_eta_phi(A, A.list_ref[base + j], e2, p2);
+                double dd = eta - e2, dq = wrap_pi(phi - p2);
+                hit = dd * dd + dq * dq < thr2;
+            }
         }
+        if (__any_sync(kFull, hit)) return true;
     }
     return false;
+}
+
+// any of the object's outer-tracker hits carries one of the mark bits
+__device__ __forceinline__ bool marked_warp(const Arena& A, const ObjHits& o, int first, int bits) {
+    const int j = first + lane_id();
+    bool m = j < o.n && (A.mark[o.slots[j]] & bits) != 0;
+    return __any_sync(kFull, m);
 }
 
 // kept pT5: mark hits and seeds, list for the eta-phi tests, track candidates
@@ -390,15 +408,15 @@ __global__ void k_clean_pt5(Arena A) {
 
 __global__ void k_clean_pt3_cross(Arena A, DevCfg c) {
     const int n3 = min(A.counters[5], A.pt3_cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n3; i += warps) {
         if (!A.keep_pt3[i]) continue;
         ObjHits o;
         object_hits(A, 1, i, o);
-        int g = A.pt3_seed[i];
-        bool drop = (A.seed_link[g] & 1) != 0;
-        for (int j = 3; j < o.n && !drop; ++j) drop = (A.mark[o.slots[j]] & 1) != 0;
-        if (!drop) drop = dr_close(A, c, o.e, 0, A.pls_eta[g], A.pls_phi[g]);
-        A.keep_pt3[i] = !drop;
+        const int g = A.pt3_seed[i];
+        bool drop = (A.seed_link[g] & 1) != 0 || marked_warp(A, o, 3, 1);
+        if (!drop) drop = dr_close_warp(A, c, o.e, 0, A.pls_eta[g], A.pls_phi[g]);
+        if (lane_id() == 0) A.keep_pt3[i] = !drop;
     }
 }
 
@@ -420,29 +438,34 @@ __global__ void k_clean_pt3_mark(Arena A) {
 
 __global__ void k_clean_t5(Arena A, DevCfg c) {
     const int nt = min(A.counters[3], A.t5_cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nt; i += warps) {
         if (!A.keep_t5[i]) continue;
         ObjHits o;
         object_hits(A, 2, i, o);
-        bool drop = false;
-        for (int j = 0; j < o.n && !drop; ++j) drop = (A.mark[o.slots[j]] & 3) != 0;
-        if (!drop) drop = dr_close(A, c, o.e, 0, A.t5_eta[i], A.t5_phi[i]);
-        A.keep_t5[i] = !drop;
-        if (drop) continue;
-        list_append(A, o.e, 1, float(A.t5_eta[i]), float(A.t5_phi[i]), (2 << 28) | i);
-        int m[5];
-        pt_mds<5>(A, i, m);
-        tc_append(A, o.e, 2, -1, i, m, 5, A.t5_pt[i], float(A.t5_eta[i]), float(A.t5_phi[i]));
+        bool drop = marked_warp(A, o, 0, 3);
+        if (!drop) drop = dr_close_warp(A, c, o.e, 0, A.t5_eta[i], A.t5_phi[i]);
+        if (lane_id() == 0) {
+            A.keep_t5[i] = !drop;
+            if (!drop) {
+                list_append(A, o.e, 1, float(A.t5_eta[i]), float(A.t5_phi[i]), (2 << 28) | i);
+                int m[5];
+                pt_mds<5>(A, i, m);
+                tc_append(A, o.e, 2, -1, i, m, 5, A.t5_pt[i], float(A.t5_eta[i]), float(A.t5_phi[i]));
+            }
+        }
     }
 }
 
 __global__ void k_clean_pls(Arena A, DevCfg c) {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < A.n_seeds; g += gridDim.x * blockDim.x) {
+    const int n_ev = A.bd->n_ev, n_seeds = A.bd->n_seeds;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < n_seeds; g += warps) {
         if (!A.pls_pass[g] || A.seed_link[g]) continue;
-        int e = event_of(A.seed_off, A.n_ev, g);
+        int e = event_of(A.seed_off, n_ev, g);
         double eta = A.pls_eta[g], phi = A.pls_phi[g];
-        if (dr_close(A, c, e, 0, eta, phi) || dr_close(A, c, e, 1, eta, phi)) continue;
-        tc_append(A, e, 3, g - A.seed_off[e], g, nullptr, 0, A.pls_pt[g], float(eta), float(phi));
+        if (dr_close_warp(A, c, e, 0, eta, phi) || dr_close_warp(A, c, e, 1, eta, phi)) continue;
+        if (lane_id() == 0) tc_append(A, e, 3, g - A.seed_off[e], g, nullptr, 0, A.pls_pt[g], float(eta), float(phi));
     }
 }
 

@@ -56,6 +56,13 @@ struct lst_ctx {
     int launches = 0;
     std::vector<int> hit_off_host, seed_off_host;
     bool profiling = false;
+    bool use_graph = true;
+    BatchDesc* d_bd = nullptr;        // device batch descriptor
+    BatchDesc* h_bd = nullptr;        // pinned staging of the descriptor
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    static constexpr int kMaxLaunch = 32;
+    int grid_mul[kMaxLaunch] = {};    // blocks per SM of each launch slot (0: the default)
     static constexpr int kMaxProf = 64;
     cudaEvent_t prof_ev[2 * kMaxProf] = {};
     const char* prof_name[kMaxProf] = {};
@@ -143,7 +150,9 @@ lst_status lst_create(lst_ctx** out, const lst_config* cfg, const lst_capacity* 
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost(&c->h_offsets, sizeof(int) * 2 * (cap->max_events + 1)) != cudaSuccess) {
+        cudaMallocHost(&c->h_offsets, sizeof(int) * 2 * (cap->max_events + 1)) != cudaSuccess ||
+        cudaMallocHost(&c->h_bd, sizeof(BatchDesc)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete c;
         return LST_ERR_CUDA;
     }
@@ -158,8 +167,11 @@ void lst_destroy(lst_ctx* c) {
         cudaEventSynchronize(c->done);
         cudaEventDestroy(c->done);
     }
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->dev_mem) cudaFree(c->dev_mem);
     if (c->h_offsets) cudaFreeHost(c->h_offsets);
+    if (c->h_bd) cudaFreeHost(c->h_bd);
     for (cudaEvent_t& e : c->prof_ev)
         if (e) cudaEventDestroy(e);
     delete c;
@@ -182,6 +194,11 @@ static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_m
     A.sb_tgt = b.take<int>(n_sbt);
     c->d_hit_off = b.take<int>(E + 1);
     c->d_seed_off = b.take<int>(E + 1);
+    c->d_bd = b.take<BatchDesc>(1);
+    A.bd = c->d_bd;
+    A.max_events = (int)E;
+    A.hit_off = c->d_hit_off;
+    A.seed_off = c->d_seed_off;
     c->in_x = b.take<float>(H);
     c->in_y = b.take<float>(H);
     c->in_z = b.take<float>(H);
@@ -195,6 +212,8 @@ static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_m
     A.sz = b.take<float>(H);
     A.sidx = b.take<int>(H);
     A.counters = b.take<int>(32);
+    A.ovf_cap = 4096;
+    A.ovf_list = b.take<int>(A.ovf_cap);
     A.ev_counts = b.take<int>(E * 8);
     A.ev_drop = b.take<int>(E * 8);
     const size_t MD = E * K.md_per_event;
@@ -289,14 +308,59 @@ lst_status lst_load_geometry(lst_ctx* c, const lst_module* mods, int32_t n_mod, 
     CK(cudaMemcpy((void*)c->A.sb_off, sb_off, sizeof(int) * (n_sb + 1), cudaMemcpyHostToDevice));
     if (n_sbt) CK(cudaMemcpy((void*)c->A.sb_tgt, sb_tgt, sizeof(int) * n_sbt, cudaMemcpyHostToDevice));
     CK(cudaFuncSetAttribute(k_md, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)md_smem_bytes()));
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
     c->geometry = true;
     c->ran = false;
     return LST_OK;
 }
 
-static int grid_for(int n, int block, int cap_blocks) {
-    int g = (n + block - 1) / block;
-    return std::max(1, std::min(g, cap_blocks));
+
+// The launch sequence of one batch (Fig. KernelFlow order). Grids are fixed
+// per context (grid-stride loops read the batch shape from the descriptor),
+// so the sequence can be captured once into a CUDA graph.
+static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile) {
+    const Arena& A = c->A;
+    const DevCfg& dc = c->dc;
+    const int nsm = c->n_sm;
+    int L = 0;
+    auto G = [&](int def) { int m = c->grid_mul[L]; return nsm * (m > 0 ? m : def); };
+#define LAUNCH(NAME, ...)                                                              \
+    do {                                                                               \
+        if (profile && L < lst_ctx::kMaxProf) {                                        \
+            c->prof_name[L] = NAME;                                                    \
+            cudaEventRecord(c->prof_ev[2 * L], st);                                    \
+        }                                                                              \
+        __VA_ARGS__;                                                                   \
+        if (profile && L < lst_ctx::kMaxProf) cudaEventRecord(c->prof_ev[2 * L + 1], st); \
+        ++L;                                                                           \
+    } while (0)
+    LAUNCH("reset", k_reset<<<G(8), 256, 0, st>>>(A));
+    LAUNCH("bin_count", k_bin_count<<<G(8), 256, 0, st>>>(A));
+    LAUNCH("bin_scan", k_bin_scan<<<A.max_events, 1024, 0, st>>>(A));
+    LAUNCH("bin_scatter", k_bin_scatter<<<G(8), 256, 0, st>>>(A));
+    LAUNCH("md", k_md<<<G(4), kMdWarps * 32, md_smem_bytes(), st>>>(A, dc));
+    LAUNCH("ls", k_ls<<<G(8), kLsWarps * 32, 0, st>>>(A, dc));
+    LAUNCH("t3", k_t3<<<G(8), kT3Warps * 32, 0, st>>>(A, dc));
+    LAUNCH("t5", k_t5<<<G(6), kT5Warps * 32, 0, st>>>(A, dc));
+    LAUNCH("t5_overflow", k_t5_overflow<<<nsm, kT5Warps * 32, 0, st>>>(A, dc));
+    LAUNCH("t5_refine", k_t5_refine<<<G(4), 128, 0, st>>>(A, dc));
+    LAUNCH("pls", k_pls<<<G(4), 128, 0, st>>>(A, dc));
+    LAUNCH("pt5", k_pt5<<<G(8), kPtWarps * 32, 0, st>>>(A, dc));
+    LAUNCH("pt5_refine", k_pt5_refine<<<G(2), 128, 0, st>>>(A, dc));
+    LAUNCH("pt3", k_pt3<<<G(8), kPtWarps * 32, 0, st>>>(A, dc));
+    LAUNCH("pt3_refine", k_pt3_refine<<<G(2), 128, 0, st>>>(A, dc));
+    LAUNCH("clean_keys", k_clean_keys<<<G(4), 256, 0, st>>>(A, 0));
+    LAUNCH("clean_keep", k_clean_keys<<<G(4), 256, 0, st>>>(A, 1));
+    LAUNCH("clean_pt5", k_clean_pt5<<<G(2), 256, 0, st>>>(A));
+    LAUNCH("clean_pt3_cross", k_clean_pt3_cross<<<G(2), 256, 0, st>>>(A, dc));
+    LAUNCH("clean_pt3_mark", k_clean_pt3_mark<<<G(2), 256, 0, st>>>(A));
+    LAUNCH("clean_t5", k_clean_t5<<<G(4), 256, 0, st>>>(A, dc));
+    LAUNCH("clean_pls", k_clean_pls<<<G(4), 128, 0, st>>>(A, dc));
+#undef LAUNCH
+    c->launches = L;
 }
 
 lst_status lst_run_batch(lst_ctx* c, const lst_hits* hits, const int32_t* hit_off, const lst_seeds* seeds,
@@ -315,23 +379,19 @@ lst_status lst_run_batch(lst_ctx* c, const lst_hits* hits, const int32_t* hit_of
     CK(cudaSetDevice(c->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream_);
     if (c->ran) CK(cudaEventSynchronize(c->done));   // the pinned staging is reused
-    Arena& A = c->A;
-    A.n_ev = n_ev;
-    A.n_hits = hits->n;
-    A.n_seeds = seeds->n;
     c->n_ev = n_ev;
     c->hit_off_host.assign(hit_off, hit_off + n_ev + 1);
     c->seed_off_host.assign(seed_off, seed_off + n_ev + 1);
     std::memcpy(c->h_offsets, hit_off, sizeof(int) * (n_ev + 1));
     std::memcpy(c->h_offsets + n_ev + 1, seed_off, sizeof(int) * (n_ev + 1));
-    CK(cudaMemcpyAsync(c->d_hit_off, c->h_offsets, sizeof(int) * (n_ev + 1), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->d_seed_off, c->h_offsets + n_ev + 1, sizeof(int) * (n_ev + 1), cudaMemcpyHostToDevice, st));
-    A.hit_off = c->d_hit_off;
-    A.seed_off = c->d_seed_off;
     const size_t H = hits->n, S = seeds->n;
+    BatchDesc& d = *c->h_bd;
+    d.n_ev = n_ev;
+    d.n_hits = (int)H;
+    d.n_seeds = (int)S;
     if (mem_is_device) {
-        A.hx = hits->x; A.hy = hits->y; A.hz = hits->z; A.hmod = hits->module; A.hside = hits->side;
-        A.seeds = seeds->xyz;
+        d.hx = hits->x; d.hy = hits->y; d.hz = hits->z; d.hmod = hits->module; d.hside = hits->side;
+        d.seeds = seeds->xyz;
     } else {
         if (H) {
             CK(cudaMemcpyAsync(c->in_x, hits->x, 4 * H, cudaMemcpyHostToDevice, st));
@@ -341,59 +401,31 @@ lst_status lst_run_batch(lst_ctx* c, const lst_hits* hits, const int32_t* hit_of
             CK(cudaMemcpyAsync(c->in_side, hits->side, H, cudaMemcpyHostToDevice, st));
         }
         if (S) CK(cudaMemcpyAsync(c->in_seeds, seeds->xyz, 36 * S, cudaMemcpyHostToDevice, st));
-        A.hx = c->in_x; A.hy = c->in_y; A.hz = c->in_z; A.hmod = c->in_mod; A.hside = c->in_side;
-        A.seeds = c->in_seeds;
+        d.hx = c->in_x; d.hy = c->in_y; d.hz = c->in_z; d.hmod = c->in_mod; d.hside = c->in_side;
+        d.seeds = c->in_seeds;
     }
-    const size_t nb = (size_t)n_ev * 2 * A.n_mod;
-    const size_t NK = H + 3 * S;
-    CK(cudaMemsetAsync(A.counters, 0, sizeof(int) * 32, st));
-    CK(cudaMemsetAsync(A.ev_counts, 0, sizeof(int) * 8 * n_ev, st));
-    CK(cudaMemsetAsync(A.ev_drop, 0, sizeof(int) * 8 * n_ev, st));
-    CK(cudaMemsetAsync(A.bcnt, 0, sizeof(int) * nb, st));
-    CK(cudaMemsetAsync(A.best, 0xff, sizeof(unsigned long long) * 3 * NK, st));
-    CK(cudaMemsetAsync(A.mark, 0, sizeof(int) * std::max<size_t>(NK, 1), st));
-    CK(cudaMemsetAsync(A.seed_link, 0, sizeof(int) * std::max<size_t>(S, 1), st));
-    CK(cudaMemsetAsync(A.list_cnt, 0, sizeof(int) * 2 * n_ev, st));
-    CK(cudaMemsetAsync(A.tc_cnt, 0, sizeof(int) * n_ev, st));
-    // The best-key arrays are laid out for the context's capacity; index them
-    // with this batch's key count.
-    const int nsm = c->n_sm;
-    const DevCfg& dc = c->dc;
-    int L = 0;
-    // each launch is bracketed by a CUDA event pair when profiling is on
-#define LAUNCH(NAME, ...)                                                              \
-    do {                                                                               \
-        if (c->profiling && L < lst_ctx::kMaxProf) {                                   \
-            c->prof_name[L] = NAME;                                                    \
-            cudaEventRecord(c->prof_ev[2 * L], st);                                    \
-        }                                                                              \
-        __VA_ARGS__;                                                                   \
-        if (c->profiling && L < lst_ctx::kMaxProf) cudaEventRecord(c->prof_ev[2 * L + 1], st); \
-        ++L;                                                                           \
-    } while (0)
-    LAUNCH("bin_count", k_bin_count<<<grid_for((int)H, 256, nsm * 8), 256, 0, st>>>(A));
-    LAUNCH("bin_scan", k_bin_scan<<<n_ev, 1024, 0, st>>>(A));
-    LAUNCH("bin_scatter", k_bin_scatter<<<grid_for((int)H, 256, nsm * 8), 256, 0, st>>>(A));
-    LAUNCH("md", k_md<<<nsm * 4, kMdWarps * 32, md_smem_bytes(), st>>>(A, dc));
-    LAUNCH("ls", k_ls<<<nsm * 8, kLsWarps * 32, 0, st>>>(A, dc));
-    LAUNCH("t3", k_t3<<<nsm * 8, kT3Warps * 32, 0, st>>>(A, dc));
-    LAUNCH("t5", k_t5<<<nsm * 6, kT5Warps * 32, 0, st>>>(A, dc));
-    LAUNCH("t5_refine", k_t5_refine<<<nsm * 4, 128, 0, st>>>(A, dc));
-    LAUNCH("pls", k_pls<<<grid_for((int)S, 128, nsm * 4), 128, 0, st>>>(A, dc));
-    LAUNCH("pt5", k_pt5<<<nsm * 8, kPtWarps * 32, 0, st>>>(A, dc));
-    LAUNCH("pt5_refine", k_pt5_refine<<<nsm * 2, 128, 0, st>>>(A, dc));
-    LAUNCH("pt3", k_pt3<<<nsm * 8, kPtWarps * 32, 0, st>>>(A, dc));
-    LAUNCH("pt3_refine", k_pt3_refine<<<nsm * 2, 128, 0, st>>>(A, dc));
-    LAUNCH("clean_keys", k_clean_keys<<<nsm * 4, 256, 0, st>>>(A, 0));
-    LAUNCH("clean_keep", k_clean_keys<<<nsm * 4, 256, 0, st>>>(A, 1));
-    LAUNCH("clean_pt5", k_clean_pt5<<<nsm * 2, 256, 0, st>>>(A));
-    LAUNCH("clean_pt3_cross", k_clean_pt3_cross<<<nsm * 2, 256, 0, st>>>(A, dc));
-    LAUNCH("clean_pt3_mark", k_clean_pt3_mark<<<nsm * 2, 256, 0, st>>>(A));
-    LAUNCH("clean_t5", k_clean_t5<<<nsm * 4, 256, 0, st>>>(A, dc));
-    LAUNCH("clean_pls", k_clean_pls<<<grid_for((int)S, 128, nsm * 4), 128, 0, st>>>(A, dc));
-#undef LAUNCH
-    c->launches = L;
-    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->d_hit_off, c->h_offsets, sizeof(int) * (n_ev + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_seed_off, c->h_offsets + n_ev + 1, sizeof(int) * (n_ev + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_bd, c->h_bd, sizeof(BatchDesc), cudaMemcpyHostToDevice, st));
+    if (c->profiling || !c->use_graph) {
+        enqueue_chain(c, st, c->profiling);
+        CK(cudaGetLastError());
+    } else {
+        if (!c->graph) {
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            enqueue_chain(c, c->cap_stream, false);
+            cudaError_t e1 = cudaStreamEndCapture(c->cap_stream, &g);
+            if (e1 != cudaSuccess) return LST_ERR_CUDA;
+            cudaError_t e2 = cudaGraphInstantiate(&c->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e2 != cudaSuccess) {
+                c->graph = nullptr;
+                return LST_ERR_CUDA;
+            }
+        }
+        CK(cudaGraphLaunch(c->graph, st));
+    }
     CK(cudaEventRecord(c->done, st));
     c->ran = true;
     return LST_OK;
@@ -448,6 +480,15 @@ static lst_status wait_batch(lst_ctx* c, int32_t event) {
         lst_status s__ = fetch(v, d, n);        \
         if (s__ != LST_OK) return s__;          \
     } while (0)
+
+lst_status lst_get_counters(lst_ctx* c, int32_t* out, int32_t n) {
+    if (!c || !out || n < 0 || n > 32) return LST_ERR_ARG;
+    if (!c->ran) return LST_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cudaEventSynchronize(c->done));
+    if (n) CK(cudaMemcpy(out, c->A.counters, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    return LST_OK;
+}
 
 lst_status lst_get_stats(lst_ctx* c, int32_t event, lst_stats* out) {
     lst_status s = wait_batch(c, event);

@@ -42,6 +42,17 @@ struct DevCfg {
     double dr_clean, k_field, b_field;
 };
 
+// Shape and inputs of the batch being processed (device memory).
+struct BatchDesc {
+    int n_ev, n_hits, n_seeds, pad;
+    const float* hx;
+    const float* hy;
+    const float* hz;
+    const int* hmod;
+    const uint8_t* hside;
+    const float* seeds;           // [n_seeds][9]
+};
+
 // Device buffers of one context (all preallocated; flat object arenas with
 // per-unit segments).
 struct Arena {
@@ -52,16 +63,12 @@ struct Arena {
     const int* conn_tgt;
     const int* sb_off;
     const int* sb_tgt;
-    // batch
-    int n_ev, n_hits, n_seeds;
+    // batch: shape and input pointers are read from device memory so that one
+    // captured launch sequence serves every batch
+    const struct BatchDesc* bd;
+    int max_events;
     const int* hit_off;           // [n_ev + 1]
     const int* seed_off;          // [n_ev + 1]
-    const float* hx;
-    const float* hy;
-    const float* hz;
-    const int* hmod;
-    const uint8_t* hside;
-    const float* seeds;           // [n_seeds][9]
     // hit binning: bucket (e, module, side) = e * 2 n_mod + 2 module + side
     int* bcnt;                    // [n_ev * 2 n_mod]: counts, then scatter cursors
     int* boff;                    // [n_ev * (2 n_mod + 1)]: offsets relative to hit_off[e]
@@ -69,8 +76,10 @@ struct Arena {
     float* sy;
     float* sz;
     int* sidx;                    // original hit index within the event
-    // counters: [0] MD [1] LS [2] T3 [3] T5 [4] pT5 [5] pT3, [8..15] dropped per kind, [16] bad hits
+    // counters: [0] MD [1] LS [2] T3 [3] T5 [4] pT5 [5] pT3, [16] bad hits, [20] T5 overflow units
     int* counters;
+    int ovf_cap;
+    int* ovf_list;                // inner MDs whose T5 survivors overflowed the stage
     int* ev_counts;               // [n_ev][8]
     int* ev_drop;                 // [n_ev][8]
     // MD

@@ -22,6 +22,7 @@ constexpr int kT3Warps = 8;
 constexpr int kT5Warps = 4;
 constexpr int kPtWarps = 4;
 
+__global__ void k_reset(Arena A);
 __global__ void k_bin_count(Arena A);
 __global__ void k_bin_scan(Arena A);
 __global__ void k_bin_scatter(Arena A);
@@ -29,6 +30,7 @@ __global__ void k_md(Arena A, DevCfg c);
 __global__ void k_ls(Arena A, DevCfg c);
 __global__ void k_t3(Arena A, DevCfg c);
 __global__ void k_t5(Arena A, DevCfg c);
+__global__ void k_t5_overflow(Arena A, DevCfg c);
 __global__ void k_t5_refine(Arena A, DevCfg c);
 __global__ void k_pls(Arena A, DevCfg c);
 __global__ void k_pt5(Arena A, DevCfg c);

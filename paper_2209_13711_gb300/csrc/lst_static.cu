@@ -32,6 +32,7 @@ constexpr int kStaticMaxMd = 131072;
 constexpr int kMaxDevices = 64;
 
 struct alignas(256) MdScratch {
+    BatchDesc bd;
     int hit_off[64];
     int counters[32];
     int ev_counts[32];
@@ -62,11 +63,21 @@ namespace {
 std::mutex g_setup_mutex;
 MdScratch* g_scratch_ptr[kMaxDevices] = {};
 
-__global__ void k_static_prepare(MdScratch* S, const lst_module* mods, int n_mod, int n_hits) {
+__global__ void k_static_prepare(MdScratch* S, const lst_module* mods, int n_mod, int n_hits, const float* x,
+                                 const float* y, const float* z, const int32_t* module, const uint8_t* side) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         S->hit_off[0] = 0;
         S->hit_off[1] = n_hits;
+        S->bd.n_ev = 1;
+        S->bd.n_hits = n_hits;
+        S->bd.n_seeds = 0;
+        S->bd.hx = x;
+        S->bd.hy = y;
+        S->bd.hz = z;
+        S->bd.hmod = module;
+        S->bd.hside = side;
+        S->bd.seeds = nullptr;
     }
     for (; i < n_mod; i += gridDim.x * blockDim.x)
         S->mod[i] = make_float4(mods[i].dsep, mods[i].sig_rphi, mods[i].sig_long, float(mods[i].subdet));
@@ -129,15 +140,9 @@ extern "C" lst_status lst_build_mini_doublets_static(const lst_config* cfg, cons
     Arena A{};
     A.n_mod = n_mod;
     A.mod = S->mod;
-    A.n_ev = 1;
-    A.n_hits = n_hits;
-    A.n_seeds = 0;
+    A.bd = &S->bd;
+    A.max_events = 1;
     A.hit_off = S->hit_off;
-    A.hx = x;
-    A.hy = y;
-    A.hz = z;
-    A.hmod = module;
-    A.hside = side;
     A.bcnt = S->bcnt;
     A.boff = S->boff;
     A.sx = S->sx;
@@ -172,7 +177,7 @@ extern "C" lst_status lst_build_mini_doublets_static(const lst_config* cfg, cons
         return LST_ERR_CUDA;
     const int hb = (n_hits + 255) / 256;
     const int hit_blocks = hb < 1 ? 1 : (hb > 8 * n_sm ? 8 * n_sm : hb);
-    k_static_prepare<<<(n_mod + 255) / 256, 256, 0, st>>>(S, modules, n_mod, n_hits);
+    k_static_prepare<<<(n_mod + 255) / 256, 256, 0, st>>>(S, modules, n_mod, n_hits, x, y, z, module, side);
     k_bin_count<<<hit_blocks, 256, 0, st>>>(A);
     k_bin_scan<<<1, 1024, 0, st>>>(A);
     k_bin_scatter<<<hit_blocks, 256, 0, st>>>(A);

@@ -91,10 +91,12 @@ def library():
         L.lst_get_stats.argtypes = [vp, i32, vp]
         L.lst_last_launch_count.argtypes = [vp]
         L.lst_set_profiling.argtypes = [vp, i32]
+        L.lst_get_counters.argtypes = [vp, vp, i32]
         L.lst_get_kernel_times.argtypes = [vp, i32, vp, vp, vp]
         for f in ("lst_config_default", "lst_capacity_default", "lst_create", "lst_load_geometry", "lst_run_batch",
                   "lst_run_event", "lst_get_track_candidates", "lst_object_columns", "lst_get_objects",
-                  "lst_get_stats", "lst_last_launch_count", "lst_set_profiling", "lst_get_kernel_times"):
+                  "lst_get_stats", "lst_last_launch_count", "lst_set_profiling", "lst_get_kernel_times",
+                  "lst_get_counters"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -217,6 +219,12 @@ class Context:
         return [(names[i].decode(), float(ms[i])) for i in range(n.value)]
 
     # -- results ----------------------------------------------------------
+    def counters(self):
+        """Batch-wide device counters (see lst_get_counters)."""
+        out = np.zeros(32, np.int32)
+        _check(library().lst_get_counters(self._h, _ptr(out), 32))
+        return out
+
     def stats(self, event=0):
         s = LstStats()
         _check(library().lst_get_stats(self._h, int(event), C.byref(s)))

@@ -56,6 +56,17 @@ def test_pu200_event_parity(ctx_full, geom_full, maps_full):
     assert s["t5"][0] > 10000 and s["tc"][0] > 2000
 
 
+def test_t5_stage_overflow_is_lossless(ctx_full, geom_full, maps_full):
+    """A PU200 event with an inner MD whose T5 candidates overflow the per-unit stage."""
+    ev = E.pu200_event(12, geom_full)
+    ctx_full.run([ev])
+    assert ctx_full.counters()[20] > 0
+    g = gpu_result(ctx_full)
+    _no_drops(g)
+    o = oracle_result(geom_full, maps_full, ev)
+    compare(g, o, A_HALF, DEFAULT_CUTS)
+
+
 def _all_tuples(ctx, event):
     g = gpu_result(ctx, event)
     T = chain_tuples(g)
