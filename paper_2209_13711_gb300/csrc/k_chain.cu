@@ -423,7 +423,13 @@ __global__ void __launch_bounds__(kT3Warps * 32) k_t3(Arena A, DevCfg c) {
 struct T5Smem {
     int pre[32], off[32], t1[32];
     int2 cand[kT5Pre];
-    int2 stage[kT5Stage];      // passing (T3_1, T3_2); outputs are recomputed when written
+    int2 stage[kT5Stage];      // passing (T3_1, T3_2)
+};
+
+// per-warp scratch of the overflow pass (no stage)
+struct T5OvfSmem {
+    int pre[32], off[32], t1[32];
+    int2 cand[kT5Pre];
 };
 
 __device__ __forceinline__ void t5_mds(const Arena& A, int2 pr, int* m) {
@@ -445,31 +451,39 @@ __device__ __forceinline__ bool t5_prefit_f32(const Arena& A, const DevCfg& c, i
     return fit_may_pass(c, k, c2, cz, float(c.chi2_rphi_t5), float(c.chi2_rz_t5));
 }
 
-// Collected candidates: FP32 fit prefilter; every group of 32 verdicts is
-// handed to the sink in candidate order (the sink places the survivors).
-template <typename Sink>
-__device__ __forceinline__ void t5_flush(const Arena& A, const DevCfg& c, T5Smem& S, int ncand, Sink& sink) {
+// Collected candidates: FP32 fit prefilter; the verdicts of each group of 32
+// are written to `keep` bits in candidate order (one out-of-line copy of the
+// fit keeps the kernel's instruction footprint small).
+__device__ __noinline__ unsigned t5_prefit_group(const Arena& A, const DevCfg& c, const int2* cand, int q, int n) {
+    bool keep = q < n && t5_prefit_f32(A, c, cand[q]);
+    return __ballot_sync(kFull, keep);
+}
+
+template <typename Smem, typename Sink>
+__device__ __forceinline__ void t5_flush(const Arena& A, const DevCfg& c, Smem& S, int ncand, Sink& sink) {
     const int lane = lane_id();
     for (int base = 0; base < ncand; base += 32) {
         int q = base + lane;
-        int2 pr = q < ncand ? S.cand[q] : make_int2(0, 0);
-        bool keep = q < ncand && t5_prefit_f32(A, c, pr);
-        int tot;
-        int r = warp_rank(keep, tot);
-        sink(keep, pr, r, tot);
+        unsigned m = t5_prefit_group(A, c, S.cand, q, ncand);
+        bool keep = (m >> lane) & 1u;
+        int tot = __popc(m);
+        int r = __popc(m & ((1u << lane) - 1u));
+        sink(keep, q < ncand ? S.cand[q] : make_int2(0, 0), r, tot);
     }
     __syncwarp();
 }
 
-// All candidates of inner MD i in a fixed order: (T3_1 from i) x (T3_2 from
-// T3_1's outer MD), curvature prefilter, FP32 fit prefilter, then the sink.
-template <typename Sink>
-__device__ __forceinline__ void t5_enumerate(const Arena& A, const DevCfg& c, T5Smem& S, int i, Sink& sink) {
+// Candidates of inner MD i whose T3_1 lies in chunks [c0, c1) (32 T3 each),
+// in a fixed order: (T3_1) x (T3_2 from T3_1's outer MD), curvature
+// prefilter, FP32 fit prefilter, then the sink.
+template <typename Smem, typename Sink>
+__device__ __forceinline__ void t5_enumerate(const Arena& A, const DevCfg& c, Smem& S, int i, int c0, int c1,
+                                             Sink& sink) {
     const int lane = lane_id();
     const float nk = float(c.n_t5);
     const int s0 = A.t3_off[i], s1 = s0 + A.t3_cnt[i];
     int ncand = 0;
-    for (int cb = s0; cb < s1; cb += 32) {
+    for (int cb = s0 + 32 * c0; cb < s1 && cb < s0 + 32 * c1; cb += 32) {
         int t1 = cb + lane;
         int off = 0, len = 0;
         if (t1 < s1) {
@@ -507,7 +521,7 @@ __device__ __forceinline__ void t5_enumerate(const Arena& A, const DevCfg& c, T5
 // T5 search (FP32 only): one warp per inner MD. The survivors are written as
 // the MD's T5 segment; k_t5_refine decides them in FP64. A unit with more
 // survivors than the stage holds is queued for k_t5_overflow.
-__global__ void __launch_bounds__(kT5Warps * 32) k_t5(Arena A, DevCfg c) {
+__global__ void __launch_bounds__(kT5Warps * 32, 6) k_t5(Arena A, DevCfg c) {
     __shared__ T5Smem sm[kT5Warps];
     T5Smem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -522,7 +536,7 @@ __global__ void __launch_bounds__(kT5Warps * 32) k_t5(Arena A, DevCfg c) {
             if (keep && cnt + r < kT5Stage) S.stage[cnt + r] = pr;
             cnt += tot;
         };
-        t5_enumerate(A, c, S, i, sink);
+        t5_enumerate(A, c, S, i, 0, 1 << 20, sink);
         if (cnt > kT5Stage) {
             if (lane == 0) {
                 A.t5_off[i] = 0;
@@ -550,35 +564,61 @@ __global__ void __launch_bounds__(kT5Warps * 32) k_t5(Arena A, DevCfg c) {
     }
 }
 
-// Units whose survivors overflowed the stage: count, reserve, then enumerate
-// again writing straight to the arena in the same order.
-__global__ void __launch_bounds__(kT5Warps * 32) k_t5_overflow(Arena A, DevCfg c) {
-    __shared__ T5Smem sm[kT5Warps];
-    T5Smem& S = sm[threadIdx.x >> 5];
-    const int lane = lane_id();
+// Units whose survivors overflowed the stage: one block per unit, its warps
+// take the unit's chunks of 32 T3_1; per-chunk counts, a scan, one
+// reservation, then every chunk is enumerated again and written at its offset
+// (the same order as one warp would produce).
+constexpr int kOvfWarps = 8;
+constexpr int kOvfChunks = (kT3Stage + 31) / 32;
+
+__global__ void __launch_bounds__(kOvfWarps * 32) k_t5_overflow(Arena A, DevCfg c) {
+    __shared__ T5OvfSmem sm[kOvfWarps];
+    __shared__ int chunk_cnt[kOvfChunks + 1];
+    __shared__ int s_base, s_n;
+    T5OvfSmem& S = sm[threadIdx.x >> 5];
+    const int w = threadIdx.x >> 5, lane = lane_id();
     const int n_ovf = min(A.counters[20], A.ovf_cap);
-    for (int k = blockIdx.x * kT5Warps + (threadIdx.x >> 5); k < n_ovf; k += gridDim.x * kT5Warps) {
+    for (int k = blockIdx.x; k < n_ovf; k += gridDim.x) {
         const int i = A.ovf_list[k];
-        int cnt = 0;
-        auto count = [&](bool, int2, int, int tot) { cnt += tot; };
-        t5_enumerate(A, c, S, i, count);
-        int n = cnt, dropped = 0;
-        const int base = reserve(&A.counters[3], A.t5_cap, n, dropped);
-        int w = 0;
-        auto write = [&](bool keep, int2 pr, int r, int tot) {
-            if (keep && w + r < n) {
-                A.t5_in[base + w + r] = pr.x;
-                A.t5_out[base + w + r] = pr.y;
+        const int n_chunks = (A.t3_cnt[i] + 31) / 32;
+        for (int ch = w; ch < n_chunks; ch += kOvfWarps) {
+            int cnt = 0;
+            auto count = [&](bool, int2, int, int tot) { cnt += tot; };
+            t5_enumerate(A, c, S, i, ch, ch + 1, count);
+            if (lane == 0) chunk_cnt[ch] = cnt;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int ch = 0; ch < n_chunks; ++ch) {
+                int v = chunk_cnt[ch];
+                chunk_cnt[ch] = run;
+                run += v;
             }
-            w += tot;
-        };
-        t5_enumerate(A, c, S, i, write);
-        if (lane == 0) {
+            int n = run, dropped = 0, base = 0;
+            base = n > 0 ? atomicAdd(&A.counters[3], n) : 0;
+            int fit = n > 0 ? max(0, min(n, A.t5_cap - base)) : 0;
+            dropped = n - fit;
+            s_base = base;
+            s_n = fit;
             A.t5_off[i] = base;
-            A.t5_cnt[i] = n;
+            A.t5_cnt[i] = fit;
             if (dropped) atomicAdd(&A.ev_drop[(A.md_gmod[i] / A.n_mod) * 8 + 3], dropped);
         }
-        __syncwarp();
+        __syncthreads();
+        const int base = s_base, n = s_n;
+        for (int ch = w; ch < n_chunks; ch += kOvfWarps) {
+            int wr = chunk_cnt[ch];
+            auto write = [&](bool keep, int2 pr, int r, int tot) {
+                if (keep && wr + r < n) {
+                    A.t5_in[base + wr + r] = pr.x;
+                    A.t5_out[base + wr + r] = pr.y;
+                }
+                wr += tot;
+            };
+            t5_enumerate(A, c, S, i, ch, ch + 1, write);
+        }
+        __syncthreads();
     }
 }
 

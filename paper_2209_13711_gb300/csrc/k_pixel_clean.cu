@@ -86,18 +86,24 @@ __device__ __forceinline__ bool pt_prefit_f32(const Arena& A, const DevCfg& c, i
                         float(NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3));
 }
 
+// FP32 fit verdicts of one group of 32 candidates (one out-of-line copy).
+template <int NT>
+__device__ __noinline__ unsigned pt_prefit_group(const Arena& A, const DevCfg& c, int g, const int* cand, int q, int n) {
+    bool keep = q < n && pt_prefit_f32<NT>(A, c, g, cand[q]);
+    return __ballot_sync(kFull, keep);
+}
+
 // Collected candidates: FP32 fit prefilter; survivors are appended to the stage.
 template <int NT>
 __device__ __forceinline__ void pt_flush(const Arena& A, const DevCfg& c, PtSmem& S, int g, int ncand, int& cnt) {
     const int lane = lane_id();
     for (int base = 0; base < ncand; base += 32) {
         int q = base + lane;
-        int obj = q < ncand ? S.cand[q] : 0;
-        bool keep = q < ncand && pt_prefit_f32<NT>(A, c, g, obj);
-        int tot;
-        int r = warp_rank(keep, tot);
-        if (keep && cnt + r < kPtStage) S.stage[cnt + r] = obj;
-        cnt += tot;
+        unsigned m = pt_prefit_group<NT>(A, c, g, S.cand, q, ncand);
+        bool keep = (m >> lane) & 1u;
+        int r = __popc(m & ((1u << lane) - 1u));
+        if (keep && cnt + r < kPtStage) S.stage[cnt + r] = S.cand[q];
+        cnt += __popc(m);
     }
     __syncwarp();
 }

@@ -345,7 +345,7 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile) {
     LAUNCH("ls", k_ls<<<G(8), kLsWarps * 32, 0, st>>>(A, dc));
     LAUNCH("t3", k_t3<<<G(8), kT3Warps * 32, 0, st>>>(A, dc));
     LAUNCH("t5", k_t5<<<G(6), kT5Warps * 32, 0, st>>>(A, dc));
-    LAUNCH("t5_overflow", k_t5_overflow<<<nsm, kT5Warps * 32, 0, st>>>(A, dc));
+    LAUNCH("t5_overflow", k_t5_overflow<<<nsm, 256, 0, st>>>(A, dc));
     LAUNCH("t5_refine", k_t5_refine<<<G(4), 128, 0, st>>>(A, dc));
     LAUNCH("pls", k_pls<<<G(4), 128, 0, st>>>(A, dc));
     LAUNCH("pt5", k_pt5<<<G(8), kPtWarps * 32, 0, st>>>(A, dc));

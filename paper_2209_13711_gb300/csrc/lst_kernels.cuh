@@ -12,7 +12,7 @@ constexpr int kMdStage = 1024;    // MDs per module
 constexpr int kLsStage = 256;     // LS per inner MD
 constexpr int kT3Stage = 512;     // T3 per inner MD
 constexpr int kT5Pre = 256;       // FP32-prefiltered T5 candidates held before an FP64 pass
-constexpr int kT5Stage = 1024;    // T5 per inner MD
+constexpr int kT5Stage = 512;     // T5 candidates per inner MD (more: lossless overflow pass)
 constexpr int kPtPre = 128;       // prefiltered pT3/pT5 candidates held before an FP64 pass
 constexpr int kPtStage = 256;     // pT3/pT5 candidates per pixel seed
 
