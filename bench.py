@@ -224,6 +224,7 @@ def run_ours(args):
         "dropped_per_event": stats0["dropped"],
     }
     out["batched"] = measure_batched(P, E, geom, maps, DEFAULT_CUTS, flush, st, steps=max(2, min(args.steps, 5)))
+    out["mlp"] = measure_mlp(P, E, geom, maps, DEFAULT_CUTS, flush, st, dev[args.warmup:])
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(out))
@@ -278,6 +279,48 @@ def measure_batched(P, E, geom, maps, cuts, flush, st, steps, n_batch=64):
             "launch": "one CUDA graph per batch", "dropped_objects": int(dropped),
             "plain_same_events": {"value": round(n_batch / (ms1 / 1e3), 2), "unit": "events/s",
                                   "launch": "one graph per event"}}
+
+
+def measure_mlp(P, E, geom, maps, cuts, flush, st, dev_events):
+    """Network-scored T5 selection: trained here (16 PU200 events, the library's
+    own kernels), judged against the hand-set cuts on 4 other events at matched
+    efficiency, then timed on the benchmark's PU200 events."""
+    import torch
+    from paper_2209_13711_gb300 import train as T
+    from synth.mlp_init import init_params
+    t0 = time.perf_counter()
+    ctx = P.Context(geom.module_table(), maps, cfg=cuts, capacity=P.default_capacity(16))
+    ctx.set_t5_selection(None, prefilter_scale=3.0, capture_features=True)
+    tr = T.collect(ctx, [E.pu200_event(40000 + i, geom) for i in range(16)], batch=16)
+    va = T.collect(ctx, [E.pu200_event(41000 + i, geom) for i in range(4)], batch=16)
+    ctx.close()
+    mlp = P.Mlp(max_batch=4096, params=init_params(0))
+    T.train(mlp, tr["X"], tr["y"], epochs=3)
+    quality = T.evaluate(mlp, va)
+    train_s = time.perf_counter() - t0
+    ctx1 = P.Context(geom.module_table(), maps, cfg=cuts, capacity=P.default_capacity(1))
+    ctx1.set_t5_selection(mlp, threshold=quality["threshold"], prefilter_scale=3.0)
+    ctx1.run_packed(dev_events[0], stream=st.cuda_stream)
+    torch.cuda.synchronize()
+    ms = 0.0
+    for i, b in enumerate(dev_events):
+        flush.fill_(i & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ctx1.run_packed(b, stream=st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    st0 = ctx1.stats(0)
+    ctx1.close()
+    mlp.close()
+    return {"value": round(len(dev_events) / (ms / 1e3), 2), "unit": "events/s",
+            "selection": "T5 validity from the BF16 network (prefilter widened x3)",
+            "t5_per_event": st0["counts"]["t5"], "tc_per_event": st0["counts"]["tc"],
+            "quality_at_matched_efficiency": {"cut": quality["cut"], "network": quality["network"],
+                                              "threshold": round(quality["threshold"], 4),
+                                              "samples_train": int(len(tr["y"])), "samples_eval": int(len(va["y"]))},
+            "train_and_eval_s": round(train_s, 1)}
 
 
 def _oracle_event_seconds(seed):

@@ -216,6 +216,54 @@ lst_status lst_build_mini_doublets_static(const lst_config* cfg, const lst_modul
  * n (<= 32) values. */
 lst_status lst_get_counters(lst_ctx* ctx, int32_t* out, int32_t n);
 
+/* ---- learned T5 selection (the north-star's scoring network; the paper's
+ * own selection is the hand-set cuts of Section 2.1, which stay the default,
+ * the fallback and the judge) --------------------------------------------
+ * Network: LST_MLP_INPUTS inputs (LST_MLP_FEATURES features, zero padded) ->
+ * 64 -> 64 -> 32 -> 1, ReLU hidden, sigmoid output; BF16 weights and layer
+ * inputs on tensor cores with FP32 accumulation. Parameters are FP32, laid out
+ * as W1[64][48], b1[64], W2[64][64], b2[64], W3[32][64], b3[32], W4[32], b4. */
+#define LST_MLP_FEATURES 38
+#define LST_MLP_INPUTS 48
+#define LST_MLP_PARAMS 9409
+typedef struct lst_mlp lst_mlp;
+
+/* A network on `device` able to take gradients over batches of up to
+ * max_batch samples; parameters start at zero (set them). */
+lst_status lst_mlp_create(lst_mlp** out, int32_t device, int32_t max_batch);
+void lst_mlp_destroy(lst_mlp* m);
+/* Host parameter vector in / out (LST_MLP_PARAMS floats); set resets Adam. */
+lst_status lst_mlp_set_params(lst_mlp* m, const float* params);
+lst_status lst_mlp_get_params(lst_mlp* m, float* params);
+/* scores[i] = network(features[i]) for n samples (DEVICE pointers, features
+ * [n][LST_MLP_INPUTS]); asynchronous on stream. */
+lst_status lst_mlp_forward(lst_mlp* m, const float* features, int32_t n, float* scores, void* stream);
+/* Gradient of the mean binary cross-entropy over n <= max_batch samples
+ * (features, labels in {0,1}: DEVICE); grad (LST_MLP_PARAMS) and loss are
+ * HOST outputs (either may be NULL). Synchronous. */
+lst_status lst_mlp_gradient(lst_mlp* m, const float* features, const float* labels, int32_t n, float* grad,
+                            float* loss, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on that loss;
+ * loss (HOST, may be NULL) receives the loss before the step (synchronizes
+ * only when requested). */
+lst_status lst_mlp_train_step(lst_mlp* m, const float* features, const float* labels, int32_t n, float lr,
+                              float* loss, void* stream);
+
+/* T5 selection of a context: mlp = NULL keeps the hand-set cuts; otherwise a
+ * T5 candidate is valid when its network score >= threshold (and its fitted
+ * curvature is within the pT window). prefilter_scale >= 1 widens the FP32
+ * fit prefilter of the T5 search (more candidates for the network);
+ * capture_features = 1 computes the features even without a network (for
+ * training). The network must outlive its use by the context. */
+lst_status lst_set_t5_selection(lst_ctx* ctx, const lst_mlp* mlp, float threshold, float prefilter_scale,
+                                int32_t capture_features);
+/* All T5 candidates of an event (before the validity decision), HOST outputs:
+ * features [n][LST_MLP_INPUTS] (when captured), hits [n][10] (lower, upper
+ * of the five MDs), cut_pass [n] (the hand-set cut decision), score [n] (the
+ * network score when attached). Any output may be NULL. */
+lst_status lst_get_t5_candidates(lst_ctx* ctx, int32_t event, int32_t capacity, int32_t* n_out, float* features,
+                                 int32_t* hits, int32_t* cut_pass, float* score);
+
 /* Message of a status code (static storage). */
 const char* lst_status_str(lst_status s);
 

@@ -303,6 +303,8 @@ bool t3_eval(const OCfg& c, const Pt& A, const Pt& B, const Pt& C, T3& o, bool& 
 // circle normal.
 // --------------------------------------------------------------------------
 struct Fit { double kappa, chi2_rphi, chi2_rz, tanl; };
+// circle and line parameters of a fit (for the scoring features)
+struct FitParams { double gg, hh, kk, S, xx, xy, ox, oy, c0, t, t_hat; };
 
 bool solve3(double M[3][3], double b[3], double x[3]) {
     double A[3][4];
@@ -325,7 +327,7 @@ bool solve3(double M[3][3], double b[3], double x[3]) {
     return true;
 }
 
-Fit fit_track(const Pt* P, int n) {
+Fit fit_track(const Pt* P, int n, FitParams* fp = nullptr) {
     Fit f;
     const Pt& O = P[n / 2];
     double ex = P[n - 1].x - P[0].x, ey = P[n - 1].y - P[0].y;
@@ -346,7 +348,11 @@ Fit fit_track(const Pt* P, int n) {
         }
     }
     double sol[3] = {0, 0, 0};
-    if (!solve3(M, b, sol)) { f.kappa = 1e30; f.chi2_rphi = 1e30; f.chi2_rz = 1e30; f.tanl = 0; return f; }
+    if (!solve3(M, b, sol)) {
+        f.kappa = 1e30; f.chi2_rphi = 1e30; f.chi2_rz = 1e30; f.tanl = 0;
+        if (fp) *fp = FitParams{0, 0, 0, 1, xx, xy, O.x, O.y, 0, 0, 0};
+        return f;
+    }
     double gg = sol[0], hh = sol[1], kk = sol[2];
     double S = std::sqrt(std::max(0.0, 1.0 + hh * hh - 4.0 * gg * kk));
     f.kappa = 2.0 * gg / S;
@@ -382,7 +388,62 @@ Fit fit_track(const Pt* P, int n) {
     for (int i = 0; i < n; ++i) chi2z += w[i] * sq(P[i].z - c0 - t * s[i]);
     f.chi2_rz = chi2z;
     f.tanl = t;
+    if (fp) *fp = FitParams{gg, hh, kk, S, xx, xy, O.x, O.y, c0, t, t_hat};
     return f;
+}
+
+// ----------------------------------------------------------------------------
+// Scoring features of a T5 (the north-star's learned selection; the paper's
+// own selection is the cut set above). Hits H[0..9] = (lower, upper) of the
+// five MDs, anchors P = the lower hits; code = layer + 6 subdet.
+//   f[0..9]   signed distance of each hit to the fitted circle over its error
+//             projected on the circle normal, clipped to [-50, 50]
+//   f[10..19] (z - line(s)) sqrt(w) of each hit (s: arc length from P[0] on the
+//             fitted circle, w: the r-z fit weight), clipped to [-50, 50]
+//   f[20..24] anchor radius / 100
+//   f[25..27] inner-triplet, outer-triplet and fitted curvature over 2a
+//   f[28..29] log(1 + chi2_rphi), log(1 + chi2_rz)
+//   f[30..31] 10 x beta of the inner and outer triplet
+//   f[32]     eta of the r-z fit
+//   f[33..37] layer code / 11;  f[38..47] = 0
+// ----------------------------------------------------------------------------
+void t5_features(const OCfg& c, const Pt* P, const Pt* H, const int* code, double* f) {
+    FitParams F;
+    Fit fit = fit_track(P, 5, &F);
+    Tri ti = tri(P[0], P[1], P[2]);
+    Tri to = tri(P[2], P[3], P[4]);
+    const double ka = std::fabs(fit.kappa);
+    const double yx = -F.xy, yy = F.xx;
+    auto clip = [](double v) { return std::min(50.0, std::max(-50.0, v)); };
+    for (int j = 0; j < 10; ++j) {
+        const Pt& Q = H[j];
+        double dx = Q.x - F.ox, dy = Q.y - F.oy;
+        double xi = dx * F.xx + dy * F.xy, et = dx * yx + dy * yy;
+        double u = F.gg * (xi * xi + et * et) + F.hh * xi + F.kk - et;
+        double e = 2.0 * u / (F.S + std::sqrt(std::max(0.0, F.S * F.S + 4.0 * F.gg * u)));
+        double nlx = 2.0 * F.gg * xi + F.hh, nly = 2.0 * F.gg * et - 1.0;
+        double nx = nlx * F.xx + nly * yx, ny = nlx * F.xy + nly * yy;
+        double nn = std::hypot(nx, ny);
+        nx /= nn; ny /= nn;
+        double rx = Q.x / Q.r, ry = Q.y / Q.r;
+        double s2 = std::max(sq(Q.srphi * (-nx * ry + ny * rx)) + sq(Q.sr * (nx * rx + ny * ry)), sq(0.01 * Q.srphi));
+        f[j] = clip(e / std::sqrt(s2));
+        double sj = arc(std::hypot(Q.x - P[0].x, Q.y - P[0].y), ka);
+        double w = 1.0 / std::max(1e-12, sq(Q.sz) + sq(F.t_hat * Q.sr));
+        f[10 + j] = clip((Q.z - F.c0 - F.t * sj) * std::sqrt(w));
+    }
+    for (int j = 0; j < 5; ++j) f[20 + j] = P[j].r / 100.0;
+    const double two_a = 2.0 * half_curv_max(c);
+    f[25] = ti.kappa / two_a;
+    f[26] = to.kappa / two_a;
+    f[27] = fit.kappa / two_a;
+    f[28] = std::log1p(std::min(fit.chi2_rphi, 1e30));
+    f[29] = std::log1p(std::min(fit.chi2_rz, 1e30));
+    f[30] = 10.0 * ti.beta;
+    f[31] = 10.0 * to.beta;
+    f[32] = std::asinh(fit.tanl);
+    for (int j = 0; j < 5; ++j) f[33 + j] = code[j] / 11.0;
+    for (int j = 38; j < 48; ++j) f[j] = 0.0;
 }
 
 // Direction at the point of closest approach to the beam line, assuming a
@@ -1089,6 +1150,23 @@ int oracle_pt_d(const OCfg* c, const double* rows, int n, double kappa_pls, doub
                       n == 8 ? c->chi2_rz_pt5 : c->chi2_rz_pt3, o, near);
     out[0] = o.kappa; out[1] = o.chi2_rphi; out[2] = o.chi2_rz; out[3] = o.score; out[4] = near;
     return ok;
+}
+
+
+// Features of the T5 formed by five MDs given as (lower, upper) hit pairs of
+// the event: out[48].
+void oracle_t5_features(const OGeom* g, const OCfg* c, const OEvent* e, const int32_t* md_hits, double* out) {
+    Pt P[5], H[10];
+    int code[5];
+    for (int j = 0; j < 5; ++j) {
+        int hl = md_hits[2 * j], hu = md_hits[2 * j + 1];
+        P[j] = make_hit_point(*g, *e, hl);
+        H[2 * j] = P[j];
+        H[2 * j + 1] = make_hit_point(*g, *e, hu);
+        int m = e->module[hl];
+        code[j] = g->layer[m] + (g->subdet[m] ? 6 : 0);
+    }
+    t5_features(*c, P, H, code, out);
 }
 
 }  // extern "C"

@@ -66,6 +66,7 @@ def lib():
         L.oracle_pls.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_fit.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
         L.oracle_tri.argtypes = [C.c_void_p, C.c_void_p]
+        L.oracle_t5_features.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_md_d.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_ls_d.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                   C.c_void_p, C.c_void_p]
@@ -142,6 +143,13 @@ class Setup:
         ok = lib().oracle_pred_md(C.byref(self.geom), C.byref(self.cfg), C.byref(self.event), int(hl), int(hu),
                                   C.byref(nr))
         return bool(ok), bool(nr.value)
+
+    def t5_features(self, md_hits):
+        """Scoring features (48) of the T5 formed by five (lower, upper) hit pairs."""
+        h = np.ascontiguousarray(np.asarray(md_hits, np.int32).ravel())
+        out = np.zeros(48)
+        lib().oracle_t5_features(C.byref(self.geom), C.byref(self.cfg), C.byref(self.event), _ptr(h), _ptr(out))
+        return out
 
     def pred_chain(self, md_hits, kind):
         h = np.ascontiguousarray(np.asarray(md_hits, np.int32).ravel())

@@ -448,7 +448,7 @@ __device__ __forceinline__ bool t5_prefit_f32(const Arena& A, const DevCfg& c, i
     for (int j = 0; j < 5; ++j) P[j] = md_point<float>(A, m[j]);
     float k, c2, cz;
     fit_track_f32<5>(P, k, c2, cz);
-    return fit_may_pass(c, k, c2, cz, float(c.chi2_rphi_t5), float(c.chi2_rz_t5));
+    return fit_may_pass(c, k, c2, cz, float(c.chi2_rphi_t5) * c.prefit_scale, float(c.chi2_rz_t5) * c.prefit_scale);
 }
 
 // Collected candidates: FP32 fit prefilter; the verdicts of each group of 32
@@ -622,9 +622,12 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_t5_overflow(Arena A, DevCfg 
     }
 }
 
-// T5 refine (FP64): one thread per searched candidate, lane-dense.
+// T5 refine (FP64): one thread per searched candidate, lane-dense. Decides
+// the hand-set cuts, writes the T5 outputs and, when enabled, the scoring
+// features; without the network the cut decision is the validity.
 __global__ void k_t5_refine(Arena A, DevCfg c) {
     const int n = min(A.counters[3], A.t5_cap);
+    const BatchDesc* B = A.bd;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int m[5];
         t5_mds(A, make_int2(A.t5_in[i], A.t5_out[i]), m);
@@ -633,7 +636,8 @@ __global__ void k_t5_refine(Arena A, DevCfg c) {
         for (int j = 0; j < 5; ++j) P[j] = md_point<double>(A, m[j]);
         T5Out o{};
         bool pass = t5_eval(c, P, o);
-        A.t5_valid[i] = pass;
+        const int e = A.md_gmod[m[0]] / A.n_mod;
+        A.t5_cut[i] = pass;
         A.t5_kappa[i] = o.kappa;
         A.t5_sigk[i] = o.sigk;
         A.t5_eta[i] = o.eta;
@@ -642,7 +646,42 @@ __global__ void k_t5_refine(Arena A, DevCfg c) {
         A.t5_chi2z[i] = float(o.chi2_rz);
         A.t5_score[i] = float(o.score);
         A.t5_pt[i] = float(o.pt);
-        if (pass) atomicAdd(&A.ev_counts[(A.md_gmod[m[0]] / A.n_mod) * 8 + 3], 1);
+        if (c.features_on) {
+            Pt<double> H[10];
+            int code[5];
+            const int h0 = A.hit_off[e];
+            for (int j = 0; j < 5; ++j) {
+                H[2 * j] = P[j];
+                Pt<double> U = P[j];
+                const int hu = h0 + A.md_up[m[j]];
+                U.x = B->hx[hu];
+                U.y = B->hy[hu];
+                U.z = B->hz[hu];
+                U.r = hypot(U.x, U.y);
+                H[2 * j + 1] = U;
+                const int mod = A.md_gmod[m[j]] % A.n_mod;
+                code[j] = A.mod_layer[mod] + (A.mod[mod].w > 0.5f ? 6 : 0);
+            }
+            t5_features(c, P, H, code, A.t5_feat + (size_t)48 * i);
+        }
+        if (!c.use_mlp) {
+            A.t5_valid[i] = pass;
+            if (pass) atomicAdd(&A.ev_counts[e * 8 + 3], 1);
+        }
+    }
+}
+
+// Validity from the network score (the hand-set cut decision stays in t5_cut).
+__global__ void k_t5_mlp_select(Arena A, DevCfg c) {
+    const int n = min(A.counters[3], A.t5_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const bool pass = A.t5_mlp[i] >= c.mlp_threshold && fabs(A.t5_kappa[i]) <= (1.0 + c.tol_r) * 2.0 * c.a;
+        A.t5_valid[i] = pass;
+        if (pass) {
+            int m[5];
+            t5_mds(A, make_int2(A.t5_in[i], A.t5_out[i]), m);
+            atomicAdd(&A.ev_counts[(A.md_gmod[m[0]] / A.n_mod) * 8 + 3], 1);
+        }
     }
 }
 

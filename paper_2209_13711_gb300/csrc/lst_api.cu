@@ -11,6 +11,9 @@
 
 #include "../../include/lst.h"
 #include "lst_kernels.cuh"
+#include "lst_mlp.cuh"
+
+lst::MlpParams lst_mlp_device_params(const lst_mlp* m);
 
 using namespace lst;
 
@@ -57,6 +60,7 @@ struct lst_ctx {
     std::vector<int> hit_off_host, seed_off_host;
     bool profiling = false;
     bool use_graph = true;
+    const lst_mlp* mlp = nullptr;     // network deciding T5 validity (NULL: the hand-set cuts)
     BatchDesc* d_bd = nullptr;        // device batch descriptor
     BatchDesc* h_bd = nullptr;        // pinned staging of the descriptor
     cudaStream_t cap_stream = nullptr;
@@ -85,6 +89,10 @@ static DevCfg make_devcfg(const lst_config& c) {
     d.pls_pt_tol = c.pls_pt_tol; d.sig_pix = c.sig_pix; d.sb_eta_max = c.sb_eta_max;
     d.sb_n_eta = c.sb_n_eta; d.sb_n_phi = c.sb_n_phi;
     d.dr_clean = c.dr_clean; d.k_field = c.k_field; d.b_field = c.b_field;
+    d.features_on = 0;
+    d.use_mlp = 0;
+    d.prefit_scale = 1.0f;
+    d.mlp_threshold = 0.5f;
     return d;
 }
 
@@ -188,6 +196,7 @@ static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_m
     A.n_mod = n_mod;
     A.n_sb = n_sb;
     A.mod = b.take<float4>(n_mod);
+    A.mod_layer = b.take<int>(n_mod);
     A.conn_off = b.take<int>(n_mod + 1);
     A.conn_tgt = b.take<int>(n_conn);
     A.sb_off = b.take<int>(n_sb + 1);
@@ -239,7 +248,8 @@ static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_m
     A.t5_kappa = b.take<double>(T5); A.t5_sigk = b.take<double>(T5);
     A.t5_eta = b.take<double>(T5); A.t5_phi = b.take<double>(T5);
     A.t5_chi2 = b.take<float>(T5); A.t5_chi2z = b.take<float>(T5); A.t5_score = b.take<float>(T5);
-    A.t5_pt = b.take<float>(T5); A.t5_valid = b.take<uint8_t>(T5);
+    A.t5_pt = b.take<float>(T5); A.t5_valid = b.take<uint8_t>(T5); A.t5_cut = b.take<uint8_t>(T5);
+    A.t5_feat = b.take<float>(48 * T5); A.t5_mlp = b.take<float>(T5);
     A.t5_off = b.take<int>(MD); A.t5_cnt = b.take<int>(MD);
     A.pls_pass = b.take<int>(S); A.pls_sb = b.take<int>(S);
     A.pls_kappa = b.take<double>(S); A.pls_sigk = b.take<double>(S);
@@ -303,6 +313,9 @@ lst_status lst_load_geometry(lst_ctx* c, const lst_module* mods, int32_t n_mod, 
     for (int i = 0; i < n_mod; ++i)
         m4[i] = make_float4(mods[i].dsep, mods[i].sig_rphi, mods[i].sig_long, float(mods[i].subdet));
     CK(cudaMemcpy((void*)c->A.mod, m4.data(), sizeof(float4) * n_mod, cudaMemcpyHostToDevice));
+    std::vector<int> lay(n_mod);
+    for (int i = 0; i < n_mod; ++i) lay[i] = mods[i].layer;
+    CK(cudaMemcpy((void*)c->A.mod_layer, lay.data(), sizeof(int) * n_mod, cudaMemcpyHostToDevice));
     CK(cudaMemcpy((void*)c->A.conn_off, conn_off, sizeof(int) * (n_mod + 1), cudaMemcpyHostToDevice));
     if (n_conn) CK(cudaMemcpy((void*)c->A.conn_tgt, conn_tgt, sizeof(int) * n_conn, cudaMemcpyHostToDevice));
     CK(cudaMemcpy((void*)c->A.sb_off, sb_off, sizeof(int) * (n_sb + 1), cudaMemcpyHostToDevice));
@@ -347,6 +360,11 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile) {
     LAUNCH("t5", k_t5<<<G(6), kT5Warps * 32, 0, st>>>(A, dc));
     LAUNCH("t5_overflow", k_t5_overflow<<<nsm, 256, 0, st>>>(A, dc));
     LAUNCH("t5_refine", k_t5_refine<<<G(4), 128, 0, st>>>(A, dc));
+    if (c->mlp) {
+        LAUNCH("t5_mlp", k_mlp_forward<<<G(4), 128, 0, st>>>(lst_mlp_device_params(c->mlp), A.t5_feat, A.t5_cap,
+                                                            A.counters + 3, A.t5_mlp, MlpSaved{}));
+        LAUNCH("t5_mlp_select", k_t5_mlp_select<<<G(4), 128, 0, st>>>(A, dc));
+    }
     LAUNCH("pls", k_pls<<<G(4), 128, 0, st>>>(A, dc));
     LAUNCH("pt5", k_pt5<<<G(8), kPtWarps * 32, 0, st>>>(A, dc));
     LAUNCH("pt5_refine", k_pt5_refine<<<G(2), 128, 0, st>>>(A, dc));
@@ -480,6 +498,65 @@ static lst_status wait_batch(lst_ctx* c, int32_t event) {
         lst_status s__ = fetch(v, d, n);        \
         if (s__ != LST_OK) return s__;          \
     } while (0)
+
+lst_status lst_set_t5_selection(lst_ctx* c, const lst_mlp* mlp, float threshold, float prefilter_scale,
+                                int32_t capture_features) {
+    if (!c || !(prefilter_scale >= 1.0f)) return LST_ERR_ARG;
+    if (c->ran) CK(cudaEventSynchronize(c->done));
+    c->mlp = mlp;
+    c->dc.use_mlp = mlp ? 1 : 0;
+    c->dc.features_on = (mlp || capture_features) ? 1 : 0;
+    c->dc.prefit_scale = prefilter_scale;
+    c->dc.mlp_threshold = threshold;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return LST_OK;
+}
+
+lst_status lst_get_t5_candidates(lst_ctx* c, int32_t event, int32_t capacity, int32_t* n_out, float* features,
+                                 int32_t* hits, int32_t* cut_pass, float* score) {
+    lst_status s = wait_batch(c, event);
+    if (s != LST_OK) return s;
+    if (capacity < 0) return LST_ERR_ARG;
+    const Arena& A = c->A;
+    int cnt[32];
+    CK(cudaMemcpy(cnt, A.counters, sizeof cnt, cudaMemcpyDeviceToHost));
+    const int n = std::min(cnt[3], A.t5_cap);
+    const int n_md = std::min(cnt[0], A.md_cap), n_t3 = std::min(cnt[2], A.t3_cap);
+    std::vector<int> ti, to, m0, m1, m2, gm, lo, up;
+    std::vector<uint8_t> cp;
+    FETCH(ti, A.t5_in, n); FETCH(to, A.t5_out, n); FETCH(cp, A.t5_cut, n);
+    FETCH(m0, A.t3_m0, n_t3); FETCH(m1, A.t3_m1, n_t3); FETCH(m2, A.t3_m2, n_t3);
+    FETCH(gm, A.md_gmod, n_md); FETCH(lo, A.md_lo, n_md); FETCH(up, A.md_up, n_md);
+    std::vector<int> rows;
+    for (int i = 0; i < n; ++i)
+        if (gm[m0[ti[i]]] / A.n_mod == event) rows.push_back(i);
+    const int k = std::min((int)rows.size(), (int)capacity);
+    if (n_out) *n_out = (int)rows.size();
+    if (features && k) {
+        std::vector<float> f;
+        FETCH(f, A.t5_feat, (size_t)48 * n);
+        for (int r = 0; r < k; ++r) std::memcpy(features + 48 * (size_t)r, f.data() + 48 * (size_t)rows[r], 48 * 4);
+    }
+    if (score && k) {
+        std::vector<float> sc;
+        FETCH(sc, A.t5_mlp, n);
+        for (int r = 0; r < k; ++r) score[r] = sc[rows[r]];
+    }
+    for (int r = 0; r < k; ++r) {
+        const int i = rows[r];
+        const int md[5] = {m0[ti[i]], m1[ti[i]], m2[ti[i]], m1[to[i]], m2[to[i]]};
+        if (hits)
+            for (int j = 0; j < 5; ++j) {
+                hits[10 * r + 2 * j] = lo[md[j]];
+                hits[10 * r + 2 * j + 1] = up[md[j]];
+            }
+        if (cut_pass) cut_pass[r] = cp[i];
+    }
+    return (int)rows.size() > capacity ? LST_WARN_TRUNCATED : LST_OK;
+}
 
 lst_status lst_get_counters(lst_ctx* c, int32_t* out, int32_t n) {
     if (!c || !out || n < 0 || n > 32) return LST_ERR_ARG;

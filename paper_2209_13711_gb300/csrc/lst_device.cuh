@@ -40,6 +40,10 @@ struct DevCfg {
     double pls_pt_tol, sig_pix, sb_eta_max;
     int sb_n_eta, sb_n_phi;
     double dr_clean, k_field, b_field;
+    int features_on;       // the T5 refine also writes the 38 scoring features
+    int use_mlp;           // T5 validity from the network score instead of the cuts
+    float prefit_scale;    // widening of the T5 FP32 prefilter (1: conservative for the cuts)
+    float mlp_threshold;
 };
 
 // Shape and inputs of the batch being processed (device memory).
@@ -59,6 +63,7 @@ struct Arena {
     // geometry
     int n_mod, n_sb;
     const float4* mod;            // {dsep, sig_rphi, sig_long, subdet}
+    const int* mod_layer;
     const int* conn_off;
     const int* conn_tgt;
     const int* sb_off;
@@ -127,6 +132,9 @@ struct Arena {
     double* t5_eta;
     double* t5_phi;
     uint8_t* t5_valid;            // the FP64 test passed (entries are FP32-prefiltered candidates)
+    uint8_t* t5_cut;              // the hand-set cuts passed (== t5_valid without the network)
+    float* t5_feat;               // [t5_cap][48] scoring features
+    float* t5_mlp;                // network score
     int* t5_off;                  // [md_cap] by inner MD
     int* t5_cnt;
     // pLS, per seed
@@ -432,7 +440,14 @@ __device__ inline bool solve3(double M[3][3], double b[3], double x[3]) {
     return true;
 }
 
-template <int N> __device__ inline Fit fit_track(const Pt<double>* P) {
+// Full output of the chord-frame fit: circle g (xi^2+eta^2) + h xi + k - eta = 0
+// in the frame (origin O, x-hat (xx, xy)), S = sqrt(1 + h^2 - 4gk), and the
+// r-z line z = c0 + t s (s: arc length from P[0]) with its t_hat.
+struct FitFull {
+    double gg, hh, kk, S, xx, xy, ox, oy, c0, t, t_hat, kappa, chi2, chi2z;
+};
+
+template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* full = nullptr) {
     Fit f;
     const Pt<double>& O = P[N / 2];
     double ex = P[N - 1].x - P[0].x, ey = P[N - 1].y - P[0].y;
@@ -458,6 +473,7 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P) {
     double sol[3] = {0, 0, 0};
     if (!solve3(M, b, sol)) {
         f.kappa = 1e30; f.chi2_rphi = 1e30; f.chi2_rz = 1e30; f.tanl = 0;
+        if (full) *full = FitFull{0, 0, 0, 1, xx, xy, O.x, O.y, 0, 0, 0, 1e30, 1e30, 1e30};
         return f;
     }
     double gg = sol[0], hh = sol[1], kk = sol[2];
@@ -504,6 +520,11 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P) {
     for (int i = 0; i < N; ++i) chi2z += w[i] * sq(P[i].z - c0 - t * s[i]);
     f.chi2_rz = chi2z;
     f.tanl = t;
+    if (full) {
+        full->gg = gg; full->hh = hh; full->kk = kk; full->S = S; full->xx = xx; full->xy = xy;
+        full->ox = O.x; full->oy = O.y; full->c0 = c0; full->t = t; full->t_hat = t_hat;
+        full->kappa = f.kappa; full->chi2 = chi2; full->chi2z = chi2z;
+    }
     return f;
 }
 
@@ -595,6 +616,56 @@ __device__ __forceinline__ double phi0_of(const Pt<double>& P, double kappa) {
 __device__ __forceinline__ double pt_of(const DevCfg& c, double kappa) {
     double ka = fabs(kappa);
     return ka > 0 ? c.k_field * c.b_field / (100.0 * ka) : 1e30;
+}
+
+// Scoring features of a T5 candidate (FP64, stored as FP32): hits H[0..9] =
+// (lower, upper) of the five MDs, P[0..4] = the lower hits (anchors), layer
+// codes (layer + 6 subdet). f[0..9] r-phi pulls of the ten hits to the fitted
+// circle, f[10..19] r-z pulls to the fitted line (both clipped to +-50),
+// f[20..24] anchor radii / 100, f[25..27] inner, outer and fitted curvature
+// over 2a, f[28..29] log(1 + chi2) (r-phi, r-z), f[30..31] 10 beta of the two
+// triplets, f[32] eta, f[33..37] layer codes / 11, f[38..47] zero.
+__device__ inline void t5_features(const DevCfg& c, const Pt<double>* P, const Pt<double>* H, const int* code,
+                                   float* f) {
+    FitFull F;
+    fit_track<5>(P, &F);
+    Tri<double> ti = tri(P[0], P[1], P[2]);
+    Tri<double> to = tri(P[2], P[3], P[4]);
+    const double ka = fabs(F.kappa);
+    const double yx = -F.xy, yy = F.xx;
+    for (int j = 0; j < 10; ++j) {
+        const Pt<double>& Q = H[j];
+        double dx = Q.x - F.ox, dy = Q.y - F.oy;
+        double xi = dx * F.xx + dy * F.xy, et = dx * yx + dy * yy;
+        double rho2 = xi * xi + et * et;
+        double u = F.gg * rho2 + F.hh * xi + F.kk - et;
+        double e = 2.0 * u / (F.S + sqrt(fmax(0.0, F.S * F.S + 4.0 * F.gg * u)));
+        double nlx = 2.0 * F.gg * xi + F.hh, nly = 2.0 * F.gg * et - 1.0;
+        double nx = nlx * F.xx + nly * yx, ny = nlx * F.xy + nly * yy;
+        double nn = hypot(nx, ny);
+        nx /= nn;
+        ny /= nn;
+        double rx = Q.x / Q.r, ry = Q.y / Q.r;
+        double s2 = fmax(sq(Q.srphi * (-nx * ry + ny * rx)) + sq(Q.sr * (nx * rx + ny * ry)), sq(0.01 * Q.srphi));
+        double pr = e / sqrt(s2);
+        double sj = arc(hypot(Q.x - P[0].x, Q.y - P[0].y), ka);
+        double w = 1.0 / fmax(1e-12, sq(Q.sz) + sq(F.t_hat * Q.sr));
+        double pz = (Q.z - F.c0 - F.t * sj) * sqrt(w);
+        f[j] = float(fmin(50.0, fmax(-50.0, pr)));
+        f[10 + j] = float(fmin(50.0, fmax(-50.0, pz)));
+    }
+    for (int j = 0; j < 5; ++j) f[20 + j] = float(P[j].r / 100.0);
+    const double two_a = 2.0 * c.a;
+    f[25] = float(ti.kappa / two_a);
+    f[26] = float(to.kappa / two_a);
+    f[27] = float(F.kappa / two_a);
+    f[28] = float(log1p(fmin(F.chi2, 1e30)));
+    f[29] = float(log1p(fmin(F.chi2z, 1e30)));
+    f[30] = float(10.0 * ti.beta);
+    f[31] = float(10.0 * to.beta);
+    f[32] = float(asinh(F.t));
+    for (int j = 0; j < 5; ++j) f[33 + j] = float(code[j] / 11.0);
+    for (int j = 38; j < 48; ++j) f[j] = 0.f;
 }
 
 // T5 on anchors P[0..4]; outputs in double

@@ -92,11 +92,23 @@ def library():
         L.lst_last_launch_count.argtypes = [vp]
         L.lst_set_profiling.argtypes = [vp, i32]
         L.lst_get_counters.argtypes = [vp, vp, i32]
+        L.lst_mlp_create.argtypes = [p(vp), i32, i32]
+        L.lst_mlp_destroy.argtypes = [vp]
+        L.lst_mlp_destroy.restype = None
+        L.lst_mlp_set_params.argtypes = [vp, vp]
+        L.lst_mlp_get_params.argtypes = [vp, vp]
+        L.lst_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
+        L.lst_mlp_gradient.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+        L.lst_mlp_train_step.argtypes = [vp, vp, vp, i32, C.c_float, vp, vp]
+        L.lst_set_t5_selection.argtypes = [vp, vp, C.c_float, C.c_float, i32]
+        L.lst_get_t5_candidates.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
         L.lst_get_kernel_times.argtypes = [vp, i32, vp, vp, vp]
         for f in ("lst_config_default", "lst_capacity_default", "lst_create", "lst_load_geometry", "lst_run_batch",
                   "lst_run_event", "lst_get_track_candidates", "lst_object_columns", "lst_get_objects",
                   "lst_get_stats", "lst_last_launch_count", "lst_set_profiling", "lst_get_kernel_times",
-                  "lst_get_counters"):
+                  "lst_get_counters", "lst_mlp_create", "lst_mlp_set_params", "lst_mlp_get_params",
+                  "lst_mlp_forward", "lst_mlp_gradient", "lst_mlp_train_step", "lst_set_t5_selection",
+                  "lst_get_t5_candidates"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -219,6 +231,25 @@ class Context:
         return [(names[i].decode(), float(ms[i])) for i in range(n.value)]
 
     # -- results ----------------------------------------------------------
+    def set_t5_selection(self, mlp=None, threshold=0.5, prefilter_scale=1.0, capture_features=False):
+        """Network-scored T5 selection (mlp: an Mlp) or the hand-set cuts (mlp=None)."""
+        self._mlp = mlp
+        _check(library().lst_set_t5_selection(self._h, mlp._h if mlp is not None else None, float(threshold),
+                                              float(prefilter_scale), 1 if capture_features else 0))
+
+    def t5_candidates(self, event=0):
+        """Every T5 candidate of an event: features [n, 48], hits [n, 10], cut_pass [n], score [n]."""
+        L = library()
+        n = C.c_int32(0)
+        _check(L.lst_get_t5_candidates(self._h, int(event), 0, C.byref(n), None, None, None, None))
+        k = n.value
+        f = np.zeros((k, 48), np.float32)
+        h = np.zeros((k, 10), np.int32)
+        cp = np.zeros(k, np.int32)
+        sc = np.zeros(k, np.float32)
+        _check(L.lst_get_t5_candidates(self._h, int(event), k, C.byref(n), _ptr(f), _ptr(h), _ptr(cp), _ptr(sc)))
+        return dict(features=f, hits=h, cut_pass=cp.astype(bool), score=sc)
+
     def counters(self):
         """Batch-wide device counters (see lst_get_counters)."""
         out = np.zeros(32, np.int32)
@@ -257,3 +288,59 @@ class Context:
         rec.update({c: F[:, j] for j, c in enumerate(fcol)})
         rec["n"] = n.value
         return rec
+
+
+N_MLP_PARAMS = 9409
+N_MLP_INPUTS = 48
+
+
+class Mlp:
+    """The T5 scoring network on a device (parameters, inference, training)."""
+
+    def __init__(self, device=0, max_batch=4096, params=None):
+        h = C.c_void_p()
+        _check(library().lst_mlp_create(C.byref(h), int(device), int(max_batch)))
+        self._h = h
+        self.max_batch = max_batch
+        if params is not None:
+            self.set_params(params)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            library().lst_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == N_MLP_PARAMS
+        _check(library().lst_mlp_set_params(self._h, _ptr(p)))
+
+    def params(self):
+        p = np.zeros(N_MLP_PARAMS, np.float32)
+        _check(library().lst_mlp_get_params(self._h, _ptr(p)))
+        return p
+
+    def forward(self, features, scores, stream=None):
+        """features, scores: CUDA tensors ([n, 48] float32, [n] float32)."""
+        _check(library().lst_mlp_forward(self._h, _ptr(features), int(features.shape[0]), _ptr(scores),
+                                         C.c_void_p(stream) if stream is not None else None))
+
+    def gradient(self, features, labels, stream=None):
+        g = np.zeros(N_MLP_PARAMS, np.float32)
+        loss = C.c_float(0)
+        _check(library().lst_mlp_gradient(self._h, _ptr(features), _ptr(labels), int(features.shape[0]), _ptr(g),
+                                          C.byref(loss), C.c_void_p(stream) if stream is not None else None))
+        return g, loss.value
+
+    def train_step(self, features, labels, lr=1e-3, want_loss=False, stream=None):
+        loss = C.c_float(0)
+        _check(library().lst_mlp_train_step(self._h, _ptr(features), _ptr(labels), int(features.shape[0]),
+                                            float(lr), C.byref(loss) if want_loss else None,
+                                            C.c_void_p(stream) if stream is not None else None))
+        return loss.value if want_loss else None

@@ -1,0 +1,151 @@
+"""Training and evaluation of the T5 scoring network on the device.
+
+The chain runs with feature capture and a widened T5 prefilter; every T5
+candidate of the training events becomes a sample (features from the FP64
+refine kernel, label 1 when all ten hits come from one generated particle).
+The network is trained with the library's own forward, backward and Adam
+kernels. Evaluation compares, on separate events, the hand-set cut selection
+with the network at the threshold that matches the cut efficiency.
+
+    python -m paper_2209_13711_gb300.train --train-events 100 --eval-events 8 --out t5_mlp.npy
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+from . import lst as L
+
+
+def label_candidates(cand, pid):
+    """1 when all ten hits of a candidate belong to one generated particle."""
+    h = cand["hits"]
+    p = pid[h]
+    true = (p[:, 0] >= 0) & np.all(p == p[:, :1], axis=1)
+    return true, np.where(true, p[:, 0], -1)
+
+
+def collect(ctx, events, batch=16, stream=None):
+    """Features, labels, cut decisions and particle ids of every T5 candidate."""
+    X, y, cut, part, ev_idx = [], [], [], [], []
+    for b0 in range(0, len(events), batch):
+        chunk = events[b0:b0 + batch]
+        ctx.run(chunk, stream=stream)
+        for j, ev in enumerate(chunk):
+            c = ctx.t5_candidates(j)
+            t, p = label_candidates(c, ev.pid)
+            X.append(c["features"])
+            y.append(t.astype(np.float32))
+            cut.append(c["cut_pass"])
+            part.append(p)
+            ev_idx.append(np.full(len(t), b0 + j))
+    cat = np.concatenate
+    return dict(X=cat(X), y=cat(y), cut=cat(cut), particle=cat(part), event=cat(ev_idx))
+
+
+def train(mlp, X, y, epochs=4, batch=4096, lr=2e-3, seed=0, log=None):
+    import torch
+    rng = np.random.default_rng(seed)
+    n = len(y)
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    yd = torch.from_numpy(np.ascontiguousarray(y)).cuda()
+    hist = []
+    for ep in range(epochs):
+        perm = torch.from_numpy(rng.permutation(n)).cuda()
+        losses = []
+        for b0 in range(0, n - batch + 1, batch):
+            idx = perm[b0:b0 + batch]
+            xb = Xd.index_select(0, idx).contiguous()
+            yb = yd.index_select(0, idx).contiguous()
+            want = (b0 // batch) % 50 == 0
+            l = mlp.train_step(xb, yb, lr=lr, want_loss=want)
+            if want:
+                losses.append(l)
+        hist.append(float(np.mean(losses)) if losses else float("nan"))
+        if log:
+            log(f"epoch {ep}: loss {hist[-1]:.4f}")
+    return hist
+
+
+def scores_of(mlp, X):
+    import torch
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    out = torch.zeros(len(X), device="cuda")
+    mlp.forward(Xd, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def selection_metrics(sel, data):
+    """Efficiency over particles with at least one true candidate; fake fraction of the selection."""
+    true = data["y"] > 0.5
+    key = data["event"].astype(np.int64) * 10 ** 7 + data["particle"]
+    findable = np.unique(key[true])
+    found = np.unique(key[true & sel])
+    eff = len(found) / max(1, len(findable))
+    fake = float((sel & ~true).sum()) / max(1, int(sel.sum()))
+    return dict(efficiency=eff, fake_rate=fake, selected=int(sel.sum()))
+
+
+def matched_threshold(scores, data, target_eff):
+    """Largest threshold whose efficiency reaches the target."""
+    lo, hi = 0.0, 1.0
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        if selection_metrics(scores >= mid, data)["efficiency"] >= target_eff:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def evaluate(mlp, data):
+    s = scores_of(mlp, data["X"])
+    cut = selection_metrics(data["cut"], data)
+    thr = matched_threshold(s, data, cut["efficiency"])
+    net = selection_metrics(s >= thr, data)
+    return dict(cut=cut, network=net, threshold=thr)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train-events", type=int, default=100)
+    ap.add_argument("--eval-events", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--prefilter-scale", type=float, default=3.0)
+    ap.add_argument("--out", default="t5_mlp.npy")
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args(argv)
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from synth import events as E, geometry as G, maps as M
+    from synth.config import DEFAULT_CUTS
+    from synth.mlp_init import init_params
+    geom = G.make_geometry(barrel_only=False)
+    maps = M.load_maps(geom)
+    ctx = L.Context(geom.module_table(), maps, cfg=DEFAULT_CUTS, capacity=L.default_capacity(16))
+    ctx.set_t5_selection(None, prefilter_scale=args.prefilter_scale, capture_features=True)
+    t0 = time.time()
+    tr_events = [E.pu200_event(10000 + i, geom) for i in range(args.train_events)]
+    tr = collect(ctx, tr_events)
+    del tr_events
+    ev_events = [E.pu200_event(20000 + i, geom) for i in range(args.eval_events)]
+    va = collect(ctx, ev_events)
+    print(f"samples: train {len(tr['y'])} ({tr['y'].mean():.3f} true), eval {len(va['y'])}; "
+          f"{time.time() - t0:.1f} s", flush=True)
+    mlp = L.Mlp(max_batch=4096, params=init_params(args.seed))
+    t1 = time.time()
+    hist = train(mlp, tr["X"], tr["y"], epochs=args.epochs, log=lambda m: print(m, flush=True))
+    print(f"training: {time.time() - t1:.1f} s", flush=True)
+    res = evaluate(mlp, va)
+    res["loss_history"] = hist
+    np.save(args.out, mlp.params())
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

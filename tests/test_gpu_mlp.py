@@ -1,0 +1,140 @@
+"""Scoring network on the GPU vs its FP64 reference, and its use in the chain (GPU)."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as R
+from synth import events as E
+from synth.config import DEFAULT_CUTS
+from synth.mlp_init import init_params
+from tests.gpu_common import make_context, oracle_result
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0, 1, (n, 48)).astype(np.float32)
+    X[:, 38:] = 0
+    y = (rng.uniform(size=n) < 0.3).astype(np.float32)
+    return X, y
+
+
+@pytest.fixture(scope="module")
+def mlp():
+    import paper_2209_13711_gb300 as P
+    m = P.Mlp(max_batch=4096, params=init_params(7))
+    yield m
+    m.close()
+
+
+@pytest.mark.parametrize("n", [1, 17, 1003])
+def test_forward_matches_reference(mlp, n):
+    X, _ = _data(n, n)
+    theta = init_params(7)
+    mlp.set_params(theta)
+    out = torch.zeros(n, device="cuda")
+    mlp.forward(torch.from_numpy(X).cuda(), out)
+    torch.cuda.synchronize()
+    ref, _ = R.forward(theta.astype(np.float64), X)
+    d = np.abs(out.cpu().numpy() - ref)
+    # FP32 vs FP64 accumulation may round a hidden activation to the neighbouring
+    # BF16 value (2^-8 relative): rare, and bounded well below 5e-3 on the score
+    assert d.max() <= 5e-3 and np.mean(d <= 2e-4) >= 0.99 and d.mean() <= 1e-4
+
+
+def test_gradient_matches_reference(mlp):
+    X, y = _data(3000, 11)
+    theta = init_params(8)
+    mlp.set_params(theta)
+    g, loss = mlp.gradient(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda())
+    gr = R.grad(theta.astype(np.float64), X, y)
+    assert abs(loss - R.loss(theta.astype(np.float64), X, y)) < 1e-4
+    assert np.linalg.norm(g - gr) <= 1e-2 * np.linalg.norm(gr)
+    big = np.abs(gr) > 1e-2 * np.abs(gr).max()
+    assert np.allclose(g[big], gr[big], rtol=3e-2, atol=1e-6)
+
+
+def test_adam_step_matches_reference(mlp):
+    X, y = _data(2048, 12)
+    theta = init_params(9)
+    mlp.set_params(theta)
+    mlp.train_step(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), lr=1e-3)
+    got = mlp.params()
+    gr = R.grad(theta.astype(np.float64), X, y)
+    want, _, _ = R.adam(theta.astype(np.float64), 0, 0, gr, 1, lr=1e-3)
+    big = np.abs(gr) > 1e-2 * np.abs(gr).max()
+    assert np.allclose(got[big], want[big], atol=2e-6)
+    assert np.all(np.abs(got - theta) <= 1e-3 * 1.0001)
+
+
+def test_training_reduces_the_loss(mlp):
+    X, y = _data(4096, 13)
+    y = (X[:, 0] + 0.5 * X[:, 3] > 0.2).astype(np.float32)      # a learnable rule
+    mlp.set_params(init_params(10))
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    l0 = mlp.train_step(Xd, yd, lr=3e-3, want_loss=True)
+    for _ in range(300):
+        mlp.train_step(Xd, yd, lr=3e-3)
+    l1 = mlp.train_step(Xd, yd, lr=3e-3, want_loss=True)
+    assert l1 < 0.3 * l0
+
+
+def test_chain_features_match_oracle(geom_full, maps_full):
+    from oracle import oracle as O
+    ctx = make_context(geom_full, maps_full, max_events=1)
+    ctx.set_t5_selection(None, capture_features=True)
+    ev = E.pileup_event(30, 77, geom_full)
+    ctx.run([ev])
+    cand = ctx.t5_candidates(0)
+    assert len(cand["hits"]) > 50
+    S = O.Setup(geom_full.module_table(), maps_full, DEFAULT_CUTS, ev)
+    for i in range(0, len(cand["hits"]), max(1, len(cand["hits"]) // 200)):
+        want = S.t5_features(cand["hits"][i])
+        got = cand["features"][i].astype(np.float64)
+        assert np.all(np.abs(got - want) <= 1e-5 * np.maximum(np.abs(want), 1.0)), i
+    ctx.close()
+
+
+def test_chain_with_the_network(geom_full, maps_full):
+    import paper_2209_13711_gb300 as P
+    m = P.Mlp(max_batch=64, params=init_params(3))
+    ctx = make_context(geom_full, maps_full, max_events=1)
+    ev = E.pileup_event(30, 78, geom_full)
+    ctx.set_t5_selection(m, threshold=0.0, prefilter_scale=2.0)
+    ctx.run([ev])
+    st = ctx.stats(0)
+    cand = ctx.t5_candidates(0)
+    kappa_ok = np.abs(cand["features"][:, 27]) <= 1.05 + 1e-6
+    assert st["counts"]["t5"] == int(kappa_ok.sum()) > 0
+    # scores are the network's on the captured features
+    ref, _ = R.forward(init_params(3).astype(np.float64), cand["features"])
+    d = np.abs(cand["score"] - ref)
+    assert d.max() <= 5e-3 and np.mean(d <= 2e-4) >= 0.99
+    ctx.set_t5_selection(m, threshold=1.5, prefilter_scale=2.0)
+    ctx.run([ev])
+    assert ctx.stats(0)["counts"]["t5"] == 0
+    ctx.set_t5_selection(None)
+    ctx.run([ev])
+    assert ctx.stats(0)["counts"]["t5"] == int(cand["cut_pass"].sum())
+    ctx.close()
+    m.close()
+
+
+def test_trained_network_beats_the_cuts(geom_full):
+    """At the cut-based efficiency, the trained network keeps far fewer fakes."""
+    import paper_2209_13711_gb300 as P
+    from paper_2209_13711_gb300 import train as T
+    from synth import maps as M
+    ctx = P.Context(geom_full.module_table(), M.load_maps(geom_full), cfg=DEFAULT_CUTS,
+                    capacity=P.default_capacity(8))
+    ctx.set_t5_selection(None, prefilter_scale=3.0, capture_features=True)
+    tr = T.collect(ctx, [E.pu200_event(30000 + i, geom_full) for i in range(8)], batch=8)
+    va = T.collect(ctx, [E.pu200_event(31000 + i, geom_full) for i in range(3)], batch=8)
+    m = P.Mlp(max_batch=4096, params=init_params(1))
+    T.train(m, tr["X"], tr["y"], epochs=3)
+    res = T.evaluate(m, va)
+    assert res["network"]["efficiency"] >= res["cut"]["efficiency"]
+    assert res["network"]["fake_rate"] < 0.5 * res["cut"]["fake_rate"]
+    ctx.close()
+    m.close()
