@@ -145,6 +145,8 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    # ---- launch shapes tuned on a warm-up event (setup, untimed) ---------
+    tune = autotune(ctx, dev[0], st)
     # ---- device-timed: inputs resident in HBM ---------------------------
     for i in range(args.warmup):
         ctx.run_packed(dev[i], stream=st.cuda_stream)
@@ -166,18 +168,19 @@ def run_ours(args):
     # ---- end to end through the C ABI from pinned host memory -----------
     e2e_s = 0.0
     h2d = d2h = 0
+    records = np.empty(ctx.capacity.tc_per_event, P.lst.TC_DTYPE)
     for i in range(args.steps):
         flush.fill_(i & 0xff)
         b = pinned[args.warmup + i]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.run_packed(b, stream=st.cuda_stream)
-        tc = ctx.track_candidates(0)
+        off, rec = ctx.batch_track_candidates(out=records)
         t1 = time.perf_counter()
         e2e_s += t1 - t0
         h2d += sum(int(v.numel() * v.element_size()) for k, v in b.items() if k not in ("hit_off", "seed_off"))
         h2d += 8 * len(b["hit_off"])
-        d2h += 4 + tc["n"] * (4 + 4 + 40 + 12)
+        d2h += off.nbytes + rec.nbytes
     # ---- per-kernel device times (profiling pass, same workload) --------
     ctx.set_profiling(True)
     per_kernel = {}
@@ -217,6 +220,7 @@ def run_ours(args):
         "e2e": {"value": round(ws * args.steps / e2e_s, 2), "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
                 "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": launches,
+        "autotune": tune,
         "clocks": clk.summary(),
         "roofline": roof,
         "kernel_ms": {k: round(v, 4) for k, v in sorted(kavg.items(), key=lambda kv: -kv[1])},
@@ -225,11 +229,21 @@ def run_ours(args):
     }
     out["batched"] = measure_batched(P, E, geom, maps, DEFAULT_CUTS, flush, st, steps=max(2, min(args.steps, 5)))
     out["mlp"] = measure_mlp(P, E, geom, maps, DEFAULT_CUTS, flush, st, dev[args.warmup:])
+    out["serving"] = measure_serving(E, geom, maps, DEFAULT_CUTS)
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(out))
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def autotune(ctx, batch, st, reps=3):
+    """Tune every stage's launch shape on the batch; report what changed."""
+    default = {c["name"]: (c["blocks_per_sm"], c["block"]) for c in ctx.launch_config()}
+    before, after = ctx.autotune(batch, reps=reps, stream=st.cuda_stream)
+    now = {c["name"]: (c["blocks_per_sm"], c["block"]) for c in ctx.launch_config()}
+    changed = {k: {"blocks_per_sm": v[0], "block": v[1]} for k, v in now.items() if v != default[k]}
+    return {"stage_sum_ms_default": round(before, 4), "stage_sum_ms_tuned": round(after, 4), "changed": changed}
 
 
 def measure_batched(P, E, geom, maps, cuts, flush, st, steps, n_batch=64):
@@ -243,6 +257,7 @@ def measure_batched(P, E, geom, maps, cuts, flush, st, steps, n_batch=64):
     ctx = P.Context(geom.module_table(), maps, cfg=cuts, capacity=P.default_capacity(n_batch))
     b = P.pack_events(events)
     bd = {k: (torch.from_numpy(v).cuda() if k not in ("hit_off", "seed_off") else v) for k, v in b.items()}
+    tune = autotune(ctx, bd, st, reps=2)
     for _ in range(2):
         ctx.run_packed(bd, stream=st.cuda_stream)
     torch.cuda.synchronize()
@@ -276,7 +291,7 @@ def measure_batched(P, E, geom, maps, cuts, flush, st, steps, n_batch=64):
     ctx1.close()
     return {"value": round(n_batch * steps / (ms / 1e3), 2), "unit": "events/s", "events_per_batch": n_batch,
             "ms_per_batch": round(ms / steps, 3), "pileup": "uniform 50-200, 40 tracks per pileup unit",
-            "launch": "one CUDA graph per batch", "dropped_objects": int(dropped),
+            "launch": "one CUDA graph per batch", "dropped_objects": int(dropped), "autotune": tune,
             "plain_same_events": {"value": round(n_batch / (ms1 / 1e3), 2), "unit": "events/s",
                                   "launch": "one graph per event"}}
 
@@ -321,6 +336,53 @@ def measure_mlp(P, E, geom, maps, cuts, flush, st, dev_events):
                                               "threshold": round(quality["threshold"], 4),
                                               "samples_train": int(len(tr["y"])), "samples_eval": int(len(va["y"]))},
             "train_and_eval_s": round(train_s, 1)}
+
+
+def measure_serving(E, geom, maps, cuts, pool_size=32):
+    """Poisson request streams (pileup uniform in 140-200) served by continuous
+    batching on three resident contexts of 16 events each, against the plain
+    path (one context, one event per launch). Latency: arrival to track
+    candidates on the host."""
+    import math
+    import numpy as np
+    from paper_2209_13711_gb300 import serve as S
+    rng = np.random.default_rng(4242)
+    pus = rng.uniform(140.0, 200.0, pool_size)
+    pool = S.EventPool([E.pileup_event(float(pu), 8000 + i, geom) for i, pu in enumerate(pus)])
+    sizes = (pool.n_hits, pool.n_seeds)
+    table = geom.module_table()
+
+    def run(slots, max_slots, max_batch, rate, n, seed):
+        reqs = S.make_requests(sizes, rate, n, seed=seed)
+        out, sch = S.serve(table, maps, pool, reqs, cfg=cuts, max_slots=max_slots, max_batch=max_batch, slots=slots)
+        return S.summarize(out), sch
+
+    def fmt(s):
+        return {k: (round(v, 3) if isinstance(v, float) else v) for k, v in s.items()}
+
+    res = {"pool": f"{pool_size} events, pileup uniform 140-200 (40 tracks per unit), inputs in pinned host memory",
+           "budget_gb": 60, "slots": 3, "events_per_slot": 16, "latency": "arrival to track candidates on the host"}
+    _, sch = run(None, 3, 16, math.inf, 96, 1)                # opens and captures every slot
+    slots = sch.slots
+    res["slot_device_gb"] = round(slots[0].device_bytes / 1e9, 3)
+    s, _ = run(slots, 3, 16, math.inf, 480, 2)
+    res["saturated"] = fmt(s)
+    res["poisson"] = {}
+    for rate in (200.0, 500.0, 1000.0):
+        s, _ = run(slots, 3, 16, rate, int(2.0 * rate), 3)
+        res["poisson"][f"{int(rate)}Hz"] = fmt(s)
+    for sl in slots:
+        sl.close()
+    _, sch1 = run(None, 1, 1, math.inf, 8, 4)
+    plain = {}
+    s, _ = run(sch1.slots, 1, 1, math.inf, 160, 5)
+    plain["saturated"] = fmt(s)
+    for rate in (200.0, 1000.0):
+        s, _ = run(sch1.slots, 1, 1, rate, int(1.0 * rate), 6)
+        plain[f"{int(rate)}Hz"] = fmt(s)
+    sch1.slots[0].close()
+    res["plain_one_event_per_launch"] = plain
+    return res
 
 
 def _oracle_event_seconds(seed):

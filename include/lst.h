@@ -134,6 +134,16 @@ lst_status lst_run_batch(lst_ctx* ctx, const lst_hits* hits, const int32_t* hit_
                          const lst_seeds* seeds, const int32_t* seed_offsets, int32_t n_events,
                          int32_t mem_is_device, void* cuda_stream);
 
+/* A batch given event by event: hits[e] and seeds[e] (n_events entries, HOST
+ * arrays of structs) point at each event's own arrays, host (mem_is_device =
+ * 0; pinned memory makes the copies asynchronous) or device (1). The library
+ * gathers them into its input staging with one copy per array and event on
+ * `cuda_stream`, then runs the chain as lst_run_batch does. The event arrays
+ * must stay valid until the stream reaches the copies. For serving loops whose
+ * requests arrive with their own buffers. */
+lst_status lst_run_events(lst_ctx* ctx, const lst_hits* hits, const lst_seeds* seeds, int32_t n_events,
+                          int32_t mem_is_device, void* cuda_stream);
+
 /* One event: lst_run_batch with n_events = 1. */
 lst_status lst_run_event(lst_ctx* ctx, const lst_hits* hits, const lst_seeds* seeds, int32_t mem_is_device,
                          void* cuda_stream);
@@ -148,6 +158,23 @@ lst_status lst_run_event(lst_ctx* ctx, const lst_hits* hits, const lst_seeds* se
  * unspecified. */
 lst_status lst_get_track_candidates(lst_ctx* ctx, int32_t event, int32_t capacity, int32_t* n_out,
                                     int32_t* type, int32_t* seed, int32_t* hits, float* pt_eta_phi);
+
+/* One track candidate of a batch, as packed by the chain's last stage. */
+typedef struct lst_tc {
+    int32_t type;        /* 0 pT5, 1 pT3, 2 T5, 3 pLS */
+    int32_t seed;        /* pixel seed index in the event, -1 for T5 */
+    int32_t hits[10];    /* outer-tracker hit indices in the event, -1 padded */
+    float pt, eta, phi0;
+    int32_t reserved;
+} lst_tc;
+
+/* Wait for the batch and copy every event's track candidates with two
+ * copies: offsets[0 .. n_events] (HOST, caller-owned; event e owns records
+ * offsets[e] .. offsets[e + 1] - 1) and at most `capacity` records into `out`
+ * (HOST; may be NULL when capacity is 0). LST_WARN_TRUNCATED when the batch
+ * holds more than `capacity` records. Candidate order within an event is
+ * unspecified. */
+lst_status lst_get_batch_track_candidates(lst_ctx* ctx, int32_t capacity, int32_t* offsets, lst_tc* out);
 
 /* Wait for the batch and copy one intermediate collection of event `event`
  * (for parity tests). kind: 0 MD, 1 LS, 2 T3, 3 T5, 4 pLS, 5 pT5, 6 pT3.
@@ -167,6 +194,47 @@ lst_status lst_get_objects(lst_ctx* ctx, int32_t event, int32_t kind, int32_t ca
 
 /* Wait for the batch and copy the per-event statistics. */
 lst_status lst_get_stats(lst_ctx* ctx, int32_t event, lst_stats* out);
+
+/* Non-blocking: 1 when the last batch has finished on the device, 0 while it
+ * runs (or when no batch was run), < 0 on error. */
+int32_t lst_query(lst_ctx* ctx);
+/* Device memory held by the context (bytes). */
+int64_t lst_device_bytes(lst_ctx* ctx);
+
+/* Launch shapes and the autotuner (batching, with per-event offsets and one
+ * graph per batch, replaces the paper's one-event-per-stream overlap of
+ * Section 2.2; the launch shape of each stage is this library's own knob, the
+ * paper fixes none).
+ *
+ * The chain is a fixed sequence of stages (lst_launch_stage_count of them,
+ * in Fig. KernelFlow order). Every stage whose flags have bit 0 set loops over
+ * its units with a grid-stride loop, so its grid (n_SM x blocks_per_sm) may be
+ * any size; bit 1 set means the stage indexes threads only through blockDim,
+ * so its block may be any multiple of 32 up to the kernel's limit. Results do
+ * not depend on the launch shape (object sets are identical; the order of
+ * objects within an event's arrays may differ).
+ *
+ * lst_get_launch_config: the stage's name (static storage), its current
+ *   blocks per SM (0 for a stage with a fixed grid), threads per block and flags.
+ * lst_set_launch_config: 0 restores the default; LST_ERR_ARG for a stage out
+ *   of range, a shape the stage does not allow, or a block above what the
+ *   kernel can launch. Waits for the running batch; the next lst_run_batch
+ *   captures a new graph.
+ * lst_autotune: runs the given batch (same arguments as lst_run_batch) `reps`
+ *   times (1..64) per candidate shape with profiling on, and keeps for every
+ *   stage the shape with the smallest median device time (candidates: 1, 2, 3,
+ *   4, 6, 8, 12 or 16 blocks per SM, with the default block or, for generic
+ *   stages, 64, 128, 256 or 512 threads). *ms_before / *ms_after (optional):
+ *   summed stage times of one run before and after. Synchronous; leaves the
+ *   profiling switch as it found it and the context's results are those of the
+ *   last tuning run of the batch. */
+int32_t lst_launch_stage_count(void);
+lst_status lst_get_launch_config(lst_ctx* ctx, int32_t stage, const char** name, int32_t* blocks_per_sm,
+                                 int32_t* block, int32_t* flags);
+lst_status lst_set_launch_config(lst_ctx* ctx, int32_t stage, int32_t blocks_per_sm, int32_t block);
+lst_status lst_autotune(lst_ctx* ctx, const lst_hits* hits, const int32_t* hit_off, const lst_seeds* seeds,
+                        const int32_t* seed_off, int32_t n_events, int32_t mem_is_device, void* stream,
+                        int32_t reps, float* ms_before, float* ms_after);
 
 /* Number of kernel launches enqueued by the last lst_run_batch. */
 int32_t lst_last_launch_count(lst_ctx* ctx);

@@ -568,7 +568,6 @@ __global__ void __launch_bounds__(kT5Warps * 32, 6) k_t5(Arena A, DevCfg c) {
 // take the unit's chunks of 32 T3_1; per-chunk counts, a scan, one
 // reservation, then every chunk is enumerated again and written at its offset
 // (the same order as one warp would produce).
-constexpr int kOvfWarps = 8;
 constexpr int kOvfChunks = (kT3Stage + 31) / 32;
 
 __global__ void __launch_bounds__(kOvfWarps * 32) k_t5_overflow(Arena A, DevCfg c) {

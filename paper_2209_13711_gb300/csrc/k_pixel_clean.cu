@@ -475,4 +475,47 @@ __global__ void k_clean_pls(Arena A, DevCfg c) {
     }
 }
 
+// The batch's track candidates, event after event, into one record array:
+// one block per event (grid-stride over events) sums the counts of the
+// events before it for its offset, then copies its slab.
+__global__ void k_tc_pack(Arena A) {
+    __shared__ int red[32];
+    __shared__ int s_off;
+    const int n_ev = A.bd->n_ev;
+    const int nw = (blockDim.x + 31) >> 5, w = threadIdx.x >> 5;
+    for (int e = blockIdx.x; e < n_ev; e += gridDim.x) {
+        int part = 0;
+        for (int j = threadIdx.x; j < e; j += blockDim.x) part += min(A.tc_cnt[j], A.tc_cap);
+        for (int d = 16; d; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+        if (lane_id() == 0) red[w] = part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int k = 0; k < nw; ++k) t += red[k];
+            s_off = t;
+        }
+        __syncthreads();
+        const int off = s_off, n = min(A.tc_cnt[e], A.tc_cap);
+        if (threadIdx.x == 0) {
+            A.tc_off[e] = off;
+            if (e == n_ev - 1) A.tc_off[n_ev] = off + n;
+        }
+        const size_t src = (size_t)e * A.tc_cap;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            TcRec r;
+            r.type = A.tc_type[src + i];
+            r.seed = A.tc_seed[src + i];
+            const int* h = A.tc_hits + 10 * (src + i);
+#pragma unroll
+            for (int k = 0; k < 10; ++k) r.hits[k] = h[k];
+            r.pt = A.tc_pt[src + i];
+            r.eta = A.tc_eta[src + i];
+            r.phi = A.tc_phi[src + i];
+            r.reserved = 0;
+            A.tc_rec[off + i] = r;
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace lst

@@ -31,6 +31,58 @@ struct Buffer {
     }
 };
 
+// The stages of the chain (Fig. KernelFlow order) with their default launch
+// shape. `generic` stages index threads only through blockDim and grid-stride
+// loops, so any block size is valid for them; the warp-per-unit stages size
+// their shared-memory stages by a compile-time warp count and keep their block.
+// `tunable` stages are grid-stride over their units, so any grid is valid.
+enum LaunchId {
+    L_RESET, L_BIN_COUNT, L_BIN_SCAN, L_BIN_SCATTER, L_MD, L_LS, L_T3, L_T5, L_T5_OVERFLOW, L_T5_REFINE,
+    L_T5_MLP, L_T5_MLP_SELECT, L_PLS, L_PT5, L_PT5_REFINE, L_PT3, L_PT3_REFINE, L_CLEAN_KEYS, L_CLEAN_KEEP,
+    L_CLEAN_PT5, L_CLEAN_PT3_CROSS, L_CLEAN_PT3_MARK, L_CLEAN_T5, L_CLEAN_PLS, L_TC_PACK, kNumLaunch
+};
+
+struct LaunchInfo {
+    const char* name;
+    int bpsm;       // default blocks per SM
+    int block;      // default threads per block
+    bool tunable;   // grid may change
+    bool generic;   // block size may change
+};
+
+const LaunchInfo kLaunch[kNumLaunch] = {
+    {"reset", 8, 256, true, true},
+    {"bin_count", 8, 256, true, true},
+    {"bin_scan", 0, 1024, false, false},        // one block per event
+    {"bin_scatter", 8, 256, true, true},
+    {"md", 4, kMdWarps * 32, true, false},
+    {"ls", 8, kLsWarps * 32, true, false},
+    {"t3", 8, kT3Warps * 32, true, false},
+    {"t5", 6, kT5Warps * 32, true, false},
+    {"t5_overflow", 1, kOvfWarps * 32, false, false},
+    {"t5_refine", 4, 128, true, true},
+    {"t5_mlp", 4, 128, true, false},
+    {"t5_mlp_select", 4, 128, true, true},
+    {"pls", 4, 128, true, true},
+    {"pt5", 8, kPtWarps * 32, true, false},
+    {"pt5_refine", 2, 128, true, true},
+    {"pt3", 8, kPtWarps * 32, true, false},
+    {"pt3_refine", 2, 128, true, true},
+    {"clean_keys", 4, 256, true, true},
+    {"clean_keep", 4, 256, true, true},
+    {"clean_pt5", 2, 256, true, true},
+    {"clean_pt3_cross", 2, 256, true, true},
+    {"clean_pt3_mark", 2, 256, true, true},
+    {"clean_t5", 4, 256, true, true},
+    {"clean_pls", 4, 128, true, true},
+    {"tc_pack", 1, 256, true, true},
+};
+
+struct LaunchCfg {
+    int bpsm = 0;    // 0: the default
+    int block = 0;
+};
+
 }  // namespace
 
 struct lst_ctx {
@@ -65,11 +117,11 @@ struct lst_ctx {
     BatchDesc* h_bd = nullptr;        // pinned staging of the descriptor
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
-    static constexpr int kMaxLaunch = 32;
-    int grid_mul[kMaxLaunch] = {};    // blocks per SM of each launch slot (0: the default)
+    LaunchCfg tune[kNumLaunch];       // per-stage launch shape (autotuner or caller)
     static constexpr int kMaxProf = 64;
     cudaEvent_t prof_ev[2 * kMaxProf] = {};
     const char* prof_name[kMaxProf] = {};
+    int prof_id[kMaxProf] = {};
 };
 
 #define CK(x)                                      \
@@ -279,6 +331,8 @@ static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_m
     A.tc_type = b.take<int>(TC); A.tc_seed = b.take<int>(TC); A.tc_obj = b.take<int>(TC);
     A.tc_hits = b.take<int>(10 * TC);
     A.tc_pt = b.take<float>(TC); A.tc_eta = b.take<float>(TC); A.tc_phi = b.take<float>(TC);
+    A.tc_rec = b.take<TcRec>(TC);
+    A.tc_off = b.take<int>(E + 1);
 }
 
 lst_status lst_load_geometry(lst_ctx* c, const lst_module* mods, int32_t n_mod, const int32_t* conn_off,
@@ -334,94 +388,70 @@ lst_status lst_load_geometry(lst_ctx* c, const lst_module* mods, int32_t n_mod, 
 // The launch sequence of one batch (Fig. KernelFlow order). Grids are fixed
 // per context (grid-stride loops read the batch shape from the descriptor),
 // so the sequence can be captured once into a CUDA graph.
+static int grid_of(const lst_ctx* c, int id) {
+    const LaunchInfo& k = kLaunch[id];
+    const int m = c->tune[id].bpsm > 0 ? c->tune[id].bpsm : k.bpsm;
+    return c->n_sm * m;
+}
+
+static int block_of(const lst_ctx* c, int id) {
+    const LaunchInfo& k = kLaunch[id];
+    return (k.generic && c->tune[id].block > 0) ? c->tune[id].block : k.block;
+}
+
 static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile) {
     const Arena& A = c->A;
     const DevCfg& dc = c->dc;
-    const int nsm = c->n_sm;
     int L = 0;
-    auto G = [&](int def) { int m = c->grid_mul[L]; return nsm * (m > 0 ? m : def); };
-#define LAUNCH(NAME, ...)                                                              \
+#define GB(ID) grid_of(c, ID), block_of(c, ID)
+#define LAUNCH(ID, ...)                                                                \
     do {                                                                               \
         if (profile && L < lst_ctx::kMaxProf) {                                        \
-            c->prof_name[L] = NAME;                                                    \
+            c->prof_name[L] = kLaunch[ID].name;                                        \
+            c->prof_id[L] = ID;                                                        \
             cudaEventRecord(c->prof_ev[2 * L], st);                                    \
         }                                                                              \
         __VA_ARGS__;                                                                   \
         if (profile && L < lst_ctx::kMaxProf) cudaEventRecord(c->prof_ev[2 * L + 1], st); \
         ++L;                                                                           \
     } while (0)
-    LAUNCH("reset", k_reset<<<G(8), 256, 0, st>>>(A));
-    LAUNCH("bin_count", k_bin_count<<<G(8), 256, 0, st>>>(A));
-    LAUNCH("bin_scan", k_bin_scan<<<A.max_events, 1024, 0, st>>>(A));
-    LAUNCH("bin_scatter", k_bin_scatter<<<G(8), 256, 0, st>>>(A));
-    LAUNCH("md", k_md<<<G(4), kMdWarps * 32, md_smem_bytes(), st>>>(A, dc));
-    LAUNCH("ls", k_ls<<<G(8), kLsWarps * 32, 0, st>>>(A, dc));
-    LAUNCH("t3", k_t3<<<G(8), kT3Warps * 32, 0, st>>>(A, dc));
-    LAUNCH("t5", k_t5<<<G(6), kT5Warps * 32, 0, st>>>(A, dc));
-    LAUNCH("t5_overflow", k_t5_overflow<<<nsm, 256, 0, st>>>(A, dc));
-    LAUNCH("t5_refine", k_t5_refine<<<G(4), 128, 0, st>>>(A, dc));
+    LAUNCH(L_RESET, k_reset<<<GB(L_RESET), 0, st>>>(A));
+    LAUNCH(L_BIN_COUNT, k_bin_count<<<GB(L_BIN_COUNT), 0, st>>>(A));
+    LAUNCH(L_BIN_SCAN, k_bin_scan<<<A.max_events, 1024, 0, st>>>(A));
+    LAUNCH(L_BIN_SCATTER, k_bin_scatter<<<GB(L_BIN_SCATTER), 0, st>>>(A));
+    LAUNCH(L_MD, k_md<<<GB(L_MD), md_smem_bytes(), st>>>(A, dc));
+    LAUNCH(L_LS, k_ls<<<GB(L_LS), 0, st>>>(A, dc));
+    LAUNCH(L_T3, k_t3<<<GB(L_T3), 0, st>>>(A, dc));
+    LAUNCH(L_T5, k_t5<<<GB(L_T5), 0, st>>>(A, dc));
+    LAUNCH(L_T5_OVERFLOW, k_t5_overflow<<<c->n_sm, kOvfWarps * 32, 0, st>>>(A, dc));
+    LAUNCH(L_T5_REFINE, k_t5_refine<<<GB(L_T5_REFINE), 0, st>>>(A, dc));
     if (c->mlp) {
-        LAUNCH("t5_mlp", k_mlp_forward<<<G(4), 128, 0, st>>>(lst_mlp_device_params(c->mlp), A.t5_feat, A.t5_cap,
-                                                            A.counters + 3, A.t5_mlp, MlpSaved{}));
-        LAUNCH("t5_mlp_select", k_t5_mlp_select<<<G(4), 128, 0, st>>>(A, dc));
+        LAUNCH(L_T5_MLP, k_mlp_forward<<<GB(L_T5_MLP), 0, st>>>(lst_mlp_device_params(c->mlp), A.t5_feat, A.t5_cap,
+                                                                A.counters + 3, A.t5_mlp, MlpSaved{}));
+        LAUNCH(L_T5_MLP_SELECT, k_t5_mlp_select<<<GB(L_T5_MLP_SELECT), 0, st>>>(A, dc));
     }
-    LAUNCH("pls", k_pls<<<G(4), 128, 0, st>>>(A, dc));
-    LAUNCH("pt5", k_pt5<<<G(8), kPtWarps * 32, 0, st>>>(A, dc));
-    LAUNCH("pt5_refine", k_pt5_refine<<<G(2), 128, 0, st>>>(A, dc));
-    LAUNCH("pt3", k_pt3<<<G(8), kPtWarps * 32, 0, st>>>(A, dc));
-    LAUNCH("pt3_refine", k_pt3_refine<<<G(2), 128, 0, st>>>(A, dc));
-    LAUNCH("clean_keys", k_clean_keys<<<G(4), 256, 0, st>>>(A, 0));
-    LAUNCH("clean_keep", k_clean_keys<<<G(4), 256, 0, st>>>(A, 1));
-    LAUNCH("clean_pt5", k_clean_pt5<<<G(2), 256, 0, st>>>(A));
-    LAUNCH("clean_pt3_cross", k_clean_pt3_cross<<<G(2), 256, 0, st>>>(A, dc));
-    LAUNCH("clean_pt3_mark", k_clean_pt3_mark<<<G(2), 256, 0, st>>>(A));
-    LAUNCH("clean_t5", k_clean_t5<<<G(4), 256, 0, st>>>(A, dc));
-    LAUNCH("clean_pls", k_clean_pls<<<G(4), 128, 0, st>>>(A, dc));
+    LAUNCH(L_PLS, k_pls<<<GB(L_PLS), 0, st>>>(A, dc));
+    LAUNCH(L_PT5, k_pt5<<<GB(L_PT5), 0, st>>>(A, dc));
+    LAUNCH(L_PT5_REFINE, k_pt5_refine<<<GB(L_PT5_REFINE), 0, st>>>(A, dc));
+    LAUNCH(L_PT3, k_pt3<<<GB(L_PT3), 0, st>>>(A, dc));
+    LAUNCH(L_PT3_REFINE, k_pt3_refine<<<GB(L_PT3_REFINE), 0, st>>>(A, dc));
+    LAUNCH(L_CLEAN_KEYS, k_clean_keys<<<GB(L_CLEAN_KEYS), 0, st>>>(A, 0));
+    LAUNCH(L_CLEAN_KEEP, k_clean_keys<<<GB(L_CLEAN_KEEP), 0, st>>>(A, 1));
+    LAUNCH(L_CLEAN_PT5, k_clean_pt5<<<GB(L_CLEAN_PT5), 0, st>>>(A));
+    LAUNCH(L_CLEAN_PT3_CROSS, k_clean_pt3_cross<<<GB(L_CLEAN_PT3_CROSS), 0, st>>>(A, dc));
+    LAUNCH(L_CLEAN_PT3_MARK, k_clean_pt3_mark<<<GB(L_CLEAN_PT3_MARK), 0, st>>>(A));
+    LAUNCH(L_CLEAN_T5, k_clean_t5<<<GB(L_CLEAN_T5), 0, st>>>(A, dc));
+    LAUNCH(L_CLEAN_PLS, k_clean_pls<<<GB(L_CLEAN_PLS), 0, st>>>(A, dc));
+    LAUNCH(L_TC_PACK, k_tc_pack<<<GB(L_TC_PACK), 0, st>>>(A));
 #undef LAUNCH
+#undef GB
     c->launches = L;
 }
 
-lst_status lst_run_batch(lst_ctx* c, const lst_hits* hits, const int32_t* hit_off, const lst_seeds* seeds,
-                         const int32_t* seed_off, int32_t n_ev, int32_t mem_is_device, void* stream_) {
-    if (!c) return LST_ERR_ARG;
-    if (!c->geometry) return LST_ERR_NO_GEOMETRY;
-    if (!hits || !hit_off || !seeds || !seed_off || n_ev <= 0) return LST_ERR_ARG;
-    if (n_ev > c->cap.max_events || hits->n > c->cap.max_hits || seeds->n > c->cap.max_seeds) return LST_ERR_CAPACITY;
-    if (hits->n < 0 || seeds->n < 0 || hit_off[0] != 0 || seed_off[0] != 0 || hit_off[n_ev] != hits->n ||
-        seed_off[n_ev] != seeds->n)
-        return LST_ERR_ARG;
-    for (int e = 0; e < n_ev; ++e)
-        if (hit_off[e + 1] < hit_off[e] || seed_off[e + 1] < seed_off[e]) return LST_ERR_ARG;
-    if ((hits->n && (!hits->x || !hits->y || !hits->z || !hits->module || !hits->side)) || (seeds->n && !seeds->xyz))
-        return LST_ERR_ARG;
-    CK(cudaSetDevice(c->device));
-    cudaStream_t st = static_cast<cudaStream_t>(stream_);
-    if (c->ran) CK(cudaEventSynchronize(c->done));   // the pinned staging is reused
-    c->n_ev = n_ev;
-    c->hit_off_host.assign(hit_off, hit_off + n_ev + 1);
-    c->seed_off_host.assign(seed_off, seed_off + n_ev + 1);
-    std::memcpy(c->h_offsets, hit_off, sizeof(int) * (n_ev + 1));
-    std::memcpy(c->h_offsets + n_ev + 1, seed_off, sizeof(int) * (n_ev + 1));
-    const size_t H = hits->n, S = seeds->n;
-    BatchDesc& d = *c->h_bd;
-    d.n_ev = n_ev;
-    d.n_hits = (int)H;
-    d.n_seeds = (int)S;
-    if (mem_is_device) {
-        d.hx = hits->x; d.hy = hits->y; d.hz = hits->z; d.hmod = hits->module; d.hside = hits->side;
-        d.seeds = seeds->xyz;
-    } else {
-        if (H) {
-            CK(cudaMemcpyAsync(c->in_x, hits->x, 4 * H, cudaMemcpyHostToDevice, st));
-            CK(cudaMemcpyAsync(c->in_y, hits->y, 4 * H, cudaMemcpyHostToDevice, st));
-            CK(cudaMemcpyAsync(c->in_z, hits->z, 4 * H, cudaMemcpyHostToDevice, st));
-            CK(cudaMemcpyAsync(c->in_mod, hits->module, 4 * H, cudaMemcpyHostToDevice, st));
-            CK(cudaMemcpyAsync(c->in_side, hits->side, H, cudaMemcpyHostToDevice, st));
-        }
-        if (S) CK(cudaMemcpyAsync(c->in_seeds, seeds->xyz, 36 * S, cudaMemcpyHostToDevice, st));
-        d.hx = c->in_x; d.hy = c->in_y; d.hz = c->in_z; d.hmod = c->in_mod; d.hside = c->in_side;
-        d.seeds = c->in_seeds;
-    }
+// Offsets and descriptor are in the pinned staging (h_offsets, h_bd); copy
+// them, launch the chain (captured graph, or direct launches when profiling)
+// and record the completion event.
+static lst_status launch_prepared(lst_ctx* c, cudaStream_t st, int n_ev) {
     CK(cudaMemcpyAsync(c->d_hit_off, c->h_offsets, sizeof(int) * (n_ev + 1), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_seed_off, c->h_offsets + n_ev + 1, sizeof(int) * (n_ev + 1), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_bd, c->h_bd, sizeof(BatchDesc), cudaMemcpyHostToDevice, st));
@@ -449,6 +479,101 @@ lst_status lst_run_batch(lst_ctx* c, const lst_hits* hits, const int32_t* hit_of
     return LST_OK;
 }
 
+// Host copies of the batch's offsets (before the staging is overwritten, the
+// previous batch must have finished: the pinned staging is reused).
+static void set_offsets(lst_ctx* c, const int32_t* hit_off, const int32_t* seed_off, int n_ev) {
+    c->n_ev = n_ev;
+    c->hit_off_host.assign(hit_off, hit_off + n_ev + 1);
+    c->seed_off_host.assign(seed_off, seed_off + n_ev + 1);
+    std::memcpy(c->h_offsets, hit_off, sizeof(int) * (n_ev + 1));
+    std::memcpy(c->h_offsets + n_ev + 1, seed_off, sizeof(int) * (n_ev + 1));
+}
+
+static void use_staging(lst_ctx* c, BatchDesc& d) {
+    d.hx = c->in_x; d.hy = c->in_y; d.hz = c->in_z; d.hmod = c->in_mod; d.hside = c->in_side;
+    d.seeds = c->in_seeds;
+}
+
+lst_status lst_run_batch(lst_ctx* c, const lst_hits* hits, const int32_t* hit_off, const lst_seeds* seeds,
+                         const int32_t* seed_off, int32_t n_ev, int32_t mem_is_device, void* stream_) {
+    if (!c) return LST_ERR_ARG;
+    if (!c->geometry) return LST_ERR_NO_GEOMETRY;
+    if (!hits || !hit_off || !seeds || !seed_off || n_ev <= 0) return LST_ERR_ARG;
+    if (n_ev > c->cap.max_events || hits->n > c->cap.max_hits || seeds->n > c->cap.max_seeds) return LST_ERR_CAPACITY;
+    if (hits->n < 0 || seeds->n < 0 || hit_off[0] != 0 || seed_off[0] != 0 || hit_off[n_ev] != hits->n ||
+        seed_off[n_ev] != seeds->n)
+        return LST_ERR_ARG;
+    for (int e = 0; e < n_ev; ++e)
+        if (hit_off[e + 1] < hit_off[e] || seed_off[e + 1] < seed_off[e]) return LST_ERR_ARG;
+    if ((hits->n && (!hits->x || !hits->y || !hits->z || !hits->module || !hits->side)) || (seeds->n && !seeds->xyz))
+        return LST_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream_);
+    if (c->ran) CK(cudaEventSynchronize(c->done));   // the pinned staging is reused
+    set_offsets(c, hit_off, seed_off, n_ev);
+    const size_t H = hits->n, S = seeds->n;
+    BatchDesc& d = *c->h_bd;
+    d.n_ev = n_ev;
+    d.n_hits = (int)H;
+    d.n_seeds = (int)S;
+    if (mem_is_device) {
+        d.hx = hits->x; d.hy = hits->y; d.hz = hits->z; d.hmod = hits->module; d.hside = hits->side;
+        d.seeds = seeds->xyz;
+    } else {
+        if (H) {
+            CK(cudaMemcpyAsync(c->in_x, hits->x, 4 * H, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(c->in_y, hits->y, 4 * H, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(c->in_z, hits->z, 4 * H, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(c->in_mod, hits->module, 4 * H, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(c->in_side, hits->side, H, cudaMemcpyHostToDevice, st));
+        }
+        if (S) CK(cudaMemcpyAsync(c->in_seeds, seeds->xyz, 36 * S, cudaMemcpyHostToDevice, st));
+        use_staging(c, d);
+    }
+    return launch_prepared(c, st, n_ev);
+}
+
+lst_status lst_run_events(lst_ctx* c, const lst_hits* hits, const lst_seeds* seeds, int32_t n_ev,
+                          int32_t mem_is_device, void* stream_) {
+    if (!c) return LST_ERR_ARG;
+    if (!c->geometry) return LST_ERR_NO_GEOMETRY;
+    if (!hits || !seeds || n_ev <= 0) return LST_ERR_ARG;
+    if (n_ev > c->cap.max_events) return LST_ERR_CAPACITY;
+    std::vector<int32_t> ho(n_ev + 1, 0), so(n_ev + 1, 0);
+    for (int e = 0; e < n_ev; ++e) {
+        const lst_hits& h = hits[e];
+        const lst_seeds& q = seeds[e];
+        if (h.n < 0 || q.n < 0) return LST_ERR_ARG;
+        if ((h.n && (!h.x || !h.y || !h.z || !h.module || !h.side)) || (q.n && !q.xyz)) return LST_ERR_ARG;
+        ho[e + 1] = ho[e] + h.n;
+        so[e + 1] = so[e] + q.n;
+        if (ho[e + 1] > c->cap.max_hits || so[e + 1] > c->cap.max_seeds) return LST_ERR_CAPACITY;
+    }
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream_);
+    if (c->ran) CK(cudaEventSynchronize(c->done));
+    set_offsets(c, ho.data(), so.data(), n_ev);
+    const cudaMemcpyKind kind = mem_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int e = 0; e < n_ev; ++e) {
+        const lst_hits& h = hits[e];
+        const size_t o = ho[e], n = h.n;
+        if (n) {
+            CK(cudaMemcpyAsync(c->in_x + o, h.x, 4 * n, kind, st));
+            CK(cudaMemcpyAsync(c->in_y + o, h.y, 4 * n, kind, st));
+            CK(cudaMemcpyAsync(c->in_z + o, h.z, 4 * n, kind, st));
+            CK(cudaMemcpyAsync(c->in_mod + o, h.module, 4 * n, kind, st));
+            CK(cudaMemcpyAsync(c->in_side + o, h.side, n, kind, st));
+        }
+        if (seeds[e].n) CK(cudaMemcpyAsync(c->in_seeds + 9 * (size_t)so[e], seeds[e].xyz, 36 * (size_t)seeds[e].n, kind, st));
+    }
+    BatchDesc& d = *c->h_bd;
+    d.n_ev = n_ev;
+    d.n_hits = ho[n_ev];
+    d.n_seeds = so[n_ev];
+    use_staging(c, d);
+    return launch_prepared(c, st, n_ev);
+}
+
 lst_status lst_run_event(lst_ctx* c, const lst_hits* hits, const lst_seeds* seeds, int32_t mem_is_device,
                          void* stream) {
     if (!hits || !seeds) return LST_ERR_ARG;
@@ -457,6 +582,18 @@ lst_status lst_run_event(lst_ctx* c, const lst_hits* hits, const lst_seeds* seed
 }
 
 int32_t lst_last_launch_count(lst_ctx* c) { return c ? c->launches : 0; }
+
+int32_t lst_query(lst_ctx* c) {
+    if (!c) return LST_ERR_ARG;
+    if (!c->ran) return 0;
+    if (cudaSetDevice(c->device) != cudaSuccess) return LST_ERR_CUDA;
+    cudaError_t e = cudaEventQuery(c->done);
+    if (e == cudaSuccess) return 1;
+    if (e == cudaErrorNotReady) return 0;
+    return LST_ERR_CUDA;
+}
+
+int64_t lst_device_bytes(lst_ctx* c) { return c ? (int64_t)c->dev_bytes : 0; }
 
 lst_status lst_set_profiling(lst_ctx* c, int32_t enable) {
     if (!c) return LST_ERR_ARG;
@@ -480,6 +617,169 @@ lst_status lst_get_kernel_times(lst_ctx* c, int32_t capacity, int32_t* n_out, co
         if (ms) CK(cudaEventElapsedTime(ms + i, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]));
     }
     return n > capacity ? LST_WARN_TRUNCATED : LST_OK;
+}
+
+static const void* launch_fn(int id) {
+    switch (id) {
+        case L_RESET: return (const void*)k_reset;
+        case L_BIN_COUNT: return (const void*)k_bin_count;
+        case L_BIN_SCAN: return (const void*)k_bin_scan;
+        case L_BIN_SCATTER: return (const void*)k_bin_scatter;
+        case L_MD: return (const void*)k_md;
+        case L_LS: return (const void*)k_ls;
+        case L_T3: return (const void*)k_t3;
+        case L_T5: return (const void*)k_t5;
+        case L_T5_OVERFLOW: return (const void*)k_t5_overflow;
+        case L_T5_REFINE: return (const void*)k_t5_refine;
+        case L_T5_MLP: return (const void*)k_mlp_forward;
+        case L_T5_MLP_SELECT: return (const void*)k_t5_mlp_select;
+        case L_PLS: return (const void*)k_pls;
+        case L_PT5: return (const void*)k_pt5;
+        case L_PT5_REFINE: return (const void*)k_pt5_refine;
+        case L_PT3: return (const void*)k_pt3;
+        case L_PT3_REFINE: return (const void*)k_pt3_refine;
+        case L_CLEAN_KEYS: case L_CLEAN_KEEP: return (const void*)k_clean_keys;
+        case L_CLEAN_PT5: return (const void*)k_clean_pt5;
+        case L_CLEAN_PT3_CROSS: return (const void*)k_clean_pt3_cross;
+        case L_CLEAN_PT3_MARK: return (const void*)k_clean_pt3_mark;
+        case L_CLEAN_T5: return (const void*)k_clean_t5;
+        case L_CLEAN_PLS: return (const void*)k_clean_pls;
+        case L_TC_PACK: return (const void*)k_tc_pack;
+        default: return nullptr;
+    }
+}
+
+// Is (blocks per SM, block) a valid shape for the stage? 0 keeps the default.
+static lst_status check_shape(int id, int bpsm, int block) {
+    if (id < 0 || id >= kNumLaunch || bpsm < 0 || bpsm > 64 || block < 0) return LST_ERR_ARG;
+    const LaunchInfo& k = kLaunch[id];
+    if (bpsm && !k.tunable) return LST_ERR_ARG;
+    if (block) {
+        if (!k.generic || block % 32 || block > 1024) return LST_ERR_ARG;
+        cudaFuncAttributes fa{};
+        CK(cudaFuncGetAttributes(&fa, launch_fn(id)));
+        if (block > fa.maxThreadsPerBlock) return LST_ERR_ARG;
+    }
+    return LST_OK;
+}
+
+static lst_status drop_graph(lst_ctx* c) {
+    if (c->ran) CK(cudaEventSynchronize(c->done));
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return LST_OK;
+}
+
+int32_t lst_launch_stage_count(void) { return kNumLaunch; }
+
+lst_status lst_get_launch_config(lst_ctx* c, int32_t stage, const char** name, int32_t* blocks_per_sm,
+                                 int32_t* block, int32_t* flags) {
+    if (!c || stage < 0 || stage >= kNumLaunch) return LST_ERR_ARG;
+    const LaunchInfo& k = kLaunch[stage];
+    if (name) *name = k.name;
+    if (blocks_per_sm) *blocks_per_sm = k.tunable ? (c->tune[stage].bpsm > 0 ? c->tune[stage].bpsm : k.bpsm) : 0;
+    if (block) *block = block_of(c, stage);
+    if (flags) *flags = (k.tunable ? 1 : 0) | (k.generic ? 2 : 0);
+    return LST_OK;
+}
+
+lst_status lst_set_launch_config(lst_ctx* c, int32_t stage, int32_t blocks_per_sm, int32_t block) {
+    if (!c) return LST_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    lst_status s = check_shape(stage, blocks_per_sm, block);
+    if (s != LST_OK) return s;
+    s = drop_graph(c);
+    if (s != LST_OK) return s;
+    c->tune[stage].bpsm = blocks_per_sm;
+    c->tune[stage].block = block;
+    return LST_OK;
+}
+
+// Median device time of every stage over `reps` profiled runs of the batch.
+static lst_status time_stages(lst_ctx* c, const lst_hits* hits, const int32_t* hit_off, const lst_seeds* seeds,
+                              const int32_t* seed_off, int32_t n_ev, int32_t mem_is_device, void* stream, int reps,
+                              float* med, float* total) {
+    std::vector<float> t[kNumLaunch];
+    float tot = 0.f;
+    for (int r = 0; r < reps; ++r) {
+        lst_status s = lst_run_batch(c, hits, hit_off, seeds, seed_off, n_ev, mem_is_device, stream);
+        if (s != LST_OK) return s;
+        CK(cudaEventSynchronize(c->done));
+        CK(cudaGetLastError());
+        const int n = std::min(c->launches, (int)lst_ctx::kMaxProf);
+        for (int i = 0; i < n; ++i) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]));
+            t[c->prof_id[i]].push_back(ms);
+            tot += ms;
+        }
+    }
+    for (int id = 0; id < kNumLaunch; ++id) {
+        auto& v = t[id];
+        if (v.empty()) {
+            med[id] = 0.f;
+            continue;
+        }
+        std::sort(v.begin(), v.end());
+        med[id] = v[v.size() / 2];
+    }
+    if (total) *total = tot / reps;
+    return LST_OK;
+}
+
+lst_status lst_autotune(lst_ctx* c, const lst_hits* hits, const int32_t* hit_off, const lst_seeds* seeds,
+                        const int32_t* seed_off, int32_t n_ev, int32_t mem_is_device, void* stream, int32_t reps,
+                        float* ms_before, float* ms_after) {
+    if (!c || reps <= 0 || reps > 64) return LST_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    const bool was_profiling = c->profiling;
+    lst_status s = lst_set_profiling(c, 1);
+    if (s != LST_OK) return s;
+    LaunchCfg start[kNumLaunch], best_cfg[kNumLaunch];
+    float best[kNumLaunch], med[kNumLaunch];
+    std::copy(c->tune, c->tune + kNumLaunch, start);
+    std::copy(c->tune, c->tune + kNumLaunch, best_cfg);
+    float t0 = 0.f;
+    s = time_stages(c, hits, hit_off, seeds, seed_off, n_ev, mem_is_device, stream, reps, best, &t0);
+    static const int kBpsm[] = {1, 2, 3, 4, 6, 8, 12, 16};
+    static const int kBlock[] = {0, 64, 128, 256, 512};
+    for (int bi = 0; s == LST_OK && bi < (int)(sizeof(kBlock) / sizeof(int)); ++bi) {
+        for (int m : kBpsm) {
+            const int b = kBlock[bi];
+            if (b * m > 4096) continue;
+            bool any = false;
+            for (int id = 0; id < kNumLaunch; ++id) {
+                c->tune[id] = start[id];
+                if (!kLaunch[id].tunable || (b && !kLaunch[id].generic)) continue;
+                if (check_shape(id, m, b) != LST_OK) continue;
+                c->tune[id] = LaunchCfg{m, b};
+                any = true;
+            }
+            if (!any) continue;
+            s = time_stages(c, hits, hit_off, seeds, seed_off, n_ev, mem_is_device, stream, reps, med, nullptr);
+            if (s != LST_OK) break;
+            for (int id = 0; id < kNumLaunch; ++id) {
+                const LaunchCfg& t = c->tune[id];
+                if (t.bpsm != m || t.block != b || med[id] <= 0.f) continue;
+                if (med[id] < best[id]) {
+                    best[id] = med[id];
+                    best_cfg[id] = t;
+                }
+            }
+        }
+    }
+    std::copy(s == LST_OK ? best_cfg : start, (s == LST_OK ? best_cfg : start) + kNumLaunch, c->tune);
+    float t1 = 0.f;
+    if (s == LST_OK && ms_after)
+        s = time_stages(c, hits, hit_off, seeds, seed_off, n_ev, mem_is_device, stream, reps, med, &t1);
+    lst_status s2 = lst_set_profiling(c, was_profiling ? 1 : 0);
+    lst_status s3 = drop_graph(c);
+    if (ms_before) *ms_before = t0;
+    if (ms_after) *ms_after = t1;
+    if (s != LST_OK) return s;
+    return s2 != LST_OK ? s2 : s3;
 }
 
 static lst_status wait_batch(lst_ctx* c, int32_t event) {
@@ -604,6 +904,21 @@ lst_status lst_get_track_candidates(lst_ctx* c, int32_t event, int32_t capacity,
         }
     }
     return n > capacity ? LST_WARN_TRUNCATED : LST_OK;
+}
+
+static_assert(sizeof(lst_tc) == sizeof(TcRec), "lst_tc mirrors the packed record");
+
+lst_status lst_get_batch_track_candidates(lst_ctx* c, int32_t capacity, int32_t* offsets, lst_tc* out) {
+    if (!c || !offsets || capacity < 0 || (capacity > 0 && !out)) return LST_ERR_ARG;
+    if (!c->ran) return LST_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cudaEventSynchronize(c->done));
+    CK(cudaGetLastError());
+    CK(cudaMemcpy(offsets, c->A.tc_off, sizeof(int) * (c->n_ev + 1), cudaMemcpyDeviceToHost));
+    const int total = offsets[c->n_ev];
+    const int k = std::min(total, (int)capacity);
+    if (k > 0) CK(cudaMemcpy(out, c->A.tc_rec, sizeof(lst_tc) * (size_t)k, cudaMemcpyDeviceToHost));
+    return total > capacity ? LST_WARN_TRUNCATED : LST_OK;
 }
 
 lst_status lst_object_columns(int32_t kind, int32_t* ni, int32_t* nf) {

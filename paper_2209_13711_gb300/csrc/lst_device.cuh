@@ -186,7 +186,18 @@ struct Arena {
     float* tc_pt;
     float* tc_eta;
     float* tc_phi;
+    // the batch's track candidates packed event after event (the last stage)
+    struct TcRec* tc_rec;         // [n_ev * tc_cap]
+    int* tc_off;                  // [n_ev + 1]
 };
+
+// One packed track candidate; the layout of lst_tc in the C ABI.
+struct __align__(16) TcRec {
+    int type, seed, hits[10];
+    float pt, eta, phi;
+    int reserved;
+};
+static_assert(sizeof(TcRec) == 64, "packed track candidate is 64 bytes");
 
 // ---------------------------------------------------------------------------
 // arithmetic helpers (float and double overloads)

@@ -21,6 +21,7 @@ constexpr int kLsWarps = 8;
 constexpr int kT3Warps = 8;
 constexpr int kT5Warps = 4;
 constexpr int kPtWarps = 4;
+constexpr int kOvfWarps = 8;       // one block per overflowed T5 unit
 
 __global__ void k_reset(Arena A);
 __global__ void k_bin_count(Arena A);
@@ -44,6 +45,7 @@ __global__ void k_clean_pt3_cross(Arena A, DevCfg c);
 __global__ void k_clean_pt3_mark(Arena A);
 __global__ void k_clean_t5(Arena A, DevCfg c);
 __global__ void k_clean_pls(Arena A, DevCfg c);
+__global__ void k_tc_pack(Arena A);
 
 size_t md_smem_bytes();
 

@@ -92,6 +92,17 @@ def library():
         L.lst_last_launch_count.argtypes = [vp]
         L.lst_set_profiling.argtypes = [vp, i32]
         L.lst_get_counters.argtypes = [vp, vp, i32]
+        L.lst_launch_stage_count.argtypes = []
+        L.lst_launch_stage_count.restype = i32
+        L.lst_get_launch_config.argtypes = [vp, i32, C.POINTER(C.c_char_p), vp, vp, vp]
+        L.lst_set_launch_config.argtypes = [vp, i32, i32, i32]
+        L.lst_autotune.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp, i32, vp, vp]
+        L.lst_run_events.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.lst_get_batch_track_candidates.argtypes = [vp, i32, vp, vp]
+        L.lst_query.argtypes = [vp]
+        L.lst_query.restype = i32
+        L.lst_device_bytes.argtypes = [vp]
+        L.lst_device_bytes.restype = C.c_int64
         L.lst_mlp_create.argtypes = [p(vp), i32, i32]
         L.lst_mlp_destroy.argtypes = [vp]
         L.lst_mlp_destroy.restype = None
@@ -118,6 +129,20 @@ def _check(status):
     if status < 0:
         raise LstError(f"lst error {status}: {library().lst_status_str(status).decode()}")
     return status
+
+
+TC_DTYPE = np.dtype([("type", "<i4"), ("seed", "<i4"), ("hits", "<i4", (10,)), ("pt", "<f4"), ("eta", "<f4"),
+                     ("phi0", "<f4"), ("reserved", "<i4")])
+
+
+def tc_dict(rec):
+    """Packed records of one event as the dict track_candidates returns."""
+    return dict(n=len(rec), type=rec["type"].copy(), seed=rec["seed"].copy(), hits=rec["hits"].copy(),
+                pt=rec["pt"].copy(), eta=rec["eta"].copy(), phi0=rec["phi0"].copy())
+
+
+def _numel(a):
+    return a.numel() if hasattr(a, "numel") else np.asarray(a).size
 
 
 def _ptr(a):
@@ -214,6 +239,78 @@ class Context:
     def run(self, events, stream=None):
         self.run_packed(pack_events(list(events)), stream)
 
+    def run_events(self, events, stream=None):
+        """events: per-event dicts with x, y, z, module, side, seeds (numpy,
+        pinned CPU tensors, or CUDA tensors; one kind for the whole batch).
+        The library gathers them into its input staging (lst_run_events)."""
+        n = len(events)
+        hits = (LstHits * n)()
+        seeds = (LstSeeds * n)()
+        dev = False
+        for i, e in enumerate(events):
+            dev = hasattr(e["x"], "is_cuda") and e["x"].is_cuda
+            hits[i] = LstHits(_ptr(e["x"]), _ptr(e["y"]), _ptr(e["z"]), _ptr(e["module"]), _ptr(e["side"]),
+                              int(len(e["x"])))
+            seeds[i] = LstSeeds(_ptr(e["seeds"]), int(_numel(e["seeds"]) // 9))
+        self._keep = (events, hits, seeds)
+        s = C.c_void_p(stream) if stream is not None else None
+        _check(library().lst_run_events(self._h, hits, seeds, n, 1 if dev else 0, s))
+        self.n_events = n
+
+    def batch_track_candidates(self, out=None):
+        """(offsets [n_events + 1], records) of the whole batch in two copies;
+        records is a structured array (TC_DTYPE: type, seed, hits[10], pt, eta,
+        phi0). out: a TC_DTYPE array to fill (its length is the capacity);
+        without it the total is read first and an array of that size made."""
+        L = library()
+        off = np.zeros(self.n_events + 1, np.int32)
+        if out is None:
+            _check(L.lst_get_batch_track_candidates(self._h, 0, _ptr(off), None))
+            out = np.empty(int(off[-1]), TC_DTYPE)
+        cap = len(out)
+        _check(L.lst_get_batch_track_candidates(self._h, cap, _ptr(off), _ptr(out) if cap else None))
+        return off, out[:min(cap, int(off[-1]))]
+
+    def _batch_args(self, b):
+        dev = hasattr(b["x"], "is_cuda") and b["x"].is_cuda
+        hits = LstHits(_ptr(b["x"]), _ptr(b["y"]), _ptr(b["z"]), _ptr(b["module"]), _ptr(b["side"]),
+                       int(b["hit_off"][-1]))
+        seeds = LstSeeds(_ptr(b["seeds"]), int(b["seed_off"][-1]))
+        ho = np.ascontiguousarray(b["hit_off"], np.int32)
+        so = np.ascontiguousarray(b["seed_off"], np.int32)
+        return hits, ho, seeds, so, dev
+
+    # -- launch shapes ----------------------------------------------------
+    def launch_config(self):
+        """[{name, blocks_per_sm, block, tunable, generic}] for every stage of the chain."""
+        L = library()
+        out = []
+        for i in range(L.lst_launch_stage_count()):
+            nm = C.c_char_p()
+            m, b, f = C.c_int32(), C.c_int32(), C.c_int32()
+            _check(L.lst_get_launch_config(self._h, i, C.byref(nm), C.byref(m), C.byref(b), C.byref(f)))
+            out.append(dict(name=nm.value.decode(), blocks_per_sm=m.value, block=b.value,
+                            tunable=bool(f.value & 1), generic=bool(f.value & 2)))
+        return out
+
+    def set_launch_config(self, stage, blocks_per_sm=0, block=0):
+        """stage: index or name; 0 restores a default."""
+        if isinstance(stage, str):
+            stage = [c["name"] for c in self.launch_config()].index(stage)
+        _check(library().lst_set_launch_config(self._h, int(stage), int(blocks_per_sm), int(block)))
+
+    def autotune(self, batch, reps=3, stream=None):
+        """Tune every stage's launch shape on a batch (list of events or a
+        pack_events dict); returns (summed stage ms before, after)."""
+        b = batch if isinstance(batch, dict) else pack_events(list(batch))
+        hits, ho, so_h, so, dev = self._batch_args(b)
+        before, after = C.c_float(), C.c_float()
+        s = C.c_void_p(stream) if stream is not None else None
+        _check(library().lst_autotune(self._h, C.byref(hits), _ptr(ho), C.byref(so_h), _ptr(so), len(ho) - 1,
+                                      1 if dev else 0, s, int(reps), C.byref(before), C.byref(after)))
+        self.n_events = len(ho) - 1
+        return before.value, after.value
+
     @property
     def launch_count(self):
         return library().lst_last_launch_count(self._h)
@@ -231,6 +328,14 @@ class Context:
         return [(names[i].decode(), float(ms[i])) for i in range(n.value)]
 
     # -- results ----------------------------------------------------------
+    def done(self):
+        """Non-blocking: has the last batch finished on the device?"""
+        return _check(library().lst_query(self._h)) == 1
+
+    @property
+    def device_bytes(self):
+        return int(library().lst_device_bytes(self._h))
+
     def set_t5_selection(self, mlp=None, threshold=0.5, prefilter_scale=1.0, capture_features=False):
         """Network-scored T5 selection (mlp: an Mlp) or the hand-set cuts (mlp=None)."""
         self._mlp = mlp

@@ -24,3 +24,13 @@ def gpu_result(ctx, event=0):
 
 def oracle_result(geom, maps, ev):
     return O.Setup(geom.module_table(), maps, DEFAULT_CUTS, ev).run()
+
+
+def all_tuples(ctx, event):
+    """Every object level of an event as sets of hit tuples, and the TC set."""
+    from tests.parity import chain_tuples
+    g = gpu_result(ctx, event)
+    T = chain_tuples(g)
+    tc = {(int(t), int(s), tuple(sorted(h[h >= 0].tolist())))
+          for t, s, h in zip(g["tc"]["type"], g["tc"]["seed"], g["tc"]["hits"])}
+    return {k: set(v) for k, v in T.items()}, tc

@@ -4,7 +4,7 @@ import pytest
 
 from synth import events as E
 from synth.config import DEFAULT_CUTS
-from tests.gpu_common import A_HALF, gpu_result, make_context, oracle_result
+from tests.gpu_common import A_HALF, all_tuples as _all_tuples, gpu_result, make_context, oracle_result
 from tests.parity import chain_tuples, compare
 
 pytestmark = pytest.mark.gpu
@@ -65,14 +65,6 @@ def test_t5_stage_overflow_is_lossless(ctx_full, geom_full, maps_full):
     _no_drops(g)
     o = oracle_result(geom_full, maps_full, ev)
     compare(g, o, A_HALF, DEFAULT_CUTS)
-
-
-def _all_tuples(ctx, event):
-    g = gpu_result(ctx, event)
-    T = chain_tuples(g)
-    tc = {(int(t), int(s), tuple(sorted(h[h >= 0].tolist())))
-          for t, s, h in zip(g["tc"]["type"], g["tc"]["seed"], g["tc"]["hits"])}
-    return {k: set(v) for k, v in T.items()}, tc
 
 
 def test_batch_equals_single_events(ctx_full, geom_full):
