@@ -228,6 +228,12 @@ int64_t lst_device_bytes(lst_ctx* ctx);
  *   summed stage times of one run before and after. Synchronous; leaves the
  *   profiling switch as it found it and the context's results are those of the
  *   last tuning run of the batch. */
+/* Survivors a T5 search work item stages in shared memory (1..512; 0 restores
+ * 512) before it falls back to enumerating its candidates a second time and
+ * writing them directly. Results do not depend on it; a small limit exercises
+ * the fallback. Waits for the running batch; the next batch captures a new
+ * graph. */
+lst_status lst_set_t5_stage_limit(lst_ctx* ctx, int32_t n);
 int32_t lst_launch_stage_count(void);
 lst_status lst_get_launch_config(lst_ctx* ctx, int32_t stage, const char** name, int32_t* blocks_per_sm,
                                  int32_t* block, int32_t* flags);
@@ -279,8 +285,9 @@ lst_status lst_build_mini_doublets_static(const lst_config* cfg, const lst_modul
 
 /* Wait for the batch and copy the batch-wide device counters: [0..5] objects
  * reserved (MD, LS, T3, T5 candidates, pT5 candidates, pT3 candidates), [16]
- * hits with an invalid module or side, [20] inner MDs whose T5 candidates
- * overflowed the per-unit stage and were written by the overflow pass. At most
+ * hits with an invalid module or side, [20] T5 search work items (chunks of up
+ * to 16 T3 of one inner MD) whose survivors exceeded the shared-memory stage
+ * and were enumerated a second time, [22] + [23] T5 work items. At most
  * n (<= 32) values. */
 lst_status lst_get_counters(lst_ctx* ctx, int32_t* out, int32_t n);
 

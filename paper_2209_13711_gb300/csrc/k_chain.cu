@@ -426,12 +426,6 @@ struct T5Smem {
     int2 stage[kT5Stage];      // passing (T3_1, T3_2)
 };
 
-// per-warp scratch of the overflow pass (no stage)
-struct T5OvfSmem {
-    int pre[32], off[32], t1[32];
-    int2 cand[kT5Pre];
-};
-
 __device__ __forceinline__ void t5_mds(const Arena& A, int2 pr, int* m) {
     m[0] = A.t3_m0[pr.x];
     m[1] = A.t3_m1[pr.x];
@@ -446,9 +440,7 @@ __device__ __forceinline__ bool t5_prefit_f32(const Arena& A, const DevCfg& c, i
     Pt<float> P[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) P[j] = md_point<float>(A, m[j]);
-    float k, c2, cz;
-    fit_track_f32<5>(P, k, c2, cz);
-    return fit_may_pass(c, k, c2, cz, float(c.chi2_rphi_t5) * c.prefit_scale, float(c.chi2_rz_t5) * c.prefit_scale);
+    return fit_may_pass_f32<5>(P, fit_limits(c, c.chi2_rphi_t5, c.chi2_rz_t5, c.prefit_scale));
 }
 
 // Collected candidates: FP32 fit prefilter; the verdicts of each group of 32
@@ -473,20 +465,19 @@ __device__ __forceinline__ void t5_flush(const Arena& A, const DevCfg& c, Smem& 
     __syncwarp();
 }
 
-// Candidates of inner MD i whose T3_1 lies in chunks [c0, c1) (32 T3 each),
-// in a fixed order: (T3_1) x (T3_2 from T3_1's outer MD), curvature
-// prefilter, FP32 fit prefilter, then the sink.
+// Candidates whose T3_1 lies in [t_begin, t_end) (T3 of one inner MD), in a
+// fixed order: (T3_1) x (T3_2 from T3_1's outer MD), curvature prefilter,
+// FP32 fit prefilter, then the sink.
 template <typename Smem, typename Sink>
-__device__ __forceinline__ void t5_enumerate(const Arena& A, const DevCfg& c, Smem& S, int i, int c0, int c1,
+__device__ __forceinline__ void t5_enumerate(const Arena& A, const DevCfg& c, Smem& S, int t_begin, int t_end,
                                              Sink& sink) {
     const int lane = lane_id();
     const float nk = float(c.n_t5);
-    const int s0 = A.t3_off[i], s1 = s0 + A.t3_cnt[i];
     int ncand = 0;
-    for (int cb = s0 + 32 * c0; cb < s1 && cb < s0 + 32 * c1; cb += 32) {
+    for (int cb = t_begin; cb < t_end; cb += 32) {
         int t1 = cb + lane;
         int off = 0, len = 0;
-        if (t1 < s1) {
+        if (t1 < t_end) {
             int C_ = A.t3_m2[t1];
             off = A.t3_off[C_];
             len = A.t3_cnt[C_];
@@ -518,106 +509,109 @@ __device__ __forceinline__ void t5_enumerate(const Arena& A, const DevCfg& c, Sm
     if (ncand) t5_flush(A, c, S, ncand, sink);
 }
 
-// T5 search (FP32 only): one warp per inner MD. The survivors are written as
-// the MD's T5 segment; k_t5_refine decides them in FP64. A unit with more
-// survivors than the stage holds is queued for k_t5_overflow.
+// T5 work items: the T3_1 of each inner MD in chunks of kT5Chunk. Chunks of
+// units with more than one chunk go to the front of the item list (they are
+// the heavy units and start first), single-chunk units to the back.
+__global__ void k_t5_plan(Arena A) {
+    const int n_md = min(A.counters[0], A.md_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_md; i += gridDim.x * blockDim.x) {
+        const int n = A.t3_cnt[i];
+        if (n == 0) continue;
+        const int s0 = A.t3_off[i], nch = (n + kT5Chunk - 1) / kT5Chunk;
+        if (nch > 1) {
+            const int k = atomicAdd(&A.counters[22], nch);
+            for (int j = 0; j < nch; ++j) A.t5_items[k + j] = s0 + j * kT5Chunk;
+        } else {
+            const int k = atomicAdd(&A.counters[23], 1);
+            A.t5_items[A.t3_cap - 1 - k] = s0;
+        }
+    }
+}
+
+// T5 search (FP32 only): each warp takes work items from a shared cursor
+// (split units first). A chunk's survivors are staged in shared memory and
+// written as one segment of t5_tmp; a chunk with more survivors than the
+// stage holds is enumerated a second time and written straight to its
+// reserved segment, in the same order. k_t5_gather orders the segments by
+// inner MD and k_t5_refine decides the candidates in FP64.
 __global__ void __launch_bounds__(kT5Warps * 32, 6) k_t5(Arena A, DevCfg c) {
     __shared__ T5Smem sm[kT5Warps];
     T5Smem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
-    const int n_md = min(A.counters[0], A.md_cap);
-    for (int i = blockIdx.x * kT5Warps + (threadIdx.x >> 5); i < n_md; i += gridDim.x * kT5Warps) {
-        if (A.t3_cnt[i] == 0) {
-            if (lane == 0) { A.t5_off[i] = 0; A.t5_cnt[i] = 0; }
-            continue;
-        }
+    const int n_front = A.counters[22], n_items = n_front + A.counters[23];
+    const int stage = min(max(c.t5_stage, 1), kT5Stage);
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&A.counters[24], 1);
+        k = __shfl_sync(kFull, k, 0);
+        if (k >= n_items) break;
+        const int t0 = k < n_front ? A.t5_items[k] : A.t5_items[A.t3_cap - 1 - (k - n_front)];
+        const int i = A.t3_m0[t0];
+        const int t_end = min(t0 + kT5Chunk, A.t3_off[i] + A.t3_cnt[i]);
         int cnt = 0;
-        auto sink = [&](bool keep, int2 pr, int r, int tot) {
-            if (keep && cnt + r < kT5Stage) S.stage[cnt + r] = pr;
+        auto stage_sink = [&](bool keep, int2 pr, int r, int tot) {
+            if (keep && cnt + r < stage) S.stage[cnt + r] = pr;
             cnt += tot;
         };
-        t5_enumerate(A, c, S, i, 0, 1 << 20, sink);
-        if (cnt > kT5Stage) {
-            if (lane == 0) {
-                A.t5_off[i] = 0;
-                A.t5_cnt[i] = 0;
-                int k = atomicAdd(&A.counters[20], 1);
-                if (k < A.ovf_cap) A.ovf_list[k] = i;
-                else atomicAdd(&A.ev_drop[(A.md_gmod[i] / A.n_mod) * 8 + 3], cnt);
-            }
-            __syncwarp();
-            continue;
-        }
+        t5_enumerate(A, c, S, t0, t_end, stage_sink);
         int n = cnt, dropped = 0;
-        const int base = reserve(&A.counters[3], A.t5_cap, n, dropped);
-        for (int k = lane; k < n; k += 32) {
-            int2 pr = S.stage[k];
-            A.t5_in[base + k] = pr.x;
-            A.t5_out[base + k] = pr.y;
+        const int base = reserve(&A.counters[21], A.t5_cap, n, dropped);
+        if (cnt <= stage) {
+            for (int q = lane; q < n; q += 32) A.t5_tmp[base + q] = S.stage[q];
+        } else {
+            if (lane == 0) atomicAdd(&A.counters[20], 1);
+            int wr = 0;
+            auto write_sink = [&](bool keep, int2 pr, int r, int tot) {
+                if (keep && wr + r < n) A.t5_tmp[base + wr + r] = pr;
+                wr += tot;
+            };
+            t5_enumerate(A, c, S, t0, t_end, write_sink);
         }
         if (lane == 0) {
-            A.t5_off[i] = base;
-            A.t5_cnt[i] = n;
+            A.t5_chunk_off[t0] = base;
+            A.t5_chunk_cnt[t0] = n;
             if (dropped) atomicAdd(&A.ev_drop[(A.md_gmod[i] / A.n_mod) * 8 + 3], dropped);
         }
         __syncwarp();
     }
 }
 
-// Units whose survivors overflowed the stage: one block per unit, its warps
-// take the unit's chunks of 32 T3_1; per-chunk counts, a scan, one
-// reservation, then every chunk is enumerated again and written at its offset
-// (the same order as one warp would produce).
-constexpr int kOvfChunks = (kT3Stage + 31) / 32;
-
-__global__ void __launch_bounds__(kOvfWarps * 32) k_t5_overflow(Arena A, DevCfg c) {
-    __shared__ T5OvfSmem sm[kOvfWarps];
-    __shared__ int chunk_cnt[kOvfChunks + 1];
-    __shared__ int s_base, s_n;
-    T5OvfSmem& S = sm[threadIdx.x >> 5];
+// One warp per inner MD: its chunks' survivors, in chunk order, become the
+// MD's T5 segment (the order a single pass over the MD's T3_1 would give).
+__global__ void __launch_bounds__(128) k_t5_gather(Arena A) {
+    __shared__ int sm_pre[4][32], sm_off[4][32];
     const int w = threadIdx.x >> 5, lane = lane_id();
-    const int n_ovf = min(A.counters[20], A.ovf_cap);
-    for (int k = blockIdx.x; k < n_ovf; k += gridDim.x) {
-        const int i = A.ovf_list[k];
-        const int n_chunks = (A.t3_cnt[i] + 31) / 32;
-        for (int ch = w; ch < n_chunks; ch += kOvfWarps) {
-            int cnt = 0;
-            auto count = [&](bool, int2, int, int tot) { cnt += tot; };
-            t5_enumerate(A, c, S, i, ch, ch + 1, count);
-            if (lane == 0) chunk_cnt[ch] = cnt;
+    const int n_md = min(A.counters[0], A.md_cap);
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + w; i < n_md; i += warps) {
+        const int n1 = A.t3_cnt[i];
+        const int nch = (n1 + kT5Chunk - 1) / kT5Chunk;      // <= 32: kT3Stage / kT5Chunk
+        int off = 0, len = 0;
+        if (lane < nch) {
+            const int t0 = A.t3_off[i] + lane * kT5Chunk;
+            off = A.t5_chunk_off[t0];
+            len = A.t5_chunk_cnt[t0];
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int run = 0;
-            for (int ch = 0; ch < n_chunks; ++ch) {
-                int v = chunk_cnt[ch];
-                chunk_cnt[ch] = run;
-                run += v;
+        int tot = len;
+#pragma unroll
+        for (int d = 16; d; d >>= 1) tot += __shfl_xor_sync(kFull, tot, d);
+        int n = tot, dropped = 0;
+        const int base = reserve(&A.counters[3], A.t5_cap, n, dropped);
+        int wr = 0;
+        for_each_flat(off, len, sm_pre[w], sm_off[w], [&](bool valid, int, int q) {
+            if (valid && wr + lane < n) {
+                const int2 pr = A.t5_tmp[q];
+                A.t5_in[base + wr + lane] = pr.x;
+                A.t5_out[base + wr + lane] = pr.y;
             }
-            int n = run, dropped = 0, base = 0;
-            base = n > 0 ? atomicAdd(&A.counters[3], n) : 0;
-            int fit = n > 0 ? max(0, min(n, A.t5_cap - base)) : 0;
-            dropped = n - fit;
-            s_base = base;
-            s_n = fit;
+            wr += 32;
+        });
+        if (lane == 0) {
             A.t5_off[i] = base;
-            A.t5_cnt[i] = fit;
+            A.t5_cnt[i] = n;
             if (dropped) atomicAdd(&A.ev_drop[(A.md_gmod[i] / A.n_mod) * 8 + 3], dropped);
         }
-        __syncthreads();
-        const int base = s_base, n = s_n;
-        for (int ch = w; ch < n_chunks; ch += kOvfWarps) {
-            int wr = chunk_cnt[ch];
-            auto write = [&](bool keep, int2 pr, int r, int tot) {
-                if (keep && wr + r < n) {
-                    A.t5_in[base + wr + r] = pr.x;
-                    A.t5_out[base + wr + r] = pr.y;
-                }
-                wr += tot;
-            };
-            t5_enumerate(A, c, S, i, ch, ch + 1, write);
-        }
-        __syncthreads();
+        __syncwarp();
     }
 }
 

@@ -80,10 +80,8 @@ __device__ __forceinline__ bool pt_prefit_f32(const Arena& A, const DevCfg& c, i
     pt_mds<NT>(A, obj, m);
 #pragma unroll
     for (int j = 0; j < NT; ++j) P[3 + j] = md_point<float>(A, m[j]);
-    float k, c2, cz;
-    fit_track_f32<NT + 3>(P, k, c2, cz);
-    return fit_may_pass(c, k, c2, cz, float(NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3),
-                        float(NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3));
+    return fit_may_pass_f32<NT + 3>(P, fit_limits(c, NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3,
+                                                  NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3, 1.0f));
 }
 
 // FP32 fit verdicts of one group of 32 candidates (one out-of-line copy).

@@ -37,7 +37,7 @@ struct Buffer {
 // their shared-memory stages by a compile-time warp count and keep their block.
 // `tunable` stages are grid-stride over their units, so any grid is valid.
 enum LaunchId {
-    L_RESET, L_BIN_COUNT, L_BIN_SCAN, L_BIN_SCATTER, L_MD, L_LS, L_T3, L_T5, L_T5_OVERFLOW, L_T5_REFINE,
+    L_RESET, L_BIN_COUNT, L_BIN_SCAN, L_BIN_SCATTER, L_MD, L_LS, L_T3, L_T5_PLAN, L_T5, L_T5_GATHER, L_T5_REFINE,
     L_T5_MLP, L_T5_MLP_SELECT, L_PLS, L_PT5, L_PT5_REFINE, L_PT3, L_PT3_REFINE, L_CLEAN_KEYS, L_CLEAN_KEEP,
     L_CLEAN_PT5, L_CLEAN_PT3_CROSS, L_CLEAN_PT3_MARK, L_CLEAN_T5, L_CLEAN_PLS, L_TC_PACK, kNumLaunch
 };
@@ -58,8 +58,9 @@ const LaunchInfo kLaunch[kNumLaunch] = {
     {"md", 4, kMdWarps * 32, true, false},
     {"ls", 8, kLsWarps * 32, true, false},
     {"t3", 8, kT3Warps * 32, true, false},
+    {"t5_plan", 4, 256, true, true},
     {"t5", 6, kT5Warps * 32, true, false},
-    {"t5_overflow", 1, kOvfWarps * 32, false, false},
+    {"t5_gather", 4, 128, true, false},
     {"t5_refine", 4, 128, true, true},
     {"t5_mlp", 4, 128, true, false},
     {"t5_mlp_select", 4, 128, true, true},
@@ -145,6 +146,7 @@ static DevCfg make_devcfg(const lst_config& c) {
     d.use_mlp = 0;
     d.prefit_scale = 1.0f;
     d.mlp_threshold = 0.5f;
+    d.t5_stage = kT5Stage;
     return d;
 }
 
@@ -273,8 +275,6 @@ static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_m
     A.sz = b.take<float>(H);
     A.sidx = b.take<int>(H);
     A.counters = b.take<int>(32);
-    A.ovf_cap = 4096;
-    A.ovf_list = b.take<int>(A.ovf_cap);
     A.ev_counts = b.take<int>(E * 8);
     A.ev_drop = b.take<int>(E * 8);
     const size_t MD = E * K.md_per_event;
@@ -303,6 +303,8 @@ static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_m
     A.t5_pt = b.take<float>(T5); A.t5_valid = b.take<uint8_t>(T5); A.t5_cut = b.take<uint8_t>(T5);
     A.t5_feat = b.take<float>(48 * T5); A.t5_mlp = b.take<float>(T5);
     A.t5_off = b.take<int>(MD); A.t5_cnt = b.take<int>(MD);
+    A.t5_items = b.take<int>(T3); A.t5_chunk_off = b.take<int>(T3); A.t5_chunk_cnt = b.take<int>(T3);
+    A.t5_tmp = b.take<int2>(T5);
     A.pls_pass = b.take<int>(S); A.pls_sb = b.take<int>(S);
     A.pls_kappa = b.take<double>(S); A.pls_sigk = b.take<double>(S);
     A.pls_eta = b.take<double>(S); A.pls_phi = b.take<double>(S);
@@ -422,8 +424,9 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile) {
     LAUNCH(L_MD, k_md<<<GB(L_MD), md_smem_bytes(), st>>>(A, dc));
     LAUNCH(L_LS, k_ls<<<GB(L_LS), 0, st>>>(A, dc));
     LAUNCH(L_T3, k_t3<<<GB(L_T3), 0, st>>>(A, dc));
+    LAUNCH(L_T5_PLAN, k_t5_plan<<<GB(L_T5_PLAN), 0, st>>>(A));
     LAUNCH(L_T5, k_t5<<<GB(L_T5), 0, st>>>(A, dc));
-    LAUNCH(L_T5_OVERFLOW, k_t5_overflow<<<c->n_sm, kOvfWarps * 32, 0, st>>>(A, dc));
+    LAUNCH(L_T5_GATHER, k_t5_gather<<<GB(L_T5_GATHER), 0, st>>>(A));
     LAUNCH(L_T5_REFINE, k_t5_refine<<<GB(L_T5_REFINE), 0, st>>>(A, dc));
     if (c->mlp) {
         LAUNCH(L_T5_MLP, k_mlp_forward<<<GB(L_T5_MLP), 0, st>>>(lst_mlp_device_params(c->mlp), A.t5_feat, A.t5_cap,
@@ -629,7 +632,8 @@ static const void* launch_fn(int id) {
         case L_LS: return (const void*)k_ls;
         case L_T3: return (const void*)k_t3;
         case L_T5: return (const void*)k_t5;
-        case L_T5_OVERFLOW: return (const void*)k_t5_overflow;
+        case L_T5_PLAN: return (const void*)k_t5_plan;
+        case L_T5_GATHER: return (const void*)k_t5_gather;
         case L_T5_REFINE: return (const void*)k_t5_refine;
         case L_T5_MLP: return (const void*)k_mlp_forward;
         case L_T5_MLP_SELECT: return (const void*)k_t5_mlp_select;
@@ -669,6 +673,15 @@ static lst_status drop_graph(lst_ctx* c) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
     }
+    return LST_OK;
+}
+
+lst_status lst_set_t5_stage_limit(lst_ctx* c, int32_t n) {
+    if (!c || n < 0 || n > kT5Stage) return LST_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    lst_status s = drop_graph(c);
+    if (s != LST_OK) return s;
+    c->dc.t5_stage = n > 0 ? n : kT5Stage;
     return LST_OK;
 }
 

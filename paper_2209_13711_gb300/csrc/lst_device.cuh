@@ -44,6 +44,7 @@ struct DevCfg {
     int use_mlp;           // T5 validity from the network score instead of the cuts
     float prefit_scale;    // widening of the T5 FP32 prefilter (1: conservative for the cuts)
     float mlp_threshold;
+    int t5_stage;          // T5 survivors staged per work item before the re-enumeration path
 };
 
 // Shape and inputs of the batch being processed (device memory).
@@ -83,8 +84,6 @@ struct Arena {
     int* sidx;                    // original hit index within the event
     // counters: [0] MD [1] LS [2] T3 [3] T5 [4] pT5 [5] pT3, [16] bad hits, [20] T5 overflow units
     int* counters;
-    int ovf_cap;
-    int* ovf_list;                // inner MDs whose T5 survivors overflowed the stage
     int* ev_counts;               // [n_ev][8]
     int* ev_drop;                 // [n_ev][8]
     // MD
@@ -137,6 +136,12 @@ struct Arena {
     float* t5_mlp;                // network score
     int* t5_off;                  // [md_cap] by inner MD
     int* t5_cnt;
+    // T5 search work items: chunks of up to kT5Chunk T3_1 of one inner MD,
+    // named by the T3 index of their first T3_1
+    int* t5_items;                // [t3_cap] split units from the front, whole units from the back
+    int* t5_chunk_off;            // [t3_cap] by chunk start: the chunk's segment of t5_tmp
+    int* t5_chunk_cnt;
+    int2* t5_tmp;                 // [t5_cap] survivors in chunk segments
     // pLS, per seed
     int* pls_pass;
     int* pls_sb;
@@ -542,7 +547,24 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
 // FP32 twin of fit_track, used only as a conservative prefilter before the
 // FP64 fit: same frame and residual definitions, with the normal equations
 // centred (2x2 solve) for conditioning in single precision.
-template <int N> __device__ inline void fit_track_f32(const Pt<float>* P, float& kappa, float& chi2, float& chi2z) {
+// Limits of the conservative FP32 verdict on the fit cuts: a candidate is
+// rejected only when a cut fails by far more than FP32 rounding can explain
+// (|kappa| above 1.01 kmax + 1e-5, a chi2 above 1.25 max + 2).
+struct FitLimits {
+    float kappa, chi2, chi2z;
+};
+
+__device__ __forceinline__ FitLimits fit_limits(const DevCfg& c, double chi2_max, double chi2z_max, float scale) {
+    const float kmax = float((1.0 + c.tol_r) * 2.0 * c.a);
+    return FitLimits{kmax * 1.01f + 1e-5f, 1.25f * (float(chi2_max) * scale) + 2.f,
+                     1.25f * (float(chi2z_max) * scale) + 2.f};
+}
+
+// FP32 twin of fit_track (same chord-frame circle fit, geometric residuals and
+// r-z line fit), evaluated cut by cut: the curvature is tested right after the
+// circle solve, chi2_rphi after the residuals, and the r-z fit runs only for
+// candidates that passed both. The verdict equals testing all three at the end.
+template <int N> __device__ inline bool fit_may_pass_f32(const Pt<float>* P, const FitLimits& L) {
     const Pt<float>& O = P[N / 2];
     float ex = P[N - 1].x - P[0].x, ey = P[N - 1].y - P[0].y;
     float il = 1.0f / hypotf(ex, ey);
@@ -565,12 +587,13 @@ template <int N> __device__ inline void fit_track_f32(const Pt<float>* P, float&
         saa += a * a; sab += a * b; sbb += b * b; sac += a * cc; sbc += b * cc;
     }
     float det = saa * sbb - sab * sab;
-    if (!(det > 0.f)) { kappa = 1e30f; chi2 = 1e30f; chi2z = 1e30f; return; }
+    if (!(det > 0.f)) return false;
     float gg = (sac * sbb - sab * sbc) / det;
     float hh = (saa * sbc - sab * sac) / det;
     float kk = me - gg * mr - hh * mx;
     float S = sqrtf(fmaxf(0.f, 1.f + hh * hh - 4.f * gg * kk));
-    kappa = 2.f * gg / S;
+    float kappa = 2.f * gg / S;
+    if (!(fabsf(kappa) <= L.kappa)) return false;
     float c2 = 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -586,7 +609,7 @@ template <int N> __device__ inline void fit_track_f32(const Pt<float>* P, float&
         float s2 = fmaxf(sq(P[i].srphi * n_phi) + sq(P[i].sr * n_r), sq(0.01f * P[i].srphi));
         c2 += e * e / s2;
     }
-    chi2 = c2;
+    if (!(c2 <= L.chi2)) return false;
     float ka = fabsf(kappa);
     float s[N];
 #pragma unroll
@@ -607,16 +630,7 @@ template <int N> __device__ inline void fit_track_f32(const Pt<float>* P, float&
     float t = Ssz / Sss, c0 = zbar - t * sbar, cz = 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) cz += w[i] * sq(P[i].z - c0 - t * s[i]);
-    chi2z = cz;
-}
-
-// Conservative FP32 verdict on the fit cuts: false only when every cut fails
-// by far more than FP32 rounding can explain.
-__device__ __forceinline__ bool fit_may_pass(const DevCfg& c, float kappa, float chi2, float chi2z, float chi2_max,
-                                             float chi2z_max) {
-    float kmax = float((1.0 + c.tol_r) * 2.0 * c.a);
-    return fabsf(kappa) <= kmax * 1.01f + 1e-5f && chi2 <= 1.25f * chi2_max + 2.f &&
-           chi2z <= 1.25f * chi2z_max + 2.f;
+    return cz <= L.chi2z;
 }
 
 __device__ __forceinline__ double phi0_of(const Pt<double>& P, double kappa) {

@@ -21,7 +21,7 @@ constexpr int kLsWarps = 8;
 constexpr int kT3Warps = 8;
 constexpr int kT5Warps = 4;
 constexpr int kPtWarps = 4;
-constexpr int kOvfWarps = 8;       // one block per overflowed T5 unit
+constexpr int kT5Chunk = 16;       // T3_1 per T5 search work item
 
 __global__ void k_reset(Arena A);
 __global__ void k_bin_count(Arena A);
@@ -31,7 +31,8 @@ __global__ void k_md(Arena A, DevCfg c);
 __global__ void k_ls(Arena A, DevCfg c);
 __global__ void k_t3(Arena A, DevCfg c);
 __global__ void k_t5(Arena A, DevCfg c);
-__global__ void k_t5_overflow(Arena A, DevCfg c);
+__global__ void k_t5_plan(Arena A);
+__global__ void k_t5_gather(Arena A);
 __global__ void k_t5_refine(Arena A, DevCfg c);
 __global__ void k_t5_mlp_select(Arena A, DevCfg c);
 __global__ void k_pls(Arena A, DevCfg c);

@@ -28,7 +28,8 @@ def test_launch_config_validation(geom_full, maps_full):
     names = [c["name"] for c in cfg]
     assert names[:5] == ["reset", "bin_count", "bin_scan", "bin_scatter", "md"]
     byname = {c["name"]: c for c in cfg}
-    assert not byname["bin_scan"]["tunable"] and not byname["t5_overflow"]["tunable"]
+    assert not byname["bin_scan"]["tunable"]
+    assert byname["t5_gather"]["tunable"] and not byname["t5_gather"]["generic"]
     assert byname["t5"]["tunable"] and not byname["t5"]["generic"]
     assert byname["t5_refine"]["generic"]
     for bad in [("md", 0, 256), ("bin_scan", 2, 0), ("t5_refine", 0, 48), ("t5_refine", 0, 2048),

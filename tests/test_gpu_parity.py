@@ -56,15 +56,24 @@ def test_pu200_event_parity(ctx_full, geom_full, maps_full):
     assert s["t5"][0] > 10000 and s["tc"][0] > 2000
 
 
-def test_t5_stage_overflow_is_lossless(ctx_full, geom_full, maps_full):
-    """A PU200 event with an inner MD whose T5 candidates overflow the per-unit stage."""
+def test_t5_stage_overflow_is_lossless(geom_full, maps_full):
+    """A PU200 event searched with a stage of 4 survivors per T5 work item: most
+    items take the second-enumeration path; every level still matches the oracle."""
+    ctx = make_context(geom_full, maps_full, max_events=1)
+    ctx.set_t5_stage_limit(4)
     ev = E.pu200_event(12, geom_full)
-    ctx_full.run([ev])
-    assert ctx_full.counters()[20] > 0
-    g = gpu_result(ctx_full)
+    ctx.run([ev])
+    assert ctx.counters()[20] > 100
+    g = gpu_result(ctx)
     _no_drops(g)
     o = oracle_result(geom_full, maps_full, ev)
     compare(g, o, A_HALF, DEFAULT_CUTS)
+    limited = _all_tuples(ctx, 0)
+    ctx.set_t5_stage_limit(0)
+    ctx.run([ev])
+    assert ctx.counters()[20] == 0
+    assert _all_tuples(ctx, 0) == limited
+    ctx.close()
 
 
 def test_batch_equals_single_events(ctx_full, geom_full):
