@@ -228,12 +228,12 @@ int64_t lst_device_bytes(lst_ctx* ctx);
  *   summed stage times of one run before and after. Synchronous; leaves the
  *   profiling switch as it found it and the context's results are those of the
  *   last tuning run of the batch. */
-/* Survivors a T5 search work item stages in shared memory (1..512; 0 restores
- * 512) before it falls back to enumerating its candidates a second time and
- * writing them directly. Results do not depend on it; a small limit exercises
- * the fallback. Waits for the running batch; the next batch captures a new
- * graph. */
-lst_status lst_set_t5_stage_limit(lst_ctx* ctx, int32_t n);
+/* Survivors a search work item stages in shared memory before it falls back
+ * to enumerating its candidates a second time and writing them directly: t5
+ * for a T5 item (1..512, 0 restores 512), pt for a pT5 / pT3 item (1..256, 0
+ * restores 256). Results do not depend on them; small limits exercise the
+ * fallback. Waits for the running batch; the next batch captures a new graph. */
+lst_status lst_set_stage_limits(lst_ctx* ctx, int32_t t5, int32_t pt);
 int32_t lst_launch_stage_count(void);
 lst_status lst_get_launch_config(lst_ctx* ctx, int32_t stage, const char** name, int32_t* blocks_per_sm,
                                  int32_t* block, int32_t* flags);
@@ -287,8 +287,9 @@ lst_status lst_build_mini_doublets_static(const lst_config* cfg, const lst_modul
  * reserved (MD, LS, T3, T5 candidates, pT5 candidates, pT3 candidates), [16]
  * hits with an invalid module or side, [20] T5 search work items (chunks of up
  * to 16 T3 of one inner MD) whose survivors exceeded the shared-memory stage
- * and were enumerated a second time, [22] + [23] T5 work items. At most
- * n (<= 32) values. */
+ * and were enumerated a second time, [22] + [23] T5 work items, [25] pT work
+ * items (seed, superbin module), [28] pT work items enumerated a second time.
+ * At most n (<= 32) values. */
 lst_status lst_get_counters(lst_ctx* ctx, int32_t* out, int32_t n);
 
 /* ---- learned T5 selection (the north-star's scoring network; the paper's

@@ -51,11 +51,11 @@ __global__ void k_pls(Arena A, DevCfg c) {
 }
 
 // ---------------------------------------------------------------------------
-// pT5 / pT3: one warp per passing seed; candidates = T objects whose inner
-// MD sits in a module listed under the seed's superbin.
+// pT5 / pT3: candidates of a passing seed = T objects whose inner MD sits in
+// a module listed under the seed's superbin.
 // ---------------------------------------------------------------------------
 struct PtSmem {
-    int pre[32], off[32];
+    int pre[32], off[32], pre2[32], off2[32];
     int cand[kPtPre];
     int stage[kPtStage];
 };
@@ -91,90 +91,141 @@ __device__ __noinline__ unsigned pt_prefit_group(const Arena& A, const DevCfg& c
     return __ballot_sync(kFull, keep);
 }
 
-// Collected candidates: FP32 fit prefilter; survivors are appended to the stage.
-template <int NT>
-__device__ __forceinline__ void pt_flush(const Arena& A, const DevCfg& c, PtSmem& S, int g, int ncand, int& cnt) {
+// Collected candidates: FP32 fit prefilter; sink(keep, obj, rank, total) per
+// group of 32, in candidate order.
+template <int NT, typename Sink>
+__device__ __forceinline__ void pt_flush(const Arena& A, const DevCfg& c, PtSmem& S, int g, int ncand, Sink& sink) {
     const int lane = lane_id();
     for (int base = 0; base < ncand; base += 32) {
         int q = base + lane;
         unsigned m = pt_prefit_group<NT>(A, c, g, S.cand, q, ncand);
         bool keep = (m >> lane) & 1u;
         int r = __popc(m & ((1u << lane) - 1u));
-        if (keep && cnt + r < kPtStage) S.stage[cnt + r] = S.cand[q];
-        cnt += __popc(m);
+        sink(keep, q < ncand ? S.cand[q] : 0, r, __popc(m));
     }
     __syncwarp();
 }
 
-// pT5 / pT3 search (FP32 only): one warp per passing seed; candidates = T
-// objects whose inner MD sits in a module listed under the seed's superbin;
-// curvature prefilter and FP32 fit prefilter. k_pt_refine decides in FP64.
+// Candidates of seed g (event e) among the T objects whose inner MD sits in
+// the superbin modules sb_tgt[j_begin .. j_end) (at most 32), in a fixed
+// order (module, MD, object): curvature prefilter, FP32 fit prefilter, then
+// the sink. Two levels of flattening keep the lanes busy: modules -> MDs,
+// then each group of 32 MDs -> their T objects.
+template <int NT, typename Sink>
+__device__ __forceinline__ void pt_enumerate(const Arena& A, const DevCfg& c, PtSmem& S, int g, int e, int j_begin,
+                                             int j_end, Sink& sink) {
+    const int lane = lane_id();
+    const float nk = float(c.n_pt);
+    const float kp = float(A.pls_kappa[g]), sp = float(A.pls_sigk[g]);
+    int ncand = 0;
+    int moff = 0, mcnt = 0;
+    if (j_begin + lane < j_end) {
+        const int u = e * A.n_mod + A.sb_tgt[j_begin + lane];
+        moff = A.md_moff[u];
+        mcnt = A.md_mcnt[u];
+    }
+    for_each_flat(moff, mcnt, S.pre, S.off, [&](bool mvalid, int, int md) {
+        int oo = 0, on = 0;
+        if (mvalid) {
+            oo = NT == 5 ? A.t5_off[md] : A.t3_off[md];
+            on = NT == 5 ? A.t5_cnt[md] : A.t3_cnt[md];
+        }
+        for_each_flat(oo, on, S.pre2, S.off2, [&](bool valid, int, int obj) {
+            bool pass = false;
+            if (valid && (NT == 3 || A.t5_valid[obj])) {
+                float kt = NT == 5 ? float(A.t5_kappa[obj]) : A.t3_kappa[obj];
+                float st = NT == 5 ? float(A.t5_sigk[obj]) : A.t3_sigk[obj];
+                float thr = nk * sqrtf(sp * sp + st * st);
+                pass = fabsf(kp - kt) <= thr * 1.01f + 1e-5f * (fabsf(kp) + fabsf(kt)) + 1e-7f;
+            }
+            int tot;
+            int r = warp_rank(pass, tot);
+            if (pass) S.cand[ncand + r] = obj;
+            ncand += tot;
+            if (ncand > kPtPre - 32) {
+                __syncwarp();
+                pt_flush<NT>(A, c, S, g, ncand, sink);
+                ncand = 0;
+            }
+        });
+    });
+    __syncwarp();
+    if (ncand) pt_flush<NT>(A, c, S, g, ncand, sink);
+}
+
+// pT work items: (passing seed, a chunk of up to kPtChunk modules of its
+// superbin list). The same list serves the pT5 and the pT3 search.
+__global__ void k_pt_plan(Arena A) {
+    const int n_seeds = A.bd->n_seeds;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_seeds; g += gridDim.x * blockDim.x) {
+        if (!A.pls_pass[g] || A.pls_sb[g] < 0) continue;
+        const int sb = A.pls_sb[g];
+        const int j0 = A.sb_off[sb], n = A.sb_off[sb + 1] - j0;
+        if (n <= 0) continue;
+        const int nch = (n + kPtChunk - 1) / kPtChunk;
+        const int k = atomicAdd(&A.counters[25], nch);
+        for (int j = 0; j < nch && k + j < A.pt_item_cap; ++j) A.pt_items[k + j] = make_int2(g, j0 + j * kPtChunk);
+    }
+}
+
+// pT5 / pT3 search (FP32 only): each warp takes (seed, module chunk) work
+// items from a shared cursor; a seed's candidates are the T objects whose
+// inner MD sits in one of the chunk's modules. An item's survivors are staged and written as one
+// segment; an item with more survivors than the stage holds is enumerated a
+// second time and written directly. k_pt_refine decides in FP64.
 template <int NT>
 __device__ __forceinline__ void pt_kernel_body(Arena& A, const DevCfg& c) {
     __shared__ PtSmem sm[kPtWarps];
     PtSmem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
-    const float nk = float(c.n_pt);
-    const int n_ev = A.bd->n_ev, n_seeds = A.bd->n_seeds;
-    for (int g = blockIdx.x * kPtWarps + (threadIdx.x >> 5); g < n_seeds; g += gridDim.x * kPtWarps) {
-        if (!A.pls_pass[g] || A.pls_sb[g] < 0) continue;
+    const int n_ev = A.bd->n_ev;
+    const int n_items = min(A.counters[25], A.pt_item_cap);
+    const int stage = min(max(c.pt_stage, 1), kPtStage);
+    const int slot = NT == 5 ? 4 : 5;
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&A.counters[NT == 5 ? 26 : 27], 1);
+        k = __shfl_sync(kFull, k, 0);
+        if (k >= n_items) break;
+        const int2 it = A.pt_items[k];
+        const int g = it.x;
         const int e = event_of(A.seed_off, n_ev, g);
-        const int sb = A.pls_sb[g];
-        const float kp = float(A.pls_kappa[g]), sp = float(A.pls_sigk[g]);
-        const int j0 = A.sb_off[sb], j1 = A.sb_off[sb + 1];
-        int cnt = 0, ncand = 0;
-        for (int cb = j0; cb < j1; cb += 32) {
-            int j = cb + lane;
-            int off = 0, len = 0;
-            if (j < j1) {
-                int u = e * A.n_mod + A.sb_tgt[j];
-                off = A.md_moff[u];
-                len = A.md_mcnt[u];
-            }
-            for_each_flat(off, len, S.pre, S.off, [&](bool valid, int seg, int md) {
-                int oo = 0, on = 0;
-                if (valid) {
-                    oo = NT == 5 ? A.t5_off[md] : A.t3_off[md];
-                    on = NT == 5 ? A.t5_cnt[md] : A.t3_cnt[md];
-                }
-                for (int k = 0; __any_sync(kFull, k < on); ++k) {
-                    bool pass = false;
-                    int obj = oo + k;
-                    if (k < on && (NT == 3 || A.t5_valid[obj])) {
-                        float kt = NT == 5 ? float(A.t5_kappa[obj]) : A.t3_kappa[obj];
-                        float st = NT == 5 ? float(A.t5_sigk[obj]) : A.t3_sigk[obj];
-                        float thr = nk * sqrtf(sp * sp + st * st);
-                        pass = fabsf(kp - kt) <= thr * 1.01f + 1e-5f * (fabsf(kp) + fabsf(kt)) + 1e-7f;
-                    }
-                    int tot;
-                    int r = warp_rank(pass, tot);
-                    if (pass) S.cand[ncand + r] = obj;
-                    ncand += tot;
-                    if (ncand > kPtPre - 32) {
-                        __syncwarp();
-                        pt_flush<NT>(A, c, S, g, ncand, cnt);
-                        ncand = 0;
-                    }
-                }
-            });
-        }
-        __syncwarp();
-        if (ncand) pt_flush<NT>(A, c, S, g, ncand, cnt);
-        int n = min(cnt, kPtStage);
-        int dropped = cnt - n;
-        const int slot = NT == 5 ? 4 : 5;
+        const int j_end = min(it.y + kPtChunk, A.sb_off[A.pls_sb[g] + 1]);
+        int cnt = 0;
+        auto stage_sink = [&](bool keep, int obj, int r, int tot) {
+            if (keep && cnt + r < stage) S.stage[cnt + r] = obj;
+            cnt += tot;
+        };
+        pt_enumerate<NT>(A, c, S, g, e, it.y, j_end, stage_sink);
+        if (cnt == 0) continue;
+        int n = cnt, dropped = 0;
         const int base = reserve(&A.counters[slot], NT == 5 ? A.pt5_cap : A.pt3_cap, n, dropped);
-        for (int k = lane; k < n; k += 32) {
-            if (NT == 5) { A.pt5_seed[base + k] = g; A.pt5_obj[base + k] = S.stage[k]; }
-            else { A.pt3_seed[base + k] = g; A.pt3_obj[base + k] = S.stage[k]; }
+        int* seed_out = NT == 5 ? A.pt5_seed : A.pt3_seed;
+        int* obj_out = NT == 5 ? A.pt5_obj : A.pt3_obj;
+        if (cnt <= stage) {
+            for (int q = lane; q < n; q += 32) {
+                seed_out[base + q] = g;
+                obj_out[base + q] = S.stage[q];
+            }
+        } else {
+            if (lane == 0) atomicAdd(&A.counters[28], 1);
+            int wr = 0;
+            auto write_sink = [&](bool keep, int obj, int r, int tot) {
+                if (keep && wr + r < n) {
+                    seed_out[base + wr + r] = g;
+                    obj_out[base + wr + r] = obj;
+                }
+                wr += tot;
+            };
+            pt_enumerate<NT>(A, c, S, g, e, it.y, j_end, write_sink);
         }
         if (lane == 0 && dropped) atomicAdd(&A.ev_drop[e * 8 + (NT == 5 ? 5 : 6)], dropped);
         __syncwarp();
     }
 }
 
-__global__ void __launch_bounds__(kPtWarps * 32) k_pt5(Arena A, DevCfg c) { pt_kernel_body<5>(A, c); }
-__global__ void __launch_bounds__(kPtWarps * 32) k_pt3(Arena A, DevCfg c) { pt_kernel_body<3>(A, c); }
+__global__ void __launch_bounds__(kPtWarps * 32, 6) k_pt5(Arena A, DevCfg c) { pt_kernel_body<5>(A, c); }
+__global__ void __launch_bounds__(kPtWarps * 32, 6) k_pt3(Arena A, DevCfg c) { pt_kernel_body<3>(A, c); }
 
 // pT5 / pT3 refine (FP64): one thread per searched candidate.
 template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const DevCfg& c) {

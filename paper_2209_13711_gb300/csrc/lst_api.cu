@@ -38,7 +38,7 @@ struct Buffer {
 // `tunable` stages are grid-stride over their units, so any grid is valid.
 enum LaunchId {
     L_RESET, L_BIN_COUNT, L_BIN_SCAN, L_BIN_SCATTER, L_MD, L_LS, L_T3, L_T5_PLAN, L_T5, L_T5_GATHER, L_T5_REFINE,
-    L_T5_MLP, L_T5_MLP_SELECT, L_PLS, L_PT5, L_PT5_REFINE, L_PT3, L_PT3_REFINE, L_CLEAN_KEYS, L_CLEAN_KEEP,
+    L_T5_MLP, L_T5_MLP_SELECT, L_PLS, L_PT_PLAN, L_PT5, L_PT5_REFINE, L_PT3, L_PT3_REFINE, L_CLEAN_KEYS, L_CLEAN_KEEP,
     L_CLEAN_PT5, L_CLEAN_PT3_CROSS, L_CLEAN_PT3_MARK, L_CLEAN_T5, L_CLEAN_PLS, L_TC_PACK, kNumLaunch
 };
 
@@ -65,6 +65,7 @@ const LaunchInfo kLaunch[kNumLaunch] = {
     {"t5_mlp", 4, 128, true, false},
     {"t5_mlp_select", 4, 128, true, true},
     {"pls", 4, 128, true, true},
+    {"pt_plan", 4, 256, true, true},
     {"pt5", 8, kPtWarps * 32, true, false},
     {"pt5_refine", 2, 128, true, true},
     {"pt3", 8, kPtWarps * 32, true, false},
@@ -147,6 +148,7 @@ static DevCfg make_devcfg(const lst_config& c) {
     d.prefit_scale = 1.0f;
     d.mlp_threshold = 0.5f;
     d.t5_stage = kT5Stage;
+    d.pt_stage = kPtStage;
     return d;
 }
 
@@ -241,9 +243,7 @@ void lst_destroy(lst_ctx* c) {
 
 // Carve every device buffer out of one allocation (first pass with a null
 // base only measures).
-static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_mod, int n_conn, int n_sb,
-                   int n_sbt) {
-    (void)mods_unused;
+static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n_sbt, int max_sbt) {
     const lst_capacity& K = c->cap;
     const size_t E = K.max_events, H = K.max_hits, S = K.max_seeds;
     Arena& A = c->A;
@@ -309,6 +309,9 @@ static void layout(lst_ctx* c, Buffer& b, const lst_module* mods_unused, int n_m
     A.pls_kappa = b.take<double>(S); A.pls_sigk = b.take<double>(S);
     A.pls_eta = b.take<double>(S); A.pls_phi = b.take<double>(S);
     A.pls_z0 = b.take<float>(S); A.pls_pt = b.take<float>(S);
+    A.pt_item_cap = (int)std::min<size_t>(S * (size_t)std::max((max_sbt + kPtChunk - 1) / kPtChunk, 1),
+                                          (size_t)INT32_MAX / 2);
+    A.pt_items = b.take<int2>(A.pt_item_cap);
     const size_t P5 = E * K.pt5_per_event, P3 = E * K.pt3_per_event;
     A.pt5_cap = (int)P5;
     A.pt5_seed = b.take<int>(P5); A.pt5_obj = b.take<int>(P5); A.pt5_kappa = b.take<float>(P5);
@@ -347,6 +350,13 @@ lst_status lst_load_geometry(lst_ctx* c, const lst_module* mods, int32_t n_mod, 
         if (conn_tgt[i] < 0 || conn_tgt[i] >= n_mod) return LST_ERR_ARG;
     for (int i = 0; i < n_sbt; ++i)
         if (sb_tgt[i] < 0 || sb_tgt[i] >= n_mod) return LST_ERR_ARG;
+    int max_sbt = 0;
+    for (int i = 0; i < n_sb; ++i) {
+        if (sb_off[i + 1] < sb_off[i] || sb_off[0] != 0) return LST_ERR_ARG;
+        max_sbt = std::max(max_sbt, sb_off[i + 1] - sb_off[i]);
+    }
+    for (int i = 0; i < n_mod; ++i)
+        if (conn_off[i + 1] < conn_off[i] || conn_off[0] != 0) return LST_ERR_ARG;
     CK(cudaSetDevice(c->device));
     if (c->dev_mem) {
         cudaEventSynchronize(c->done);
@@ -354,7 +364,7 @@ lst_status lst_load_geometry(lst_ctx* c, const lst_module* mods, int32_t n_mod, 
         c->dev_mem = nullptr;
     }
     Buffer probe;
-    layout(c, probe, mods, n_mod, n_conn, n_sb, n_sbt);
+    layout(c, probe, n_mod, n_conn, n_sb, n_sbt, max_sbt);
     if (cudaMalloc(&c->dev_mem, probe.used) != cudaSuccess) {
         c->dev_mem = nullptr;
         c->geometry = false;
@@ -364,7 +374,7 @@ lst_status lst_load_geometry(lst_ctx* c, const lst_module* mods, int32_t n_mod, 
     Buffer real;
     real.base = c->dev_mem;
     real.size = probe.used;
-    layout(c, real, mods, n_mod, n_conn, n_sb, n_sbt);
+    layout(c, real, n_mod, n_conn, n_sb, n_sbt, max_sbt);
     std::vector<float4> m4(n_mod);
     for (int i = 0; i < n_mod; ++i)
         m4[i] = make_float4(mods[i].dsep, mods[i].sig_rphi, mods[i].sig_long, float(mods[i].subdet));
@@ -434,6 +444,7 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile) {
         LAUNCH(L_T5_MLP_SELECT, k_t5_mlp_select<<<GB(L_T5_MLP_SELECT), 0, st>>>(A, dc));
     }
     LAUNCH(L_PLS, k_pls<<<GB(L_PLS), 0, st>>>(A, dc));
+    LAUNCH(L_PT_PLAN, k_pt_plan<<<GB(L_PT_PLAN), 0, st>>>(A));
     LAUNCH(L_PT5, k_pt5<<<GB(L_PT5), 0, st>>>(A, dc));
     LAUNCH(L_PT5_REFINE, k_pt5_refine<<<GB(L_PT5_REFINE), 0, st>>>(A, dc));
     LAUNCH(L_PT3, k_pt3<<<GB(L_PT3), 0, st>>>(A, dc));
@@ -638,6 +649,7 @@ static const void* launch_fn(int id) {
         case L_T5_MLP: return (const void*)k_mlp_forward;
         case L_T5_MLP_SELECT: return (const void*)k_t5_mlp_select;
         case L_PLS: return (const void*)k_pls;
+        case L_PT_PLAN: return (const void*)k_pt_plan;
         case L_PT5: return (const void*)k_pt5;
         case L_PT5_REFINE: return (const void*)k_pt5_refine;
         case L_PT3: return (const void*)k_pt3;
@@ -676,12 +688,13 @@ static lst_status drop_graph(lst_ctx* c) {
     return LST_OK;
 }
 
-lst_status lst_set_t5_stage_limit(lst_ctx* c, int32_t n) {
-    if (!c || n < 0 || n > kT5Stage) return LST_ERR_ARG;
+lst_status lst_set_stage_limits(lst_ctx* c, int32_t t5, int32_t pt) {
+    if (!c || t5 < 0 || t5 > kT5Stage || pt < 0 || pt > kPtStage) return LST_ERR_ARG;
     CK(cudaSetDevice(c->device));
     lst_status s = drop_graph(c);
     if (s != LST_OK) return s;
-    c->dc.t5_stage = n > 0 ? n : kT5Stage;
+    c->dc.t5_stage = t5 > 0 ? t5 : kT5Stage;
+    c->dc.pt_stage = pt > 0 ? pt : kPtStage;
     return LST_OK;
 }
 

@@ -45,6 +45,7 @@ struct DevCfg {
     float prefit_scale;    // widening of the T5 FP32 prefilter (1: conservative for the cuts)
     float mlp_threshold;
     int t5_stage;          // T5 survivors staged per work item before the re-enumeration path
+    int pt_stage;          // the same for the pT5 / pT3 search
 };
 
 // Shape and inputs of the batch being processed (device memory).
@@ -152,6 +153,8 @@ struct Arena {
     double* pls_eta;
     double* pls_phi;
     // pT5 / pT3
+    int pt_item_cap;
+    int2* pt_items;               // pT search work items: (seed, index into sb_tgt)
     int pt5_cap;
     int* pt5_seed;
     int* pt5_obj;

@@ -22,6 +22,7 @@ constexpr int kT3Warps = 8;
 constexpr int kT5Warps = 4;
 constexpr int kPtWarps = 4;
 constexpr int kT5Chunk = 16;       // T3_1 per T5 search work item
+constexpr int kPtChunk = 8;        // superbin modules per pT search work item (<= 32)
 
 __global__ void k_reset(Arena A);
 __global__ void k_bin_count(Arena A);
@@ -36,6 +37,7 @@ __global__ void k_t5_gather(Arena A);
 __global__ void k_t5_refine(Arena A, DevCfg c);
 __global__ void k_t5_mlp_select(Arena A, DevCfg c);
 __global__ void k_pls(Arena A, DevCfg c);
+__global__ void k_pt_plan(Arena A);
 __global__ void k_pt5(Arena A, DevCfg c);
 __global__ void k_pt3(Arena A, DevCfg c);
 __global__ void k_pt5_refine(Arena A, DevCfg c);

@@ -92,7 +92,7 @@ def library():
         L.lst_last_launch_count.argtypes = [vp]
         L.lst_set_profiling.argtypes = [vp, i32]
         L.lst_get_counters.argtypes = [vp, vp, i32]
-        L.lst_set_t5_stage_limit.argtypes = [vp, i32]
+        L.lst_set_stage_limits.argtypes = [vp, i32, i32]
         L.lst_launch_stage_count.argtypes = []
         L.lst_launch_stage_count.restype = i32
         L.lst_get_launch_config.argtypes = [vp, i32, C.POINTER(C.c_char_p), vp, vp, vp]
@@ -294,9 +294,9 @@ class Context:
                             tunable=bool(f.value & 1), generic=bool(f.value & 2)))
         return out
 
-    def set_t5_stage_limit(self, n=0):
-        """Survivors a T5 work item stages before re-enumerating (0: the default 512)."""
-        _check(library().lst_set_t5_stage_limit(self._h, int(n)))
+    def set_stage_limits(self, t5=0, pt=0):
+        """Survivors a T5 / pT work item stages before re-enumerating (0: the defaults 512 / 256)."""
+        _check(library().lst_set_stage_limits(self._h, int(t5), int(pt)))
 
     def set_launch_config(self, stage, blocks_per_sm=0, block=0):
         """stage: index or name; 0 restores a default."""

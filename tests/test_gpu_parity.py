@@ -57,21 +57,22 @@ def test_pu200_event_parity(ctx_full, geom_full, maps_full):
 
 
 def test_t5_stage_overflow_is_lossless(geom_full, maps_full):
-    """A PU200 event searched with a stage of 4 survivors per T5 work item: most
-    items take the second-enumeration path; every level still matches the oracle."""
+    """A PU200 event searched with stages of 4 (T5) and 2 (pT) survivors per work
+    item: many items take the second-enumeration path; every level still
+    matches the oracle."""
     ctx = make_context(geom_full, maps_full, max_events=1)
-    ctx.set_t5_stage_limit(4)
+    ctx.set_stage_limits(4, 2)
     ev = E.pu200_event(12, geom_full)
     ctx.run([ev])
-    assert ctx.counters()[20] > 100
+    assert ctx.counters()[20] > 100 and ctx.counters()[28] > 100
     g = gpu_result(ctx)
     _no_drops(g)
     o = oracle_result(geom_full, maps_full, ev)
     compare(g, o, A_HALF, DEFAULT_CUTS)
     limited = _all_tuples(ctx, 0)
-    ctx.set_t5_stage_limit(0)
+    ctx.set_stage_limits(0, 0)
     ctx.run([ev])
-    assert ctx.counters()[20] == 0
+    assert ctx.counters()[20] == 0 and ctx.counters()[28] == 0
     assert _all_tuples(ctx, 0) == limited
     ctx.close()
 
