@@ -254,6 +254,246 @@ __global__ void __launch_bounds__(kMdWarps * 32) k_md(Arena A, DevCfg c) {
 }
 
 // ---------------------------------------------------------------------------
+// MD as work items (the chain's path; k_md above serves the allocation-free
+// entry point). k_bin_sort puts every sensor bucket in original-index order,
+// k_md_plan cuts each module's lower hits into chunks so no item holds more
+// than about kMdItemPairs pairs, k_md_search writes each chunk's passing
+// (lower, upper) positions, k_md_write concatenates the chunks of a module in
+// order and writes its MDs.
+// ---------------------------------------------------------------------------
+constexpr int kMdItemPairs = 1024;
+constexpr int kMdCodeStage = 256;
+
+// Warp per sensor bucket: rank by original index; the first kMaxHits (all of
+// them in practice) are written back in that order.
+__global__ void __launch_bounds__(128) k_bin_sort(Arena A) {
+    __shared__ int s_idx[4][kMaxHits];
+    __shared__ float s_x[4][kMaxHits], s_y[4][kMaxHits], s_z[4][kMaxHits];
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    const int nb = 2 * A.n_mod;
+    const int n_buckets = A.bd->n_ev * nb;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int b = blockIdx.x * (blockDim.x >> 5) + w; b < n_buckets; b += warps) {
+        const int e = b / nb, k = b - e * nb;
+        const int* bo = A.boff + (size_t)e * (nb + 1);
+        const int g0 = A.hit_off[e] + bo[k], n = bo[k + 1] - bo[k];
+        if (n <= 1) continue;
+        for (int j = lane; j < n; j += 32) {
+            const int ij = A.sidx[g0 + j];
+            int rank = 0;
+            for (int t = 0; t < n; ++t) rank += A.sidx[g0 + t] < ij;
+            if (rank < kMaxHits) {
+                s_idx[w][rank] = ij;
+                s_x[w][rank] = A.sx[g0 + j];
+                s_y[w][rank] = A.sy[g0 + j];
+                s_z[w][rank] = A.sz[g0 + j];
+            }
+        }
+        __syncwarp();
+        for (int j = lane; j < min(n, kMaxHits); j += 32) {
+            A.sidx[g0 + j] = s_idx[w][j];
+            A.sx[g0 + j] = s_x[w][j];
+            A.sy[g0 + j] = s_y[w][j];
+            A.sz[g0 + j] = s_z[w][j];
+        }
+        __syncwarp();
+    }
+}
+
+// Lower hits per chunk of module (e, m): at most 32 chunks of about
+// kMdItemPairs pairs each.
+__device__ __forceinline__ int md_chunk_len(int nl, int nu) {
+    int nch = (nl * nu + kMdItemPairs - 1) / kMdItemPairs;
+    nch = max(1, min(nch, min(32, nl)));
+    return (nl + nch - 1) / nch;
+}
+
+__device__ __forceinline__ void md_sizes(const Arena& A, int u, int& e, int& m, int& gl, int& gu, int& nl, int& nu,
+                                         int& dropped) {
+    e = u / A.n_mod;
+    m = u - e * A.n_mod;
+    const int* bo = A.boff + (size_t)e * (2 * A.n_mod + 1);
+    const int h0 = A.hit_off[e];
+    gl = h0 + bo[2 * m];
+    gu = h0 + bo[2 * m + 1];
+    nl = bo[2 * m + 1] - bo[2 * m];
+    nu = bo[2 * m + 2] - bo[2 * m + 1];
+    dropped = max(0, nl - kMaxHits) + max(0, nu - kMaxHits);
+    nl = min(nl, kMaxHits);
+    nu = min(nu, kMaxHits);
+}
+
+// Work items {unit, first lower rank | chunk length << 16}: split modules at
+// the front of the list, single-chunk modules at the back.
+__global__ void k_md_plan(Arena A) {
+    const int n_units = A.bd->n_ev * A.n_mod;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += gridDim.x * blockDim.x) {
+        int e, m, gl, gu, nl, nu, dropped;
+        md_sizes(A, u, e, m, gl, gu, nl, nu, dropped);
+        if (nl == 0 || nu == 0) continue;
+        const int len = md_chunk_len(nl, nu), nch = (nl + len - 1) / len;
+        if (nch > 1) {
+            const int k = atomicAdd(&A.counters[8], nch);
+            for (int j = 0; j < nch; ++j) A.md_items[k + j] = make_int2(u, (j * len) | (len << 16));
+        } else {
+            const int k = atomicAdd(&A.counters[9], 1);
+            A.md_items[A.md_item_cap - 1 - k] = make_int2(u, len << 16);
+        }
+    }
+}
+
+struct MdSearchSmem {
+    float lx[kMaxHits], ly[kMaxHits], lz[kMaxHits];
+    float ux[kMaxHits], uy[kMaxHits], uz[kMaxHits];
+    int2 stage[kMdCodeStage];
+};
+
+// The pairs of lower ranks [r0, r1) x all upper hits of one module, in order.
+template <typename Sink>
+__device__ __forceinline__ void md_enumerate(const DevCfg& c, const MdSearchSmem& S, float4 mi, int gl, int gu,
+                                             int r0, int r1, int nu, Sink& sink) {
+    const int lane = lane_id();
+    const int total = (r1 - r0) * nu;
+    for (int base = 0; base < total; base += 32) {
+        const int p = base + lane;
+        bool pass = false;
+        int l = 0, k = 0;
+        if (p < total) {
+            l = p / nu;
+            k = p - l * nu;
+            Pt<float> L = hit_pt<float>(S.lx[l], S.ly[l], S.lz[l], mi);
+            Pt<float> U = hit_pt<float>(S.ux[k], S.uy[k], S.uz[k], mi);
+            float dp, dl;
+            int st = md_eval<float>(c, mi, L, U, dp, dl);
+            if (st == 2) {
+                Pt<double> Ld = hit_pt<double>(S.lx[l], S.ly[l], S.lz[l], mi);
+                Pt<double> Ud = hit_pt<double>(S.ux[k], S.uy[k], S.uz[k], mi);
+                double dpd, dld;
+                st = md_eval<double>(c, mi, Ld, Ud, dpd, dld);
+            }
+            pass = st == 1;
+        }
+        int tot;
+        int r = warp_rank(pass, tot);
+        sink(pass, make_int2(gl + r0 + l, gu + k), r, tot);
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kMdWarps * 32) k_md_search(Arena A, DevCfg c) {
+    __shared__ MdSearchSmem sm[kMdWarps];
+    MdSearchSmem& S = sm[threadIdx.x >> 5];
+    const int lane = lane_id();
+    const int n_front = A.counters[8], n_items = n_front + A.counters[9];
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&A.counters[7], 1);
+        k = __shfl_sync(kFull, k, 0);
+        if (k >= n_items) break;
+        const int2 it = k < n_front ? A.md_items[k] : A.md_items[A.md_item_cap - 1 - (k - n_front)];
+        const int u = it.x, r0 = it.y & 0xffff, len = it.y >> 16;
+        int e, m, gl, gu, nl, nu, dropped;
+        md_sizes(A, u, e, m, gl, gu, nl, nu, dropped);
+        const int r1 = min(nl, r0 + len);
+        for (int j = lane; j < r1 - r0; j += 32) {
+            S.lx[j] = A.sx[gl + r0 + j];
+            S.ly[j] = A.sy[gl + r0 + j];
+            S.lz[j] = A.sz[gl + r0 + j];
+        }
+        for (int j = lane; j < nu; j += 32) {
+            S.ux[j] = A.sx[gu + j];
+            S.uy[j] = A.sy[gu + j];
+            S.uz[j] = A.sz[gu + j];
+        }
+        __syncwarp();
+        const float4 mi = A.mod[m];
+        int cnt = 0;
+        auto stage_sink = [&](bool keep, int2 code, int r, int tot) {
+            if (keep && cnt + r < kMdCodeStage) S.stage[cnt + r] = code;
+            cnt += tot;
+        };
+        md_enumerate(c, S, mi, gl, gu, r0, r1, nu, stage_sink);
+        int n = cnt, drop = 0;
+        const int base = reserve(&A.counters[6], A.md_cap, n, drop);
+        if (cnt <= kMdCodeStage) {
+            for (int q = lane; q < n; q += 32) A.md_tmp[base + q] = S.stage[q];
+        } else {
+            int wr = 0;
+            auto write_sink = [&](bool keep, int2 code, int r, int tot) {
+                if (keep && wr + r < n) A.md_tmp[base + wr + r] = code;
+                wr += tot;
+            };
+            md_enumerate(c, S, mi, gl, gu, r0, r1, nu, write_sink);
+        }
+        if (lane == 0) {
+            A.md_chunk_off[gl + r0] = base;
+            A.md_chunk_cnt[gl + r0] = n;
+            if (drop) atomicAdd(&A.ev_drop[e * 8 + 0], drop);
+        }
+        __syncwarp();
+    }
+}
+
+// Warp per module: its chunks in order become the module's MD segment (at
+// most kMdStage MDs, the rest counted as dropped).
+__global__ void __launch_bounds__(128) k_md_write(Arena A, DevCfg c) {
+    __shared__ int sm_pre[4][32], sm_off[4][32];
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    const int n_units = A.bd->n_ev * A.n_mod;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int u = blockIdx.x * (blockDim.x >> 5) + w; u < n_units; u += warps) {
+        int e, m, gl, gu, nl, nu, dropped;
+        md_sizes(A, u, e, m, gl, gu, nl, nu, dropped);
+        int off = 0, len = 0;
+        if (nl > 0 && nu > 0) {
+            const int clen = md_chunk_len(nl, nu), nch = (nl + clen - 1) / clen;
+            if (lane < nch) {
+                off = A.md_chunk_off[gl + lane * clen];
+                len = A.md_chunk_cnt[gl + lane * clen];
+            }
+        }
+        int tot = len;
+#pragma unroll
+        for (int d = 16; d; d >>= 1) tot += __shfl_xor_sync(kFull, tot, d);
+        int n = min(tot, kMdStage);
+        dropped += tot - n;
+        const int base = reserve(&A.counters[0], A.md_cap, n, dropped);
+        const float4 mi = A.mod[m];
+        int wr = 0;
+        for_each_flat(off, len, sm_pre[w], sm_off[w], [&](bool valid, int, int q) {
+            const int o = wr + lane;
+            if (valid && o < n) {
+                const int2 code = A.md_tmp[q];
+                const float lx = A.sx[code.x], ly = A.sy[code.x], lz = A.sz[code.x];
+                const float ux = A.sx[code.y], uy = A.sy[code.y], uz = A.sz[code.y];
+                Pt<float> L = hit_pt<float>(lx, ly, lz, mi);
+                Pt<float> U = hit_pt<float>(ux, uy, uz, mi);
+                float dp, dl;
+                md_eval<float>(c, mi, L, U, dp, dl);
+                const int t = base + o;
+                A.md_lo[t] = A.sidx[code.x];
+                A.md_up[t] = A.sidx[code.y];
+                A.md_gmod[t] = u;
+                A.md_p4[t] = make_float4(lx, ly, lz, mi.w < 0.5f ? mi.z : -mi.z);
+                A.md_srp[t] = mi.y;
+                A.md_dx[t] = ux - lx;
+                A.md_dy[t] = uy - ly;
+                A.md_dphi[t] = dp;
+                A.md_dlong[t] = dl;
+            }
+            wr += 32;
+        });
+        if (lane == 0) {
+            A.md_moff[u] = base;
+            A.md_mcnt[u] = n;
+            if (n) atomicAdd(&A.ev_counts[e * 8 + 0], n);
+            if (dropped) atomicAdd(&A.ev_drop[e * 8 + 0], dropped);
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // LS: one warp per inner MD A, candidates = MDs of the connected modules
 // ---------------------------------------------------------------------------
 struct LsSmem {

@@ -37,7 +37,7 @@ struct Buffer {
 // their shared-memory stages by a compile-time warp count and keep their block.
 // `tunable` stages are grid-stride over their units, so any grid is valid.
 enum LaunchId {
-    L_RESET, L_BIN_COUNT, L_BIN_SCAN, L_BIN_SCATTER, L_MD, L_LS, L_T3, L_T5_PLAN, L_T5, L_T5_GATHER, L_T5_REFINE,
+    L_RESET, L_BIN_COUNT, L_BIN_SCAN, L_BIN_SCATTER, L_BIN_SORT, L_MD_PLAN, L_MD, L_MD_WRITE, L_LS, L_T3, L_T5_PLAN, L_T5, L_T5_GATHER, L_T5_REFINE,
     L_T5_MLP, L_T5_MLP_SELECT, L_PLS, L_PT_PLAN, L_PT5, L_PT5_REFINE, L_PT3, L_PT3_REFINE, L_CLEAN_KEYS, L_CLEAN_KEEP,
     L_CLEAN_PT5, L_CLEAN_PT3_CROSS, L_CLEAN_PT3_MARK, L_CLEAN_T5, L_CLEAN_PLS, L_TC_PACK, kNumLaunch
 };
@@ -55,7 +55,10 @@ const LaunchInfo kLaunch[kNumLaunch] = {
     {"bin_count", 8, 256, true, true},
     {"bin_scan", 0, 1024, false, false},        // one block per event
     {"bin_scatter", 8, 256, true, true},
+    {"bin_sort", 4, 128, true, false},
+    {"md_plan", 4, 256, true, true},
     {"md", 4, kMdWarps * 32, true, false},
+    {"md_write", 4, 128, true, false},
     {"ls", 8, kLsWarps * 32, true, false},
     {"t3", 8, kT3Warps * 32, true, false},
     {"t5_plan", 4, 256, true, true},
@@ -284,6 +287,10 @@ static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n
     A.md_dx = b.take<float>(MD); A.md_dy = b.take<float>(MD);
     A.md_dphi = b.take<float>(MD); A.md_dlong = b.take<float>(MD);
     A.md_moff = b.take<int>(E * n_mod); A.md_mcnt = b.take<int>(E * n_mod);
+    A.md_item_cap = (int)std::max<size_t>(H, 1);
+    A.md_items = b.take<int2>(A.md_item_cap);
+    A.md_chunk_off = b.take<int>(H); A.md_chunk_cnt = b.take<int>(H);
+    A.md_tmp = b.take<int2>(MD);
     const size_t LS = E * K.ls_per_event;
     A.ls_cap = (int)LS;
     A.ls_in = b.take<int>(LS); A.ls_out = b.take<int>(LS); A.ls_dphi = b.take<float>(LS);
@@ -386,7 +393,6 @@ lst_status lst_load_geometry(lst_ctx* c, const lst_module* mods, int32_t n_mod, 
     if (n_conn) CK(cudaMemcpy((void*)c->A.conn_tgt, conn_tgt, sizeof(int) * n_conn, cudaMemcpyHostToDevice));
     CK(cudaMemcpy((void*)c->A.sb_off, sb_off, sizeof(int) * (n_sb + 1), cudaMemcpyHostToDevice));
     if (n_sbt) CK(cudaMemcpy((void*)c->A.sb_tgt, sb_tgt, sizeof(int) * n_sbt, cudaMemcpyHostToDevice));
-    CK(cudaFuncSetAttribute(k_md, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)md_smem_bytes()));
     if (c->graph) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
@@ -431,7 +437,10 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile) {
     LAUNCH(L_BIN_COUNT, k_bin_count<<<GB(L_BIN_COUNT), 0, st>>>(A));
     LAUNCH(L_BIN_SCAN, k_bin_scan<<<A.max_events, 1024, 0, st>>>(A));
     LAUNCH(L_BIN_SCATTER, k_bin_scatter<<<GB(L_BIN_SCATTER), 0, st>>>(A));
-    LAUNCH(L_MD, k_md<<<GB(L_MD), md_smem_bytes(), st>>>(A, dc));
+    LAUNCH(L_BIN_SORT, k_bin_sort<<<GB(L_BIN_SORT), 0, st>>>(A));
+    LAUNCH(L_MD_PLAN, k_md_plan<<<GB(L_MD_PLAN), 0, st>>>(A));
+    LAUNCH(L_MD, k_md_search<<<GB(L_MD), 0, st>>>(A, dc));
+    LAUNCH(L_MD_WRITE, k_md_write<<<GB(L_MD_WRITE), 0, st>>>(A, dc));
     LAUNCH(L_LS, k_ls<<<GB(L_LS), 0, st>>>(A, dc));
     LAUNCH(L_T3, k_t3<<<GB(L_T3), 0, st>>>(A, dc));
     LAUNCH(L_T5_PLAN, k_t5_plan<<<GB(L_T5_PLAN), 0, st>>>(A));
@@ -639,7 +648,10 @@ static const void* launch_fn(int id) {
         case L_BIN_COUNT: return (const void*)k_bin_count;
         case L_BIN_SCAN: return (const void*)k_bin_scan;
         case L_BIN_SCATTER: return (const void*)k_bin_scatter;
-        case L_MD: return (const void*)k_md;
+        case L_BIN_SORT: return (const void*)k_bin_sort;
+        case L_MD_PLAN: return (const void*)k_md_plan;
+        case L_MD: return (const void*)k_md_search;
+        case L_MD_WRITE: return (const void*)k_md_write;
         case L_LS: return (const void*)k_ls;
         case L_T3: return (const void*)k_t3;
         case L_T5: return (const void*)k_t5;

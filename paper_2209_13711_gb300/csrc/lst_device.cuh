@@ -98,6 +98,12 @@ struct Arena {
     float* md_dy;
     float* md_dphi;
     float* md_dlong;
+    // MD search work items: chunks of a module's lower hits
+    int md_item_cap;
+    int2* md_items;               // {unit, first lower rank | chunk length << 16}
+    int* md_chunk_off;            // [max_hits] by the chunk's first lower-hit position
+    int* md_chunk_cnt;
+    int2* md_tmp;                 // [md_cap] passing (lower, upper) sorted-hit positions by chunk
     int* md_moff;                 // [n_ev * n_mod]
     int* md_mcnt;
     // LS

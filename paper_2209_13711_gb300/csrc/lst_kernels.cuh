@@ -29,6 +29,10 @@ __global__ void k_bin_count(Arena A);
 __global__ void k_bin_scan(Arena A);
 __global__ void k_bin_scatter(Arena A);
 __global__ void k_md(Arena A, DevCfg c);
+__global__ void k_bin_sort(Arena A);
+__global__ void k_md_plan(Arena A);
+__global__ void k_md_search(Arena A, DevCfg c);
+__global__ void k_md_write(Arena A, DevCfg c);
 __global__ void k_ls(Arena A, DevCfg c);
 __global__ void k_t3(Arena A, DevCfg c);
 __global__ void k_t5(Arena A, DevCfg c);

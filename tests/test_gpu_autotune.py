@@ -26,7 +26,8 @@ def test_launch_config_validation(geom_full, maps_full):
     ctx = make_context(geom_full, maps_full, max_events=1)
     cfg = ctx.launch_config()
     names = [c["name"] for c in cfg]
-    assert names[:5] == ["reset", "bin_count", "bin_scan", "bin_scatter", "md"]
+    assert names[:4] == ["reset", "bin_count", "bin_scan", "bin_scatter"] and names[-1] == "tc_pack"
+    assert {"md", "ls", "t3", "t5", "pt5", "pt3", "clean_pls"} <= set(names)
     byname = {c["name"]: c for c in cfg}
     assert not byname["bin_scan"]["tunable"]
     assert byname["t5_gather"]["tunable"] and not byname["t5_gather"]["generic"]
