@@ -54,7 +54,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
         return self
@@ -88,6 +88,32 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+EVENT_POOL = 32
+
+
+def event_seeds(rank, n):
+    """Generator seeds of rank `rank`'s n events (disjoint across ranks)."""
+    return [rank * 100000 + i for i in range(n)]
+
+
+def max_over_ranks(values, ws):
+    """Element-wise maximum of per-rank timings (identity on one rank). Uses the
+    default process group: NCCL with CUDA tensors, gloo with CPU tensors."""
+    import torch
+    if ws <= 1:
+        return [float(v) for v in values]
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(ws, steps, seconds):
+    """Units processed by all ranks per second of the slowest rank."""
+    return ws * steps / seconds
 
 
 def _peaks():
@@ -131,8 +157,11 @@ def run_ours(args):
     maps = M.load_maps(geom)
     ctx = P.Context(geom.module_table(), maps, cfg=DEFAULT_CUTS, capacity=P.default_capacity(1), device=local)
     n_ev = args.steps + args.warmup
-    events = [E.pu200_event(rank * 100000 + i, geom) for i in range(n_ev)]
+    pool = min(n_ev, EVENT_POOL)
+    # rank r processes its own events (disjoint seeds); steps cycle over a pool of distinct events
+    events = [E.pu200_event(s, geom) for s in event_seeds(rank, pool)]
     packed = [P.pack_events([e]) for e in events]
+    pick = lambda i: i % pool
     dev = [{k: (torch.from_numpy(v).cuda() if k not in ("hit_off", "seed_off") else v) for k, v in b.items()}
            for b in packed]
     pinned = [{k: (torch.from_numpy(v).pin_memory() if k not in ("hit_off", "seed_off") else v)
@@ -149,7 +178,7 @@ def run_ours(args):
     tune = autotune(ctx, dev[0], st)
     # ---- device-timed: inputs resident in HBM ---------------------------
     for i in range(args.warmup):
-        ctx.run_packed(dev[i], stream=st.cuda_stream)
+        ctx.run_packed(dev[pick(i)], stream=st.cuda_stream)
     barrier()
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -159,7 +188,7 @@ def run_ours(args):
         for i in range(args.steps):
             flush.fill_(i & 0xff)
             ev0[i].record(st)
-            ctx.run_packed(dev[args.warmup + i], stream=st.cuda_stream)
+            ctx.run_packed(dev[pick(args.warmup + i)], stream=st.cuda_stream)
             ev1[i].record(st)
             launches += ctx.launch_count
         barrier()
@@ -171,7 +200,7 @@ def run_ours(args):
     records = np.empty(ctx.capacity.tc_per_event, P.lst.TC_DTYPE)
     for i in range(args.steps):
         flush.fill_(i & 0xff)
-        b = pinned[args.warmup + i]
+        b = pinned[pick(args.warmup + i)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.run_packed(b, stream=st.cuda_stream)
@@ -186,24 +215,22 @@ def run_ours(args):
     per_kernel = {}
     for i in range(min(args.steps, 5)):
         flush.fill_(i & 0xff)
-        ctx.run_packed(dev[args.warmup + i], stream=st.cuda_stream)
+        ctx.run_packed(dev[pick(args.warmup + i)], stream=st.cuda_stream)
         for name, ms in ctx.kernel_times():
             per_kernel.setdefault(name, []).append(ms)
     ctx.set_profiling(False)
     kavg = {k: sum(v) / len(v) for k, v in per_kernel.items()}
     top = max(kavg, key=kavg.get)
     # timing across ranks
-    tot = torch.tensor([dev_ms, e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
-    dev_ms, e2e_s = float(tot[0]), float(tot[1])
+    dev_ms, e2e_s = max_over_ranks([dev_ms, e2e_s], ws)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
-    value = ws * args.steps / (dev_ms / 1e3)
+    value = whole_job_rate(ws, args.steps, dev_ms / 1e3)
     hbm_peak, peak_kind = _peaks()
-    b_alg = algorithmic_bytes(top, stats0, len(events[args.warmup].x), len(events[args.warmup].seeds), geom.n_mod)
+    last = events[pick(args.warmup + args.steps - 1)]
+    b_alg = algorithmic_bytes(top, stats0, len(last.x), len(last.seeds), geom.n_mod)
     roof = None
     if b_alg is not None:
         achieved = b_alg / (kavg[top] / 1e3) / 1e9
@@ -215,9 +242,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "events_per_step": 1, "path": "plain, one event per launch sequence",
+                   "events": f"{pool} distinct PU200 events per rank, cycled over the {args.steps} steps",
                    "l2": "flushed between steps (256 MiB write, outside the timed spans)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-        "e2e": {"value": round(ws * args.steps / e2e_s, 2), "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+        "e2e": {"value": round(whole_job_rate(ws, args.steps, e2e_s), 2), "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
                 "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": launches,
         "autotune": tune,
@@ -228,7 +256,7 @@ def run_ours(args):
         "dropped_per_event": stats0["dropped"],
     }
     out["batched"] = measure_batched(P, E, geom, maps, DEFAULT_CUTS, flush, st, steps=max(2, min(args.steps, 5)))
-    out["mlp"] = measure_mlp(P, E, geom, maps, DEFAULT_CUTS, flush, st, dev[args.warmup:])
+    out["mlp"] = measure_mlp(P, E, geom, maps, DEFAULT_CUTS, flush, st, dev)
     out["serving"] = measure_serving(E, geom, maps, DEFAULT_CUTS)
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
@@ -441,7 +469,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")

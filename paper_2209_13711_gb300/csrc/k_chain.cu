@@ -508,7 +508,7 @@ __device__ __forceinline__ float4 md_mod(const Arena& A, int i) {
     return A.mod[gm % A.n_mod];
 }
 
-__global__ void __launch_bounds__(kLsWarps * 32) k_ls(Arena A, DevCfg c) {
+__global__ void __launch_bounds__(kLsWarps * 32, 3) k_ls(Arena A, DevCfg c) {
     __shared__ LsSmem sm[kLsWarps];
     LsSmem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -581,7 +581,7 @@ struct T3Smem {
     int2 stage[kT3Stage];
 };
 
-__global__ void __launch_bounds__(kT3Warps * 32) k_t3(Arena A, DevCfg c) {
+__global__ void __launch_bounds__(kT3Warps * 32, 3) k_t3(Arena A, DevCfg c) {
     __shared__ T3Smem sm[kT3Warps];
     T3Smem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -680,7 +680,7 @@ __device__ __forceinline__ bool t5_prefit_f32(const Arena& A, const DevCfg& c, i
     Pt<float> P[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) P[j] = md_point<float>(A, m[j]);
-    return fit_may_pass_f32<5>(P, fit_limits(c, c.chi2_rphi_t5, c.chi2_rz_t5, c.prefit_scale));
+    return fit_may_pass_f32<5>(P, c.lim_t5);
 }
 
 // Collected candidates: FP32 fit prefilter; the verdicts of each group of 32

@@ -75,13 +75,12 @@ __device__ __forceinline__ bool pt_prefit_f32(const Arena& A, const DevCfg& c, i
     Pt<float> P[NT + 3];
     const float* sd = A.bd->seeds + 9 * (size_t)g;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) P[j] = pix_pt<float>(sd + 3 * j, c.sig_pix);
+    for (int j = 0; j < 3; ++j) P[j] = pix_pt<float>(sd + 3 * j, c.f.sig_pix);
     int m[NT];
     pt_mds<NT>(A, obj, m);
 #pragma unroll
     for (int j = 0; j < NT; ++j) P[3 + j] = md_point<float>(A, m[j]);
-    return fit_may_pass_f32<NT + 3>(P, fit_limits(c, NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3,
-                                                  NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3, 1.0f));
+    return fit_may_pass_f32<NT + 3>(P, NT == 5 ? c.lim_pt5 : c.lim_pt3);
 }
 
 // FP32 fit verdicts of one group of 32 candidates (one out-of-line copy).

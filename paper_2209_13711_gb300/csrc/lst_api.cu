@@ -135,6 +135,21 @@ struct lst_ctx {
         if (err__ != cudaSuccess) return LST_ERR_CUDA; \
     } while (0)
 
+// FP32 limits of the fit prefilter: rejected only when a cut fails by far
+// more than FP32 rounding can explain (1.01 kmax + 1e-5; 1.25 chi2_max + 2).
+static FitLimits prefit_limits(const DevCfg& d, double chi2_max, double chi2z_max, float scale) {
+    const float kmax = float((1.0 + d.tol_r) * 2.0 * d.a);
+    return FitLimits{kmax * 1.01f + 1e-5f, 1.25f * (float(chi2_max) * scale) + 2.f,
+                     1.25f * (float(chi2z_max) * scale) + 2.f};
+}
+
+static void derive_fp32(DevCfg& d) {
+    d.f = CfgF{float(d.a), float(d.z_lumi), float(d.n_md), float(d.n_ls), float(d.n_t3), float(d.sig_pix)};
+    d.lim_t5 = prefit_limits(d, d.chi2_rphi_t5, d.chi2_rz_t5, d.prefit_scale);
+    d.lim_pt5 = prefit_limits(d, d.chi2_rphi_pt5, d.chi2_rz_pt5, 1.0f);
+    d.lim_pt3 = prefit_limits(d, d.chi2_rphi_pt3, d.chi2_rz_pt3, 1.0f);
+}
+
 static DevCfg make_devcfg(const lst_config& c) {
     DevCfg d{};
     d.a = c.k_field * c.b_field / (200.0 * c.pt_min);
@@ -152,6 +167,7 @@ static DevCfg make_devcfg(const lst_config& c) {
     d.mlp_threshold = 0.5f;
     d.t5_stage = kT5Stage;
     d.pt_stage = kPtStage;
+    derive_fp32(d);
     return d;
 }
 
@@ -846,6 +862,7 @@ lst_status lst_set_t5_selection(lst_ctx* c, const lst_mlp* mlp, float threshold,
     c->dc.features_on = (mlp || capture_features) ? 1 : 0;
     c->dc.prefit_scale = prefilter_scale;
     c->dc.mlp_threshold = threshold;
+    derive_fp32(c->dc);
     if (c->graph) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;

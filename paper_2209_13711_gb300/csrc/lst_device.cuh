@@ -33,6 +33,19 @@ constexpr float kBand = 2e-3f;   // relative width of the FP32 undecided band ar
 constexpr double kPi = 3.14159265358979323846;
 
 // Cut constants as seen by the kernels (derived on the host from lst_config).
+// Limits of the conservative FP32 verdict on the fit cuts: a candidate is
+// rejected only when a cut fails by far more than FP32 rounding can explain
+// (|kappa| above 1.01 kmax + 1e-5, a chi2 above 1.25 max + 2).
+struct FitLimits {
+    float kappa, chi2, chi2z;
+};
+
+// FP32 copies of the constants the FP32 predicates use, converted once on the
+// host (a double-to-float conversion per candidate would run on the FP64 pipe).
+struct CfgF {
+    float a, z_lumi, n_md, n_ls, n_t3, sig_pix;
+};
+
 struct DevCfg {
     double a;              // 1 / (2 R_min), R_min = 100 pT_min / (k B) cm
     double z_lumi, n_md, n_ls, n_t3, n_t5, n_pt, tol_r;
@@ -46,7 +59,14 @@ struct DevCfg {
     float mlp_threshold;
     int t5_stage;          // T5 survivors staged per work item before the re-enumeration path
     int pt_stage;          // the same for the pT5 / pT3 search
+    CfgF f;
+    FitLimits lim_t5, lim_pt5, lim_pt3;   // FP32 prefilter limits (T5 widened by prefit_scale)
 };
+
+// The constant in the predicate's precision: FP32 predicates take the host-made copy.
+template <typename T> __device__ __forceinline__ T cval(double d, float f);
+template <> __device__ __forceinline__ float cval<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double cval<double>(double d, float) { return d; }
 
 // Shape and inputs of the batch being processed (device memory).
 struct BatchDesc {
@@ -277,7 +297,7 @@ template <typename T> __device__ __forceinline__ Pt<T> hit_pt(float x, float y, 
     return p;
 }
 
-template <typename T> __device__ __forceinline__ Pt<T> pix_pt(const float* q, double sig_pix) {
+template <typename T, typename S> __device__ __forceinline__ Pt<T> pix_pt(const float* q, S sig_pix) {
     Pt<T> p;
     p.x = T(q[0]); p.y = T(q[1]); p.z = T(q[2]);
     p.r = m_hypot(p.x, p.y);
@@ -311,7 +331,7 @@ template <typename T> __device__ __forceinline__ T sigma_perp(const Pt<T>& P, T 
 template <typename T>
 __device__ __forceinline__ int md_eval(const DevCfg& c, float4 mi, const Pt<T>& L, const Pt<T>& U, T& dphi_o,
                                        T& dlong_o) {
-    const T a = T(c.a);
+    const T a = cval<T>(c.a, c.f.a);
     T dx = U.x - L.x, dy = U.y - L.y, dz = U.z - L.z;
     T rL = L.r;
     T dsep = T(mi.x), srphi = T(mi.y), sl = T(mi.z);
@@ -319,17 +339,17 @@ __device__ __forceinline__ int md_eval(const DevCfg& c, float4 mi, const Pt<T>& 
     T dlong, thr_phi, thr_long;
     const T rt2 = T(1.4142135623730951);
     if (mi.w < 0.5f) {
-        thr_phi = asinc((rL + dsep) * a) - asinc(rL * a) + T(c.n_md) * rt2 * srphi / rL;
+        thr_phi = asinc((rL + dsep) * a) - asinc(rL * a) + cval<T>(c.n_md, c.f.n_md) * rt2 * srphi / rL;
         dlong = dz - dsep * L.z / rL;
-        thr_long = T(c.n_md) * rt2 * sl + dsep * T(c.z_lumi) / rL;
+        thr_long = cval<T>(c.n_md, c.f.n_md) * rt2 * sl + dsep * cval<T>(c.z_lumi, c.f.z_lumi) / rL;
     } else {
         T az = m_abs(L.z);
         // r_U - r_L from the exact coordinate differences (no cancellation)
         T dr = (dx * (U.x + L.x) + dy * (U.y + L.y)) / (U.r + rL);
         dlong = dr - dsep * rL / az;
-        thr_long = T(c.n_md) * rt2 * sl;
-        T ds_max = T(1.2) * dsep * (rL + T(c.n_md) * sl) / (az - T(c.z_lumi));
-        thr_phi = a * ds_max + T(c.n_md) * rt2 * srphi / rL;
+        thr_long = cval<T>(c.n_md, c.f.n_md) * rt2 * sl;
+        T ds_max = T(1.2) * dsep * (rL + cval<T>(c.n_md, c.f.n_md) * sl) / (az - cval<T>(c.z_lumi, c.f.z_lumi));
+        thr_phi = a * ds_max + cval<T>(c.n_md, c.f.n_md) * rt2 * srphi / rL;
     }
     Cuts<T> cut;
     cut(m_abs(dphi), thr_phi);
@@ -345,13 +365,13 @@ __device__ __forceinline__ int md_eval(const DevCfg& c, float4 mi, const Pt<T>& 
 template <typename T>
 __device__ __forceinline__ int ls_eval(const DevCfg& c, const Pt<T>& P, T sAx, T sAy, float4 mA, const Pt<T>& Q,
                                        T sBx, T sBy, float4 mB, T& dphi_o) {
-    const T a = T(c.a);
-    const T n = T(c.n_ls);
+    const T a = cval<T>(c.a, c.f.a);
+    const T n = cval<T>(c.n_ls, c.f.n_ls);
     Cuts<T> cut;
     T num = P.z * Q.r - Q.z * P.r;
     T den = Q.r - P.r;
     T sig_num = m_sqrt(sq(Q.r * P.sz) + sq(P.r * Q.sz) + sq(Q.z * P.sr) + sq(P.z * Q.sr));
-    cut(m_abs(num), T(c.z_lumi) * m_abs(den) + n * sig_num);
+    cut(m_abs(num), cval<T>(c.z_lumi, c.f.z_lumi) * m_abs(den) + n * sig_num);
     T dphi = m_atan2(P.x * Q.y - P.y * Q.x, P.x * Q.x + P.y * Q.y);
     dphi_o = dphi;
     if (cut.fail) return 0;
@@ -407,13 +427,13 @@ template <typename T> __device__ __forceinline__ Tri<T> tri(const Pt<T>& A, cons
 template <typename T>
 __device__ __forceinline__ int t3_eval(const DevCfg& c, const Pt<T>& A, const Pt<T>& B, const Pt<T>& C, T& beta_o,
                                        T& kappa_o, T& rz_o, T& sigk_o) {
-    const T a = T(c.a);
+    const T a = cval<T>(c.a, c.f.a);
     Tri<T> t = tri(A, B, C);
     Cuts<T> cut;
     beta_o = t.beta;
     kappa_o = t.kappa;
     sigk_o = t.sigk;
-    cut(m_abs(t.beta), asinc(t.lu * a) + asinc(t.lv * a) + T(c.n_t3) * t.sig_beta);
+    cut(m_abs(t.beta), asinc(t.lu * a) + asinc(t.lv * a) + cval<T>(c.n_t3, c.f.n_t3) * t.sig_beta);
     T ka = m_abs(t.kappa);
     T sB = arc(t.lu, ka), sC = arc(t.lw, ka);
     T d = (B.z - A.z) * sC - (C.z - A.z) * sB;
@@ -421,7 +441,7 @@ __device__ __forceinline__ int t3_eval(const DevCfg& c, const Pt<T>& A, const Pt
     if (cut.fail) return 0;
     T sig_d = m_sqrt(sq((sB - sC) * A.sz) + sq(sC * B.sz) + sq(sB * C.sz) + sq((C.z - B.z) * A.sr) +
                      sq((C.z - A.z) * B.sr) + sq((B.z - A.z) * C.sr));
-    cut(m_abs(d), T(c.n_t3) * sig_d);
+    cut(m_abs(d), cval<T>(c.n_t3, c.f.n_t3) * sig_d);
     return cut.state();
 }
 
@@ -556,19 +576,6 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
 // FP32 twin of fit_track, used only as a conservative prefilter before the
 // FP64 fit: same frame and residual definitions, with the normal equations
 // centred (2x2 solve) for conditioning in single precision.
-// Limits of the conservative FP32 verdict on the fit cuts: a candidate is
-// rejected only when a cut fails by far more than FP32 rounding can explain
-// (|kappa| above 1.01 kmax + 1e-5, a chi2 above 1.25 max + 2).
-struct FitLimits {
-    float kappa, chi2, chi2z;
-};
-
-__device__ __forceinline__ FitLimits fit_limits(const DevCfg& c, double chi2_max, double chi2z_max, float scale) {
-    const float kmax = float((1.0 + c.tol_r) * 2.0 * c.a);
-    return FitLimits{kmax * 1.01f + 1e-5f, 1.25f * (float(chi2_max) * scale) + 2.f,
-                     1.25f * (float(chi2z_max) * scale) + 2.f};
-}
-
 // FP32 twin of fit_track (same chord-frame circle fit, geometric residuals and
 // r-z line fit), evaluated cut by cut: the curvature is tested right after the
 // circle solve, chi2_rphi after the residuals, and the r-z fit runs only for

@@ -97,6 +97,9 @@ DevCfg static_devcfg(const lst_config& c) {
     d.n_md = c.n_md;
     d.k_field = c.k_field;
     d.b_field = c.b_field;
+    d.f.a = float(d.a);
+    d.f.z_lumi = float(d.z_lumi);
+    d.f.n_md = float(d.n_md);
     return d;
 }
 
