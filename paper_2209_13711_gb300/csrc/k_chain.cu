@@ -863,12 +863,14 @@ __global__ void k_t5_refine(Arena A, DevCfg c) {
     const BatchDesc* B = A.bd;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int m[5];
-        t5_mds(A, make_int2(A.t5_in[i], A.t5_out[i]), m);
+        const int2 pr = make_int2(A.t5_in[i], A.t5_out[i]);
+        t5_mds(A, pr, m);
         Pt<double> P[5];
 #pragma unroll
         for (int j = 0; j < 5; ++j) P[j] = md_point<double>(A, m[j]);
-        T5Out o{};
-        bool pass = t5_eval(c, P, o);
+        T5Out o;
+        bool pass = t5_eval(c, P, A.t3_kappa[pr.x], A.t3_sigk[pr.x], A.t3_kappa[pr.y], A.t3_sigk[pr.y],
+                            c.use_mlp != 0, o);
         const int e = A.md_gmod[m[0]] / A.n_mod;
         A.t5_cut[i] = pass;
         A.t5_kappa[i] = o.kappa;

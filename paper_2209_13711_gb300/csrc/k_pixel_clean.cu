@@ -240,18 +240,21 @@ template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const
         pt_mds<NT>(A, obj, m);
 #pragma unroll
         for (int j = 0; j < NT; ++j) P[3 + j] = md_point<double>(A, m[j]);
-        double kt, st;
+        const double kp = A.pls_kappa[g], sp = A.pls_sigk[g];
+        bool kc;
         if (NT == 5) {
-            kt = A.t5_kappa[obj];
-            st = A.t5_sigk[obj];
+            kc = fabs(kp - A.t5_kappa[obj]) <= c.n_pt * sqrt(sq(sp) + sq(A.t5_sigk[obj]));
         } else {
-            Tri<double> tt = tri(P[3], P[4], P[5]);
-            kt = tt.kappa;
-            st = tt.sigk;
+            // the triplet's FP32 curvature decides unless undecided; then FP64
+            int k = kappa_test_f32(float(kp), float(sp), A.t3_kappa[obj], A.t3_sigk[obj], c.f.n_pt);
+            if (k < 0) {
+                Tri<double> tt = tri(P[3], P[4], P[5]);
+                k = fabs(kp - tt.kappa) <= c.n_pt * sqrt(sq(sp) + sq(tt.sigk));
+            }
+            kc = k != 0;
         }
-        PTOut o{};
-        bool pass = pt_eval<NT + 3>(c, P, A.pls_kappa[g], A.pls_sigk[g], kt, st,
-                                    NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3,
+        PTOut o;
+        bool pass = pt_eval<NT + 3>(c, P, kc, NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3,
                                     NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3, o);
         if (NT == 5) {
             A.pt5_valid[i] = pass; A.pt5_kappa[i] = float(o.kappa); A.pt5_chi2[i] = float(o.chi2_rphi);

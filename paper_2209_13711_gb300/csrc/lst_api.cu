@@ -144,7 +144,8 @@ static FitLimits prefit_limits(const DevCfg& d, double chi2_max, double chi2z_ma
 }
 
 static void derive_fp32(DevCfg& d) {
-    d.f = CfgF{float(d.a), float(d.z_lumi), float(d.n_md), float(d.n_ls), float(d.n_t3), float(d.sig_pix)};
+    d.f = CfgF{float(d.a),    float(d.z_lumi), float(d.n_md), float(d.n_ls),
+               float(d.n_t3), float(d.n_t5),   float(d.n_pt), float(d.sig_pix)};
     d.lim_t5 = prefit_limits(d, d.chi2_rphi_t5, d.chi2_rz_t5, d.prefit_scale);
     d.lim_pt5 = prefit_limits(d, d.chi2_rphi_pt5, d.chi2_rz_pt5, 1.0f);
     d.lim_pt3 = prefit_limits(d, d.chi2_rphi_pt3, d.chi2_rz_pt3, 1.0f);

@@ -43,7 +43,7 @@ struct FitLimits {
 // FP32 copies of the constants the FP32 predicates use, converted once on the
 // host (a double-to-float conversion per candidate would run on the FP64 pipe).
 struct CfgF {
-    float a, z_lumi, n_md, n_ls, n_t3, sig_pix;
+    float a, z_lumi, n_md, n_ls, n_t3, n_t5, n_pt, sig_pix;
 };
 
 struct DevCfg {
@@ -496,8 +496,8 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
     Fit f;
     const Pt<double>& O = P[N / 2];
     double ex = P[N - 1].x - P[0].x, ey = P[N - 1].y - P[0].y;
-    double le = hypot(ex, ey);
-    double xx = ex / le, xy = ey / le;
+    double il = 1.0 / sqrt(ex * ex + ey * ey);
+    double xx = ex * il, xy = ey * il;
     double yx = -xy, yy = xx;
     double xi[N], et[N], rho2[N];
     double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, b[3] = {0, 0, 0};
@@ -527,24 +527,26 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
     double chi2 = 0.0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
+        // geometric residual e, and the point's error projected on the circle
+        // normal; the normal is left unnormalised and the squared norm divides
+        // once: s2 = (srphi^2 n_phi^2 + sr^2 n_r^2) / |n|^2 (|n| >= ~1 here)
         double u = gg * rho2[i] + hh * xi[i] + kk - et[i];
         double e = 2.0 * u / (S + sqrt(fmax(0.0, S * S + 4.0 * gg * u)));
         double nlx = 2.0 * gg * xi[i] + hh, nly = 2.0 * gg * et[i] - 1.0;
         double nx = nlx * xx + nly * yx, ny = nlx * xy + nly * yy;
-        double nn = hypot(nx, ny);
-        nx /= nn;
-        ny /= nn;
-        double rx = P[i].x / P[i].r, ry = P[i].y / P[i].r;
+        double nn2 = nx * nx + ny * ny;
+        double ir = 1.0 / P[i].r;
+        double rx = P[i].x * ir, ry = P[i].y * ir;
         double n_phi = -nx * ry + ny * rx;
         double n_r = nx * rx + ny * ry;
-        double s2 = fmax(sq(P[i].srphi * n_phi) + sq(P[i].sr * n_r), sq(0.01 * P[i].srphi));
-        chi2 += e * e / s2;
+        double s2 = fmax(sq(P[i].srphi * n_phi) + sq(P[i].sr * n_r), sq(0.01 * P[i].srphi) * nn2);
+        chi2 += e * e * nn2 / s2;
     }
     f.chi2_rphi = chi2;
     double ka = fabs(f.kappa);
     double s[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) s[i] = arc(hypot(P[i].x - P[0].x, P[i].y - P[0].y), ka);
+    for (int i = 0; i < N; ++i) s[i] = arc(sqrt(sq(P[i].x - P[0].x) + sq(P[i].y - P[0].y)), ka);
     double t_hat = (P[N - 1].z - P[0].z) / s[N - 1];
     double w[N], W = 0, Ws = 0, Wz = 0;
 #pragma unroll
@@ -554,7 +556,8 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
         Ws += w[i] * s[i];
         Wz += w[i] * P[i].z;
     }
-    double sbar = Ws / W, zbar = Wz / W, Sss = 0, Ssz = 0;
+    const double iW = 1.0 / W;
+    double sbar = Ws * iW, zbar = Wz * iW, Sss = 0, Ssz = 0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         Sss += w[i] * sq(s[i] - sbar);
@@ -573,9 +576,6 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
     return f;
 }
 
-// FP32 twin of fit_track, used only as a conservative prefilter before the
-// FP64 fit: same frame and residual definitions, with the normal equations
-// centred (2x2 solve) for conditioning in single precision.
 // FP32 twin of fit_track (same chord-frame circle fit, geometric residuals and
 // r-z line fit), evaluated cut by cut: the curvature is tested right after the
 // circle solve, chi2_rphi after the residuals, and the r-z fit runs only for
@@ -714,33 +714,58 @@ struct T5Out {
     double kappa, chi2_rphi, chi2_rz, eta, phi0, pt, score, sigk;
 };
 
-__device__ inline bool t5_eval(const DevCfg& c, const Pt<double>* P, T5Out& o) {
-    Tri<double> ti = tri(P[0], P[1], P[2]);
-    Tri<double> to = tri(P[2], P[3], P[4]);
-    o.sigk = 0.5 * sqrt(sq(ti.sigk) + sq(to.sigk));
-    if (!(fabs(ti.kappa - to.kappa) <= c.n_t5 * sqrt(sq(ti.sigk) + sq(to.sigk)))) return false;
+// Curvature consistency |k1 - k2| <= n sqrt(s1^2 + s2^2) on FP32 inputs: 1 or
+// 0 when the FP32 values are farther from the threshold than their rounding
+// can move them (a band of 2e-3 of the threshold), -1 (undecided) otherwise.
+__device__ __forceinline__ int kappa_test_f32(float k1, float s1, float k2, float s2, float n) {
+    const float d = fabsf(k1 - k2), thr = n * sqrtf(s1 * s1 + s2 * s2);
+    const float band = 2e-3f * thr + 1e-7f;
+    if (d < thr - band) return 1;
+    if (d > thr + band) return 0;
+    return -1;
+}
+
+// T5 on anchors P[0..4]; the two triplets' curvatures (k, s) come from the T3
+// arrays (FP32) and decide the consistency test unless it is undecided, in
+// which case both triplets are recomputed in FP64. all_outputs = false skips
+// eta, phi0 and pT of a rejected candidate.
+__device__ inline bool t5_eval(const DevCfg& c, const Pt<double>* P, float k1, float s1, float k2, float s2,
+                               bool all_outputs, T5Out& o) {
+    o = T5Out{};
+    o.sigk = 0.5 * sqrt(sq(double(s1)) + sq(double(s2)));
+    int kc = kappa_test_f32(k1, s1, k2, s2, c.f.n_t5);
+    if (kc < 0) {
+        Tri<double> ti = tri(P[0], P[1], P[2]);
+        Tri<double> to = tri(P[2], P[3], P[4]);
+        o.sigk = 0.5 * sqrt(sq(ti.sigk) + sq(to.sigk));
+        kc = fabs(ti.kappa - to.kappa) <= c.n_t5 * sqrt(sq(ti.sigk) + sq(to.sigk));
+    }
+    if (!kc && !all_outputs) return false;
     Fit f = fit_track<5>(P);
     o.kappa = f.kappa;
     o.chi2_rphi = f.chi2_rphi;
     o.chi2_rz = f.chi2_rz;
-    o.eta = asinh(f.tanl);
-    o.phi0 = phi0_of(P[0], f.kappa);
-    o.pt = pt_of(c, f.kappa);
     o.score = f.chi2_rphi + f.chi2_rz;
-    if (!(fabs(f.kappa) <= (1.0 + c.tol_r) * 2.0 * c.a)) return false;
-    if (!(f.chi2_rphi <= c.chi2_rphi_t5)) return false;
-    if (!(f.chi2_rz <= c.chi2_rz_t5)) return false;
-    return true;
+    const bool pass = kc && fabs(f.kappa) <= (1.0 + c.tol_r) * 2.0 * c.a && f.chi2_rphi <= c.chi2_rphi_t5 &&
+                      f.chi2_rz <= c.chi2_rz_t5;
+    if (pass || all_outputs) {
+        o.eta = asinh(f.tanl);
+        o.phi0 = phi0_of(P[0], f.kappa);
+        o.pt = pt_of(c, f.kappa);
+    }
+    return pass;
 }
 
 struct PTOut {
     double kappa, chi2_rphi, chi2_rz, score, pt;
 };
 
+// pT5 / pT3 with the curvature-consistency verdict kc decided by the caller.
 template <int N>
-__device__ inline bool pt_eval(const DevCfg& c, const Pt<double>* P, double kp, double sp, double kt, double st,
-                               double chi2_rphi_max, double chi2_rz_max, PTOut& o) {
-    if (!(fabs(kp - kt) <= c.n_pt * sqrt(sq(sp) + sq(st)))) return false;
+__device__ inline bool pt_eval(const DevCfg& c, const Pt<double>* P, bool kc, double chi2_rphi_max,
+                               double chi2_rz_max, PTOut& o) {
+    o = PTOut{};
+    if (!kc) return false;
     Fit f = fit_track<N>(P);
     o.kappa = f.kappa;
     o.chi2_rphi = f.chi2_rphi;
