@@ -242,8 +242,10 @@ __device__ __forceinline__ float m_asin(float v) { return asinf(v); }
 __device__ __forceinline__ double m_asin(double v) { return asin(v); }
 __device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
 __device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
-__device__ __forceinline__ float m_hypot(float a, float b) { return hypotf(a, b); }
-__device__ __forceinline__ double m_hypot(double a, double b) { return hypot(a, b); }
+// Coordinates and their differences are bounded (|x| < 1e4 cm), so the
+// plain root of the sum of squares neither overflows nor underflows.
+__device__ __forceinline__ float m_hypot(float a, float b) { return sqrtf(a * a + b * b); }
+__device__ __forceinline__ double m_hypot(double a, double b) { return sqrt(a * a + b * b); }
 __device__ __forceinline__ float m_abs(float v) { return fabsf(v); }
 __device__ __forceinline__ double m_abs(double v) { return fabs(v); }
 __device__ __forceinline__ float m_max(float a, float b) { return fmaxf(a, b); }
@@ -583,7 +585,7 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
 template <int N> __device__ inline bool fit_may_pass_f32(const Pt<float>* P, const FitLimits& L) {
     const Pt<float>& O = P[N / 2];
     float ex = P[N - 1].x - P[0].x, ey = P[N - 1].y - P[0].y;
-    float il = 1.0f / hypotf(ex, ey);
+    float il = rsqrtf(ex * ex + ey * ey);
     float xx = ex * il, xy = ey * il, yx = -xy, yy = xx;
     float xi[N], et[N], rho2[N];
     float mr = 0.f, mx = 0.f, me = 0.f;
@@ -617,7 +619,7 @@ template <int N> __device__ inline bool fit_may_pass_f32(const Pt<float>* P, con
         float e = 2.f * u / (S + sqrtf(fmaxf(0.f, S * S + 4.f * gg * u)));
         float nlx = 2.f * gg * xi[i] + hh, nly = 2.f * gg * et[i] - 1.f;
         float nx = nlx * xx + nly * yx, ny = nlx * xy + nly * yy;
-        float inn = 1.0f / hypotf(nx, ny);
+        float inn = rsqrtf(nx * nx + ny * ny);
         nx *= inn; ny *= inn;
         float ir = 1.0f / P[i].r;
         float rx = P[i].x * ir, ry = P[i].y * ir;
@@ -629,7 +631,7 @@ template <int N> __device__ inline bool fit_may_pass_f32(const Pt<float>* P, con
     float ka = fabsf(kappa);
     float s[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) s[i] = arc(hypotf(P[i].x - P[0].x, P[i].y - P[0].y), ka);
+    for (int i = 0; i < N; ++i) s[i] = arc(m_hypot(P[i].x - P[0].x, P[i].y - P[0].y), ka);
     float t_hat = (P[N - 1].z - P[0].z) / s[N - 1];
     float w[N], W = 0.f, Ws = 0.f, Wz = 0.f;
 #pragma unroll
