@@ -29,7 +29,7 @@
 
 namespace lst {
 
-constexpr float kBand = 2e-3f;   // relative width of the FP32 undecided band around a threshold
+constexpr float kBand = 5e-4f;   // relative width of the FP32 undecided band around a threshold
 constexpr double kPi = 3.14159265358979323846;
 
 // Cut constants as seen by the kernels (derived on the host from lst_config).
@@ -319,11 +319,21 @@ template <typename T> __device__ __forceinline__ Pt<T> md_point(const Arena& A, 
     return q;
 }
 
-// error of P perpendicular to a chord of unit direction (cx, cy)
-template <typename T> __device__ __forceinline__ T sigma_perp(const Pt<T>& P, T cx, T cy) {
-    T rx = P.x / P.r, ry = P.y / P.r;
-    T along = cx * rx + cy * ry;
-    T across = m_abs(cx * ry - cy * rx);
+// a b - c d with one rounding (Kahan's difference of products with an FMA)
+__device__ __forceinline__ float m_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double m_fma(double a, double b, double c) { return fma(a, b, c); }
+template <typename T> __device__ __forceinline__ T diff_prod(T a, T b, T c, T d) {
+    const T w = c * d;
+    return m_fma(a, b, -w) + m_fma(-c, d, w);
+}
+
+// error of P perpendicular to a chord of unit direction (cx, cy); across =
+// |chord x r-hat|, passed in because it is computed from the exact
+// coordinates of the chord's end points (|A x B| / (|AB| r_P)): for a chord
+// nearly parallel to r-hat the rounded unit vectors would lose it
+template <typename T> __device__ __forceinline__ T sigma_perp(const Pt<T>& P, T cx, T cy, T across) {
+    T ir = T(1) / P.r;
+    T along = (cx * P.x + cy * P.y) * ir;
     return m_sqrt(sq(P.srphi * along) + sq(P.sr * across));
 }
 
@@ -374,14 +384,15 @@ __device__ __forceinline__ int ls_eval(const DevCfg& c, const Pt<T>& P, T sAx, T
     T den = Q.r - P.r;
     T sig_num = m_sqrt(sq(Q.r * P.sz) + sq(P.r * Q.sz) + sq(Q.z * P.sr) + sq(P.z * Q.sr));
     cut(m_abs(num), cval<T>(c.z_lumi, c.f.z_lumi) * m_abs(den) + n * sig_num);
-    T dphi = m_atan2(P.x * Q.y - P.y * Q.x, P.x * Q.x + P.y * Q.y);
+    // P x Q as P x (Q - P): products of the anchor with the short segment
+    T ux = Q.x - P.x, uy = Q.y - P.y;
+    T dphi = m_atan2(P.x * uy - P.y * ux, P.x * Q.x + P.y * Q.y);
     dphi_o = dphi;
     if (cut.fail) return 0;
     T lo = asinc(m_max(T(0), P.r - n * P.sr) * a);
     T thr_phi = asinc((Q.r + n * Q.sr) * a) - lo + n * m_sqrt(sq(P.srphi / P.r) + sq(Q.srphi / Q.r));
     cut(m_abs(dphi), thr_phi);
     if (cut.fail) return 0;
-    T ux = Q.x - P.x, uy = Q.y - P.y;
     T lu = m_hypot(ux, uy);
     T base = asinc((Q.r + T(mB.x) + n * Q.sr) * a) - lo;
     T rt2 = T(1.4142135623730951);
@@ -416,10 +427,12 @@ template <typename T> __device__ __forceinline__ Tri<T> tri(const Pt<T>& A, cons
     t.lw = m_hypot(wx, wy);
     t.beta = m_atan2(ux * vy - uy * vx, ux * vx + uy * vy);
     T iu = T(1) / t.lu, iv = T(1) / t.lv;
-    T sAu = sigma_perp(A, ux * iu, uy * iu);
-    T sBu = sigma_perp(B, ux * iu, uy * iu);
-    T sBv = sigma_perp(B, vx * iv, vy * iv);
-    T sCv = sigma_perp(C, vx * iv, vy * iv);
+    const T xAB = m_abs(diff_prod(A.x, B.y, A.y, B.x)) * iu;   // |A x B| / |AB|
+    const T xBC = m_abs(diff_prod(B.x, C.y, B.y, C.x)) * iv;
+    T sAu = sigma_perp(A, ux * iu, uy * iu, xAB / A.r);
+    T sBu = sigma_perp(B, ux * iu, uy * iu, xAB / B.r);
+    T sBv = sigma_perp(B, vx * iv, vy * iv, xBC / B.r);
+    T sCv = sigma_perp(C, vx * iv, vy * iv, xBC / C.r);
     t.sig_beta = m_sqrt(sq(sAu * iu) + sq(sBu * iu + sBv * iv) + sq(sCv * iv));
     t.kappa = T(2) * (ux * wy - uy * wx) / (t.lu * t.lv * t.lw);
     t.sigk = T(2) * t.sig_beta / (t.lu + t.lv);

@@ -45,9 +45,10 @@ def test_pileup_event_parity(ctx_full, geom_full, maps_full, pu, seed):
     compare(g, o, A_HALF, DEFAULT_CUTS)
 
 
-def test_pu200_event_parity(ctx_full, geom_full, maps_full):
-    """Full-size PU200 event (the benchmark's workload), every object level."""
-    ev = E.pu200_event(0, geom_full)
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_pu200_event_parity(ctx_full, geom_full, maps_full, seed):
+    """Full-size PU200 events (the benchmark's workload), every object level."""
+    ev = E.pu200_event(seed, geom_full)
     ctx_full.run([ev])
     g = gpu_result(ctx_full)
     _no_drops(g)
