@@ -116,6 +116,33 @@ def whole_job_rate(ws, steps, seconds):
     return ws * steps / seconds
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when there is none or the kernel's sources changed since it was taken."""
+    import glob
+    import hashlib
+    for fn in sorted(glob.glob(os.path.join(ROOT, "profiles", "*_traffic.md"))):
+        kv = {}
+        with open(fn) as f:
+            for line in f:
+                if ":" in line and not line.startswith(("|", "#", "`")):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel") != kernel or "dram_bytes_per_launch" not in kv:
+            continue
+        h = hashlib.sha256()
+        try:
+            for src in kv.get("sources", "").split():
+                with open(os.path.join(ROOT, src), "rb") as f:
+                    h.update(f.read())
+        except OSError:
+            return None
+        if h.hexdigest() != kv.get("sources_sha256"):
+            return None
+        return int(kv["dram_bytes_per_launch"])
+    return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -235,7 +262,7 @@ def run_ours(args):
     if b_alg is not None:
         achieved = b_alg / (kavg[top] / 1e3) / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 5), "traffic": None, "peak_source": peak_kind,
+                "frac": round(achieved / hbm_peak, 5), "traffic": measured_traffic(top), "peak_source": peak_kind,
                 "algorithmic_bytes": int(b_alg), "kernel_ms": round(kavg[top], 4)}
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,

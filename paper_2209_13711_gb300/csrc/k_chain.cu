@@ -253,6 +253,27 @@ __global__ void __launch_bounds__(kMdWarps * 32) k_md(Arena A, DevCfg c) {
     }
 }
 
+// FP64 re-tests of candidates the FP32 predicates left undecided. Out of line,
+// so that no double-precision work is scheduled on the FP32 path (the FP64
+// pipe is narrow on this GPU); a warp pays for one only when a lane needs it.
+__device__ __noinline__ int md_retest(const DevCfg& c, float4 mi, float lx, float ly, float lz, float ux, float uy,
+                                      float uz) {
+    Pt<double> L = hit_pt<double>(lx, ly, lz, mi), U = hit_pt<double>(ux, uy, uz, mi);
+    double dp, dl;
+    return md_eval<double>(c, mi, L, U, dp, dl);
+}
+
+__device__ __noinline__ int ls_retest(const Arena& A, const DevCfg& c, int i, int B, float4 miA, float4 miB) {
+    double dp;
+    return ls_eval<double>(c, md_point<double>(A, i), double(A.md_dx[i]), double(A.md_dy[i]), miA,
+                           md_point<double>(A, B), double(A.md_dx[B]), double(A.md_dy[B]), miB, dp);
+}
+
+__device__ __noinline__ int t3_retest(const Arena& A, const DevCfg& c, int i, int B, int C) {
+    double b, k, r, s;
+    return t3_eval<double>(c, md_point<double>(A, i), md_point<double>(A, B), md_point<double>(A, C), b, k, r, s);
+}
+
 // ---------------------------------------------------------------------------
 // MD as work items (the chain's path; k_md above serves the allocation-free
 // entry point). k_bin_sort puts every sensor bucket in original-index order,
@@ -365,12 +386,7 @@ __device__ __forceinline__ void md_enumerate(const DevCfg& c, const MdSearchSmem
             Pt<float> U = hit_pt<float>(S.ux[k], S.uy[k], S.uz[k], mi);
             float dp, dl;
             int st = md_eval<float>(c, mi, L, U, dp, dl);
-            if (st == 2) {
-                Pt<double> Ld = hit_pt<double>(S.lx[l], S.ly[l], S.lz[l], mi);
-                Pt<double> Ud = hit_pt<double>(S.ux[k], S.uy[k], S.uz[k], mi);
-                double dpd, dld;
-                st = md_eval<double>(c, mi, Ld, Ud, dpd, dld);
-            }
+            if (st == 2) st = md_retest(c, mi, S.lx[l], S.ly[l], S.lz[l], S.ux[k], S.uy[k], S.uz[k]);
             pass = st == 1;
         }
         int tot;
@@ -502,7 +518,6 @@ struct LsSmem {
 };
 
 __device__ __forceinline__ Pt<float> md_pt_f(const Arena& A, int i, float4) { return md_point<float>(A, i); }
-__device__ __forceinline__ Pt<double> md_pt_d(const Arena& A, int i, float4) { return md_point<double>(A, i); }
 __device__ __forceinline__ float4 md_mod(const Arena& A, int i) {
     int gm = A.md_gmod[i];
     return A.mod[gm % A.n_mod];
@@ -538,11 +553,7 @@ __global__ void __launch_bounds__(kLsWarps * 32, 3) k_ls(Arena A, DevCfg c) {
                     Pt<float> Q = md_pt_f(A, B, miB);
                     float dp;
                     int st = ls_eval<float>(c, P, sAx, sAy, miA, Q, A.md_dx[B], A.md_dy[B], miB, dp);
-                    if (st == 2) {
-                        double dpd;
-                        st = ls_eval<double>(c, md_pt_d(A, i, miA), double(sAx), double(sAy), miA, md_pt_d(A, B, miB),
-                                             double(A.md_dx[B]), double(A.md_dy[B]), miB, dpd);
-                    }
+                    if (st == 2) st = ls_retest(A, c, i, B, miA, miB);
                     pass = st == 1;
                 }
                 int tot;
@@ -614,11 +625,7 @@ __global__ void __launch_bounds__(kT3Warps * 32, 3) k_t3(Arena A, DevCfg c) {
                     float4 miB = md_mod(A, B_), miC = md_mod(A, C_);
                     float beta, kap, rz, sk;
                     int st = t3_eval<float>(c, PA, md_pt_f(A, B_, miB), md_pt_f(A, C_, miC), beta, kap, rz, sk);
-                    if (st == 2) {
-                        double bd, kd, rd, sd;
-                        st = t3_eval<double>(c, md_pt_d(A, i, miA), md_pt_d(A, B_, miB), md_pt_d(A, C_, miC), bd, kd,
-                                             rd, sd);
-                    }
+                    if (st == 2) st = t3_retest(A, c, i, B_, C_);
                     pass = st == 1;
                 }
                 int tot;
