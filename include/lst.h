@@ -260,7 +260,7 @@ lst_status lst_get_kernel_times(lst_ctx* ctx, int32_t capacity, int32_t* n_out, 
  * not pay for an allocation. It runs the hit binning and mini-doublet kernels
  * of lst_run_batch on one event and allocates nothing: its scratch (bucket
  * counters, sorted hits, module table in device layout, MD anchors) lives in
- * one file-scope device array of about 8.3 MB that every device loading the
+ * one file-scope device array of about 9 MB that every device loading the
  * library keeps until the process exits.
  *   All pointers except cfg are DEVICE memory owned by the caller: modules
  *   (n_mod rows), the event's hits (x, y, z, module, side; n_hits), and the

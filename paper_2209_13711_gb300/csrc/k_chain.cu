@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kMdWarps * 32) k_md(Arena A, DevCfg c) {
             A.md_up[o] = S.ui[k];
             A.md_gmod[o] = u;
             A.md_p4[o] = make_float4(S.lx[l], S.ly[l], S.lz[l], mi.w < 0.5f ? mi.z : -mi.z);
-            A.md_srp[o] = mi.y;
+            A.md_sr[o] = make_float2(mi.y, m_hypot(S.lx[l], S.ly[l]));
             A.md_dx[o] = S.ux[k] - S.lx[l];
             A.md_dy[o] = S.uy[k] - S.ly[l];
             A.md_dphi[o] = dp;
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(128) k_md_write(Arena A, DevCfg c) {
                 A.md_up[t] = A.sidx[code.y];
                 A.md_gmod[t] = u;
                 A.md_p4[t] = make_float4(lx, ly, lz, mi.w < 0.5f ? mi.z : -mi.z);
-                A.md_srp[t] = mi.y;
+                A.md_sr[t] = make_float2(mi.y, m_hypot(lx, ly));
                 A.md_dx[t] = ux - lx;
                 A.md_dy[t] = uy - ly;
                 A.md_dphi[t] = dp;
@@ -645,12 +645,9 @@ __global__ void __launch_bounds__(kT3Warps * 32, 3) k_t3(Arena A, DevCfg c) {
             int o = base + k;
             A.t3_lsin[o] = pr.x;
             A.t3_lsout[o] = pr.y;
-            A.t3_m0[o] = i;
-            A.t3_m1[o] = B_;
-            A.t3_m2[o] = C_;
+            A.t3_md[o] = make_int4(i, B_, C_, 0);
             A.t3_beta[o] = beta;
-            A.t3_kappa[o] = kap;
-            A.t3_sigk[o] = sk;
+            A.t3_ks[o] = make_float2(kap, sk);
         }
         if (lane == 0) {
             A.t3_off[i] = base;
@@ -669,16 +666,18 @@ __global__ void __launch_bounds__(kT3Warps * 32, 3) k_t3(Arena A, DevCfg c) {
 // ---------------------------------------------------------------------------
 struct T5Smem {
     int pre[32], off[32], t1[32];
+    float2 ks1[32];            // curvature and sigma of each lane's T3_1
     int2 cand[kT5Pre];
     int2 stage[kT5Stage];      // passing (T3_1, T3_2)
 };
 
 __device__ __forceinline__ void t5_mds(const Arena& A, int2 pr, int* m) {
-    m[0] = A.t3_m0[pr.x];
-    m[1] = A.t3_m1[pr.x];
-    m[2] = A.t3_m2[pr.x];
-    m[3] = A.t3_m1[pr.y];
-    m[4] = A.t3_m2[pr.y];
+    const int4 a = A.t3_md[pr.x], b = A.t3_md[pr.y];
+    m[0] = a.x;
+    m[1] = a.y;
+    m[2] = a.z;
+    m[3] = b.y;
+    m[4] = b.z;
 }
 
 __device__ __forceinline__ bool t5_prefit_f32(const Arena& A, const DevCfg& c, int2 pr) {
@@ -724,19 +723,23 @@ __device__ __forceinline__ void t5_enumerate(const Arena& A, const DevCfg& c, Sm
     for (int cb = t_begin; cb < t_end; cb += 32) {
         int t1 = cb + lane;
         int off = 0, len = 0;
+        float2 ks = make_float2(0.f, 0.f);
         if (t1 < t_end) {
-            int C_ = A.t3_m2[t1];
+            int C_ = A.t3_md[t1].z;
             off = A.t3_off[C_];
             len = A.t3_cnt[C_];
+            ks = A.t3_ks[t1];
         }
         S.t1[lane] = t1;
+        S.ks1[lane] = ks;
         for_each_flat(off, len, S.pre, S.off, [&](bool valid, int seg, int t2) {
             bool pass = false;
             int t1_ = 0;
             if (valid) {
                 t1_ = S.t1[seg];
-                float k1 = A.t3_kappa[t1_], k2 = A.t3_kappa[t2];
-                float s1_ = A.t3_sigk[t1_], s2_ = A.t3_sigk[t2];
+                const float2 a = S.ks1[seg], b = A.t3_ks[t2];
+                float k1 = a.x, k2 = b.x;
+                float s1_ = a.y, s2_ = b.y;
                 float thr = nk * sqrtf(s1_ * s1_ + s2_ * s2_);
                 // slack covers the FP32 rounding of the stored curvatures
                 pass = fabsf(k1 - k2) <= thr * 1.01f + 1e-5f * (fabsf(k1) + fabsf(k2)) + 1e-7f;
@@ -793,7 +796,7 @@ __global__ void __launch_bounds__(kT5Warps * 32, 6) k_t5(Arena A, DevCfg c) {
         k = __shfl_sync(kFull, k, 0);
         if (k >= n_items) break;
         const int t0 = k < n_front ? A.t5_items[k] : A.t5_items[A.t3_cap - 1 - (k - n_front)];
-        const int i = A.t3_m0[t0];
+        const int i = A.t3_md[t0].x;
         const int t_end = min(t0 + kT5Chunk, A.t3_off[i] + A.t3_cnt[i]);
         int cnt = 0;
         auto stage_sink = [&](bool keep, int2 pr, int r, int tot) {
@@ -876,8 +879,8 @@ __global__ void k_t5_refine(Arena A, DevCfg c) {
 #pragma unroll
         for (int j = 0; j < 5; ++j) P[j] = md_point<double>(A, m[j]);
         T5Out o;
-        bool pass = t5_eval(c, P, A.t3_kappa[pr.x], A.t3_sigk[pr.x], A.t3_kappa[pr.y], A.t3_sigk[pr.y],
-                            c.use_mlp != 0, o);
+        const float2 ka = A.t3_ks[pr.x], kb = A.t3_ks[pr.y];
+        bool pass = t5_eval(c, P, ka.x, ka.y, kb.x, kb.y, c.use_mlp != 0, o);
         const int e = A.md_gmod[m[0]] / A.n_mod;
         A.t5_cut[i] = pass;
         A.t5_kappa[i] = o.kappa;

@@ -64,9 +64,11 @@ template <int NT>
 __device__ __forceinline__ void pt_mds(const Arena& A, int obj, int* m) {
     if (NT == 5) {
         int a = A.t5_in[obj], b = A.t5_out[obj];
-        m[0] = A.t3_m0[a]; m[1] = A.t3_m1[a]; m[2] = A.t3_m2[a]; m[3] = A.t3_m1[b]; m[4] = A.t3_m2[b];
+        const int4 ta = A.t3_md[a], tb = A.t3_md[b];
+        m[0] = ta.x; m[1] = ta.y; m[2] = ta.z; m[3] = tb.y; m[4] = tb.z;
     } else {
-        m[0] = A.t3_m0[obj]; m[1] = A.t3_m1[obj]; m[2] = A.t3_m2[obj];
+        const int4 t = A.t3_md[obj];
+        m[0] = t.x; m[1] = t.y; m[2] = t.z;
     }
 }
 
@@ -132,8 +134,15 @@ __device__ __forceinline__ void pt_enumerate(const Arena& A, const DevCfg& c, Pt
         for_each_flat(oo, on, S.pre2, S.off2, [&](bool valid, int, int obj) {
             bool pass = false;
             if (valid && (NT == 3 || A.t5_valid[obj])) {
-                float kt = NT == 5 ? float(A.t5_kappa[obj]) : A.t3_kappa[obj];
-                float st = NT == 5 ? float(A.t5_sigk[obj]) : A.t3_sigk[obj];
+                float kt, st;
+                if (NT == 5) {
+                    kt = float(A.t5_kappa[obj]);
+                    st = float(A.t5_sigk[obj]);
+                } else {
+                    const float2 ks = A.t3_ks[obj];
+                    kt = ks.x;
+                    st = ks.y;
+                }
                 float thr = nk * sqrtf(sp * sp + st * st);
                 pass = fabsf(kp - kt) <= thr * 1.01f + 1e-5f * (fabsf(kp) + fabsf(kt)) + 1e-7f;
             }
@@ -246,7 +255,8 @@ template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const
             kc = fabs(kp - A.t5_kappa[obj]) <= c.n_pt * sqrt(sq(sp) + sq(A.t5_sigk[obj]));
         } else {
             // the triplet's FP32 curvature decides unless undecided; then FP64
-            int k = kappa_test_f32(float(kp), float(sp), A.t3_kappa[obj], A.t3_sigk[obj], c.f.n_pt);
+            const float2 ks = A.t3_ks[obj];
+            int k = kappa_test_f32(float(kp), float(sp), ks.x, ks.y, c.f.n_pt);
             if (k < 0) {
                 Tri<double> tt = tri(P[3], P[4], P[5]);
                 k = fabs(kp - tt.kappa) <= c.n_pt * sqrt(sq(sp) + sq(tt.sigk));

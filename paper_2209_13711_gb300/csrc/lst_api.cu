@@ -300,7 +300,7 @@ static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n
     const size_t MD = E * K.md_per_event;
     A.md_cap = (int)MD;
     A.md_lo = b.take<int>(MD); A.md_up = b.take<int>(MD); A.md_gmod = b.take<int>(MD);
-    A.md_p4 = b.take<float4>(MD); A.md_srp = b.take<float>(MD);
+    A.md_p4 = b.take<float4>(MD); A.md_sr = b.take<float2>(MD);
     A.md_dx = b.take<float>(MD); A.md_dy = b.take<float>(MD);
     A.md_dphi = b.take<float>(MD); A.md_dlong = b.take<float>(MD);
     A.md_moff = b.take<int>(E * n_mod); A.md_mcnt = b.take<int>(E * n_mod);
@@ -315,8 +315,8 @@ static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n
     const size_t T3 = E * K.t3_per_event;
     A.t3_cap = (int)T3;
     A.t3_lsin = b.take<int>(T3); A.t3_lsout = b.take<int>(T3);
-    A.t3_beta = b.take<float>(T3); A.t3_kappa = b.take<float>(T3); A.t3_sigk = b.take<float>(T3);
-    A.t3_m0 = b.take<int>(T3); A.t3_m1 = b.take<int>(T3); A.t3_m2 = b.take<int>(T3);
+    A.t3_beta = b.take<float>(T3); A.t3_ks = b.take<float2>(T3);
+    A.t3_md = b.take<int4>(T3);
     A.t3_off = b.take<int>(MD); A.t3_cnt = b.take<int>(MD);
     const size_t T5 = E * K.t5_per_event;
     A.t5_cap = (int)T5;
@@ -883,8 +883,14 @@ lst_status lst_get_t5_candidates(lst_ctx* c, int32_t event, int32_t capacity, in
     const int n_md = std::min(cnt[0], A.md_cap), n_t3 = std::min(cnt[2], A.t3_cap);
     std::vector<int> ti, to, m0, m1, m2, gm, lo, up;
     std::vector<uint8_t> cp;
+    std::vector<int4> t3md;
     FETCH(ti, A.t5_in, n); FETCH(to, A.t5_out, n); FETCH(cp, A.t5_cut, n);
-    FETCH(m0, A.t3_m0, n_t3); FETCH(m1, A.t3_m1, n_t3); FETCH(m2, A.t3_m2, n_t3);
+    FETCH(t3md, A.t3_md, n_t3);
+    for (const int4& q : t3md) {
+        m0.push_back(q.x);
+        m1.push_back(q.y);
+        m2.push_back(q.z);
+    }
     FETCH(gm, A.md_gmod, n_md); FETCH(lo, A.md_lo, n_md); FETCH(up, A.md_up, n_md);
     std::vector<int> rows;
     for (int i = 0; i < n; ++i)
@@ -1048,12 +1054,13 @@ lst_status lst_get_objects(lst_ctx* c, int32_t event, int32_t kind, int32_t capa
             if (ls_row[t3i[i]] >= 0) t3_row[i] = r++;
     }
     if (kind == 2) {
-        std::vector<float> b, k, sk;
-        FETCH(b, A.t3_beta, n_t3); FETCH(k, A.t3_kappa, n_t3); FETCH(sk, A.t3_sigk, n_t3);
+        std::vector<float> b;
+        std::vector<float2> ks;
+        FETCH(b, A.t3_beta, n_t3); FETCH(ks, A.t3_ks, n_t3);
         for (int i = 0; i < n_t3; ++i)
             if (t3_row[i] >= 0) {
                 iv.insert(iv.end(), {ls_row[t3i[i]], ls_row[t3o[i]]});
-                fv.insert(fv.end(), {b[i], k[i], sk[i]});
+                fv.insert(fv.end(), {b[i], ks[i].x, ks[i].y});
             }
     }
     std::vector<int> t5i, t5o;

@@ -113,7 +113,7 @@ struct Arena {
     int* md_up;
     int* md_gmod;                 // e * n_mod + module
     float4* md_p4;                // anchor (lower hit) x, y, z and +sig_z (barrel) / -sig_r (endcap)
-    float* md_srp;                // anchor r-phi resolution
+    float2* md_sr;                // anchor {r-phi resolution, r = sqrtf(x^2 + y^2)}
     float* md_dx;
     float* md_dy;
     float* md_dphi;
@@ -138,11 +138,8 @@ struct Arena {
     int* t3_lsin;
     int* t3_lsout;
     float* t3_beta;
-    float* t3_kappa;
-    float* t3_sigk;
-    int* t3_m0;                   // the three MDs (inner, middle, outer)
-    int* t3_m1;
-    int* t3_m2;
+    float2* t3_ks;                // {curvature, its sigma} (FP32)
+    int4* t3_md;                  // the three MDs {inner, middle, outer, 0}
     int* t3_off;                  // [md_cap] by inner MD
     int* t3_cnt;
     // T5
@@ -311,9 +308,11 @@ template <typename T, typename S> __device__ __forceinline__ Pt<T> pix_pt(const 
 template <typename T> __device__ __forceinline__ Pt<T> md_point(const Arena& A, int i) {
     float4 p = A.md_p4[i];
     Pt<T> q;
+    const float2 sr = A.md_sr[i];
     q.x = T(p.x); q.y = T(p.y); q.z = T(p.z);
-    q.r = m_hypot(q.x, q.y);
-    q.srphi = T(A.md_srp[i]);
+    // FP32: the radius stored with the MD (the same sqrtf value); FP64: recomputed
+    q.r = sizeof(T) == 4 ? T(sr.y) : m_hypot(q.x, q.y);
+    q.srphi = T(sr.x);
     q.sz = p.w > 0.f ? T(p.w) : T(0);
     q.sr = p.w > 0.f ? T(0) : T(-p.w);
     return q;

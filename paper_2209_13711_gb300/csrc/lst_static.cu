@@ -11,7 +11,7 @@
 // caller passes device inputs and device outputs; nothing is allocated.
 //
 // Limits: 262144 hits, 16384 modules, 131072 mini-doublets per call; the
-// array holds about 8.3 MB on every device that loads the library, until the
+// array holds about 9 MB on every device that loads the library, until the
 // process exits. Every call reuses the same array: calls that overlap on the
 // GPU (two streams, two host threads) race on it and must be serialized by
 // the caller.
@@ -47,7 +47,7 @@ struct alignas(256) MdScratch {
     int md_moff[kStaticMaxModules];
     int md_mcnt[kStaticMaxModules];
     float4 md_p4[kStaticMaxMd];
-    float md_srp[kStaticMaxMd];
+    float2 md_sr[kStaticMaxMd];
     float md_dx[kStaticMaxMd];
     float md_dy[kStaticMaxMd];
 };
@@ -160,7 +160,7 @@ extern "C" lst_status lst_build_mini_doublets_static(const lst_config* cfg, cons
     A.md_up = md_upper;
     A.md_gmod = md_module;          // one event: the unit index is the module id
     A.md_p4 = S->md_p4;
-    A.md_srp = S->md_srp;
+    A.md_sr = S->md_sr;
     A.md_dx = S->md_dx;
     A.md_dy = S->md_dy;
     A.md_dphi = md_dphi;
