@@ -56,47 +56,53 @@ __global__ void k_bin_count(Arena A) {
 }
 
 // One block per event: exclusive scan of the event's bucket counts into boff;
-// the counts are turned into scatter cursors (= offsets).
+// the counts are turned into scatter cursors (= offsets). Each warp owns a
+// contiguous slice of the buckets: it sums the slice (coalesced), the block
+// scans the 32 slice totals, then every warp scans its slice 32 buckets at a
+// time with shuffles and writes offsets and cursors.
 __global__ void __launch_bounds__(1024) k_bin_scan(Arena A) {
     const int nb = 2 * A.n_mod;
     const int e = blockIdx.x;
     if (e >= A.bd->n_ev) return;
     int* cnt = A.bcnt + (size_t)e * nb;
     int* off = A.boff + (size_t)e * (nb + 1);
-    __shared__ int warp_sums[32];
-    const int per = (nb + blockDim.x - 1) / blockDim.x;
-    const int b0 = threadIdx.x * per;
-    const int b1 = min(nb, b0 + per);
-    int local = 0;
-    for (int b = b0; b < b1; ++b) local += cnt[b];
-    // block exclusive scan of `local`
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int incl = local;
-    for (int d = 1; d < 32; d <<= 1) {
-        int v = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += v;
-    }
-    if (lane == 31) warp_sums[w] = incl;
+    __shared__ int warp_base[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int per = (nb + nw - 1) / nw;
+    const int b0 = min(nb, w * per), b1 = min(nb, b0 + per);
+    int sum = 0;
+    for (int b = b0 + lane; b < b1; b += 32) sum += cnt[b];
+#pragma unroll
+    for (int d = 16; d; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    if (lane == 0) warp_base[w] = sum;
     __syncthreads();
     if (w == 0) {
-        int nw = (blockDim.x + 31) / 32;
-        int v = lane < nw ? warp_sums[lane] : 0;
-        int inc2 = v;
+        int v = lane < nw ? warp_base[lane] : 0, incl = v;
+#pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, inc2, d);
-            if (lane >= d) inc2 += u;
+            int u = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += u;
         }
-        if (lane < nw) warp_sums[lane] = inc2 - v;
+        if (lane < nw) warp_base[lane] = incl - v;
+        if (lane == nw - 1) off[nb] = incl;
     }
     __syncthreads();
-    int run = warp_sums[w] + incl - local;
-    for (int b = b0; b < b1; ++b) {
-        int c = cnt[b];
-        off[b] = run;
-        cnt[b] = run;           // cursor
-        run += c;
+    int run = warp_base[w];
+    for (int base = b0; base < b1; base += 32) {
+        const int b = base + lane;
+        const int c = b < b1 ? cnt[b] : 0;
+        int incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += u;
+        }
+        if (b < b1) {
+            off[b] = run + incl - c;
+            cnt[b] = run + incl - c;      // cursor
+        }
+        run += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (threadIdx.x == blockDim.x - 1) off[nb] = run;
 }
 
 __global__ void k_bin_scatter(Arena A) {
@@ -876,11 +882,15 @@ __global__ void k_t5_refine(Arena A, DevCfg c) {
         const int2 pr = make_int2(A.t5_in[i], A.t5_out[i]);
         t5_mds(A, pr, m);
         Pt<double> P[5];
+        Pt<float> Pf[5];
 #pragma unroll
-        for (int j = 0; j < 5; ++j) P[j] = md_point<double>(A, m[j]);
+        for (int j = 0; j < 5; ++j) {
+            P[j] = md_point<double>(A, m[j]);
+            Pf[j] = md_point<float>(A, m[j]);
+        }
         T5Out o;
         const float2 ka = A.t3_ks[pr.x], kb = A.t3_ks[pr.y];
-        bool pass = t5_eval(c, P, ka.x, ka.y, kb.x, kb.y, c.use_mlp != 0, o);
+        bool pass = t5_eval(c, P, Pf, ka.x, ka.y, kb.x, kb.y, c.use_mlp != 0, o);
         const int e = A.md_gmod[m[0]] / A.n_mod;
         A.t5_cut[i] = pass;
         A.t5_kappa[i] = o.kappa;

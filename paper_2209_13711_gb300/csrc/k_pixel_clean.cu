@@ -242,13 +242,20 @@ template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const
         const int g = NT == 5 ? A.pt5_seed[i] : A.pt3_seed[i];
         const int obj = NT == 5 ? A.pt5_obj[i] : A.pt3_obj[i];
         Pt<double> P[NT + 3];
+        Pt<float> Pf[NT + 3];
         const float* sd = A.bd->seeds + 9 * (size_t)g;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) P[j] = pix_pt<double>(sd + 3 * j, c.sig_pix);
+        for (int j = 0; j < 3; ++j) {
+            P[j] = pix_pt<double>(sd + 3 * j, c.sig_pix);
+            Pf[j] = pix_pt<float>(sd + 3 * j, c.f.sig_pix);
+        }
         int m[NT];
         pt_mds<NT>(A, obj, m);
 #pragma unroll
-        for (int j = 0; j < NT; ++j) P[3 + j] = md_point<double>(A, m[j]);
+        for (int j = 0; j < NT; ++j) {
+            P[3 + j] = md_point<double>(A, m[j]);
+            Pf[3 + j] = md_point<float>(A, m[j]);
+        }
         const double kp = A.pls_kappa[g], sp = A.pls_sigk[g];
         bool kc;
         if (NT == 5) {
@@ -264,7 +271,7 @@ template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const
             kc = k != 0;
         }
         PTOut o;
-        bool pass = pt_eval<NT + 3>(c, P, kc, NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3,
+        bool pass = pt_eval<NT + 3>(c, P, Pf, kc, NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3,
                                     NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3, o);
         if (NT == 5) {
             A.pt5_valid[i] = pass; A.pt5_kappa[i] = float(o.kappa); A.pt5_chi2[i] = float(o.chi2_rphi);

@@ -506,7 +506,13 @@ struct FitFull {
     double gg, hh, kk, S, xx, xy, ox, oy, c0, t, t_hat, kappa, chi2, chi2z;
 };
 
-template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* full = nullptr) {
+// Pf (optional) holds the same points in FP32. With it, the quantities that
+// are well conditioned given the FP64 residual u -- the geometric residual e
+// from u, the circle normal, the error projected on it and the r-z weights --
+// are computed in FP32 (relative error ~1e-7 of chi2); the fit itself, the
+// residuals and the arc lengths stay FP64. Without it everything is FP64.
+template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* full = nullptr,
+                                                 const Pt<float>* Pf = nullptr) {
     Fit f;
     const Pt<double>& O = P[N / 2];
     double ex = P[N - 1].x - P[0].x, ey = P[N - 1].y - P[0].y;
@@ -539,6 +545,38 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
     double S = sqrt(fmax(0.0, 1.0 + hh * hh - 4.0 * gg * kk));
     f.kappa = 2.0 * gg / S;
     double chi2 = 0.0;
+    if (Pf) {
+        const float gf = float(gg), hf = float(hh), Sf = float(S), xxf = float(xx), xyf = float(xy);
+        const float oxf = Pf[N / 2].x, oyf = Pf[N / 2].y;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const float uf = float(gg * rho2[i] + hh * xi[i] + kk - et[i]);
+            const float e = 2.f * uf / (Sf + sqrtf(fmaxf(0.f, Sf * Sf + 4.f * gf * uf)));
+            const float dxf = Pf[i].x - oxf, dyf = Pf[i].y - oyf;
+            const float xif = dxf * xxf + dyf * xyf, etf = dyf * xxf - dxf * xyf;
+            if (Pf[i].sr > 0.f) {
+                // endcap strip: sr >> srphi, so the radial component of the
+                // normal (small, from a cancelling dot product) needs FP64
+                const double nlx = 2.0 * gg * xi[i] + hh, nly = 2.0 * gg * et[i] - 1.0;
+                const double nx = nlx * xx - nly * xy, ny = nlx * xy + nly * xx;
+                const double nn2 = nx * nx + ny * ny;
+                const double ir = 1.0 / P[i].r;
+                const double rx = P[i].x * ir, ry = P[i].y * ir;
+                const double n_phi = ny * rx - nx * ry, n_r = nx * rx + ny * ry;
+                const double s2 = fmax(sq(P[i].srphi * n_phi) + sq(P[i].sr * n_r), sq(0.01 * P[i].srphi) * nn2);
+                chi2 += double(e) * double(e) * nn2 / s2;
+                continue;
+            }
+            const float nlx = 2.f * gf * xif + hf, nly = 2.f * gf * etf - 1.f;
+            const float nx = nlx * xxf - nly * xyf, ny = nlx * xyf + nly * xxf;
+            const float nn2 = nx * nx + ny * ny;
+            const float ir = 1.f / Pf[i].r;
+            const float rx = Pf[i].x * ir, ry = Pf[i].y * ir;
+            const float n_phi = ny * rx - nx * ry;
+            const float s2 = fmaxf(sq(Pf[i].srphi * n_phi), sq(0.01f * Pf[i].srphi) * nn2);
+            chi2 += double(e * e * nn2 / s2);
+        }
+    } else {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         // geometric residual e, and the point's error projected on the circle
@@ -556,6 +594,7 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
         double s2 = fmax(sq(P[i].srphi * n_phi) + sq(P[i].sr * n_r), sq(0.01 * P[i].srphi) * nn2);
         chi2 += e * e * nn2 / s2;
     }
+    }
     f.chi2_rphi = chi2;
     double ka = fabs(f.kappa);
     double s[N];
@@ -564,8 +603,10 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
     double t_hat = (P[N - 1].z - P[0].z) / s[N - 1];
     double w[N], W = 0, Ws = 0, Wz = 0;
 #pragma unroll
+    const float tf = float(t_hat);
     for (int i = 0; i < N; ++i) {
-        w[i] = 1.0 / fmax(1e-12, sq(P[i].sz) + sq(t_hat * P[i].sr));
+        w[i] = Pf ? double(1.f / fmaxf(1e-12f, sq(Pf[i].sz) + sq(tf * Pf[i].sr)))
+                  : 1.0 / fmax(1e-12, sq(P[i].sz) + sq(t_hat * P[i].sr));
         W += w[i];
         Ws += w[i] * s[i];
         Wz += w[i] * P[i].z;
@@ -743,8 +784,8 @@ __device__ __forceinline__ int kappa_test_f32(float k1, float s1, float k2, floa
 // arrays (FP32) and decide the consistency test unless it is undecided, in
 // which case both triplets are recomputed in FP64. all_outputs = false skips
 // eta, phi0 and pT of a rejected candidate.
-__device__ inline bool t5_eval(const DevCfg& c, const Pt<double>* P, float k1, float s1, float k2, float s2,
-                               bool all_outputs, T5Out& o) {
+__device__ inline bool t5_eval(const DevCfg& c, const Pt<double>* P, const Pt<float>* Pf, float k1, float s1,
+                               float k2, float s2, bool all_outputs, T5Out& o) {
     o = T5Out{};
     o.sigk = 0.5 * sqrt(sq(double(s1)) + sq(double(s2)));
     int kc = kappa_test_f32(k1, s1, k2, s2, c.f.n_t5);
@@ -755,7 +796,7 @@ __device__ inline bool t5_eval(const DevCfg& c, const Pt<double>* P, float k1, f
         kc = fabs(ti.kappa - to.kappa) <= c.n_t5 * sqrt(sq(ti.sigk) + sq(to.sigk));
     }
     if (!kc && !all_outputs) return false;
-    Fit f = fit_track<5>(P);
+    Fit f = fit_track<5>(P, nullptr, Pf);
     o.kappa = f.kappa;
     o.chi2_rphi = f.chi2_rphi;
     o.chi2_rz = f.chi2_rz;
@@ -776,11 +817,11 @@ struct PTOut {
 
 // pT5 / pT3 with the curvature-consistency verdict kc decided by the caller.
 template <int N>
-__device__ inline bool pt_eval(const DevCfg& c, const Pt<double>* P, bool kc, double chi2_rphi_max,
-                               double chi2_rz_max, PTOut& o) {
+__device__ inline bool pt_eval(const DevCfg& c, const Pt<double>* P, const Pt<float>* Pf, bool kc,
+                               double chi2_rphi_max, double chi2_rz_max, PTOut& o) {
     o = PTOut{};
     if (!kc) return false;
-    Fit f = fit_track<N>(P);
+    Fit f = fit_track<N>(P, nullptr, Pf);
     o.kappa = f.kappa;
     o.chi2_rphi = f.chi2_rphi;
     o.chi2_rz = f.chi2_rz;
