@@ -765,18 +765,27 @@ __device__ __forceinline__ void t5_enumerate(const Arena& A, const DevCfg& c, Sm
     if (ncand) t5_flush(A, c, S, ncand, sink);
 }
 
-// T5 work items: the T3_1 of each inner MD in chunks of kT5Chunk. Chunks of
+// Chunk length of the batch's T5 work items: a small batch splits its heavy
+// units finer (their tail sets the kernel's time), a large one keeps the
+// per-item overhead low (measured: 8 for one PU200 event, 32 for 64 events).
+__device__ __forceinline__ int t5_chunk_len(const Arena& A) {
+    const int n_t3 = min(A.counters[2], A.t3_cap);
+    return n_t3 < (1 << 21) ? 8 : (n_t3 < (1 << 23) ? 16 : 32);
+}
+
+// T5 work items: the T3_1 of each inner MD in chunks of t5_chunk_len. Chunks of
 // units with more than one chunk go to the front of the item list (they are
 // the heavy units and start first), single-chunk units to the back.
 __global__ void k_t5_plan(Arena A) {
     const int n_md = min(A.counters[0], A.md_cap);
+    const int clen = t5_chunk_len(A);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_md; i += gridDim.x * blockDim.x) {
         const int n = A.t3_cnt[i];
         if (n == 0) continue;
-        const int s0 = A.t3_off[i], nch = (n + kT5Chunk - 1) / kT5Chunk;
+        const int s0 = A.t3_off[i], nch = (n + clen - 1) / clen;
         if (nch > 1) {
             const int k = atomicAdd(&A.counters[22], nch);
-            for (int j = 0; j < nch; ++j) A.t5_items[k + j] = s0 + j * kT5Chunk;
+            for (int j = 0; j < nch; ++j) A.t5_items[k + j] = s0 + j * clen;
         } else {
             const int k = atomicAdd(&A.counters[23], 1);
             A.t5_items[A.t3_cap - 1 - k] = s0;
@@ -796,6 +805,7 @@ __global__ void __launch_bounds__(kT5Warps * 32, 6) k_t5(Arena A, DevCfg c) {
     const int lane = lane_id();
     const int n_front = A.counters[22], n_items = n_front + A.counters[23];
     const int stage = min(max(c.t5_stage, 1), kT5Stage);
+    const int clen = t5_chunk_len(A);
     for (;;) {
         int k = 0;
         if (lane == 0) k = atomicAdd(&A.counters[24], 1);
@@ -803,7 +813,7 @@ __global__ void __launch_bounds__(kT5Warps * 32, 6) k_t5(Arena A, DevCfg c) {
         if (k >= n_items) break;
         const int t0 = k < n_front ? A.t5_items[k] : A.t5_items[A.t3_cap - 1 - (k - n_front)];
         const int i = A.t3_md[t0].x;
-        const int t_end = min(t0 + kT5Chunk, A.t3_off[i] + A.t3_cnt[i]);
+        const int t_end = min(t0 + clen, A.t3_off[i] + A.t3_cnt[i]);
         int cnt = 0;
         auto stage_sink = [&](bool keep, int2 pr, int r, int tot) {
             if (keep && cnt + r < stage) S.stage[cnt + r] = pr;
@@ -839,29 +849,43 @@ __global__ void __launch_bounds__(128) k_t5_gather(Arena A) {
     const int w = threadIdx.x >> 5, lane = lane_id();
     const int n_md = min(A.counters[0], A.md_cap);
     const int warps = gridDim.x * (blockDim.x >> 5);
+    const int clen = t5_chunk_len(A);
     for (int i = blockIdx.x * (blockDim.x >> 5) + w; i < n_md; i += warps) {
         const int n1 = A.t3_cnt[i];
-        const int nch = (n1 + kT5Chunk - 1) / kT5Chunk;      // <= 32: kT3Stage / kT5Chunk
-        int off = 0, len = 0;
-        if (lane < nch) {
-            const int t0 = A.t3_off[i] + lane * kT5Chunk;
-            off = A.t5_chunk_off[t0];
-            len = A.t5_chunk_cnt[t0];
-        }
-        int tot = len;
+        const int nch = (n1 + clen - 1) / clen;      // <= kT3Stage / 8 = 64
+        int tot = 0;
+        for (int g0 = 0; g0 < nch; g0 += 32) {
+            const int j = g0 + lane;
+            int len = j < nch ? A.t5_chunk_cnt[A.t3_off[i] + j * clen] : 0;
 #pragma unroll
-        for (int d = 16; d; d >>= 1) tot += __shfl_xor_sync(kFull, tot, d);
+            for (int d = 16; d; d >>= 1) len += __shfl_xor_sync(kFull, len, d);
+            tot += len;
+        }
         int n = tot, dropped = 0;
         const int base = reserve(&A.counters[3], A.t5_cap, n, dropped);
         int wr = 0;
-        for_each_flat(off, len, sm_pre[w], sm_off[w], [&](bool valid, int, int q) {
-            if (valid && wr + lane < n) {
-                const int2 pr = A.t5_tmp[q];
-                A.t5_in[base + wr + lane] = pr.x;
-                A.t5_out[base + wr + lane] = pr.y;
+        for (int g0 = 0; g0 < nch; g0 += 32) {
+            const int j = g0 + lane;
+            int off = 0, len = 0;
+            if (j < nch) {
+                const int t0 = A.t3_off[i] + j * clen;
+                off = A.t5_chunk_off[t0];
+                len = A.t5_chunk_cnt[t0];
             }
-            wr += 32;
-        });
+            int gsum = len;
+#pragma unroll
+            for (int d = 16; d; d >>= 1) gsum += __shfl_xor_sync(kFull, gsum, d);
+            int pos = wr;
+            for_each_flat(off, len, sm_pre[w], sm_off[w], [&](bool valid, int, int q) {
+                if (valid && pos + lane < n) {
+                    const int2 pr = A.t5_tmp[q];
+                    A.t5_in[base + pos + lane] = pr.x;
+                    A.t5_out[base + pos + lane] = pr.y;
+                }
+                pos += 32;
+            });
+            wr += gsum;
+        }
         if (lane == 0) {
             A.t5_off[i] = base;
             A.t5_cnt[i] = n;

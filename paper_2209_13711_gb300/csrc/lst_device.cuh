@@ -160,7 +160,7 @@ struct Arena {
     float* t5_mlp;                // network score
     int* t5_off;                  // [md_cap] by inner MD
     int* t5_cnt;
-    // T5 search work items: chunks of up to kT5Chunk T3_1 of one inner MD,
+    // T5 search work items: chunks of 8, 16 or 32 T3_1 of one inner MD,
     // named by the T3 index of their first T3_1
     int* t5_items;                // [t3_cap] split units from the front, whole units from the back
     int* t5_chunk_off;            // [t3_cap] by chunk start: the chunk's segment of t5_tmp

@@ -21,7 +21,6 @@ constexpr int kLsWarps = 8;
 constexpr int kT3Warps = 8;
 constexpr int kT5Warps = 4;
 constexpr int kPtWarps = 4;
-constexpr int kT5Chunk = 16;       // T3_1 per T5 search work item
 constexpr int kPtChunk = 8;        // superbin modules per pT search work item (<= 32)
 
 __global__ void k_reset(Arena A);
