@@ -610,8 +610,7 @@ __global__ void __launch_bounds__(kT3Warps * 32, 3) k_t3(Arena A, DevCfg c) {
             continue;
         }
         const int e = A.md_gmod[i] / A.n_mod;
-        const float4 miA = md_mod(A, i);
-        const Pt<float> PA = md_pt_f(A, i, miA);
+        const Pt<float> PA = md_point<float>(A, i);
         int cnt = 0;
         for (int cb = s0; cb < s1; cb += 32) {
             int l1 = cb + lane;
@@ -628,9 +627,8 @@ __global__ void __launch_bounds__(kT3Warps * 32, 3) k_t3(Arena A, DevCfg c) {
                 if (valid) {
                     int B_ = S.mb[seg];
                     int C_ = A.ls_out[l2];
-                    float4 miB = md_mod(A, B_), miC = md_mod(A, C_);
                     float beta, kap, rz, sk;
-                    int st = t3_eval<float>(c, PA, md_pt_f(A, B_, miB), md_pt_f(A, C_, miC), beta, kap, rz, sk);
+                    int st = t3_eval<float>(c, PA, md_point<float>(A, B_), md_point<float>(A, C_), beta, kap, rz, sk);
                     if (st == 2) st = t3_retest(A, c, i, B_, C_);
                     pass = st == 1;
                 }
@@ -646,8 +644,9 @@ __global__ void __launch_bounds__(kT3Warps * 32, 3) k_t3(Arena A, DevCfg c) {
         for (int k = lane; k < n; k += 32) {
             int2 pr = S.stage[k];
             int B_ = A.ls_out[pr.x], C_ = A.ls_out[pr.y];
-            float beta, kap, rz, sk;
-            t3_eval<float>(c, PA, md_pt_f(A, B_, md_mod(A, B_)), md_pt_f(A, C_, md_mod(A, C_)), beta, kap, rz, sk);
+            // the outputs are the three-point quantities t3_eval decided on
+            const Tri<float> t = tri(PA, md_point<float>(A, B_), md_point<float>(A, C_));
+            const float beta = t.beta, kap = t.kappa, sk = t.sigk;
             int o = base + k;
             A.t3_lsin[o] = pr.x;
             A.t3_lsout[o] = pr.y;
