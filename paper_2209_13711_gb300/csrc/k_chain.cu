@@ -21,6 +21,7 @@ namespace lst {
 // ---------------------------------------------------------------------------
 // Zero the per-batch counters and lists; the key arrays start at all ones.
 __global__ void k_reset(Arena A) {
+    pdl_begin();
     const BatchDesc B = *A.bd;
     const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
     const size_t n_keys = (size_t)B.n_hits + 3 * (size_t)B.n_seeds;
@@ -41,6 +42,7 @@ __global__ void k_reset(Arena A) {
 }
 
 __global__ void k_bin_count(Arena A) {
+    pdl_begin();
     const int nb = 2 * A.n_mod;
     const BatchDesc B = *A.bd;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n_hits; i += gridDim.x * blockDim.x) {
@@ -61,6 +63,7 @@ __global__ void k_bin_count(Arena A) {
 // scans the 32 slice totals, then every warp scans its slice 32 buckets at a
 // time with shuffles and writes offsets and cursors.
 __global__ void __launch_bounds__(1024) k_bin_scan(Arena A) {
+    pdl_begin();
     const int nb = 2 * A.n_mod;
     const int e = blockIdx.x;
     if (e >= A.bd->n_ev) return;
@@ -106,6 +109,7 @@ __global__ void __launch_bounds__(1024) k_bin_scan(Arena A) {
 }
 
 __global__ void k_bin_scatter(Arena A) {
+    pdl_begin();
     const int nb = 2 * A.n_mod;
     const BatchDesc B = *A.bd;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n_hits; i += gridDim.x * blockDim.x) {
@@ -177,6 +181,7 @@ __device__ __forceinline__ void stage_hits(const Arena& A, int g0, int n, float*
 size_t md_smem_bytes() { return kMdWarps * sizeof(MdSmem); }
 
 __global__ void __launch_bounds__(kMdWarps * 32) k_md(Arena A, DevCfg c) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char md_raw[];
     MdSmem& S = reinterpret_cast<MdSmem*>(md_raw)[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -294,6 +299,7 @@ constexpr int kMdCodeStage = 256;
 // Warp per sensor bucket: rank by original index; the first kMaxHits (all of
 // them in practice) are written back in that order.
 __global__ void __launch_bounds__(128) k_bin_sort(Arena A) {
+    pdl_begin();
     __shared__ int s_idx[4][kMaxHits];
     __shared__ float s_x[4][kMaxHits], s_y[4][kMaxHits], s_z[4][kMaxHits];
     const int w = threadIdx.x >> 5, lane = lane_id();
@@ -353,6 +359,7 @@ __device__ __forceinline__ void md_sizes(const Arena& A, int u, int& e, int& m, 
 // Work items {unit, first lower rank | chunk length << 16}: split modules at
 // the front of the list, single-chunk modules at the back.
 __global__ void k_md_plan(Arena A) {
+    pdl_begin();
     const int n_units = A.bd->n_ev * A.n_mod;
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += gridDim.x * blockDim.x) {
         int e, m, gl, gu, nl, nu, dropped;
@@ -403,6 +410,7 @@ __device__ __forceinline__ void md_enumerate(const DevCfg& c, const MdSearchSmem
 }
 
 __global__ void __launch_bounds__(kMdWarps * 32) k_md_search(Arena A, DevCfg c) {
+    pdl_begin();
     __shared__ MdSearchSmem sm[kMdWarps];
     MdSearchSmem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -459,6 +467,7 @@ __global__ void __launch_bounds__(kMdWarps * 32) k_md_search(Arena A, DevCfg c) 
 // Warp per module: its chunks in order become the module's MD segment (at
 // most kMdStage MDs, the rest counted as dropped).
 __global__ void __launch_bounds__(128) k_md_write(Arena A, DevCfg c) {
+    pdl_begin();
     __shared__ int sm_pre[4][32], sm_off[4][32];
     const int w = threadIdx.x >> 5, lane = lane_id();
     const int n_units = A.bd->n_ev * A.n_mod;
@@ -530,6 +539,7 @@ __device__ __forceinline__ float4 md_mod(const Arena& A, int i) {
 }
 
 __global__ void __launch_bounds__(kLsWarps * 32, 3) k_ls(Arena A, DevCfg c) {
+    pdl_begin();
     __shared__ LsSmem sm[kLsWarps];
     LsSmem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -599,6 +609,7 @@ struct T3Smem {
 };
 
 __global__ void __launch_bounds__(kT3Warps * 32, 3) k_t3(Arena A, DevCfg c) {
+    pdl_begin();
     __shared__ T3Smem sm[kT3Warps];
     T3Smem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -776,6 +787,7 @@ __device__ __forceinline__ int t5_chunk_len(const Arena& A) {
 // units with more than one chunk go to the front of the item list (they are
 // the heavy units and start first), single-chunk units to the back.
 __global__ void k_t5_plan(Arena A) {
+    pdl_begin();
     const int n_md = min(A.counters[0], A.md_cap);
     const int clen = t5_chunk_len(A);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_md; i += gridDim.x * blockDim.x) {
@@ -799,6 +811,7 @@ __global__ void k_t5_plan(Arena A) {
 // reserved segment, in the same order. k_t5_gather orders the segments by
 // inner MD and k_t5_refine decides the candidates in FP64.
 __global__ void __launch_bounds__(kT5Warps * 32, 6) k_t5(Arena A, DevCfg c) {
+    pdl_begin();
     __shared__ T5Smem sm[kT5Warps];
     T5Smem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -844,6 +857,7 @@ __global__ void __launch_bounds__(kT5Warps * 32, 6) k_t5(Arena A, DevCfg c) {
 // One warp per inner MD: its chunks' survivors, in chunk order, become the
 // MD's T5 segment (the order a single pass over the MD's T3_1 would give).
 __global__ void __launch_bounds__(128) k_t5_gather(Arena A) {
+    pdl_begin();
     __shared__ int sm_pre[4][32], sm_off[4][32];
     const int w = threadIdx.x >> 5, lane = lane_id();
     const int n_md = min(A.counters[0], A.md_cap);
@@ -898,6 +912,7 @@ __global__ void __launch_bounds__(128) k_t5_gather(Arena A) {
 // the hand-set cuts, writes the T5 outputs and, when enabled, the scoring
 // features; without the network the cut decision is the validity.
 __global__ void k_t5_refine(Arena A, DevCfg c) {
+    pdl_begin();
     const int n = min(A.counters[3], A.t5_cap);
     const BatchDesc* B = A.bd;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -951,6 +966,7 @@ __global__ void k_t5_refine(Arena A, DevCfg c) {
 
 // Validity from the network score (the hand-set cut decision stays in t5_cut).
 __global__ void k_t5_mlp_select(Arena A, DevCfg c) {
+    pdl_begin();
     const int n = min(A.counters[3], A.t5_cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const bool pass = A.t5_mlp[i] >= c.mlp_threshold && fabs(A.t5_kappa[i]) <= (1.0 + c.tol_r) * 2.0 * c.a;

@@ -55,6 +55,7 @@ __device__ __forceinline__ void bfrag(const __nv_bfloat16* W, int n_in, int s, i
 // for the backward pass.
 __global__ void __launch_bounds__(128) k_mlp_forward(MlpParams P, const float* __restrict__ X, int n,
                                                      const int* n_dev, float* __restrict__ scores, MlpSaved save) {
+    pdl_begin();
     __shared__ MlpSmem S;
     if (n_dev) n = min(*n_dev, n);      // in the chain the candidate count lives on the device
     for (int i = threadIdx.x; i < kH1 * kIn; i += blockDim.x) S.w1[i] = P.w1_bf[i];

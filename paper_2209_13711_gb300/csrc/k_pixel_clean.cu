@@ -10,6 +10,7 @@ namespace lst {
 // pLS: one thread per seed, FP64 (three-point circle, r-z line, superbin)
 // ---------------------------------------------------------------------------
 __global__ void k_pls(Arena A, DevCfg c) {
+    pdl_begin();
     const BatchDesc B = *A.bd;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < B.n_seeds; g += gridDim.x * blockDim.x) {
         const float* q = B.seeds + 9 * (size_t)g;
@@ -164,6 +165,7 @@ __device__ __forceinline__ void pt_enumerate(const Arena& A, const DevCfg& c, Pt
 // pT work items: (passing seed, a chunk of up to kPtChunk modules of its
 // superbin list). The same list serves the pT5 and the pT3 search.
 __global__ void k_pt_plan(Arena A) {
+    pdl_begin();
     const int n_seeds = A.bd->n_seeds;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_seeds; g += gridDim.x * blockDim.x) {
         if (!A.pls_pass[g] || A.pls_sb[g] < 0) continue;
@@ -232,8 +234,14 @@ __device__ __forceinline__ void pt_kernel_body(Arena& A, const DevCfg& c) {
     }
 }
 
-__global__ void __launch_bounds__(kPtWarps * 32, 6) k_pt5(Arena A, DevCfg c) { pt_kernel_body<5>(A, c); }
-__global__ void __launch_bounds__(kPtWarps * 32, 6) k_pt3(Arena A, DevCfg c) { pt_kernel_body<3>(A, c); }
+__global__ void __launch_bounds__(kPtWarps * 32, 6) k_pt5(Arena A, DevCfg c) {
+    pdl_begin();
+    pt_kernel_body<5>(A, c);
+}
+__global__ void __launch_bounds__(kPtWarps * 32, 6) k_pt3(Arena A, DevCfg c) {
+    pdl_begin();
+    pt_kernel_body<3>(A, c);
+}
 
 // pT5 / pT3 refine (FP64): one thread per searched candidate.
 template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const DevCfg& c) {
@@ -284,8 +292,14 @@ template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const
     }
 }
 
-__global__ void k_pt5_refine(Arena A, DevCfg c) { pt_refine_body<5>(A, c); }
-__global__ void k_pt3_refine(Arena A, DevCfg c) { pt_refine_body<3>(A, c); }
+__global__ void k_pt5_refine(Arena A, DevCfg c) {
+    pdl_begin();
+    pt_refine_body<5>(A, c);
+}
+__global__ void k_pt3_refine(Arena A, DevCfg c) {
+    pdl_begin();
+    pt_refine_body<3>(A, c);
+}
 
 // ---------------------------------------------------------------------------
 // cross-cleaning
@@ -354,6 +368,7 @@ __device__ __forceinline__ unsigned long long object_key(ObjHits& o) {
 // pass 0: per hit, the smallest key of each category; pass 1: keep an object
 // when it holds the smallest key on every one of its hits.
 __global__ void k_clean_keys(Arena A, int pass) {
+    pdl_begin();
     const int n5 = min(A.counters[4], A.pt5_cap);
     const int n3 = min(A.counters[5], A.pt3_cap);
     const int nt = min(A.counters[3], A.t5_cap);
@@ -465,6 +480,7 @@ __device__ __forceinline__ bool marked_warp(const Arena& A, const ObjHits& o, in
 
 // kept pT5: mark hits and seeds, list for the eta-phi tests, track candidates
 __global__ void k_clean_pt5(Arena A) {
+    pdl_begin();
     const int n5 = min(A.counters[4], A.pt5_cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n5; i += gridDim.x * blockDim.x) {
         if (!A.keep_pt5[i]) continue;
@@ -481,6 +497,7 @@ __global__ void k_clean_pt5(Arena A) {
 }
 
 __global__ void k_clean_pt3_cross(Arena A, DevCfg c) {
+    pdl_begin();
     const int n3 = min(A.counters[5], A.pt3_cap);
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n3; i += warps) {
@@ -495,6 +512,7 @@ __global__ void k_clean_pt3_cross(Arena A, DevCfg c) {
 }
 
 __global__ void k_clean_pt3_mark(Arena A) {
+    pdl_begin();
     const int n3 = min(A.counters[5], A.pt3_cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
         if (!A.keep_pt3[i]) continue;
@@ -511,6 +529,7 @@ __global__ void k_clean_pt3_mark(Arena A) {
 }
 
 __global__ void k_clean_t5(Arena A, DevCfg c) {
+    pdl_begin();
     const int nt = min(A.counters[3], A.t5_cap);
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nt; i += warps) {
@@ -532,6 +551,7 @@ __global__ void k_clean_t5(Arena A, DevCfg c) {
 }
 
 __global__ void k_clean_pls(Arena A, DevCfg c) {
+    pdl_begin();
     const int n_ev = A.bd->n_ev, n_seeds = A.bd->n_seeds;
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < n_seeds; g += warps) {
@@ -547,6 +567,7 @@ __global__ void k_clean_pls(Arena A, DevCfg c) {
 // one block per event (grid-stride over events) sums the counts of the
 // events before it for its offset, then copies its slab.
 __global__ void k_tc_pack(Arena A) {
+    pdl_begin();
     __shared__ int red[32];
     __shared__ int s_off;
     const int n_ev = A.bd->n_ev;

@@ -434,8 +434,27 @@ static int block_of(const lst_ctx* c, int id) {
     return (k.generic && c->tune[id].block > 0) ? c->tune[id].block : k.block;
 }
 
+// One launch of the chain; with pdl, the kernel may be scheduled while its
+// predecessor drains (every kernel starts with pdl_begin()).
+extern "C++" template <typename... KArgs, typename... Args>
+void run_k(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, bool pdl,
+                  Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile) {
     const Arena& A = c->A;
+    const bool pdl = !profile;     // profiling events between launches would serialise them anyway
     const DevCfg& dc = c->dc;
     int L = 0;
 #define GB(ID) grid_of(c, ID), block_of(c, ID)
@@ -450,39 +469,39 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile) {
         if (profile && L < lst_ctx::kMaxProf) cudaEventRecord(c->prof_ev[2 * L + 1], st); \
         ++L;                                                                           \
     } while (0)
-    LAUNCH(L_RESET, k_reset<<<GB(L_RESET), 0, st>>>(A));
-    LAUNCH(L_BIN_COUNT, k_bin_count<<<GB(L_BIN_COUNT), 0, st>>>(A));
-    LAUNCH(L_BIN_SCAN, k_bin_scan<<<A.max_events, 1024, 0, st>>>(A));
-    LAUNCH(L_BIN_SCATTER, k_bin_scatter<<<GB(L_BIN_SCATTER), 0, st>>>(A));
-    LAUNCH(L_BIN_SORT, k_bin_sort<<<GB(L_BIN_SORT), 0, st>>>(A));
-    LAUNCH(L_MD_PLAN, k_md_plan<<<GB(L_MD_PLAN), 0, st>>>(A));
-    LAUNCH(L_MD, k_md_search<<<GB(L_MD), 0, st>>>(A, dc));
-    LAUNCH(L_MD_WRITE, k_md_write<<<GB(L_MD_WRITE), 0, st>>>(A, dc));
-    LAUNCH(L_LS, k_ls<<<GB(L_LS), 0, st>>>(A, dc));
-    LAUNCH(L_T3, k_t3<<<GB(L_T3), 0, st>>>(A, dc));
-    LAUNCH(L_T5_PLAN, k_t5_plan<<<GB(L_T5_PLAN), 0, st>>>(A));
-    LAUNCH(L_T5, k_t5<<<GB(L_T5), 0, st>>>(A, dc));
-    LAUNCH(L_T5_GATHER, k_t5_gather<<<GB(L_T5_GATHER), 0, st>>>(A));
-    LAUNCH(L_T5_REFINE, k_t5_refine<<<GB(L_T5_REFINE), 0, st>>>(A, dc));
+    LAUNCH(L_RESET, run_k(k_reset, GB(L_RESET), 0, st, pdl, A));
+    LAUNCH(L_BIN_COUNT, run_k(k_bin_count, GB(L_BIN_COUNT), 0, st, pdl, A));
+    LAUNCH(L_BIN_SCAN, run_k(k_bin_scan, A.max_events, 1024, 0, st, pdl, A));
+    LAUNCH(L_BIN_SCATTER, run_k(k_bin_scatter, GB(L_BIN_SCATTER), 0, st, pdl, A));
+    LAUNCH(L_BIN_SORT, run_k(k_bin_sort, GB(L_BIN_SORT), 0, st, pdl, A));
+    LAUNCH(L_MD_PLAN, run_k(k_md_plan, GB(L_MD_PLAN), 0, st, pdl, A));
+    LAUNCH(L_MD, run_k(k_md_search, GB(L_MD), 0, st, pdl, A, dc));
+    LAUNCH(L_MD_WRITE, run_k(k_md_write, GB(L_MD_WRITE), 0, st, pdl, A, dc));
+    LAUNCH(L_LS, run_k(k_ls, GB(L_LS), 0, st, pdl, A, dc));
+    LAUNCH(L_T3, run_k(k_t3, GB(L_T3), 0, st, pdl, A, dc));
+    LAUNCH(L_T5_PLAN, run_k(k_t5_plan, GB(L_T5_PLAN), 0, st, pdl, A));
+    LAUNCH(L_T5, run_k(k_t5, GB(L_T5), 0, st, pdl, A, dc));
+    LAUNCH(L_T5_GATHER, run_k(k_t5_gather, GB(L_T5_GATHER), 0, st, pdl, A));
+    LAUNCH(L_T5_REFINE, run_k(k_t5_refine, GB(L_T5_REFINE), 0, st, pdl, A, dc));
     if (c->mlp) {
-        LAUNCH(L_T5_MLP, k_mlp_forward<<<GB(L_T5_MLP), 0, st>>>(lst_mlp_device_params(c->mlp), A.t5_feat, A.t5_cap,
+        LAUNCH(L_T5_MLP, run_k(k_mlp_forward, GB(L_T5_MLP), 0, st, pdl, lst_mlp_device_params(c->mlp), A.t5_feat, A.t5_cap,
                                                                 A.counters + 3, A.t5_mlp, MlpSaved{}));
-        LAUNCH(L_T5_MLP_SELECT, k_t5_mlp_select<<<GB(L_T5_MLP_SELECT), 0, st>>>(A, dc));
+        LAUNCH(L_T5_MLP_SELECT, run_k(k_t5_mlp_select, GB(L_T5_MLP_SELECT), 0, st, pdl, A, dc));
     }
-    LAUNCH(L_PLS, k_pls<<<GB(L_PLS), 0, st>>>(A, dc));
-    LAUNCH(L_PT_PLAN, k_pt_plan<<<GB(L_PT_PLAN), 0, st>>>(A));
-    LAUNCH(L_PT5, k_pt5<<<GB(L_PT5), 0, st>>>(A, dc));
-    LAUNCH(L_PT5_REFINE, k_pt5_refine<<<GB(L_PT5_REFINE), 0, st>>>(A, dc));
-    LAUNCH(L_PT3, k_pt3<<<GB(L_PT3), 0, st>>>(A, dc));
-    LAUNCH(L_PT3_REFINE, k_pt3_refine<<<GB(L_PT3_REFINE), 0, st>>>(A, dc));
-    LAUNCH(L_CLEAN_KEYS, k_clean_keys<<<GB(L_CLEAN_KEYS), 0, st>>>(A, 0));
-    LAUNCH(L_CLEAN_KEEP, k_clean_keys<<<GB(L_CLEAN_KEEP), 0, st>>>(A, 1));
-    LAUNCH(L_CLEAN_PT5, k_clean_pt5<<<GB(L_CLEAN_PT5), 0, st>>>(A));
-    LAUNCH(L_CLEAN_PT3_CROSS, k_clean_pt3_cross<<<GB(L_CLEAN_PT3_CROSS), 0, st>>>(A, dc));
-    LAUNCH(L_CLEAN_PT3_MARK, k_clean_pt3_mark<<<GB(L_CLEAN_PT3_MARK), 0, st>>>(A));
-    LAUNCH(L_CLEAN_T5, k_clean_t5<<<GB(L_CLEAN_T5), 0, st>>>(A, dc));
-    LAUNCH(L_CLEAN_PLS, k_clean_pls<<<GB(L_CLEAN_PLS), 0, st>>>(A, dc));
-    LAUNCH(L_TC_PACK, k_tc_pack<<<GB(L_TC_PACK), 0, st>>>(A));
+    LAUNCH(L_PLS, run_k(k_pls, GB(L_PLS), 0, st, pdl, A, dc));
+    LAUNCH(L_PT_PLAN, run_k(k_pt_plan, GB(L_PT_PLAN), 0, st, pdl, A));
+    LAUNCH(L_PT5, run_k(k_pt5, GB(L_PT5), 0, st, pdl, A, dc));
+    LAUNCH(L_PT5_REFINE, run_k(k_pt5_refine, GB(L_PT5_REFINE), 0, st, pdl, A, dc));
+    LAUNCH(L_PT3, run_k(k_pt3, GB(L_PT3), 0, st, pdl, A, dc));
+    LAUNCH(L_PT3_REFINE, run_k(k_pt3_refine, GB(L_PT3_REFINE), 0, st, pdl, A, dc));
+    LAUNCH(L_CLEAN_KEYS, run_k(k_clean_keys, GB(L_CLEAN_KEYS), 0, st, pdl, A, 0));
+    LAUNCH(L_CLEAN_KEEP, run_k(k_clean_keys, GB(L_CLEAN_KEEP), 0, st, pdl, A, 1));
+    LAUNCH(L_CLEAN_PT5, run_k(k_clean_pt5, GB(L_CLEAN_PT5), 0, st, pdl, A));
+    LAUNCH(L_CLEAN_PT3_CROSS, run_k(k_clean_pt3_cross, GB(L_CLEAN_PT3_CROSS), 0, st, pdl, A, dc));
+    LAUNCH(L_CLEAN_PT3_MARK, run_k(k_clean_pt3_mark, GB(L_CLEAN_PT3_MARK), 0, st, pdl, A));
+    LAUNCH(L_CLEAN_T5, run_k(k_clean_t5, GB(L_CLEAN_T5), 0, st, pdl, A, dc));
+    LAUNCH(L_CLEAN_PLS, run_k(k_clean_pls, GB(L_CLEAN_PLS), 0, st, pdl, A, dc));
+    LAUNCH(L_TC_PACK, run_k(k_tc_pack, GB(L_TC_PACK), 0, st, pdl, A));
 #undef LAUNCH
 #undef GB
     c->launches = L;

@@ -27,6 +27,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "lst_pdl.cuh"
+
 namespace lst {
 
 constexpr float kBand = 5e-4f;   // relative width of the FP32 undecided band around a threshold
@@ -602,8 +604,8 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
     for (int i = 0; i < N; ++i) s[i] = arc(sqrt(sq(P[i].x - P[0].x) + sq(P[i].y - P[0].y)), ka);
     double t_hat = (P[N - 1].z - P[0].z) / s[N - 1];
     double w[N], W = 0, Ws = 0, Wz = 0;
-#pragma unroll
     const float tf = float(t_hat);
+#pragma unroll
     for (int i = 0; i < N; ++i) {
         w[i] = Pf ? double(1.f / fmaxf(1e-12f, sq(Pf[i].sz) + sq(tf * Pf[i].sr)))
                   : 1.0 / fmax(1e-12, sq(P[i].sz) + sq(t_hat * P[i].sr));

@@ -3,6 +3,8 @@
 
 #include <cuda_bf16.h>
 
+#include "lst_pdl.cuh"
+
 namespace lst {
 
 constexpr int kFeatures = 38;        // defined features; the input is zero padded to kIn
