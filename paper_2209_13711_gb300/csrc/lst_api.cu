@@ -121,6 +121,8 @@ struct lst_ctx {
     BatchDesc* d_bd = nullptr;        // device batch descriptor
     BatchDesc* h_bd = nullptr;        // pinned staging of the descriptor
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t side_stream = nullptr;   // second branch of the captured graph (pLS, pT3)
+    cudaEvent_t ev_fork = nullptr, ev_t3 = nullptr, ev_plan = nullptr, ev_pt3 = nullptr;
     cudaGraphExec_t graph = nullptr;
     LaunchCfg tune[kNumLaunch];       // per-stage launch shape (autotuner or caller)
     static constexpr int kMaxProf = 64;
@@ -236,7 +238,12 @@ lst_status lst_create(lst_ctx** out, const lst_config* cfg, const lst_capacity* 
         cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&c->h_offsets, sizeof(int) * 2 * (cap->max_events + 1)) != cudaSuccess ||
         cudaMallocHost(&c->h_bd, sizeof(BatchDesc)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_t3, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_plan, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_pt3, cudaEventDisableTiming) != cudaSuccess) {
         delete c;
         return LST_ERR_CUDA;
     }
@@ -253,6 +260,9 @@ void lst_destroy(lst_ctx* c) {
     }
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    for (cudaEvent_t e : {c->ev_fork, c->ev_t3, c->ev_plan, c->ev_pt3})
+        if (e) cudaEventDestroy(e);
     if (c->dev_mem) cudaFree(c->dev_mem);
     if (c->h_offsets) cudaFreeHost(c->h_offsets);
     if (c->h_bd) cudaFreeHost(c->h_bd);
@@ -452,7 +462,11 @@ void run_k(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t s
     cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 
-static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile) {
+// The launch sequence. With `side` (graph capture), pLS and the pT3 search
+// run on a second branch: pLS and the pT plan after the reset, the pT3 search
+// and refine once T3 exist; the main branch joins them before pT5 and before
+// the cleaning. Without it everything is one stream in the listed order.
+static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile, cudaStream_t side = nullptr) {
     const Arena& A = c->A;
     const bool pdl = !profile;     // profiling events between launches would serialise them anyway
     const DevCfg& dc = c->dc;
@@ -470,6 +484,13 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile) {
         ++L;                                                                           \
     } while (0)
     LAUNCH(L_RESET, run_k(k_reset, GB(L_RESET), 0, st, pdl, A));
+    if (side) {
+        cudaEventRecord(c->ev_fork, st);
+        cudaStreamWaitEvent(side, c->ev_fork, 0);
+        LAUNCH(L_PLS, run_k(k_pls, GB(L_PLS), 0, side, false, A, dc));
+        LAUNCH(L_PT_PLAN, run_k(k_pt_plan, GB(L_PT_PLAN), 0, side, pdl, A));
+        cudaEventRecord(c->ev_plan, side);
+    }
     LAUNCH(L_BIN_COUNT, run_k(k_bin_count, GB(L_BIN_COUNT), 0, st, pdl, A));
     LAUNCH(L_BIN_SCAN, run_k(k_bin_scan, A.max_events, 1024, 0, st, pdl, A));
     LAUNCH(L_BIN_SCATTER, run_k(k_bin_scatter, GB(L_BIN_SCATTER), 0, st, pdl, A));
@@ -479,22 +500,37 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile) {
     LAUNCH(L_MD_WRITE, run_k(k_md_write, GB(L_MD_WRITE), 0, st, pdl, A, dc));
     LAUNCH(L_LS, run_k(k_ls, GB(L_LS), 0, st, pdl, A, dc));
     LAUNCH(L_T3, run_k(k_t3, GB(L_T3), 0, st, pdl, A, dc));
+    if (side) {
+        cudaEventRecord(c->ev_t3, st);
+        cudaStreamWaitEvent(side, c->ev_t3, 0);
+        LAUNCH(L_PT3, run_k(k_pt3, GB(L_PT3), 0, side, false, A, dc));
+        LAUNCH(L_PT3_REFINE, run_k(k_pt3_refine, GB(L_PT3_REFINE), 0, side, pdl, A, dc));
+        cudaEventRecord(c->ev_pt3, side);
+    }
     LAUNCH(L_T5_PLAN, run_k(k_t5_plan, GB(L_T5_PLAN), 0, st, pdl, A));
     LAUNCH(L_T5, run_k(k_t5, GB(L_T5), 0, st, pdl, A, dc));
     LAUNCH(L_T5_GATHER, run_k(k_t5_gather, GB(L_T5_GATHER), 0, st, pdl, A));
     LAUNCH(L_T5_REFINE, run_k(k_t5_refine, GB(L_T5_REFINE), 0, st, pdl, A, dc));
     if (c->mlp) {
-        LAUNCH(L_T5_MLP, run_k(k_mlp_forward, GB(L_T5_MLP), 0, st, pdl, lst_mlp_device_params(c->mlp), A.t5_feat, A.t5_cap,
-                                                                A.counters + 3, A.t5_mlp, MlpSaved{}));
+        LAUNCH(L_T5_MLP, run_k(k_mlp_forward, GB(L_T5_MLP), 0, st, pdl, lst_mlp_device_params(c->mlp), A.t5_feat,
+                               A.t5_cap, A.counters + 3, A.t5_mlp, MlpSaved{}));
         LAUNCH(L_T5_MLP_SELECT, run_k(k_t5_mlp_select, GB(L_T5_MLP_SELECT), 0, st, pdl, A, dc));
     }
-    LAUNCH(L_PLS, run_k(k_pls, GB(L_PLS), 0, st, pdl, A, dc));
-    LAUNCH(L_PT_PLAN, run_k(k_pt_plan, GB(L_PT_PLAN), 0, st, pdl, A));
-    LAUNCH(L_PT5, run_k(k_pt5, GB(L_PT5), 0, st, pdl, A, dc));
+    if (side) {
+        cudaStreamWaitEvent(st, c->ev_plan, 0);
+    } else {
+        LAUNCH(L_PLS, run_k(k_pls, GB(L_PLS), 0, st, pdl, A, dc));
+        LAUNCH(L_PT_PLAN, run_k(k_pt_plan, GB(L_PT_PLAN), 0, st, pdl, A));
+    }
+    LAUNCH(L_PT5, run_k(k_pt5, GB(L_PT5), 0, st, side ? false : pdl, A, dc));
     LAUNCH(L_PT5_REFINE, run_k(k_pt5_refine, GB(L_PT5_REFINE), 0, st, pdl, A, dc));
-    LAUNCH(L_PT3, run_k(k_pt3, GB(L_PT3), 0, st, pdl, A, dc));
-    LAUNCH(L_PT3_REFINE, run_k(k_pt3_refine, GB(L_PT3_REFINE), 0, st, pdl, A, dc));
-    LAUNCH(L_CLEAN_KEYS, run_k(k_clean_keys, GB(L_CLEAN_KEYS), 0, st, pdl, A, 0));
+    if (side) {
+        cudaStreamWaitEvent(st, c->ev_pt3, 0);
+    } else {
+        LAUNCH(L_PT3, run_k(k_pt3, GB(L_PT3), 0, st, pdl, A, dc));
+        LAUNCH(L_PT3_REFINE, run_k(k_pt3_refine, GB(L_PT3_REFINE), 0, st, pdl, A, dc));
+    }
+    LAUNCH(L_CLEAN_KEYS, run_k(k_clean_keys, GB(L_CLEAN_KEYS), 0, st, side ? false : pdl, A, 0));
     LAUNCH(L_CLEAN_KEEP, run_k(k_clean_keys, GB(L_CLEAN_KEEP), 0, st, pdl, A, 1));
     LAUNCH(L_CLEAN_PT5, run_k(k_clean_pt5, GB(L_CLEAN_PT5), 0, st, pdl, A));
     LAUNCH(L_CLEAN_PT3_CROSS, run_k(k_clean_pt3_cross, GB(L_CLEAN_PT3_CROSS), 0, st, pdl, A, dc));
@@ -521,7 +557,7 @@ static lst_status launch_prepared(lst_ctx* c, cudaStream_t st, int n_ev) {
         if (!c->graph) {
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-            enqueue_chain(c, c->cap_stream, false);
+            enqueue_chain(c, c->cap_stream, false, c->side_stream);
             cudaError_t e1 = cudaStreamEndCapture(c->cap_stream, &g);
             if (e1 != cudaSuccess) return LST_ERR_CUDA;
             cudaError_t e2 = cudaGraphInstantiate(&c->graph, g, 0);
