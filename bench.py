@@ -382,11 +382,15 @@ def measure_mlp(P, E, geom, maps, cuts, flush, st, dev_events):
         torch.cuda.synchronize()
         ms += e0.elapsed_time(e1)
     st0 = ctx1.stats(0)
+    ctx1.set_profiling(True)
+    ctx1.run_packed(dev_events[0], stream=st.cuda_stream)
+    stage = {n: round(t, 4) for n, t in ctx1.kernel_times() if n.startswith("t5")}
+    ctx1.set_profiling(False)
     ctx1.close()
     mlp.close()
     return {"value": round(len(dev_events) / (ms / 1e3), 2), "unit": "events/s",
             "selection": "T5 validity from the BF16 network (prefilter widened x3)",
-            "t5_per_event": st0["counts"]["t5"], "tc_per_event": st0["counts"]["tc"],
+            "t5_per_event": st0["counts"]["t5"], "tc_per_event": st0["counts"]["tc"], "t5_stage_ms": stage,
             "quality_at_matched_efficiency": {"cut": quality["cut"], "network": quality["network"],
                                               "threshold": round(quality["threshold"], 4),
                                               "samples_train": int(len(tr["y"])), "samples_eval": int(len(va["y"]))},

@@ -347,6 +347,17 @@ __device__ __forceinline__ void object_hits(const Arena& A, int cat, int idx, Ob
     for (int j = 0; j < nm; ++j) md_hits_into(A, m[j], h0, o);
 }
 
+// The cached hits of object f (written by the first cleaning pass).
+struct CachedHits {
+    int n, e;
+    const int* slots;
+};
+
+__device__ __forceinline__ CachedHits cached_hits(const Arena& A, int f) {
+    const int meta = A.obj_meta[f];
+    return CachedHits{meta & 15, meta >> 4, A.obj_slot + 16 * (size_t)f};
+}
+
 // key = (score as FP32 bits, FNV-1a of the sorted local hit ids as 32-bit words)
 __device__ __forceinline__ unsigned long long object_key(ObjHits& o) {
     int s[13];
@@ -382,13 +393,19 @@ __global__ void k_clean_keys(Arena A, int pass) {
             if (pass == 1) kf[idx] = 0;
             continue;
         }
-        ObjHits o;
-        object_hits(A, cat, idx, o);
-        unsigned long long key = object_key(o);
         unsigned long long* best = A.best + cat * n_keys;
         if (pass == 0) {
+            ObjHits o;
+            object_hits(A, cat, idx, o);
+            const unsigned long long key = object_key(o);
             for (int i = 0; i < o.n; ++i) atomicMin(best + o.slots[i], key);
+            A.obj_key[f] = key;
+            A.obj_meta[f] = (o.e << 4) | o.n;
+            int* sl = A.obj_slot + 16 * (size_t)f;
+            for (int i = 0; i < o.n; ++i) sl[i] = o.slots[i];
         } else {
+            const CachedHits o = cached_hits(A, f);
+            const unsigned long long key = A.obj_key[f];
             bool keep = true;
             for (int i = 0; i < o.n; ++i) keep &= best[o.slots[i]] == key;
             kf[idx] = keep;
@@ -396,25 +413,44 @@ __global__ void k_clean_keys(Arena A, int pass) {
     }
 }
 
-__device__ __forceinline__ void tc_append(const Arena& A, int e, int type, int seed_local, int obj, const int* m,
-                                          int nm, float pt, float eta, float phi) {
+// A track candidate from a cached object: its outer-tracker hits are the
+// cached slots from `first` on, minus the event's hit offset.
+__device__ __forceinline__ void tc_append(const Arena& A, int e, int type, int seed_local, int obj,
+                                          const CachedHits& o, int first, float pt, float eta, float phi) {
     int k = atomicAdd(&A.tc_cnt[e], 1);
     if (k >= A.tc_cap) {
         atomicAdd(&A.ev_drop[e * 8 + 7], 1);
         return;
     }
-    size_t o = (size_t)e * A.tc_cap + k;
-    A.tc_type[o] = type;
-    A.tc_seed[o] = seed_local;
-    A.tc_obj[o] = obj;
-    int* h = A.tc_hits + 10 * o;
-    for (int j = 0; j < 5; ++j) {
-        h[2 * j] = j < nm ? A.md_lo[m[j]] : -1;
-        h[2 * j + 1] = j < nm ? A.md_up[m[j]] : -1;
+    size_t t = (size_t)e * A.tc_cap + k;
+    A.tc_type[t] = type;
+    A.tc_seed[t] = seed_local;
+    A.tc_obj[t] = obj;
+    int* h = A.tc_hits + 10 * t;
+    const int h0 = A.hit_off[e];
+    for (int j = 0; j < 10; ++j) h[j] = first + j < o.n ? o.slots[first + j] - h0 : -1;
+    A.tc_pt[t] = pt;
+    A.tc_eta[t] = eta;
+    A.tc_phi[t] = phi;
+}
+
+// pLS track candidate (no outer-tracker hits)
+__device__ __forceinline__ void tc_append_pls(const Arena& A, int e, int seed_local, int g, float pt, float eta,
+                                              float phi) {
+    int k = atomicAdd(&A.tc_cnt[e], 1);
+    if (k >= A.tc_cap) {
+        atomicAdd(&A.ev_drop[e * 8 + 7], 1);
+        return;
     }
-    A.tc_pt[o] = pt;
-    A.tc_eta[o] = eta;
-    A.tc_phi[o] = phi;
+    size_t t = (size_t)e * A.tc_cap + k;
+    A.tc_type[t] = 3;
+    A.tc_seed[t] = seed_local;
+    A.tc_obj[t] = g;
+    int* h = A.tc_hits + 10 * t;
+    for (int j = 0; j < 10; ++j) h[j] = -1;
+    A.tc_pt[t] = pt;
+    A.tc_eta[t] = eta;
+    A.tc_phi[t] = phi;
 }
 
 __device__ __forceinline__ void list_append(const Arena& A, int e, int list, float eta, float phi, int ref) {
@@ -472,7 +508,7 @@ __device__ __forceinline__ bool dr_close_warp(const Arena& A, const DevCfg& c, i
 }
 
 // any of the object's outer-tracker hits carries one of the mark bits
-__device__ __forceinline__ bool marked_warp(const Arena& A, const ObjHits& o, int first, int bits) {
+__device__ __forceinline__ bool marked_warp(const Arena& A, const CachedHits& o, int first, int bits) {
     const int j = first + lane_id();
     bool m = j < o.n && (A.mark[o.slots[j]] & bits) != 0;
     return __any_sync(kFull, m);
@@ -484,26 +520,24 @@ __global__ void k_clean_pt5(Arena A) {
     const int n5 = min(A.counters[4], A.pt5_cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n5; i += gridDim.x * blockDim.x) {
         if (!A.keep_pt5[i]) continue;
-        ObjHits o;
-        object_hits(A, 0, i, o);
+        const CachedHits o = cached_hits(A, i);
         for (int j = 3; j < o.n; ++j) atomicOr(&A.mark[o.slots[j]], 1);
         int g = A.pt5_seed[i];
         atomicOr(&A.seed_link[g], 1);
-        list_append(A, o.e, 0, float(A.pls_eta[g]), float(A.pls_phi[g]), (0 << 28) | i);
-        int m[5];
-        pt_mds<5>(A, A.pt5_obj[i], m);
-        tc_append(A, o.e, 0, g - A.seed_off[o.e], i, m, 5, A.pt5_pt[i], float(A.pls_eta[g]), float(A.pls_phi[g]));
+        const float eta = float(A.pls_eta[g]), phi = float(A.pls_phi[g]);
+        list_append(A, o.e, 0, eta, phi, (0 << 28) | i);
+        tc_append(A, o.e, 0, g - A.seed_off[o.e], i, o, 3, A.pt5_pt[i], eta, phi);
     }
 }
 
 __global__ void k_clean_pt3_cross(Arena A, DevCfg c) {
     pdl_begin();
+    const int n5 = min(A.counters[4], A.pt5_cap);
     const int n3 = min(A.counters[5], A.pt3_cap);
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n3; i += warps) {
         if (!A.keep_pt3[i]) continue;
-        ObjHits o;
-        object_hits(A, 1, i, o);
+        const CachedHits o = cached_hits(A, n5 + i);
         const int g = A.pt3_seed[i];
         bool drop = (A.seed_link[g] & 1) != 0 || marked_warp(A, o, 3, 1);
         if (!drop) drop = dr_close_warp(A, c, o.e, 0, A.pls_eta[g], A.pls_phi[g]);
@@ -513,38 +547,37 @@ __global__ void k_clean_pt3_cross(Arena A, DevCfg c) {
 
 __global__ void k_clean_pt3_mark(Arena A) {
     pdl_begin();
+    const int n5 = min(A.counters[4], A.pt5_cap);
     const int n3 = min(A.counters[5], A.pt3_cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
         if (!A.keep_pt3[i]) continue;
-        ObjHits o;
-        object_hits(A, 1, i, o);
+        const CachedHits o = cached_hits(A, n5 + i);
         for (int j = 3; j < o.n; ++j) atomicOr(&A.mark[o.slots[j]], 2);
         int g = A.pt3_seed[i];
         atomicOr(&A.seed_link[g], 2);
-        list_append(A, o.e, 0, float(A.pls_eta[g]), float(A.pls_phi[g]), (1 << 28) | i);
-        int m[3];
-        pt_mds<3>(A, A.pt3_obj[i], m);
-        tc_append(A, o.e, 1, g - A.seed_off[o.e], i, m, 3, A.pt3_pt[i], float(A.pls_eta[g]), float(A.pls_phi[g]));
+        const float eta = float(A.pls_eta[g]), phi = float(A.pls_phi[g]);
+        list_append(A, o.e, 0, eta, phi, (1 << 28) | i);
+        tc_append(A, o.e, 1, g - A.seed_off[o.e], i, o, 3, A.pt3_pt[i], eta, phi);
     }
 }
 
 __global__ void k_clean_t5(Arena A, DevCfg c) {
     pdl_begin();
+    const int n5 = min(A.counters[4], A.pt5_cap);
+    const int n3 = min(A.counters[5], A.pt3_cap);
     const int nt = min(A.counters[3], A.t5_cap);
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nt; i += warps) {
         if (!A.keep_t5[i]) continue;
-        ObjHits o;
-        object_hits(A, 2, i, o);
+        const CachedHits o = cached_hits(A, n5 + n3 + i);
         bool drop = marked_warp(A, o, 0, 3);
         if (!drop) drop = dr_close_warp(A, c, o.e, 0, A.t5_eta[i], A.t5_phi[i]);
         if (lane_id() == 0) {
             A.keep_t5[i] = !drop;
             if (!drop) {
-                list_append(A, o.e, 1, float(A.t5_eta[i]), float(A.t5_phi[i]), (2 << 28) | i);
-                int m[5];
-                pt_mds<5>(A, i, m);
-                tc_append(A, o.e, 2, -1, i, m, 5, A.t5_pt[i], float(A.t5_eta[i]), float(A.t5_phi[i]));
+                const float eta = float(A.t5_eta[i]), phi = float(A.t5_phi[i]);
+                list_append(A, o.e, 1, eta, phi, (2 << 28) | i);
+                tc_append(A, o.e, 2, -1, i, o, 0, A.t5_pt[i], eta, phi);
             }
         }
     }
@@ -559,7 +592,7 @@ __global__ void k_clean_pls(Arena A, DevCfg c) {
         int e = event_of(A.seed_off, n_ev, g);
         double eta = A.pls_eta[g], phi = A.pls_phi[g];
         if (dr_close_warp(A, c, e, 0, eta, phi) || dr_close_warp(A, c, e, 1, eta, phi)) continue;
-        if (lane_id() == 0) tc_append(A, e, 3, g - A.seed_off[e], g, nullptr, 0, A.pls_pt[g], float(eta), float(phi));
+        if (lane_id() == 0) tc_append_pls(A, e, g - A.seed_off[e], g, A.pls_pt[g], float(eta), float(phi));
     }
 }
 

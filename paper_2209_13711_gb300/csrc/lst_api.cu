@@ -358,6 +358,9 @@ static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n
     const size_t NK = H + 3 * S;
     A.best = b.take<unsigned long long>(3 * NK);
     A.mark = b.take<int>(NK);
+    A.obj_key = b.take<unsigned long long>(P5 + P3 + T5);
+    A.obj_meta = b.take<int>(P5 + P3 + T5);
+    A.obj_slot = b.take<int>(16 * (P5 + P3 + T5));
     A.keep_pt5 = b.take<uint8_t>(P5); A.keep_pt3 = b.take<uint8_t>(P3); A.keep_t5 = b.take<uint8_t>(T5);
     A.seed_link = b.take<int>(S);
     A.list_cap = 32768;

@@ -201,6 +201,11 @@ struct Arena {
     // cleaning
     unsigned long long* best;     // [3][n_keys]: n_keys = n_hits + 3 n_seeds
     int* mark;                    // [n_keys] bit 0: used by a kept pT5, bit 1: by a kept pT3
+    // per object (flat index over pT5, pT3, T5), written by the first cleaning
+    // pass: its key, (event << 4) | number of hits, and its hits' key slots
+    unsigned long long* obj_key;
+    int* obj_meta;
+    int* obj_slot;                // [16 per object]
     uint8_t* keep_pt5;
     uint8_t* keep_pt3;
     uint8_t* keep_t5;
