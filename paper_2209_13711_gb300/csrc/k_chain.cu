@@ -507,6 +507,7 @@ __global__ void __launch_bounds__(128) k_md_write(Arena A, DevCfg c) {
                 A.md_gmod[t] = u;
                 A.md_p4[t] = make_float4(lx, ly, lz, mi.w < 0.5f ? mi.z : -mi.z);
                 A.md_sr[t] = make_float2(mi.y, m_hypot(lx, ly));
+                A.md_lsc[t] = ls_terms_f32(c, L, mi.x);
                 A.md_dx[t] = ux - lx;
                 A.md_dy[t] = uy - ly;
                 A.md_dphi[t] = dp;
@@ -549,6 +550,7 @@ __global__ void __launch_bounds__(kLsWarps * 32, 3) k_ls(Arena A, DevCfg c) {
         const int e = gm / A.n_mod, m1 = gm - e * A.n_mod;
         const float4 miA = A.mod[m1];
         const Pt<float> P = md_pt_f(A, i, miA);
+        const float4 tP = A.md_lsc[i];
         const float sAx = A.md_dx[i], sAy = A.md_dy[i];
         const int c0 = A.conn_off[m1], c1 = A.conn_off[m1 + 1];
         int cnt = 0;
@@ -568,7 +570,7 @@ __global__ void __launch_bounds__(kLsWarps * 32, 3) k_ls(Arena A, DevCfg c) {
                     const float4 miB = A.mod[S.mod[seg]];
                     Pt<float> Q = md_pt_f(A, B, miB);
                     float dp;
-                    int st = ls_eval<float>(c, P, sAx, sAy, miA, Q, A.md_dx[B], A.md_dy[B], miB, dp);
+                    int st = ls_eval_f32(c, P, tP, sAx, sAy, miA, Q, A.md_lsc[B], A.md_dx[B], A.md_dy[B], miB, dp);
                     if (st == 2) st = ls_retest(A, c, i, B, miA, miB);
                     pass = st == 1;
                 }

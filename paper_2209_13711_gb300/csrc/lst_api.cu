@@ -310,7 +310,7 @@ static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n
     const size_t MD = E * K.md_per_event;
     A.md_cap = (int)MD;
     A.md_lo = b.take<int>(MD); A.md_up = b.take<int>(MD); A.md_gmod = b.take<int>(MD);
-    A.md_p4 = b.take<float4>(MD); A.md_sr = b.take<float2>(MD);
+    A.md_p4 = b.take<float4>(MD); A.md_sr = b.take<float2>(MD); A.md_lsc = b.take<float4>(MD);
     A.md_dx = b.take<float>(MD); A.md_dy = b.take<float>(MD);
     A.md_dphi = b.take<float>(MD); A.md_dlong = b.take<float>(MD);
     A.md_moff = b.take<int>(E * n_mod); A.md_mcnt = b.take<int>(E * n_mod);

@@ -116,6 +116,7 @@ struct Arena {
     int* md_gmod;                 // e * n_mod + module
     float4* md_p4;                // anchor (lower hit) x, y, z and +sig_z (barrel) / -sig_r (endcap)
     float2* md_sr;                // anchor {r-phi resolution, r = sqrtf(x^2 + y^2)}
+    float4* md_lsc;               // FP32 LS terms of the MD (ls_terms_f32)
     float* md_dx;
     float* md_dy;
     float* md_dphi;
@@ -411,6 +412,52 @@ __device__ __forceinline__ int ls_eval(const DevCfg& c, const Pt<T>& P, T sAx, T
     if (mB.w < 0.5f) {
         T ls_ = m_hypot(sBx, sBy);
         T al = m_atan2(sBx * uy - sBy * ux, sBx * ux + sBy * uy);
+        cut(m_abs(al), base + n * (rt2 * Q.srphi / ls_ + (P.sr + Q.sr) / lu));
+    }
+    return cut.state();
+}
+
+// The per-MD terms of the LS test in FP32, computed once when the MD is
+// written: {asinc((r + n sr) a), asinc((r + dsep + n sr) a),
+// asinc(max(0, r - n sr) a), srphi / r}.
+__device__ __forceinline__ float4 ls_terms_f32(const DevCfg& c, const Pt<float>& P, float dsep) {
+    const float a = c.f.a, n = c.f.n_ls;
+    return make_float4(asinc((P.r + n * P.sr) * a), asinc((P.r + dsep + n * P.sr) * a),
+                       asinc(m_max(0.f, P.r - n * P.sr) * a), P.srphi / P.r);
+}
+
+// ls_eval<float> with the per-MD terms of anchor (tP) and candidate (tQ)
+// taken from the MD records; the same cuts in the same order.
+__device__ __forceinline__ int ls_eval_f32(const DevCfg& c, const Pt<float>& P, float4 tP, float sAx, float sAy,
+                                           float4 mA, const Pt<float>& Q, float4 tQ, float sBx, float sBy,
+                                           float4 mB, float& dphi_o) {
+    const float a = c.f.a;
+    const float n = c.f.n_ls;
+    Cuts<float> cut;
+    float num = P.z * Q.r - Q.z * P.r;
+    float den = Q.r - P.r;
+    float sig_num = m_sqrt(sq(Q.r * P.sz) + sq(P.r * Q.sz) + sq(Q.z * P.sr) + sq(P.z * Q.sr));
+    cut(m_abs(num), c.f.z_lumi * m_abs(den) + n * sig_num);
+    float ux = Q.x - P.x, uy = Q.y - P.y;
+    float dphi = m_atan2(P.x * uy - P.y * ux, P.x * Q.x + P.y * Q.y);
+    dphi_o = dphi;
+    if (cut.fail) return 0;
+    const float lo = tP.z;
+    float thr_phi = tQ.x - lo + n * m_sqrt(sq(tP.w) + sq(tQ.w));
+    cut(m_abs(dphi), thr_phi);
+    if (cut.fail) return 0;
+    float lu = m_hypot(ux, uy);
+    float base = tQ.y - lo;
+    const float rt2 = 1.4142135623730951f;
+    if (mA.w < 0.5f) {
+        float ls_ = m_hypot(sAx, sAy);
+        float al = m_atan2(sAx * uy - sAy * ux, sAx * ux + sAy * uy);
+        cut(m_abs(al), base + n * (rt2 * P.srphi / ls_ + (P.sr + Q.sr) / lu));
+        if (cut.fail) return 0;
+    }
+    if (mB.w < 0.5f) {
+        float ls_ = m_hypot(sBx, sBy);
+        float al = m_atan2(sBx * uy - sBy * ux, sBx * ux + sBy * uy);
         cut(m_abs(al), base + n * (rt2 * Q.srphi / ls_ + (P.sr + Q.sr) / lu));
     }
     return cut.state();
