@@ -282,6 +282,7 @@ def run_ours(args):
         "objects_per_event": stats0["counts"],
         "dropped_per_event": stats0["dropped"],
     }
+    out["physics"] = measure_physics(P, ctx, dev, events, st)
     out["batched"] = measure_batched(P, E, geom, maps, DEFAULT_CUTS, flush, st, steps=max(2, min(args.steps, 5)))
     out["mlp"] = measure_mlp(P, E, geom, maps, DEFAULT_CUTS, flush, st, dev)
     out["serving"] = measure_serving(E, geom, maps, DEFAULT_CUTS)
@@ -299,6 +300,27 @@ def autotune(ctx, batch, st, reps=3):
     now = {c["name"]: (c["blocks_per_sm"], c["block"]) for c in ctx.launch_config()}
     changed = {k: {"blocks_per_sm": v[0], "block": v[1]} for k, v in now.items() if v != default[k]}
     return {"stage_sum_ms_default": round(before, 4), "stage_sum_ms_tuned": round(after, 4), "changed": changed}
+
+
+def measure_physics(P, ctx, dev, events, st, n=4):
+    """Efficiency, fake and duplicate rates of the device TCs on generator truth
+    (Section 2.2's figures of merit), pooled over the first n pool events."""
+    from paper_2209_13711_gb300 import metrics as MT
+    out = {}
+    res = {1.0: [], 5.0: []}
+    for i in range(min(n, len(events))):
+        ctx.run_packed(dev[i], stream=st.cuda_stream)
+        off, rec = ctx.batch_track_candidates()
+        tc = P.lst.tc_dict(rec[off[0]:off[1]])
+        ev = events[i]
+        for ptm in res:
+            res[ptm].append(MT.rates(tc, ev.pid, ev.seed_pid, ev.tracks, pt_min=ptm, eta_max=2.4))
+    for ptm, r in res.items():
+        c = MT.combine(r)
+        out[f"pt_ge_{ptm:g}GeV"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in c.items()}
+    out["definition"] = ("TC matched when >= 75% of its hits (seed pixel hits included) come from one particle; "
+                         "findable: generated pT above the bin edge and |eta| <= 2.4")
+    return out
 
 
 def measure_batched(P, E, geom, maps, cuts, flush, st, steps, n_batch=64):

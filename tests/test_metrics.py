@@ -1,0 +1,59 @@
+"""Efficiency / fake / duplicate rates on generator truth (CPU)."""
+import numpy as np
+import pytest
+
+from paper_2209_13711_gb300.metrics import combine, match, rates
+
+
+class _Tracks:
+    def __init__(self, pt, eta):
+        self.pt = np.asarray(pt, float)
+        self.eta = np.asarray(eta, float)
+
+
+def _tc(rows, seeds):
+    hits = np.full((len(rows), 10), -1, np.int32)
+    for i, r in enumerate(rows):
+        hits[i, :len(r)] = r
+    return dict(n=len(rows), hits=hits, seed=np.asarray(seeds, np.int32))
+
+
+def test_match_majority_with_seed_hits():
+    pid = np.array([0] * 10 + [1] * 10 + [-1] * 5)
+    seed_pid = np.array([0, 1, -1])
+    tc = _tc([list(range(10)),                       # 10/10 from particle 0
+              list(range(6)) + list(range(10, 14)),  # 6/10: fake
+              list(range(2, 10)) + [20, 21],         # 8/10 from 0 (noise hits count against)
+              list(range(6)) + list(range(10, 14)),  # 6 + 3 seed hits of 0 = 9/13 = 0.69: fake
+              list(range(10, 18)) + [3, 4],          # 8/10 from 1, seed of 1: 11/13
+              []],                                   # pLS only: the seed's particle
+             [-1, -1, -1, 0, 1, 1])
+    assert list(match(tc, pid, seed_pid)) == [0, -1, 0, -1, 1, 1]
+    assert match(tc, pid, seed_pid, frac=0.6)[1] == 0
+
+
+def test_rates_count_efficiency_fakes_duplicates():
+    pid = np.array([0] * 10 + [1] * 10 + [2] * 10)
+    tr = _Tracks([2.0, 8.0, 0.5], [0.1, -1.0, 0.2])   # particle 2 below pT threshold
+    tc = _tc([list(range(10)), list(range(10)), list(range(20, 30)), [0, 10, 20, 1, 11]], [-1, -1, -1, -1])
+    r = rates(tc, pid, np.zeros(0, np.int32), tr, pt_min=1.0)
+    assert r["findable"] == 2 and r["found"] == 1
+    assert r["efficiency"] == pytest.approx(0.5)
+    assert r["fake_rate"] == pytest.approx(0.25)       # the mixed TC
+    assert r["duplicate_rate"] == pytest.approx(0.25)  # second TC of particle 0
+    c = combine([r, r])
+    assert c["efficiency"] == pytest.approx(0.5) and c["tcs"] == 8 and c["events"] == 2
+
+
+def test_oracle_chain_physics_on_a_pileup_event(geom_full, maps_full):
+    """The chain (oracle) finds most tracks above 2 GeV with few fakes and duplicates."""
+    from oracle import oracle as O
+    from synth import events as E
+    from synth.config import DEFAULT_CUTS
+    ev = E.pileup_event(10, 5, geom_full)
+    o = O.Setup(geom_full.module_table(), maps_full, DEFAULT_CUTS, ev).run()["tc"]
+    tc = dict(n=o["n"], hits=np.stack([o[f"h{i}"] for i in range(10)], 1), seed=o["seed"])
+    r = rates(tc, ev.pid, ev.seed_pid, ev.tracks, pt_min=2.0, eta_max=2.4)
+    assert r["findable"] > 20
+    assert r["efficiency"] > 0.85
+    assert r["fake_rate"] < 0.2 and r["duplicate_rate"] < 0.2
