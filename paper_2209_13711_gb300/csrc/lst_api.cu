@@ -138,19 +138,23 @@ struct lst_ctx {
     } while (0)
 
 // FP32 limits of the fit prefilter: rejected only when a cut fails by far
-// more than FP32 rounding can explain (1.01 kmax + 1e-5; 1.25 chi2_max + 2).
-static FitLimits prefit_limits(const DevCfg& d, double chi2_max, double chi2z_max, float scale) {
+// more than FP32 rounding can explain: |kappa| above 1.01 kmax + 1e-5, a chi2
+// above rel * chi2_max + abs. T5: rel 1.05, abs 0.2 (the FP32 five-point fit's
+// chi2 differs from FP64 by at most 1.3e-3 relative over the 2e6 candidates of
+// a PU200 event); pT5/pT3 (pixel points, 10 um errors): rel 1.25, abs 2.
+static FitLimits prefit_limits(const DevCfg& d, double chi2_max, double chi2z_max, float scale, float rel,
+                               float abs_) {
     const float kmax = float((1.0 + d.tol_r) * 2.0 * d.a);
-    return FitLimits{kmax * 1.01f + 1e-5f, 1.25f * (float(chi2_max) * scale) + 2.f,
-                     1.25f * (float(chi2z_max) * scale) + 2.f};
+    return FitLimits{kmax * 1.01f + 1e-5f, rel * (float(chi2_max) * scale) + abs_,
+                     rel * (float(chi2z_max) * scale) + abs_};
 }
 
 static void derive_fp32(DevCfg& d) {
     d.f = CfgF{float(d.a),    float(d.z_lumi), float(d.n_md), float(d.n_ls),
                float(d.n_t3), float(d.n_t5),   float(d.n_pt), float(d.sig_pix)};
-    d.lim_t5 = prefit_limits(d, d.chi2_rphi_t5, d.chi2_rz_t5, d.prefit_scale);
-    d.lim_pt5 = prefit_limits(d, d.chi2_rphi_pt5, d.chi2_rz_pt5, 1.0f);
-    d.lim_pt3 = prefit_limits(d, d.chi2_rphi_pt3, d.chi2_rz_pt3, 1.0f);
+    d.lim_t5 = prefit_limits(d, d.chi2_rphi_t5, d.chi2_rz_t5, d.prefit_scale, 1.05f, 0.2f);
+    d.lim_pt5 = prefit_limits(d, d.chi2_rphi_pt5, d.chi2_rz_pt5, 1.0f, 1.25f, 2.f);
+    d.lim_pt3 = prefit_limits(d, d.chi2_rphi_pt3, d.chi2_rz_pt3, 1.0f, 1.25f, 2.f);
 }
 
 static DevCfg make_devcfg(const lst_config& c) {

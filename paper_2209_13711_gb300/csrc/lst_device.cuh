@@ -37,7 +37,8 @@ constexpr double kPi = 3.14159265358979323846;
 // Cut constants as seen by the kernels (derived on the host from lst_config).
 // Limits of the conservative FP32 verdict on the fit cuts: a candidate is
 // rejected only when a cut fails by far more than FP32 rounding can explain
-// (|kappa| above 1.01 kmax + 1e-5, a chi2 above 1.25 max + 2).
+// (|kappa| above 1.01 kmax + 1e-5, a chi2 above rel * max + abs; the
+// per-object slack is set on the host).
 struct FitLimits {
     float kappa, chi2, chi2z;
 };
