@@ -477,19 +477,25 @@ __device__ __forceinline__ void ref_eta_phi(const Arena& A, int ref, double& eta
 // threshold.
 __device__ __forceinline__ bool dr_close_warp(const Arena& A, const DevCfg& c, int e, int list, double eta,
                                               double phi) {
+    constexpr int kU = 8;                 // list entries per lane per round: 8 loads in flight
     const int n = min(A.list_cnt[e * 2 + list], A.list_cap);
     const size_t base = ((size_t)e * 2 + list) * A.list_cap;
     const double thr2 = c.dr_clean * c.dr_clean;
     const float thr2f = float(thr2);
     const float ef = float(eta), pf = float(phi);
     const float two_pi = float(2 * kPi);
-    for (int j0 = 0; j0 < n; j0 += 32) {
-        const int j = j0 + lane_id();
+    for (int j0 = 0; j0 < n; j0 += 32 * kU) {
+        float2 v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int j = j0 + 32 * u + lane_id();
+            v[u] = j < n ? A.list_ef[base + j] : make_float2(1e30f, 0.f);
+        }
         bool hit = false;
-        if (j < n) {
-            float2 v = A.list_ef[base + j];
-            float de = v.x - ef;
-            float dp = v.y - pf;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            float de = v[u].x - ef;
+            float dp = v[u].y - pf;
             if (dp > float(kPi)) dp -= two_pi;
             if (dp <= -float(kPi)) dp += two_pi;
             float d2 = de * de + dp * dp;
@@ -497,9 +503,9 @@ __device__ __forceinline__ bool dr_close_warp(const Arena& A, const DevCfg& c, i
                 hit = true;
             } else if (d2 <= thr2f * (1.0f + 1e-3f)) {
                 double e2, p2;
-                ref_eta_phi(A, A.list_ref[base + j], e2, p2);
+                ref_eta_phi(A, A.list_ref[base + j0 + 32 * u + lane_id()], e2, p2);
                 double dd = eta - e2, dq = wrap_pi(phi - p2);
-                hit = dd * dd + dq * dq < thr2;
+                hit = hit || dd * dd + dq * dq < thr2;
             }
         }
         if (__any_sync(kFull, hit)) return true;
