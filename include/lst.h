@@ -18,10 +18,11 @@
  *   seed s of an event owns pixel hits 3s, 3s+1, 3s+2.
  *   Every function returns an lst_status: 0 success, > 0 warning, < 0 error.
  *   Nothing is thrown across the ABI.
- *   Ownership: the caller owns every buffer it passes. Inputs must stay valid
- *   until the call returns (host memory; the library copies them) or until
- *   the stream reaches the work (device memory). The library copies the
- *   geometry and keeps it until lst_destroy.
+ *   Ownership: the caller owns every buffer it passes. Input arrays in
+ *   pageable host memory must stay valid until the call returns (the copy is
+ *   staged during the call); arrays in pinned host memory or device memory
+ *   until the stream reaches the work (the copies are asynchronous). The
+ *   library copies the geometry and keeps it until lst_destroy.
  *   Threading: one context per host thread; a context runs one batch at a
  *   time, and a new lst_run_batch call invalidates the previous results.
  */
@@ -129,7 +130,11 @@ lst_status lst_load_geometry(lst_ctx* ctx, const lst_module* modules, int32_t n_
  * concatenated hits and seeds. mem_is_device = 0: hits and seeds are host
  * pointers and are copied (pinned host memory makes the copy asynchronous);
  * 1: they are device pointers read in place. Returns when the work is
- * enqueued; results are read with lst_get_track_candidates / lst_get_objects. */
+ * enqueued; results are read with lst_get_track_candidates / lst_get_objects.
+ * The chain is one CUDA graph per context, captured on the first call (and
+ * again after a change of launch shapes, stage limits or T5 selection) and
+ * replayed on `cuda_stream`; with profiling on, the kernels are launched
+ * one by one instead. */
 lst_status lst_run_batch(lst_ctx* ctx, const lst_hits* hits, const int32_t* hit_offsets,
                          const lst_seeds* seeds, const int32_t* seed_offsets, int32_t n_events,
                          int32_t mem_is_device, void* cuda_stream);

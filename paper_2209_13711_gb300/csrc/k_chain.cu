@@ -533,13 +533,8 @@ struct LsSmem {
     int stage[kLsStage];
 };
 
-__device__ __forceinline__ Pt<float> md_pt_f(const Arena& A, int i, float4) { return md_point<float>(A, i); }
-__device__ __forceinline__ float4 md_mod(const Arena& A, int i) {
-    int gm = A.md_gmod[i];
-    return A.mod[gm % A.n_mod];
-}
 
-__global__ void __launch_bounds__(kLsWarps * 32, 3) k_ls(Arena A, DevCfg c) {
+__global__ void __launch_bounds__(kLsWarps * 32, 4) k_ls(Arena A, DevCfg c) {
     pdl_begin();
     __shared__ LsSmem sm[kLsWarps];
     LsSmem& S = sm[threadIdx.x >> 5];
@@ -549,7 +544,7 @@ __global__ void __launch_bounds__(kLsWarps * 32, 3) k_ls(Arena A, DevCfg c) {
         const int gm = A.md_gmod[i];
         const int e = gm / A.n_mod, m1 = gm - e * A.n_mod;
         const float4 miA = A.mod[m1];
-        const Pt<float> P = md_pt_f(A, i, miA);
+        const Pt<float> P = md_point<float>(A, i);
         const float4 tP = A.md_lsc[i];
         const float sAx = A.md_dx[i], sAy = A.md_dy[i];
         const int c0 = A.conn_off[m1], c1 = A.conn_off[m1 + 1];
@@ -568,7 +563,7 @@ __global__ void __launch_bounds__(kLsWarps * 32, 3) k_ls(Arena A, DevCfg c) {
                 bool pass = false;
                 if (valid) {
                     const float4 miB = A.mod[S.mod[seg]];
-                    Pt<float> Q = md_pt_f(A, B, miB);
+                    Pt<float> Q = md_point<float>(A, B);
                     float dp;
                     int st = ls_eval_f32(c, P, tP, sAx, sAy, miA, Q, A.md_lsc[B], A.md_dx[B], A.md_dy[B], miB, dp);
                     if (st == 2) st = ls_retest(A, c, i, B, miA, miB);
@@ -610,7 +605,7 @@ struct T3Smem {
     int2 stage[kT3Stage];
 };
 
-__global__ void __launch_bounds__(kT3Warps * 32, 3) k_t3(Arena A, DevCfg c) {
+__global__ void __launch_bounds__(kT3Warps * 32, 4) k_t3(Arena A, DevCfg c) {
     pdl_begin();
     __shared__ T3Smem sm[kT3Warps];
     T3Smem& S = sm[threadIdx.x >> 5];

@@ -5,16 +5,18 @@
 
 namespace lst {
 
-// Per-unit stage sizes: the most objects one unit may produce (occupancy
-// truncation); excess objects are counted as dropped.
+// Per-unit stage sizes. MD, LS and T3: the most objects one unit may produce
+// (occupancy truncation; excess objects are counted as dropped). T5 and pT:
+// shared-memory staging per work item; an item with more survivors is
+// enumerated a second time and written directly, so nothing is dropped.
 constexpr int kMaxHits = 256;     // hits per sensor of one module
 constexpr int kMdStage = 1024;    // MDs per module
 constexpr int kLsStage = 256;     // LS per inner MD
 constexpr int kT3Stage = 512;     // T3 per inner MD
 constexpr int kT5Pre = 256;       // FP32-prefiltered T5 candidates held before an FP64 pass
-constexpr int kT5Stage = 512;     // T5 candidates per inner MD (more: lossless overflow pass)
+constexpr int kT5Stage = 512;     // T5 survivors staged per work item (more: the item is enumerated again)
 constexpr int kPtPre = 128;       // prefiltered pT3/pT5 candidates held before an FP64 pass
-constexpr int kPtStage = 256;     // pT3/pT5 candidates per pixel seed
+constexpr int kPtStage = 256;     // pT3/pT5 survivors staged per work item (more: enumerated again)
 
 constexpr int kMdWarps = 4;
 constexpr int kLsWarps = 8;
