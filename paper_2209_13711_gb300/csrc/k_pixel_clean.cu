@@ -243,9 +243,92 @@ __global__ void __launch_bounds__(kPtWarps * 32, 6) k_pt3(Arena A, DevCfg c) {
     pt_kernel_body<3>(A, c);
 }
 
-// pT5 / pT3 refine (FP64): one thread per searched candidate.
-template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const DevCfg& c) {
-    const int n = min(A.counters[NT == 5 ? 4 : 5], NT == 5 ? A.pt5_cap : A.pt3_cap);
+// A point from lane `src` of this lane's group of 8
+__device__ __forceinline__ Pt<double> shfl_pt8(const Pt<double>& q, int src) {
+    const unsigned F = 0xffffffffu;
+    Pt<double> p;
+    p.x = __shfl_sync(F, q.x, src, 8);
+    p.y = __shfl_sync(F, q.y, src, 8);
+    p.z = __shfl_sync(F, q.z, src, 8);
+    p.r = __shfl_sync(F, q.r, src, 8);
+    p.srphi = __shfl_sync(F, q.srphi, src, 8);
+    p.sz = __shfl_sync(F, q.sz, src, 8);
+    p.sr = __shfl_sync(F, q.sr, src, 8);
+    return p;
+}
+
+// pT5 / pT3 refine, one candidate per group of 8 lanes, one point per lane
+// (fit_track_group): for few candidates (one event), where a thread per
+// candidate would leave the FP64 latency exposed.
+template <int NT> __device__ __forceinline__ void pt_refine_group(Arena& A, const DevCfg& c, int n) {
+    constexpr int N = NT + 3;
+    const int lane = lane_id(), j = lane & 7;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int i0 = warp * 4; i0 < n; i0 += warps * 4) {
+        const int i_raw = i0 + (lane >> 3);
+        const bool valid = i_raw < n;
+        const int i = valid ? i_raw : n - 1;
+        const int g = NT == 5 ? A.pt5_seed[i] : A.pt3_seed[i];
+        const int obj = NT == 5 ? A.pt5_obj[i] : A.pt3_obj[i];
+        const float* sd = A.bd->seeds + 9 * (size_t)g;
+        Pt<double> Q;
+        Pt<float> Qf;
+        if (j >= 3 && j < N) {
+            int m[NT];
+            pt_mds<NT>(A, obj, m);
+            Q = md_point<double>(A, m[j - 3]);
+            Qf = md_point<float>(A, m[j - 3]);
+        } else {
+            const int k = j < 3 ? j : 0;      // lanes past the last point repeat pixel point 0 (unused)
+            Q = pix_pt<double>(sd + 3 * k, c.sig_pix);
+            Qf = pix_pt<float>(sd + 3 * k, c.f.sig_pix);
+        }
+        const double kp = A.pls_kappa[g], sp = A.pls_sigk[g];
+        // the triplet's points for an undecided pT3 curvature test (all lanes shuffle)
+        const Pt<double> T0 = shfl_pt8(Q, 3), T1 = shfl_pt8(Q, 4), T2 = shfl_pt8(Q, 5 < N ? 5 : 3);
+        bool kc;
+        if (NT == 5) {
+            kc = fabs(kp - A.t5_kappa[obj]) <= c.n_pt * sqrt(sq(sp) + sq(A.t5_sigk[obj]));
+        } else {
+            // the triplet's FP32 curvature decides unless undecided; then FP64
+            const float2 ks = A.t3_ks[obj];
+            int k = kappa_test_f32(float(kp), float(sp), ks.x, ks.y, c.f.n_pt);
+            if (k < 0) {
+                Tri<double> tt = tri(T0, T1, T2);
+                k = fabs(kp - tt.kappa) <= c.n_pt * sqrt(sq(sp) + sq(tt.sigk));
+            }
+            kc = k != 0;
+        }
+        const Fit f = fit_track_group<N>(Q, Qf, j);
+        const double chi2_max = NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3;
+        const double chi2z_max = NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3;
+        const bool pass = kc && fabs(f.kappa) <= (1.0 + c.tol_r) * 2.0 * c.a && f.chi2_rphi <= chi2_max &&
+                          f.chi2_rz <= chi2z_max;
+        if (valid && j == 0) {
+            PTOut o{};
+            if (kc) {
+                o.kappa = f.kappa;
+                o.chi2_rphi = f.chi2_rphi;
+                o.chi2_rz = f.chi2_rz;
+                o.score = f.chi2_rphi + f.chi2_rz;
+                o.pt = pt_of(c, f.kappa);
+            }
+            if (NT == 5) {
+                A.pt5_valid[i] = pass; A.pt5_kappa[i] = float(o.kappa); A.pt5_chi2[i] = float(o.chi2_rphi);
+                A.pt5_chi2z[i] = float(o.chi2_rz); A.pt5_score[i] = float(o.score); A.pt5_pt[i] = float(o.pt);
+            } else {
+                A.pt3_valid[i] = pass; A.pt3_kappa[i] = float(o.kappa); A.pt3_chi2[i] = float(o.chi2_rphi);
+                A.pt3_chi2z[i] = float(o.chi2_rz); A.pt3_score[i] = float(o.score); A.pt3_pt[i] = float(o.pt);
+            }
+            if (pass) atomicAdd(&A.ev_counts[event_of(A.seed_off, A.bd->n_ev, g) * 8 + (NT == 5 ? 5 : 6)], 1);
+        }
+    }
+}
+
+// pT5 / pT3 refine, one thread per candidate: for many candidates (batches),
+// where the FP64 pipe is the bound and lanes should not repeat work.
+template <int NT> __device__ __forceinline__ void pt_refine_thread(Arena& A, const DevCfg& c, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int g = NT == 5 ? A.pt5_seed[i] : A.pt3_seed[i];
         const int obj = NT == 5 ? A.pt5_obj[i] : A.pt3_obj[i];
@@ -290,6 +373,16 @@ template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const
         }
         if (pass) atomicAdd(&A.ev_counts[event_of(A.seed_off, A.bd->n_ev, g) * 8 + (NT == 5 ? 5 : 6)], 1);
     }
+}
+
+// Below this many candidates the grouped refine is faster (measured: one
+// PU200 event has ~5k pT5 / ~8k pT3 candidates; 64 events ~50x more).
+constexpr int kPtGroupRefineMax = 16384;
+
+template <int NT> __device__ __forceinline__ void pt_refine_body(Arena& A, const DevCfg& c) {
+    const int n = min(A.counters[NT == 5 ? 4 : 5], NT == 5 ? A.pt5_cap : A.pt3_cap);
+    if (n <= kPtGroupRefineMax) pt_refine_group<NT>(A, c, n);
+    else pt_refine_thread<NT>(A, c, n);
 }
 
 __global__ void k_pt5_refine(Arena A, DevCfg c) {

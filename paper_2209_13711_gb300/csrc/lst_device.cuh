@@ -686,6 +686,96 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
     return f;
 }
 
+// The same fit with one candidate per group of 8 lanes: lane j of the group
+// holds point j (j < N) in FP64 (Q) and FP32 (Qf); the per-point work runs in
+// parallel, the sums are taken with shuffles and every lane of the group
+// returns the fit. For kernels with few candidates, where one thread per
+// candidate would leave the FP64 latency exposed. All 32 lanes must call.
+__device__ __forceinline__ double grp_sum8(double v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
+    return v;
+}
+
+template <int N> __device__ inline Fit fit_track_group(const Pt<double>& Q, const Pt<float>& Qf, int j) {
+    static_assert(N <= 8, "one point per lane of a group of 8");
+    const unsigned F = 0xffffffffu;
+    const bool act = j < N;
+    Fit f;
+    const double x0 = __shfl_sync(F, Q.x, 0, 8), y0 = __shfl_sync(F, Q.y, 0, 8), z0 = __shfl_sync(F, Q.z, 0, 8);
+    const double xn = __shfl_sync(F, Q.x, N - 1, 8), yn = __shfl_sync(F, Q.y, N - 1, 8);
+    const double zn = __shfl_sync(F, Q.z, N - 1, 8);
+    const double ox = __shfl_sync(F, Q.x, N / 2, 8), oy = __shfl_sync(F, Q.y, N / 2, 8);
+    const float oxf = __shfl_sync(F, Qf.x, N / 2, 8), oyf = __shfl_sync(F, Qf.y, N / 2, 8);
+    const double ex = xn - x0, ey = yn - y0;
+    const double il = 1.0 / sqrt(ex * ex + ey * ey);
+    const double xx = ex * il, xy = ey * il, yx = -xy, yy = xx;
+    const double dx = Q.x - ox, dy = Q.y - oy;
+    const double xi = dx * xx + dy * xy, et = dx * yx + dy * yy, rho2 = xi * xi + et * et;
+    const double a = act ? 1.0 : 0.0;
+    double M[3][3], b[3], sol[3] = {0, 0, 0};
+    M[0][0] = grp_sum8(a * rho2 * rho2);
+    M[0][1] = M[1][0] = grp_sum8(a * rho2 * xi);
+    M[0][2] = M[2][0] = grp_sum8(a * rho2);
+    M[1][1] = grp_sum8(a * xi * xi);
+    M[1][2] = M[2][1] = grp_sum8(a * xi);
+    M[2][2] = double(N);
+    b[0] = grp_sum8(a * rho2 * et);
+    b[1] = grp_sum8(a * xi * et);
+    b[2] = grp_sum8(a * et);
+    if (!solve3(M, b, sol)) {
+        f.kappa = 1e30; f.chi2_rphi = 1e30; f.chi2_rz = 1e30; f.tanl = 0;
+        return f;
+    }
+    const double gg = sol[0], hh = sol[1], kk = sol[2];
+    const double S = sqrt(fmax(0.0, 1.0 + hh * hh - 4.0 * gg * kk));
+    f.kappa = 2.0 * gg / S;
+    // residual and error projection of this lane's point (as in fit_track with Pf)
+    double term = 0.0;
+    {
+        const float gf = float(gg), hf = float(hh), Sf = float(S), xxf = float(xx), xyf = float(xy);
+        const float uf = float(gg * rho2 + hh * xi + kk - et);
+        const float e = 2.f * uf / (Sf + sqrtf(fmaxf(0.f, Sf * Sf + 4.f * gf * uf)));
+        if (Qf.sr > 0.f) {
+            const double nlx = 2.0 * gg * xi + hh, nly = 2.0 * gg * et - 1.0;
+            const double nx = nlx * xx - nly * xy, ny = nlx * xy + nly * xx;
+            const double nn2 = nx * nx + ny * ny;
+            const double ir = 1.0 / Q.r;
+            const double rx = Q.x * ir, ry = Q.y * ir;
+            const double n_phi = ny * rx - nx * ry, n_r = nx * rx + ny * ry;
+            const double s2 = fmax(sq(Q.srphi * n_phi) + sq(Q.sr * n_r), sq(0.01 * Q.srphi) * nn2);
+            term = double(e) * double(e) * nn2 / s2;
+        } else {
+            const float dxf = Qf.x - oxf, dyf = Qf.y - oyf;
+            const float xif = dxf * xxf + dyf * xyf, etf = dyf * xxf - dxf * xyf;
+            const float nlx = 2.f * gf * xif + hf, nly = 2.f * gf * etf - 1.f;
+            const float nx = nlx * xxf - nly * xyf, ny = nlx * xyf + nly * xxf;
+            const float nn2 = nx * nx + ny * ny;
+            const float ir = 1.f / Qf.r;
+            const float rx = Qf.x * ir, ry = Qf.y * ir;
+            const float n_phi = ny * rx - nx * ry;
+            const float s2 = fmaxf(sq(Qf.srphi * n_phi), sq(0.01f * Qf.srphi) * nn2);
+            term = double(e * e * nn2 / s2);
+        }
+    }
+    f.chi2_rphi = grp_sum8(act ? term : 0.0);
+    const double ka = fabs(f.kappa);
+    const double sj = arc(sqrt(sq(Q.x - x0) + sq(Q.y - y0)), ka);
+    const double sn = __shfl_sync(F, sj, N - 1, 8);
+    const double t_hat = (zn - z0) / sn;
+    const float tf = float(t_hat);
+    const double w = act ? double(1.f / fmaxf(1e-12f, sq(Qf.sz) + sq(tf * Qf.sr))) : 0.0;
+    const double W = grp_sum8(w), Ws = grp_sum8(w * sj), Wz = grp_sum8(w * Q.z);
+    const double iW = 1.0 / W;
+    const double sbar = Ws * iW, zbar = Wz * iW;
+    const double Sss = grp_sum8(w * sq(sj - sbar)), Ssz = grp_sum8(w * (sj - sbar) * (Q.z - zbar));
+    const double t = Ssz / Sss, c0 = zbar - t * sbar;
+    f.chi2_rz = grp_sum8(w * sq(Q.z - c0 - t * sj));
+    f.tanl = t;
+    return f;
+}
+
 // FP32 twin of fit_track (same chord-frame circle fit, geometric residuals and
 // r-z line fit), evaluated cut by cut: the curvature is tested right after the
 // circle solve, chi2_rphi after the residuals, and the r-z fit runs only for

@@ -159,3 +159,20 @@ def test_truncation_is_counted(geom_full, maps_full):
     tc = ctx.track_candidates(0)
     assert tc["n"] >= 0
     ctx.close()
+
+
+def test_grouped_and_per_thread_refine_agree(geom_full, maps_full):
+    """Four PU200 events in one batch take the per-thread pT refine (more than
+    16384 candidates); each event alone takes the grouped one. Same objects."""
+    evs = [E.pu200_event(70 + i, geom_full) for i in range(4)]
+    ctx = make_context(geom_full, maps_full, max_events=4)
+    ctx.run(evs)
+    assert ctx.counters()[4] > 16384 and ctx.counters()[5] > 16384
+    batched = [_all_tuples(ctx, i) for i in range(4)]
+    one = make_context(geom_full, maps_full, max_events=1)
+    for i, ev in enumerate(evs):
+        one.run([ev])
+        assert one.counters()[4] <= 16384
+        assert _all_tuples(one, 0) == batched[i]
+    ctx.close()
+    one.close()
