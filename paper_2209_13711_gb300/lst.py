@@ -2,8 +2,9 @@
 
 Every step of the chain runs in the CUDA kernels of liblst.so; this module
 packs arrays, passes pointers and unpacks results. Inputs are numpy arrays
-(host memory: the library copies them) or CUDA torch tensors (device memory:
-read in place). Importing this module without a built library raises.
+or pinned CPU tensors (host memory: the library copies them) or CUDA torch
+tensors (device memory: read in place). Calling into it without a built
+library raises LstError.
 """
 from __future__ import annotations
 
