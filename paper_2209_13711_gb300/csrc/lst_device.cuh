@@ -949,8 +949,15 @@ __device__ inline bool t5_eval(const DevCfg& c, const Pt<double>* P, const Pt<fl
     const bool pass = kc && fabs(f.kappa) <= (1.0 + c.tol_r) * 2.0 * c.a && f.chi2_rphi <= c.chi2_rphi_t5 &&
                       f.chi2_rz <= c.chi2_rz_t5;
     if (pass || all_outputs) {
-        o.eta = asinh(f.tanl);
-        o.phi0 = phi0_of(P[0], f.kappa);
+        // direction in FP32 (well conditioned; ~1e-7 rad): eta from the FP64
+        // r-z slope, phi0 from the first anchor and the FP64 curvature
+        o.eta = double(asinhf(float(f.tanl)));
+        const float kf = float(f.kappa);
+        const float turn = asinf(fminf(1.f, fmaxf(0.f, Pf[0].r * fabsf(kf) * 0.5f)));
+        float ph = atan2f(Pf[0].y, Pf[0].x) - (kf < 0.f ? -turn : turn);
+        if (ph > float(kPi)) ph -= float(2 * kPi);
+        if (ph <= -float(kPi)) ph += float(2 * kPi);
+        o.phi0 = double(ph);
         o.pt = pt_of(c, f.kappa);
     }
     return pass;
