@@ -2,15 +2,18 @@
 // segments (LS), triplets (T3) and quintuplets (T5), in the launch order of
 // the paper's Fig. KernelFlow.
 //
-// Work decomposition: one warp per unit (an (event, module) for MDs, an inner
-// MD for LS/T3/T5). A unit evaluates all of its candidates lane-parallel,
-// compacts the passing ones in order into a shared-memory stage with
-// __ballot_sync, reserves one contiguous segment of the flat arena with a
-// single atomicAdd and writes it. The (offset, count) of every unit's
-// segment is kept, so the next stage finds "all LS whose inner MD is B" as
-// one contiguous range. Stage sizes bound the objects one unit may produce
-// (the occupancy truncation of Section 3); anything beyond is counted as
-// dropped, never written out of bounds.
+// Work decomposition: a warp evaluates the candidates of one unit
+// lane-parallel, compacts the passing ones in order into a shared-memory stage
+// with __ballot_sync, reserves one contiguous segment of the flat arena with a
+// single atomicAdd and writes it. The (offset, count) of every unit's segment
+// is kept, so the next stage finds "all LS whose inner MD is B" as one
+// contiguous range. Units: an inner MD for LS and T3 (one warp each); for MD
+// and T5, whose unit costs vary by more than an order of magnitude, work items
+// (chunks of a module's lower hits / of an inner MD's T3) taken from a shared
+// cursor, heavy items first, whose segments a gather kernel concatenates in
+// order. Stage sizes bound the objects one unit may produce (the occupancy
+// truncation of Section 3); anything beyond is counted as dropped, never
+// written out of bounds (T5 items instead enumerate again and lose nothing).
 #include "lst_kernels.cuh"
 #include "lst_warp.cuh"
 
@@ -127,7 +130,8 @@ __global__ void k_bin_scatter(Arena A) {
 }
 
 // ---------------------------------------------------------------------------
-// MD: one warp per (event, module)
+// MD, one warp per (event, module): the allocation-free entry point's kernel
+// (the chain uses the work items below)
 // ---------------------------------------------------------------------------
 struct MdSmem {
     float lx[kMaxHits], ly[kMaxHits], lz[kMaxHits];
@@ -673,9 +677,9 @@ __global__ void __launch_bounds__(kT3Warps * 32, 4) k_t3(Arena A, DevCfg c) {
 }
 
 // ---------------------------------------------------------------------------
-// T5: one warp per inner MD A; candidates = (T3_1 from A) x (T3_2 from T3_1's
-// outer MD). FP32 curvature prefilter (conservative), then the full test in
-// FP64 for the survivors.
+// T5: candidates = (T3_1 from inner MD A) x (T3_2 from T3_1's outer MD), in
+// work items of 8-32 T3_1. FP32 curvature and fit prefilters (conservative),
+// then the full test in FP64 for the survivors (k_t5_refine).
 // ---------------------------------------------------------------------------
 struct T5Smem {
     int pre[32], off[32], t1[32];
