@@ -934,6 +934,7 @@ __global__ void k_t5_refine(Arena A, DevCfg c) {
         A.t5_cut[i] = pass;
         A.t5_kappa[i] = o.kappa;
         A.t5_sigk[i] = o.sigk;
+        A.t5_ks[i] = make_float2(float(o.kappa), float(o.sigk));
         A.t5_eta[i] = o.eta;
         A.t5_phi[i] = o.phi0;
         A.t5_chi2[i] = float(o.chi2_rphi);

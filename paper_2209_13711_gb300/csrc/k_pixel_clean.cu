@@ -135,15 +135,8 @@ __device__ __forceinline__ void pt_enumerate(const Arena& A, const DevCfg& c, Pt
         for_each_flat(oo, on, S.pre2, S.off2, [&](bool valid, int, int obj) {
             bool pass = false;
             if (valid && (NT == 3 || A.t5_valid[obj])) {
-                float kt, st;
-                if (NT == 5) {
-                    kt = float(A.t5_kappa[obj]);
-                    st = float(A.t5_sigk[obj]);
-                } else {
-                    const float2 ks = A.t3_ks[obj];
-                    kt = ks.x;
-                    st = ks.y;
-                }
+                const float2 ks = NT == 5 ? A.t5_ks[obj] : A.t3_ks[obj];
+                const float kt = ks.x, st = ks.y;
                 float thr = nk * sqrtf(sp * sp + st * st);
                 pass = fabsf(kp - kt) <= thr * 1.01f + 1e-5f * (fabsf(kp) + fabsf(kt)) + 1e-7f;
             }

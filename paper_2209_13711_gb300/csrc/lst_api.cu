@@ -341,6 +341,7 @@ static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n
     A.t5_pt = b.take<float>(T5); A.t5_valid = b.take<uint8_t>(T5); A.t5_cut = b.take<uint8_t>(T5);
     A.t5_feat = b.take<float>(48 * T5); A.t5_mlp = b.take<float>(T5);
     A.t5_off = b.take<int>(MD); A.t5_cnt = b.take<int>(MD);
+    A.t5_ks = b.take<float2>(T5);
     A.t5_items = b.take<int>(T3); A.t5_chunk_off = b.take<int>(T3); A.t5_chunk_cnt = b.take<int>(T3);
     A.t5_tmp = b.take<int2>(T5);
     A.pls_pass = b.take<int>(S); A.pls_sb = b.take<int>(S);

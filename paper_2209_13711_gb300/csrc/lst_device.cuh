@@ -162,6 +162,7 @@ struct Arena {
     uint8_t* t5_cut;              // the hand-set cuts passed (== t5_valid without the network)
     float* t5_feat;               // [t5_cap][48] scoring features
     float* t5_mlp;                // network score
+    float2* t5_ks;                // FP32 {curvature, sigma} of each T5 (the pT5 search's prefilter)
     int* t5_off;                  // [md_cap] by inner MD
     int* t5_cnt;
     // T5 search work items: chunks of 8, 16 or 32 T3_1 of one inner MD,
