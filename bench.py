@@ -116,19 +116,21 @@ def whole_job_rate(ws, steps, seconds):
     return ws * steps / seconds
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when there is none or the kernel's sources changed since it was taken."""
+def measured_counters(kernel):
+    """Per-launch ncu counters of `kernel` from the committed profile
+    summaries (their machine-readable blocks), merged; a block whose kernel
+    sources changed since its capture is skipped."""
     import glob
     import hashlib
-    for fn in sorted(glob.glob(os.path.join(ROOT, "profiles", "*_traffic.md"))):
+    out = {}
+    for fn in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         kv = {}
         with open(fn) as f:
             for line in f:
-                if ":" in line and not line.startswith(("|", "#", "`")):
+                if ":" in line and not line.startswith(("|", "#", "`", " ", "*")):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("kernel") != kernel or "dram_bytes_per_launch" not in kv:
+        if kv.get("kernel") != kernel or "sources_sha256" not in kv:
             continue
         h = hashlib.sha256()
         try:
@@ -136,11 +138,20 @@ def measured_traffic(kernel):
                 with open(os.path.join(ROOT, src), "rb") as f:
                     h.update(f.read())
         except OSError:
-            return None
-        if h.hexdigest() != kv.get("sources_sha256"):
-            return None
-        return int(kv["dram_bytes_per_launch"])
-    return None
+            continue
+        if h.hexdigest() != kv["sources_sha256"]:
+            continue
+        for k, v in kv.items():
+            if k.endswith("_per_launch"):
+                out[k] = float(v)
+    return out
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when there is none or the kernel's sources changed since it was taken."""
+    v = measured_counters(kernel).get("dram_bytes_per_launch")
+    return None if v is None else int(v)
 
 
 def _peaks():
@@ -172,6 +183,7 @@ def run_ours(args):
     import torch
 
     import paper_2209_13711_gb300 as P
+    from paper_2209_13711_gb300.metrics import candidate_tests
     from synth import events as E, geometry as G, maps as M
     from synth.config import DEFAULT_CUTS
 
@@ -201,6 +213,8 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    # ---- the device's FP32 / FP64 / atomic rates (calibration, untimed) --
+    peaks = P.measure_peaks(local)
     # ---- launch shapes tuned on a warm-up event (setup, untimed) ---------
     tune = autotune(ctx, dev[0], st)
     # ---- device-timed: inputs resident in HBM ---------------------------
@@ -239,14 +253,19 @@ def run_ours(args):
         d2h += off.nbytes + rec.nbytes
     # ---- per-kernel device times (profiling pass, same workload) --------
     ctx.set_profiling(True)
-    per_kernel = {}
-    for i in range(min(args.steps, 5)):
+    per_kernel, tests = {}, []
+    n_prof = min(args.steps, 5)
+    for i in range(n_prof):
         flush.fill_(i & 0xff)
         ctx.run_packed(dev[pick(args.warmup + i)], stream=st.cuda_stream)
         for name, ms in ctx.kernel_times():
             per_kernel.setdefault(name, []).append(ms)
+        e = events[pick(args.warmup + i)]
+        objs = {k: ctx.objects(k, 0) for k in ("md", "ls", "t3", "t5", "pls")}
+        tests.append(candidate_tests(objs, e.module, e.side, *maps, geom.n_mod))
     ctx.set_profiling(False)
     kavg = {k: sum(v) / len(v) for k, v in per_kernel.items()}
+    tests_ev = {k: sum(t[k] for t in tests) / n_prof for k in tests[0]}
     top = max(kavg, key=kavg.get)
     # timing across ranks
     dev_ms, e2e_s = max_over_ranks([dev_ms, e2e_s], ws)
@@ -264,6 +283,29 @@ def run_ours(args):
         roof = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 5), "traffic": measured_traffic(top), "peak_source": peak_kind,
                 "algorithmic_bytes": int(b_alg), "kernel_ms": round(kavg[top], 4)}
+    cnt = measured_counters(top)
+    alu = atomics = None
+    if "fp32_flop_per_launch" in cnt:
+        a = cnt["fp32_flop_per_launch"] / (kavg[top] / 1e3) / 1e12
+        alu = {"kernel": top, "bound": "alu", "achieved": round(a, 3), "peak": round(peaks["fp32_tflops"], 2),
+               "unit": "TFLOP/s", "frac": round(a / peaks["fp32_tflops"], 4),
+               "peak_source": "measured (lst_measure_peaks FFMA probe)",
+               "fp32_flop_per_launch": int(cnt["fp32_flop_per_launch"]),
+               "fp64_flop_per_launch": int(cnt.get("fp64_flop_per_launch", 0))}
+    if "atom_inst_per_launch" in cnt:
+        n_at = cnt["atom_inst_per_launch"] + cnt.get("red_inst_per_launch", 0.0)
+        a = n_at / (kavg[top] / 1e3) / 1e9
+        atomics = {"kernel": top, "achieved": round(a, 4), "peak": round(peaks["atom_warp_gops"], 3),
+                   "unit": "G atomic instructions/s", "frac": round(a / peaks["atom_warp_gops"], 5),
+                   "peak_source": "measured (lst_measure_peaks, single-lane atomics on distinct lines)",
+                   "atomic_inst_per_launch": int(n_at)}
+    stage_of = {"md": "md", "ls": "ls", "t3": "t3", "t5": "t5", "pt5": "pt5", "pt3": "pt3"}
+    cand = {"per_event": {k: int(v) for k, v in tests_ev.items()},
+            "per_s": {k: round(v / (kavg[stage_of[k]] / 1e3), 1) for k, v in tests_ev.items()
+                      if kavg.get(stage_of[k])},
+            "chain_per_s": round(sum(tests_ev.values()) / (dev_ms / args.steps / 1e3), 1),
+            "definition": "candidates put to each stage's predicates (metrics.candidate_tests), mean over "
+                          f"the {n_prof} profiled events; per_s divides by the stage's search-kernel time"}
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
@@ -278,6 +320,10 @@ def run_ours(args):
         "autotune": tune,
         "clocks": clk.summary(),
         "roofline": roof,
+        "alu_roofline": alu,
+        "atomics": atomics,
+        "candidate_tests": cand,
+        "peaks_probe": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in peaks.items() if k != "ms"},
         "kernel_ms": {k: round(v, 4) for k, v in sorted(kavg.items(), key=lambda kv: -kv[1])},
         "objects_per_event": stats0["counts"],
         "dropped_per_event": stats0["dropped"],

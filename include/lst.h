@@ -345,6 +345,31 @@ lst_status lst_set_t5_selection(lst_ctx* ctx, const lst_mlp* mlp, float threshol
 lst_status lst_get_t5_candidates(lst_ctx* ctx, int32_t event, int32_t capacity, int32_t* n_out, float* features,
                                  int32_t* hits, int32_t* cut_pass, float* score);
 
+/* ---- calibration (measurement support; not on the track-finding path) ----
+ * Rates of the device measured with the library's own kernels, the
+ * denominators of the per-kernel ALU and atomic fractions:
+ *   fp32_tflops / fp64_tflops: FMA chains (2 flops per lane and FMA),
+ *     8 (FP32) or 4 (FP64) independent chains per thread;
+ *   atom_warp_gops: single-lane atomicAdd instructions with a used return,
+ *     one per warp and iteration, each on its own 128-byte line (the form of
+ *     the chain's warp-aggregated counters), per second, in 1e9;
+ *   atom_same_gops: the same on one address shared by every warp;
+ *   red_lane_gops: per-lane atomicAdd without a used return (reductions) to
+ *     consecutive words;
+ *   ms: best of three launches of each probe, in that order; sm_count;
+ *   clock_khz: the device's reported maximum SM clock.
+ * Each probe runs 8 blocks of 256 threads per SM for a fixed number of
+ * iterations. Synchronous; allocates and frees 16 MB on `device` (which
+ * becomes the calling thread's current device). LST_ERR_ARG for a negative
+ * device or a NULL out, LST_ERR_OOM / LST_ERR_CUDA on a failed call. */
+typedef struct lst_peaks {
+    double fp32_tflops, fp64_tflops;
+    double atom_warp_gops, atom_same_gops, red_lane_gops;
+    float ms[5];
+    int32_t sm_count, clock_khz;
+} lst_peaks;
+lst_status lst_measure_peaks(int32_t device, lst_peaks* out);
+
 /* Message of a status code (static storage). */
 const char* lst_status_str(lst_status s);
 

@@ -61,6 +61,12 @@ class LstStats(C.Structure):
     _fields_ = [("counts", C.c_int32 * 8), ("dropped", C.c_int32 * 8)]
 
 
+class LstPeaks(C.Structure):
+    _fields_ = [("fp32_tflops", C.c_double), ("fp64_tflops", C.c_double), ("atom_warp_gops", C.c_double),
+                ("atom_same_gops", C.c_double), ("red_lane_gops", C.c_double), ("ms", C.c_float * 5),
+                ("sm_count", C.c_int32), ("clock_khz", C.c_int32)]
+
+
 class LstError(RuntimeError):
     pass
 
@@ -116,12 +122,13 @@ def library():
         L.lst_set_t5_selection.argtypes = [vp, vp, C.c_float, C.c_float, i32]
         L.lst_get_t5_candidates.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
         L.lst_get_kernel_times.argtypes = [vp, i32, vp, vp, vp]
+        L.lst_measure_peaks.argtypes = [i32, vp]
         for f in ("lst_config_default", "lst_capacity_default", "lst_create", "lst_load_geometry", "lst_run_batch",
                   "lst_run_event", "lst_get_track_candidates", "lst_object_columns", "lst_get_objects",
                   "lst_get_stats", "lst_last_launch_count", "lst_set_profiling", "lst_get_kernel_times",
                   "lst_get_counters", "lst_mlp_create", "lst_mlp_set_params", "lst_mlp_get_params",
                   "lst_mlp_forward", "lst_mlp_gradient", "lst_mlp_train_step", "lst_set_t5_selection",
-                  "lst_get_t5_candidates"):
+                  "lst_get_t5_candidates", "lst_measure_peaks"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -170,6 +177,16 @@ def default_capacity(max_events=1, **overrides):
     for n, v in overrides.items():
         setattr(k, n, int(v))
     return k
+
+
+def measure_peaks(device=0):
+    """The device's FP32/FP64 FMA and global atomic rates, measured by the
+    library's calibration kernels (lst_measure_peaks), as a dict."""
+    p = LstPeaks()
+    _check(library().lst_measure_peaks(device, C.byref(p)))
+    return {"fp32_tflops": p.fp32_tflops, "fp64_tflops": p.fp64_tflops, "atom_warp_gops": p.atom_warp_gops,
+            "atom_same_gops": p.atom_same_gops, "red_lane_gops": p.red_lane_gops, "ms": list(p.ms),
+            "sm_count": p.sm_count, "clock_mhz": p.clock_khz / 1000.0}
 
 
 def pack_events(events):

@@ -11,6 +11,11 @@ truth instead of CMS simulation:
   at least one TC is matched to;
 * duplicate rate: the fraction of TCs matched to a particle that an earlier
   TC is already matched to.
+
+`candidate_tests` counts the combinatorics of one event: how many candidates
+each stage's kernel puts to its predicates (Section 2.1: every hit pair of a
+module, every MD pair of connected modules, every pair of objects sharing an
+MD, every passing pLS against the objects of its superbin's modules).
 """
 from __future__ import annotations
 
@@ -66,3 +71,54 @@ def combine(per_event):
                 fake_rate=sum(r["fake_rate"] * r["tcs"] for r in per_event) / max(1, tcs),
                 duplicate_rate=sum(r["duplicate_rate"] * r["tcs"] for r in per_event) / max(1, tcs),
                 tcs=tcs, findable=fnd, events=len(per_event))
+
+
+def _csr_sums(off, tgt, w):
+    """Per row r of a CSR map: sum of w[t] over its targets t."""
+    cs = np.concatenate([[0], np.cumsum(w[np.asarray(tgt, np.int64)], dtype=np.int64)])
+    off = np.asarray(off, np.int64)
+    return cs[off[1:]] - cs[off[:-1]]
+
+
+def candidate_tests(obj, hit_module, hit_side, conn_off, conn_tgt, sb_off, sb_tgt, n_mod):
+    """Candidates put to each stage's predicates in one event.
+
+    obj: the event's objects by kind ("md", "ls", "t3", "t5", "pls"), with the
+    columns of lst_get_objects; hit_module / hit_side: the event's hits;
+    conn_*: module connectivity CSR; sb_*: superbin -> modules CSR.
+      md:  lower x upper hits of each module;
+      ls:  each MD x the MDs of the modules its module connects to;
+      t3:  each LS x the LS whose inner MD is its outer MD;
+      t5:  each T3 x the T3 whose inner MD is its outer MD;
+      pt5 / pt3: each passing pLS x the T5 / T3 whose inner MD lies in a module
+           of the pLS's superbin.
+    """
+    hit_module = np.asarray(hit_module, np.int64)
+    side = np.asarray(hit_side)
+    lo = np.bincount(hit_module[side == 0], minlength=n_mod).astype(np.int64)
+    up = np.bincount(hit_module[side == 1], minlength=n_mod).astype(np.int64)
+    md, ls, t3, t5, pls = obj["md"], obj["ls"], obj["t3"], obj["t5"], obj["pls"]
+    n_md = int(md["n"])
+    md_mod = np.asarray(md["mod"], np.int64) % n_mod
+    md_per_mod = np.bincount(md_mod, minlength=n_mod).astype(np.int64)
+    ls_in, ls_out = np.asarray(ls["md_in"], np.int64), np.asarray(ls["md_out"], np.int64)
+    ls_from = np.bincount(ls_in, minlength=n_md).astype(np.int64)
+    t3_inner = ls_in[np.asarray(t3["ls_in"], np.int64)]
+    t3_outer = ls_out[np.asarray(t3["ls_out"], np.int64)]
+    t3_from = np.bincount(t3_inner, minlength=n_md).astype(np.int64)
+    t5_inner = t3_inner[np.asarray(t5["t3_in"], np.int64)]
+    t5_from = np.bincount(t5_inner, minlength=n_md).astype(np.int64)
+    sb = np.asarray(pls["sb"], np.int64)[(np.asarray(pls["pass"]) != 0) & (np.asarray(pls["sb"]) >= 0)]
+
+    def per_sb(from_md):
+        per_mod = np.bincount(md_mod, weights=from_md, minlength=n_mod).astype(np.int64)
+        return _csr_sums(sb_off, sb_tgt, per_mod)
+
+    return {
+        "md": int((lo * up).sum()),
+        "ls": int((md_per_mod * _csr_sums(conn_off, conn_tgt, md_per_mod)).sum()),
+        "t3": int(ls_from[ls_out].sum()),
+        "t5": int(t3_from[t3_outer].sum()),
+        "pt5": int(per_sb(t5_from)[sb].sum()),
+        "pt3": int(per_sb(t3_from)[sb].sum()),
+    }
