@@ -329,6 +329,7 @@ def run_ours(args):
         "dropped_per_event": stats0["dropped"],
     }
     out["physics"] = measure_physics(P, ctx, dev, events, st)
+    out["streams"] = measure_streams(P, geom, maps, DEFAULT_CUTS, dev, st)
     out["batched"] = measure_batched(P, E, geom, maps, DEFAULT_CUTS, flush, st, steps=max(2, min(args.steps, 5)))
     out["mlp"] = measure_mlp(P, E, geom, maps, DEFAULT_CUTS, flush, st, dev)
     out["serving"] = measure_serving(E, geom, maps, DEFAULT_CUTS)
@@ -348,12 +349,14 @@ def autotune(ctx, batch, st, reps=3):
     return {"stage_sum_ms_default": round(before, 4), "stage_sum_ms_tuned": round(after, 4), "changed": changed}
 
 
-def measure_physics(P, ctx, dev, events, st, n=4):
+def measure_physics(P, ctx, dev, events, st, n=16):
     """Efficiency, fake and duplicate rates of the device TCs on generator truth
-    (Section 2.2's figures of merit), pooled over the first n pool events."""
+    (Section 2.2's figures of merit), pooled over the first n pool events, and
+    the same binned in pT and eta and split by TC type."""
     from paper_2209_13711_gb300 import metrics as MT
     out = {}
     res = {1.0: [], 5.0: []}
+    per_event = []
     for i in range(min(n, len(events))):
         ctx.run_packed(dev[i], stream=st.cuda_stream)
         off, rec = ctx.batch_track_candidates()
@@ -361,11 +364,49 @@ def measure_physics(P, ctx, dev, events, st, n=4):
         ev = events[i]
         for ptm in res:
             res[ptm].append(MT.rates(tc, ev.pid, ev.seed_pid, ev.tracks, pt_min=ptm, eta_max=2.4))
+        per_event.append((tc, ev.pid, ev.seed_pid, ev.tracks))
     for ptm, r in res.items():
         c = MT.combine(r)
         out[f"pt_ge_{ptm:g}GeV"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in c.items()}
+    cv = MT.curves(per_event)
+    for t in cv["by_type"].values():
+        t["fake_rate"], t["duplicate_rate"] = round(t["fake_rate"], 4), round(t["duplicate_rate"], 4)
+    out["curves"] = cv
     out["definition"] = ("TC matched when >= 75% of its hits (seed pixel hits included) come from one particle; "
                          "findable: generated pT above the bin edge and |eta| <= 2.4")
+    return out
+
+
+def measure_streams(P, geom, maps, cuts, dev, st, n_events=96, streams=(1, 2, 4, 8)):
+    """The paper's multi-stream comparison (Section 2.2: 1 vs 8 CUDA streams):
+    one PU200 event per launch sequence, with n contexts each on its own
+    stream running different events at once, L2 not flushed (the streams
+    overlap). events/s = events / wall time on the device."""
+    import torch
+    out = {}
+    ctxs = [P.Context(geom.module_table(), maps, cfg=cuts, capacity=P.default_capacity(1)) for _ in range(max(streams))]
+    sts = [torch.cuda.Stream() for _ in ctxs]
+    for c, s in zip(ctxs, sts):                      # capture every context's graph
+        c.run_packed(dev[0], stream=s.cuda_stream)
+    torch.cuda.synchronize()
+    for n in streams:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for s in sts[:n]:
+            s.wait_event(e0)
+        for i in range(n_events):
+            ctxs[i % n].run_packed(dev[i % len(dev)], stream=sts[i % n].cuda_stream)
+        for s in sts[:n]:
+            st.wait_stream(s)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[f"{n}_streams"] = round(n_events / (ms / 1e3), 1)
+    for c in ctxs:
+        c.close()
+    out["unit"] = "events/s"
+    out["events"] = n_events
     return out
 
 

@@ -63,6 +63,65 @@ def rates(tc, pid, seed_pid, tracks, pt_min=1.0, eta_max=2.4, frac=0.75):
                 duplicate_rate=dup / max(1, n_tc), tcs=n_tc, findable=int(len(findable)), found=int(found))
 
 
+PT_EDGES = (0.5, 0.8, 1.0, 1.5, 2.0, 3.0, 5.0, 10.0, 20.0, 50.0, 100.0)
+ETA_EDGES = tuple(round(-2.4 + 0.4 * i, 1) for i in range(13))
+TC_TYPES = ("pT5", "pT3", "T5", "pLS")
+
+
+def curves(per_event, pt_min=1.0, eta_max=2.4, frac=0.75, pt_edges=PT_EDGES, eta_edges=ETA_EDGES):
+    """Binned figures of merit over several events (Section 2.2's plots).
+
+    per_event: (tc, pid, seed_pid, tracks) per event; tc as in rates(), plus
+    its "type" (0 pT5, 1 pT3, 2 T5, 3 pLS), "pt" and "eta".
+      efficiency vs generated pT (|eta| <= eta_max) and vs generated eta
+        (pT >= pt_min): found / findable per bin;
+      fake and duplicate rates vs the TC's own pT and eta: per bin of TCs;
+      by TC type: TC count, fake and duplicate rates.
+    Each bin holds [numerator, denominator]; bins are [lo, hi)."""
+    pe, ee = np.asarray(pt_edges, float), np.asarray(eta_edges, float)
+    z = lambda e: np.zeros((len(e) - 1, 2), np.int64)
+    eff_pt, eff_eta, fake_pt, fake_eta, dup_pt, dup_eta = z(pe), z(ee), z(pe), z(ee), z(pe), z(ee)
+    by_type = {t: [0, 0, 0] for t in TC_TYPES}        # TCs, fakes, duplicates
+
+    def add(h, edges, x, num):
+        b = np.searchsorted(edges, x, side="right") - 1
+        ok = (b >= 0) & (b < len(edges) - 1)
+        np.add.at(h[:, 1], b[ok], 1)
+        np.add.at(h[:, 0], b[ok], np.asarray(num, np.int64)[ok])
+
+    for tc, pid, seed_pid, tracks in per_event:
+        m = match(tc, pid, seed_pid, frac)
+        found = np.zeros(len(tracks.pt), bool)
+        found[m[m >= 0]] = True
+        gpt, geta = np.asarray(tracks.pt, float), np.asarray(tracks.eta, float)
+        sel = np.abs(geta) <= eta_max
+        add(eff_pt, pe, gpt[sel], found[sel])
+        sel = gpt >= pt_min
+        add(eff_eta, ee, geta[sel], found[sel])
+        seen, dup = set(), np.zeros(len(m), bool)
+        for i, p in enumerate(m):
+            if p >= 0:
+                dup[i] = p in seen
+                seen.add(int(p))
+        fake = m < 0
+        tpt, teta = np.asarray(tc["pt"], float), np.asarray(tc["eta"], float)
+        add(fake_pt, pe, tpt, fake)
+        add(fake_eta, ee, teta, fake)
+        add(dup_pt, pe, tpt, dup)
+        add(dup_eta, ee, teta, dup)
+        for t, name in enumerate(TC_TYPES):
+            k = np.asarray(tc["type"]) == t
+            by_type[name][0] += int(k.sum())
+            by_type[name][1] += int((k & fake).sum())
+            by_type[name][2] += int((k & dup).sum())
+    L = lambda h: h.tolist()
+    return dict(pt_edges=list(pe), eta_edges=list(ee), efficiency_vs_pt=L(eff_pt), efficiency_vs_eta=L(eff_eta),
+                fake_vs_pt=L(fake_pt), fake_vs_eta=L(fake_eta), duplicate_vs_pt=L(dup_pt),
+                duplicate_vs_eta=L(dup_eta),
+                by_type={t: dict(tcs=v[0], fake_rate=v[1] / max(1, v[0]), duplicate_rate=v[2] / max(1, v[0]))
+                         for t, v in by_type.items()})
+
+
 def combine(per_event):
     """Pool the counts of several events' rates() results."""
     tcs = sum(r["tcs"] for r in per_event)

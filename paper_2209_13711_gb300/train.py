@@ -30,29 +30,49 @@ def label_candidates(cand, pid):
     return true, np.where(true, p[:, 0], -1)
 
 
-def collect(ctx, events, batch=16, stream=None):
-    """Features, labels, cut decisions and particle ids of every T5 candidate."""
+def collect(ctx, events, batch=16, stream=None, device=False):
+    """Features, labels, cut decisions and particle ids of every T5 candidate.
+
+    events: a list of events or an iterable of them (a generator keeps only one
+    batch of events on the host). device=True moves each event's features to
+    the GPU as it is read, so the training set is held in device memory and
+    the host holds one event's features at a time."""
+    import itertools
     X, y, cut, part, ev_idx = [], [], [], [], []
-    for b0 in range(0, len(events), batch):
-        chunk = events[b0:b0 + batch]
+    it, b0 = iter(events), 0
+    while True:
+        chunk = list(itertools.islice(it, batch))
+        if not chunk:
+            break
         ctx.run(chunk, stream=stream)
         for j, ev in enumerate(chunk):
             c = ctx.t5_candidates(j)
             t, p = label_candidates(c, ev.pid)
-            X.append(c["features"])
+            if device:
+                import torch
+                X.append(torch.from_numpy(c["features"]).cuda())
+            else:
+                X.append(c["features"])
             y.append(t.astype(np.float32))
             cut.append(c["cut_pass"])
             part.append(p)
             ev_idx.append(np.full(len(t), b0 + j))
+        b0 += len(chunk)
     cat = np.concatenate
-    return dict(X=cat(X), y=cat(y), cut=cat(cut), particle=cat(part), event=cat(ev_idx))
+    if device:
+        import torch
+        Xc = torch.cat(X)
+        X.clear()
+    else:
+        Xc = cat(X)
+    return dict(X=Xc, y=cat(y), cut=cat(cut), particle=cat(part), event=cat(ev_idx))
 
 
 def train(mlp, X, y, epochs=4, batch=4096, lr=2e-3, seed=0, log=None):
     import torch
     rng = np.random.default_rng(seed)
     n = len(y)
-    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    Xd = X if torch.is_tensor(X) else torch.from_numpy(np.ascontiguousarray(X)).cuda()
     yd = torch.from_numpy(np.ascontiguousarray(y)).cuda()
     hist = []
     for ep in range(epochs):
@@ -74,7 +94,7 @@ def train(mlp, X, y, epochs=4, batch=4096, lr=2e-3, seed=0, log=None):
 
 def scores_of(mlp, X):
     import torch
-    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    Xd = X if torch.is_tensor(X) else torch.from_numpy(np.ascontiguousarray(X)).cuda()
     out = torch.zeros(len(X), device="cuda")
     mlp.forward(Xd, out)
     torch.cuda.synchronize()
@@ -130,11 +150,8 @@ def main(argv=None):
     ctx = L.Context(geom.module_table(), maps, cfg=DEFAULT_CUTS, capacity=L.default_capacity(16))
     ctx.set_t5_selection(None, prefilter_scale=args.prefilter_scale, capture_features=True)
     t0 = time.time()
-    tr_events = [E.pu200_event(10000 + i, geom) for i in range(args.train_events)]
-    tr = collect(ctx, tr_events)
-    del tr_events
-    ev_events = [E.pu200_event(20000 + i, geom) for i in range(args.eval_events)]
-    va = collect(ctx, ev_events)
+    tr = collect(ctx, (E.pu200_event(10000 + i, geom) for i in range(args.train_events)), device=True)
+    va = collect(ctx, [E.pu200_event(20000 + i, geom) for i in range(args.eval_events)])
     print(f"samples: train {len(tr['y'])} ({tr['y'].mean():.3f} true), eval {len(va['y'])}; "
           f"{time.time() - t0:.1f} s", flush=True)
     mlp = L.Mlp(max_batch=4096, params=init_params(args.seed))
@@ -143,6 +160,8 @@ def main(argv=None):
     print(f"training: {time.time() - t1:.1f} s", flush=True)
     res = evaluate(mlp, va)
     res["loss_history"] = hist
+    res["train_events"], res["eval_events"] = args.train_events, args.eval_events
+    res["samples_train"], res["samples_eval"] = int(len(tr["y"])), int(len(va["y"]))
     np.save(args.out, mlp.params())
     print(json.dumps(res))
 

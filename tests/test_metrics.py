@@ -57,3 +57,28 @@ def test_oracle_chain_physics_on_a_pileup_event(geom_full, maps_full):
     assert r["findable"] > 20
     assert r["efficiency"] > 0.85
     assert r["fake_rate"] < 0.2 and r["duplicate_rate"] < 0.2
+
+
+def test_curves_bin_counts_agree_with_rates():
+    from paper_2209_13711_gb300.metrics import curves
+    pid = np.array([0] * 10 + [1] * 10 + [2] * 10)
+    tr = _Tracks([2.0, 8.0, 0.5], [0.1, -1.0, 0.2])
+    tc = _tc([list(range(10)), list(range(10)), list(range(20, 30)), [0, 10, 20, 1, 11]], [-1, -1, -1, 5])
+    tc.update(type=np.array([2, 2, 2, 1]), pt=np.array([2.1, 1.9, 0.6, 30.0]), eta=np.array([0.1, 0.1, 0.2, 2.0]))
+    c = curves([(tc, pid, np.full(6, -1, np.int32), tr)])
+    pe = c["pt_edges"]
+    eff = np.array(c["efficiency_vs_pt"])
+    # generated pT 2.0 -> bin [2, 3), 8.0 -> [5, 10), 0.5 -> [0.5, 0.8); particle 1 only in the mixed TC (a fake)
+    assert eff[pe.index(2.0)].tolist() == [1, 1] and eff[pe.index(5.0)].tolist() == [0, 1]
+    assert eff[pe.index(0.5)].tolist() == [1, 1] and eff[:, 1].sum() == 3
+    # efficiency vs eta only for pT >= 1: two particles
+    assert np.array(c["efficiency_vs_eta"])[:, 1].sum() == 2
+    fake = np.array(c["fake_vs_pt"])
+    assert fake[:, 1].sum() == 4 and fake[:, 0].sum() == 1 and fake[pe.index(20.0)].tolist() == [1, 1]
+    dup = np.array(c["duplicate_vs_pt"])
+    assert dup[:, 0].sum() == 1 and dup[pe.index(1.5)].tolist() == [1, 1]   # the second TC of particle 0
+    assert c["by_type"]["T5"]["tcs"] == 3 and c["by_type"]["pT3"]["fake_rate"] == 1.0
+    assert c["by_type"]["T5"]["duplicate_rate"] == pytest.approx(1 / 3)
+    # pooled over bins the rates equal rates()
+    r = rates(tc, pid, np.full(6, -1, np.int32), tr, pt_min=1.0)
+    assert fake[:, 0].sum() / fake[:, 1].sum() == pytest.approx(r["fake_rate"])
