@@ -46,12 +46,20 @@ def rates(tc, pid, seed_pid, tracks, pt_min=1.0, eta_max=2.4, frac=0.75):
     """Efficiency, fake and duplicate rates of one event's TCs.
 
     tracks: the generated particles (pt, eta arrays indexed by particle id).
+    When tc has a "type" column, efficiency_ot also counts the particles
+    found by TCs with outer-tracker objects only (pT5, pT3, T5: not a bare
+    pLS, which matches its seed's particle by construction).
     """
     m = match(tc, pid, seed_pid, frac)
     n_tc = len(m)
     findable = np.flatnonzero((tracks.pt >= pt_min) & (np.abs(tracks.eta) <= eta_max))
     matched = set(int(p) for p in m if p >= 0)
     found = sum(1 for p in findable if int(p) in matched)
+    found_ot = found
+    if "type" in tc:
+        ot = np.asarray(tc["type"]) != 3
+        matched_ot = set(int(p) for p in m[ot] if p >= 0)
+        found_ot = sum(1 for p in findable if int(p) in matched_ot)
     seen, dup = set(), 0
     for p in m:
         if p < 0:
@@ -60,7 +68,8 @@ def rates(tc, pid, seed_pid, tracks, pt_min=1.0, eta_max=2.4, frac=0.75):
             dup += 1
         seen.add(p)
     return dict(efficiency=found / max(1, len(findable)), fake_rate=float(np.sum(m < 0)) / max(1, n_tc),
-                duplicate_rate=dup / max(1, n_tc), tcs=n_tc, findable=int(len(findable)), found=int(found))
+                duplicate_rate=dup / max(1, n_tc), tcs=n_tc, findable=int(len(findable)), found=int(found),
+                efficiency_ot=found_ot / max(1, len(findable)), found_ot=int(found_ot))
 
 
 PT_EDGES = (0.5, 0.8, 1.0, 1.5, 2.0, 3.0, 5.0, 10.0, 20.0, 50.0, 100.0)
@@ -127,6 +136,7 @@ def combine(per_event):
     tcs = sum(r["tcs"] for r in per_event)
     fnd = sum(r["findable"] for r in per_event)
     return dict(efficiency=sum(r["found"] for r in per_event) / max(1, fnd),
+                efficiency_ot=sum(r.get("found_ot", r["found"]) for r in per_event) / max(1, fnd),
                 fake_rate=sum(r["fake_rate"] * r["tcs"] for r in per_event) / max(1, tcs),
                 duplicate_rate=sum(r["duplicate_rate"] * r["tcs"] for r in per_event) / max(1, tcs),
                 tcs=tcs, findable=fnd, events=len(per_event))

@@ -14,8 +14,10 @@ The study measures both on generated PU200 events:
   the memory a per-module slot layout sized at those quantiles would take;
 * per-event totals and their quantiles, and the memory of this library's
   layout at those capacities (measured with lst_device_bytes);
-* the chain run with per-event capacities scaled below the largest observed
-  totals: counted drops, efficiency, fake rate and device memory.
+* the chain run with one kind's per-event capacity scaled below its largest
+  observed total: counted drops, efficiency (also without bare-pLS TCs, which
+  match their seed's particle whatever the outer tracker found), fake and
+  duplicate rates, and the memory saved.
 
     python -m paper_2209_13711_gb300.occupancy --events 64 --batch 16
 """
@@ -58,7 +60,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--events", type=int, default=64)
     ap.add_argument("--batch", type=int, default=16)
-    ap.add_argument("--scales", type=float, nargs="+", default=[1.0, 0.9, 0.75, 0.5])
+    ap.add_argument("--scales", type=float, nargs="+", default=[0.9, 0.75, 0.5])
     args = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from synth import events as E, geometry as G, maps as M
@@ -115,27 +117,35 @@ def main(argv=None):
            "flat_layout_bytes_per_event_at_max_totals": int(sum(totals[k].max() * bytes_per[k] for k in KINDS)),
            "baseline": MT.combine(base_rates)}
 
-    # ---- truncation: per-event capacities scaled below the largest totals -
-    trunc = []
-    for s in args.scales:
-        caps = {CAP_FIELD[k]: max(1, int(s * totals[k].max())) for k in KINDS}
+    # ---- truncation: one kind's per-event capacity scaled below its largest
+    # total at a time (the others at their defaults) --------------------------
+    def run_with(caps):
         ctx = L.Context(geom.module_table(), maps, cfg=DEFAULT_CUTS, capacity=L.default_capacity(args.batch, **caps))
         dropped = {k: 0 for k in KINDS}
         rates = []
-        for b in batches:
-            ctx.run(b)
-            for j, ev in enumerate(b):
-                st = ctx.stats(j)
-                for k in KINDS:
-                    dropped[k] += st["dropped"][k]
-                rates.append(MT.rates(ctx.track_candidates(j), ev.pid, ev.seed_pid, ev.tracks))
-        ctx.close()
+        try:
+            for b in batches:
+                ctx.run(b)
+                for j, ev in enumerate(b):
+                    st = ctx.stats(j)
+                    for k in KINDS:
+                        dropped[k] += st["dropped"][k]
+                    rates.append(MT.rates(ctx.track_candidates(j), ev.pid, ev.seed_pid, ev.tracks))
+        finally:
+            ctx.close()
         c = MT.combine(rates)
-        trunc.append({"scale_of_max_total": s, "caps_per_event": caps,
-                      "arena_bytes_per_event": int(sum(caps[CAP_FIELD[k]] * bytes_per[k] for k in KINDS)),
-                      "dropped_per_event": {k: v / args.events for k, v in dropped.items()},
-                      "efficiency": round(c["efficiency"], 4), "fake_rate": round(c["fake_rate"], 4),
-                      "duplicate_rate": round(c["duplicate_rate"], 4)})
+        return {"dropped_per_event": {k: v / args.events for k, v in dropped.items()},
+                "efficiency": round(c["efficiency"], 4), "efficiency_ot": round(c["efficiency_ot"], 4),
+                "fake_rate": round(c["fake_rate"], 4), "duplicate_rate": round(c["duplicate_rate"], 4)}
+
+    trunc = []
+    for k in KINDS:
+        for s in args.scales:
+            cap = max(1, int(s * totals[k].max()))
+            r = run_with({CAP_FIELD[k]: cap})
+            r.update(kind=k, scale_of_max_total=s, cap_per_event=cap,
+                     arena_bytes_saved_per_event=int((totals[k].max() - cap) * bytes_per[k]))
+            trunc.append(r)
     out["truncation"] = trunc
     print(json.dumps(out))
 

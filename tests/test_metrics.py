@@ -82,3 +82,13 @@ def test_curves_bin_counts_agree_with_rates():
     # pooled over bins the rates equal rates()
     r = rates(tc, pid, np.full(6, -1, np.int32), tr, pt_min=1.0)
     assert fake[:, 0].sum() / fake[:, 1].sum() == pytest.approx(r["fake_rate"])
+
+
+def test_efficiency_without_bare_seeds():
+    pid = np.array([0] * 10 + [1] * 10)
+    tr = _Tracks([2.0, 3.0], [0.1, 0.2])
+    tc = _tc([list(range(10)), []], [-1, 0])
+    tc["type"] = np.array([2, 3])                       # a T5 of particle 0, a bare pLS of particle 1
+    r = rates(tc, pid, np.array([1], np.int32), tr)
+    assert r["efficiency"] == pytest.approx(1.0) and r["efficiency_ot"] == pytest.approx(0.5)
+    assert combine([r, r])["efficiency_ot"] == pytest.approx(0.5)
