@@ -757,7 +757,7 @@ __device__ __forceinline__ void t5_enumerate(const Arena& A, const DevCfg& c, Sm
                 const float2 a = S.ks1[seg], b = A.t3_ks[t2];
                 float k1 = a.x, k2 = b.x;
                 float s1_ = a.y, s2_ = b.y;
-                float thr = nk * sqrtf(s1_ * s1_ + s2_ * s2_);
+                float thr = nk * fast_sqrtf(s1_ * s1_ + s2_ * s2_);
                 // slack covers the FP32 rounding of the stored curvatures
                 pass = fabsf(k1 - k2) <= thr * 1.01f + 1e-5f * (fabsf(k1) + fabsf(k2)) + 1e-7f;
             }

@@ -137,7 +137,7 @@ __device__ __forceinline__ void pt_enumerate(const Arena& A, const DevCfg& c, Pt
             if (valid && (NT == 3 || A.t5_valid[obj])) {
                 const float2 ks = NT == 5 ? A.t5_ks[obj] : A.t3_ks[obj];
                 const float kt = ks.x, st = ks.y;
-                float thr = nk * sqrtf(sp * sp + st * st);
+                float thr = nk * fast_sqrtf(sp * sp + st * st);
                 pass = fabsf(kp - kt) <= thr * 1.01f + 1e-5f * (fabsf(kp) + fabsf(kt)) + 1e-7f;
             }
             int tot;

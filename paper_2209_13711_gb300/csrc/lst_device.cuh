@@ -243,15 +243,21 @@ static_assert(sizeof(TcRec) == 64, "packed track candidate is 64 bytes");
 // ---------------------------------------------------------------------------
 // arithmetic helpers (float and double overloads)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float m_sqrt(float v) { return sqrtf(v); }
+// FP32 square roots and divisions are the approximate ones (rsqrtf,
+// __fdividef: a few ulp). Every FP32 quantity here either feeds a decision
+// that is retested in FP64 within a band far wider than that error, or is
+// compared with a limit that carries slack for it; FP64 stays exact.
+__device__ __forceinline__ float m_sqrt(float v) { return v > 1e-30f ? v * rsqrtf(v) : sqrtf(v); }
 __device__ __forceinline__ double m_sqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double m_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float m_asin(float v) { return asinf(v); }
 __device__ __forceinline__ double m_asin(double v) { return asin(v); }
 __device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
 __device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
 // Coordinates and their differences are bounded (|x| < 1e4 cm), so the
 // plain root of the sum of squares neither overflows nor underflows.
-__device__ __forceinline__ float m_hypot(float a, float b) { return sqrtf(a * a + b * b); }
+__device__ __forceinline__ float m_hypot(float a, float b) { return m_sqrt(a * a + b * b); }
 __device__ __forceinline__ double m_hypot(double a, double b) { return sqrt(a * a + b * b); }
 __device__ __forceinline__ float m_abs(float v) { return fabsf(v); }
 __device__ __forceinline__ double m_abs(double v) { return fabs(v); }
@@ -264,7 +270,7 @@ template <typename T> __device__ __forceinline__ T sq(T v) { return v * v; }
 template <typename T> __device__ __forceinline__ T asinc(T v) { return m_asin(m_min(T(1), m_max(T(0), v))); }
 // transverse arc length of a chord c on a circle of curvature k
 template <typename T> __device__ __forceinline__ T arc(T c, T k) {
-    return k > T(0) ? T(2) * m_asin(m_min(T(1), c * k / T(2))) / k : c;
+    return k > T(0) ? m_div(T(2) * m_asin(m_min(T(1), c * k / T(2))), k) : c;
 }
 // angle in (-pi, pi]; loop-free (a non-finite input gives NaN)
 __device__ __forceinline__ double wrap_pi(double p) {
@@ -341,7 +347,7 @@ template <typename T> __device__ __forceinline__ T diff_prod(T a, T b, T c, T d)
 // coordinates of the chord's end points (|A x B| / (|AB| r_P)): for a chord
 // nearly parallel to r-hat the rounded unit vectors would lose it
 template <typename T> __device__ __forceinline__ T sigma_perp(const Pt<T>& P, T cx, T cy, T across) {
-    T ir = T(1) / P.r;
+    T ir = m_div(T(1), P.r);
     T along = (cx * P.x + cy * P.y) * ir;
     return m_sqrt(sq(P.srphi * along) + sq(P.sr * across));
 }
@@ -408,13 +414,13 @@ __device__ __forceinline__ int ls_eval(const DevCfg& c, const Pt<T>& P, T sAx, T
     if (mA.w < 0.5f) {
         T ls_ = m_hypot(sAx, sAy);
         T al = m_atan2(sAx * uy - sAy * ux, sAx * ux + sAy * uy);
-        cut(m_abs(al), base + n * (rt2 * P.srphi / ls_ + (P.sr + Q.sr) / lu));
+        cut(m_abs(al), base + n * (m_div(rt2 * P.srphi, ls_) + m_div(P.sr + Q.sr, lu)));
         if (cut.fail) return 0;
     }
     if (mB.w < 0.5f) {
         T ls_ = m_hypot(sBx, sBy);
         T al = m_atan2(sBx * uy - sBy * ux, sBx * ux + sBy * uy);
-        cut(m_abs(al), base + n * (rt2 * Q.srphi / ls_ + (P.sr + Q.sr) / lu));
+        cut(m_abs(al), base + n * (m_div(rt2 * Q.srphi, ls_) + m_div(P.sr + Q.sr, lu)));
     }
     return cut.state();
 }
@@ -433,7 +439,6 @@ __device__ __forceinline__ float4 ls_terms_f32(const DevCfg& c, const Pt<float>&
 __device__ __forceinline__ int ls_eval_f32(const DevCfg& c, const Pt<float>& P, float4 tP, float sAx, float sAy,
                                            float4 mA, const Pt<float>& Q, float4 tQ, float sBx, float sBy,
                                            float4 mB, float& dphi_o) {
-    const float a = c.f.a;
     const float n = c.f.n_ls;
     Cuts<float> cut;
     float num = P.z * Q.r - Q.z * P.r;
@@ -454,13 +459,13 @@ __device__ __forceinline__ int ls_eval_f32(const DevCfg& c, const Pt<float>& P, 
     if (mA.w < 0.5f) {
         float ls_ = m_hypot(sAx, sAy);
         float al = m_atan2(sAx * uy - sAy * ux, sAx * ux + sAy * uy);
-        cut(m_abs(al), base + n * (rt2 * P.srphi / ls_ + (P.sr + Q.sr) / lu));
+        cut(m_abs(al), base + n * (m_div(rt2 * P.srphi, ls_) + m_div(P.sr + Q.sr, lu)));
         if (cut.fail) return 0;
     }
     if (mB.w < 0.5f) {
         float ls_ = m_hypot(sBx, sBy);
         float al = m_atan2(sBx * uy - sBy * ux, sBx * ux + sBy * uy);
-        cut(m_abs(al), base + n * (rt2 * Q.srphi / ls_ + (P.sr + Q.sr) / lu));
+        cut(m_abs(al), base + n * (m_div(rt2 * Q.srphi, ls_) + m_div(P.sr + Q.sr, lu)));
     }
     return cut.state();
 }
@@ -481,16 +486,16 @@ template <typename T> __device__ __forceinline__ Tri<T> tri(const Pt<T>& A, cons
     t.lv = m_hypot(vx, vy);
     t.lw = m_hypot(wx, wy);
     t.beta = m_atan2(ux * vy - uy * vx, ux * vx + uy * vy);
-    T iu = T(1) / t.lu, iv = T(1) / t.lv;
+    T iu = m_div(T(1), t.lu), iv = m_div(T(1), t.lv);
     const T xAB = m_abs(diff_prod(A.x, B.y, A.y, B.x)) * iu;   // |A x B| / |AB|
     const T xBC = m_abs(diff_prod(B.x, C.y, B.y, C.x)) * iv;
-    T sAu = sigma_perp(A, ux * iu, uy * iu, xAB / A.r);
-    T sBu = sigma_perp(B, ux * iu, uy * iu, xAB / B.r);
-    T sBv = sigma_perp(B, vx * iv, vy * iv, xBC / B.r);
-    T sCv = sigma_perp(C, vx * iv, vy * iv, xBC / C.r);
+    T sAu = sigma_perp(A, ux * iu, uy * iu, m_div(xAB, A.r));
+    T sBu = sigma_perp(B, ux * iu, uy * iu, m_div(xAB, B.r));
+    T sBv = sigma_perp(B, vx * iv, vy * iv, m_div(xBC, B.r));
+    T sCv = sigma_perp(C, vx * iv, vy * iv, m_div(xBC, C.r));
     t.sig_beta = m_sqrt(sq(sAu * iu) + sq(sBu * iu + sBv * iv) + sq(sCv * iv));
-    t.kappa = T(2) * (ux * wy - uy * wx) / (t.lu * t.lv * t.lw);
-    t.sigk = T(2) * t.sig_beta / (t.lu + t.lv);
+    t.kappa = m_div(T(2) * (ux * wy - uy * wx), t.lu * t.lv * t.lw);
+    t.sigk = m_div(T(2) * t.sig_beta, t.lu + t.lv);
     return t;
 }
 
@@ -777,10 +782,16 @@ template <int N> __device__ inline Fit fit_track_group(const Pt<double>& Q, cons
     return f;
 }
 
+// Square root through the approximate reciprocal square root (a few ulp;
+// the FP32 prefilters carry far larger slack); 0 for x <= 0.
+__device__ __forceinline__ float fast_sqrtf(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
 // FP32 twin of fit_track (same chord-frame circle fit, geometric residuals and
 // r-z line fit), evaluated cut by cut: the curvature is tested right after the
 // circle solve, chi2_rphi after the residuals, and the r-z fit runs only for
 // candidates that passed both. The verdict equals testing all three at the end.
+// Divisions and square roots are the approximate ones (__fdividef, rsqrtf: a
+// few ulp each), well inside the slack of the limits (prefit_limits).
 template <int N> __device__ inline bool fit_may_pass_f32(const Pt<float>* P, const FitLimits& L) {
     const Pt<float>& O = P[N / 2];
     float ex = P[N - 1].x - P[0].x, ey = P[N - 1].y - P[0].y;
@@ -805,46 +816,51 @@ template <int N> __device__ inline bool fit_may_pass_f32(const Pt<float>* P, con
     }
     float det = saa * sbb - sab * sab;
     if (!(det > 0.f)) return false;
-    float gg = (sac * sbb - sab * sbc) / det;
-    float hh = (saa * sbc - sab * sac) / det;
+    const float idet = __fdividef(1.f, det);
+    float gg = (sac * sbb - sab * sbc) * idet;
+    float hh = (saa * sbc - sab * sac) * idet;
     float kk = me - gg * mr - hh * mx;
-    float S = sqrtf(fmaxf(0.f, 1.f + hh * hh - 4.f * gg * kk));
-    float kappa = 2.f * gg / S;
+    float S = fast_sqrtf(1.f + hh * hh - 4.f * gg * kk);
+    float kappa = __fdividef(2.f * gg, S);
     if (!(fabsf(kappa) <= L.kappa)) return false;
     float c2 = 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         float u = gg * rho2[i] + hh * xi[i] + kk - et[i];
-        float e = 2.f * u / (S + sqrtf(fmaxf(0.f, S * S + 4.f * gg * u)));
+        float e = __fdividef(2.f * u, S + fast_sqrtf(S * S + 4.f * gg * u));
         float nlx = 2.f * gg * xi[i] + hh, nly = 2.f * gg * et[i] - 1.f;
         float nx = nlx * xx + nly * yx, ny = nlx * xy + nly * yy;
         float inn = rsqrtf(nx * nx + ny * ny);
         nx *= inn; ny *= inn;
-        float ir = 1.0f / P[i].r;
+        float ir = __fdividef(1.f, P[i].r);
         float rx = P[i].x * ir, ry = P[i].y * ir;
         float n_phi = -nx * ry + ny * rx, n_r = nx * rx + ny * ry;
         float s2 = fmaxf(sq(P[i].srphi * n_phi) + sq(P[i].sr * n_r), sq(0.01f * P[i].srphi));
-        c2 += e * e / s2;
+        c2 += __fdividef(e * e, s2);
     }
     if (!(c2 <= L.chi2)) return false;
     float ka = fabsf(kappa);
     float s[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) s[i] = arc(m_hypot(P[i].x - P[0].x, P[i].y - P[0].y), ka);
-    float t_hat = (P[N - 1].z - P[0].z) / s[N - 1];
+    for (int i = 0; i < N; ++i) {
+        const float c = fast_sqrtf(sq(P[i].x - P[0].x) + sq(P[i].y - P[0].y));
+        s[i] = ka > 0.f ? __fdividef(2.f * asinf(fminf(1.f, 0.5f * c * ka)), ka) : c;
+    }
+    float t_hat = __fdividef(P[N - 1].z - P[0].z, s[N - 1]);
     float w[N], W = 0.f, Ws = 0.f, Wz = 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        w[i] = 1.0f / fmaxf(1e-12f, sq(P[i].sz) + sq(t_hat * P[i].sr));
+        w[i] = __fdividef(1.f, fmaxf(1e-12f, sq(P[i].sz) + sq(t_hat * P[i].sr)));
         W += w[i]; Ws += w[i] * s[i]; Wz += w[i] * P[i].z;
     }
-    float sbar = Ws / W, zbar = Wz / W, Sss = 0.f, Ssz = 0.f;
+    const float iW = __fdividef(1.f, W);
+    float sbar = Ws * iW, zbar = Wz * iW, Sss = 0.f, Ssz = 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         Sss += w[i] * sq(s[i] - sbar);
         Ssz += w[i] * (s[i] - sbar) * (P[i].z - zbar);
     }
-    float t = Ssz / Sss, c0 = zbar - t * sbar, cz = 0.f;
+    float t = __fdividef(Ssz, Sss), c0 = zbar - t * sbar, cz = 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) cz += w[i] * sq(P[i].z - c0 - t * s[i]);
     return cz <= L.chi2z;
@@ -919,7 +935,7 @@ struct T5Out {
 // 0 when the FP32 values are farther from the threshold than their rounding
 // can move them (a band of 2e-3 of the threshold), -1 (undecided) otherwise.
 __device__ __forceinline__ int kappa_test_f32(float k1, float s1, float k2, float s2, float n) {
-    const float d = fabsf(k1 - k2), thr = n * sqrtf(s1 * s1 + s2 * s2);
+    const float d = fabsf(k1 - k2), thr = n * fast_sqrtf(s1 * s1 + s2 * s2);
     const float band = 2e-3f * thr + 1e-7f;
     if (d < thr - band) return 1;
     if (d > thr + band) return 0;
