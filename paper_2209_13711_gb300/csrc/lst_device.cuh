@@ -577,32 +577,37 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
     Fit f;
     const Pt<double>& O = P[N / 2];
     double ex = P[N - 1].x - P[0].x, ey = P[N - 1].y - P[0].y;
-    double il = 1.0 / sqrt(ex * ex + ey * ey);
+    double il = rsqrt(ex * ex + ey * ey);
     double xx = ex * il, xy = ey * il;
     double yx = -xy, yy = xx;
     double xi[N], et[N], rho2[N];
-    double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, b[3] = {0, 0, 0};
+    double mr = 0.0, mx = 0.0, me = 0.0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         double dx = P[i].x - O.x, dy = P[i].y - O.y;
         xi[i] = dx * xx + dy * xy;
         et[i] = dx * yx + dy * yy;
         rho2[i] = xi[i] * xi[i] + et[i] * et[i];
-        double row[3] = {rho2[i], xi[i], 1.0};
-#pragma unroll
-        for (int p = 0; p < 3; ++p) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) M[p][q] += row[p] * row[q];
-            b[p] += row[p] * et[i];
-        }
+        mr += rho2[i]; mx += xi[i]; me += et[i];
     }
-    double sol[3] = {0, 0, 0};
-    if (!solve3(M, b, sol)) {
+    // least squares of et ~ gg rho2 + hh xi + kk through the centred moments
+    // (the normal equations with the intercept eliminated)
+    mr *= 1.0 / N; mx *= 1.0 / N; me *= 1.0 / N;
+    double saa = 0.0, sab = 0.0, sbb = 0.0, sac = 0.0, sbc = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const double a = rho2[i] - mr, b = xi[i] - mx, cc = et[i] - me;
+        saa += a * a; sab += a * b; sbb += b * b; sac += a * cc; sbc += b * cc;
+    }
+    const double det = saa * sbb - sab * sab;
+    if (!(det > 0.0)) {
         f.kappa = 1e30; f.chi2_rphi = 1e30; f.chi2_rz = 1e30; f.tanl = 0;
         if (full) *full = FitFull{0, 0, 0, 1, xx, xy, O.x, O.y, 0, 0, 0, 1e30, 1e30, 1e30};
         return f;
     }
-    double gg = sol[0], hh = sol[1], kk = sol[2];
+    const double idet = 1.0 / det;
+    double gg = (sac * sbb - sab * sbc) * idet, hh = (saa * sbc - sab * sac) * idet;
+    double kk = me - gg * mr - hh * mx;
     double S = sqrt(fmax(0.0, 1.0 + hh * hh - 4.0 * gg * kk));
     f.kappa = 2.0 * gg / S;
     double chi2 = 0.0;
@@ -658,9 +663,16 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
     }
     f.chi2_rphi = chi2;
     double ka = fabs(f.kappa);
+    // arc lengths from the first point (arc(): 2 asin(c ka / 2) / ka), the
+    // division by ka taken once
+    const double k2 = 0.5 * ka, ik = ka > 0.0 ? 2.0 / ka : 0.0;
     double s[N];
+    s[0] = 0.0;
 #pragma unroll
-    for (int i = 0; i < N; ++i) s[i] = arc(sqrt(sq(P[i].x - P[0].x) + sq(P[i].y - P[0].y)), ka);
+    for (int i = 1; i < N; ++i) {
+        const double c = sqrt(sq(P[i].x - P[0].x) + sq(P[i].y - P[0].y));
+        s[i] = ka > 0.0 ? asin(fmin(1.0, c * k2)) * ik : c;
+    }
     double t_hat = (P[N - 1].z - P[0].z) / s[N - 1];
     double w[N], W = 0, Ws = 0, Wz = 0;
     const float tf = float(t_hat);
