@@ -527,39 +527,6 @@ struct Fit {
     double kappa, chi2_rphi, chi2_rz, tanl;
 };
 
-__device__ inline bool solve3(double M[3][3], double b[3], double x[3]) {
-    double A[3][4];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) A[i][j] = M[i][j];
-        A[i][3] = b[i];
-    }
-#pragma unroll
-    for (int col = 0; col < 3; ++col) {
-        int piv = col;
-        for (int r = col + 1; r < 3; ++r)
-            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
-        if (A[piv][col] == 0.0) return false;
-        if (piv != col)
-            for (int j = 0; j < 4; ++j) {
-                double tmp = A[piv][j];
-                A[piv][j] = A[col][j];
-                A[col][j] = tmp;
-            }
-        for (int r = col + 1; r < 3; ++r) {
-            double f = A[r][col] / A[col][col];
-            for (int j = col; j < 4; ++j) A[r][j] -= f * A[col][j];
-        }
-    }
-    for (int i = 2; i >= 0; --i) {
-        double s = A[i][3];
-        for (int j = i + 1; j < 3; ++j) s -= A[i][j] * x[j];
-        x[i] = s / A[i][i];
-    }
-    return true;
-}
-
 // Full output of the chord-frame fit: circle g (xi^2+eta^2) + h xi + k - eta = 0
 // in the frame (origin O, x-hat (xx, xy)), S = sqrt(1 + h^2 - 4gk), and the
 // r-z line z = c0 + t s (s: arc length from P[0]) with its t_hat.
@@ -727,26 +694,25 @@ template <int N> __device__ inline Fit fit_track_group(const Pt<double>& Q, cons
     const double ox = __shfl_sync(F, Q.x, N / 2, 8), oy = __shfl_sync(F, Q.y, N / 2, 8);
     const float oxf = __shfl_sync(F, Qf.x, N / 2, 8), oyf = __shfl_sync(F, Qf.y, N / 2, 8);
     const double ex = xn - x0, ey = yn - y0;
-    const double il = 1.0 / sqrt(ex * ex + ey * ey);
+    const double il = rsqrt(ex * ex + ey * ey);
     const double xx = ex * il, xy = ey * il, yx = -xy, yy = xx;
     const double dx = Q.x - ox, dy = Q.y - oy;
     const double xi = dx * xx + dy * xy, et = dx * yx + dy * yy, rho2 = xi * xi + et * et;
-    const double a = act ? 1.0 : 0.0;
-    double M[3][3], b[3], sol[3] = {0, 0, 0};
-    M[0][0] = grp_sum8(a * rho2 * rho2);
-    M[0][1] = M[1][0] = grp_sum8(a * rho2 * xi);
-    M[0][2] = M[2][0] = grp_sum8(a * rho2);
-    M[1][1] = grp_sum8(a * xi * xi);
-    M[1][2] = M[2][1] = grp_sum8(a * xi);
-    M[2][2] = double(N);
-    b[0] = grp_sum8(a * rho2 * et);
-    b[1] = grp_sum8(a * xi * et);
-    b[2] = grp_sum8(a * et);
-    if (!solve3(M, b, sol)) {
+    const double w1 = act ? 1.0 : 0.0;
+    // centred least squares, as in fit_track
+    const double mr = grp_sum8(w1 * rho2) * (1.0 / N), mx = grp_sum8(w1 * xi) * (1.0 / N);
+    const double me = grp_sum8(w1 * et) * (1.0 / N);
+    const double ca = w1 * (rho2 - mr), cb = w1 * (xi - mx), cc = w1 * (et - me);
+    const double saa = grp_sum8(ca * ca), sab = grp_sum8(ca * cb), sbb = grp_sum8(cb * cb);
+    const double sac = grp_sum8(ca * cc), sbc = grp_sum8(cb * cc);
+    const double det = saa * sbb - sab * sab;
+    if (!(det > 0.0)) {
         f.kappa = 1e30; f.chi2_rphi = 1e30; f.chi2_rz = 1e30; f.tanl = 0;
         return f;
     }
-    const double gg = sol[0], hh = sol[1], kk = sol[2];
+    const double idet = 1.0 / det;
+    const double gg = (sac * sbb - sab * sbc) * idet, hh = (saa * sbc - sab * sac) * idet;
+    const double kk = me - gg * mr - hh * mx;
     const double S = sqrt(fmax(0.0, 1.0 + hh * hh - 4.0 * gg * kk));
     f.kappa = 2.0 * gg / S;
     // residual and error projection of this lane's point (as in fit_track with Pf)
