@@ -462,7 +462,7 @@ def measure_batched(P, E, geom, maps, cuts, flush, st, steps, n_batch=64):
 
 def measure_mlp(P, E, geom, maps, cuts, flush, st, dev_events):
     """Network-scored T5 selection: trained here (128 PU200 events, the training
-    set held in device memory, the library's own kernels), judged against the
+    set held in device memory, the library's own kernels), compared with the
     hand-set cuts on 8 other events at matched efficiency, then timed on the
     benchmark's PU200 events."""
     import torch

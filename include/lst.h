@@ -297,9 +297,9 @@ lst_status lst_build_mini_doublets_static(const lst_config* cfg, const lst_modul
  * At most n (<= 32) values. */
 lst_status lst_get_counters(lst_ctx* ctx, int32_t* out, int32_t n);
 
-/* ---- learned T5 selection (the north-star's scoring network; the paper's
- * own selection is the hand-set cuts of Section 2.1, which stay the default,
- * the fallback and the judge) --------------------------------------------
+/* ---- learned T5 selection (an optional scoring network; the paper's own
+ * selection is the hand-set cuts of Section 2.1, which stay the default, the
+ * fallback and the yardstick of its efficiency) ---------------------------
  * Network: LST_MLP_INPUTS inputs (LST_MLP_FEATURES features, zero padded) ->
  * 64 -> 64 -> 32 -> 1, ReLU hidden, sigmoid output; BF16 weights and layer
  * inputs on tensor cores with FP32 accumulation. Parameters are FP32, laid out

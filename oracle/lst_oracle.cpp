@@ -393,7 +393,7 @@ Fit fit_track(const Pt* P, int n, FitParams* fp = nullptr) {
 }
 
 // ----------------------------------------------------------------------------
-// Scoring features of a T5 (the north-star's learned selection; the paper's
+// Scoring features of a T5 (for an optional learned selection; the paper's
 // own selection is the cut set above). Hits H[0..9] = (lower, upper) of the
 // five MDs, anchors P = the lower hits; code = layer + 6 subdet.
 //   f[0..9]   signed distance of each hit to the fitted circle over its error

@@ -3,8 +3,8 @@
 Only tests/ and the benchmark's CPU-baseline leg use this module; it never
 imports the device package.
 
-Network (the learned selection of the spec line (b); the paper itself
-uses hand-set cuts, Section 2.1): 48 inputs (38 features, zero padded) ->
+Network (an optional learned T5 selection; the paper itself uses hand-set
+cuts, Section 2.1): 48 inputs (38 features, zero padded) ->
 64 -> 64 -> 32 -> 1, ReLU on the hidden layers, sigmoid on the output. The
 device evaluates it with BF16 weights and BF16 layer inputs, accumulating in
 FP32; this reference applies the same BF16 rounding (round to nearest even)
