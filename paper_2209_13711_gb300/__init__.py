@@ -7,4 +7,4 @@ the device), `metrics` (efficiency, fake and duplicate rates on generator
 truth) and `run` (a command-line driver).
 """
 from .lst import (Context, LstError, Mlp, TC_DTYPE, default_capacity, default_config, library,  # noqa: F401
-                  measure_peaks, pack_events, tc_dict)
+                  build_mini_doublets_static, measure_peaks, pack_events, tc_dict)

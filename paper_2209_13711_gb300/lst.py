@@ -123,12 +123,13 @@ def library():
         L.lst_get_t5_candidates.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
         L.lst_get_kernel_times.argtypes = [vp, i32, vp, vp, vp]
         L.lst_measure_peaks.argtypes = [i32, vp]
+        L.lst_build_mini_doublets_static.argtypes = [vp, vp, i32] + [vp] * 5 + [i32, i32] + [vp] * 7 + [vp]
         for f in ("lst_config_default", "lst_capacity_default", "lst_create", "lst_load_geometry", "lst_run_batch",
                   "lst_run_event", "lst_get_track_candidates", "lst_object_columns", "lst_get_objects",
                   "lst_get_stats", "lst_last_launch_count", "lst_set_profiling", "lst_get_kernel_times",
                   "lst_get_counters", "lst_mlp_create", "lst_mlp_set_params", "lst_mlp_get_params",
                   "lst_mlp_forward", "lst_mlp_gradient", "lst_mlp_train_step", "lst_set_t5_selection",
-                  "lst_get_t5_candidates", "lst_measure_peaks"):
+                  "lst_get_t5_candidates", "lst_measure_peaks", "lst_build_mini_doublets_static"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -187,6 +188,26 @@ def measure_peaks(device=0):
     return {"fp32_tflops": p.fp32_tflops, "fp64_tflops": p.fp64_tflops, "atom_warp_gops": p.atom_warp_gops,
             "atom_same_gops": p.atom_same_gops, "red_lane_gops": p.red_lane_gops, "ms": list(p.ms),
             "sm_count": p.sm_count, "clock_mhz": p.clock_khz / 1000.0}
+
+
+def build_mini_doublets_static(cfg, modules, n_mod, x, y, z, module, side, n_hits, md_capacity, md_lower,
+                               md_upper, md_module, md_dphi, md_dlong, md_count, md_dropped=None, stream=None):
+    """lst_build_mini_doublets_static: the allocation-free MD builder of one
+    event. cfg is an LstConfig; every array is a CUDA tensor (modules: the
+    lst_module rows as bytes; x, y, z float32; module int32; side uint8;
+    outputs int32 / float32 with md_capacity rows, md_count and md_dropped one
+    int32 each, md_dropped optional). Asynchronous on `stream` (a
+    cudaStream_t handle; None: the legacy default stream)."""
+    arrays = (modules, x, y, z, module, side, md_lower, md_upper, md_module, md_dphi, md_dlong, md_count)
+    for t in arrays + ((md_dropped,) if md_dropped is not None else ()):
+        if t is not None and not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise LstError("build_mini_doublets_static: every array must be a CUDA tensor")
+    p = _ptr
+    s = C.c_void_p(stream) if stream is not None else None
+    _check(library().lst_build_mini_doublets_static(
+        C.byref(cfg), p(modules), int(n_mod), p(x), p(y), p(z), p(module), p(side), int(n_hits),
+        int(md_capacity), p(md_lower), p(md_upper), p(md_module), p(md_dphi), p(md_dlong), p(md_count),
+        p(md_dropped), s))
 
 
 def pack_events(events):

@@ -46,3 +46,18 @@ def test_argument_errors_without_device():
     assert L.lst_object_columns(7, ctypes.byref(ni), ctypes.byref(nf)) == -1
     assert L.lst_object_columns(3, ctypes.byref(ni), ctypes.byref(nf)) == 0 and (ni.value, nf.value) == (2, 7)
     assert L.lst_status_str(-6) == b"batch exceeds the context capacity"
+
+
+def test_static_md_builder_binding_checks_arguments_without_device():
+    """The binding refuses host arrays before any device work, and the library
+    answers a missing pointer with LST_ERR_ARG (no CUDA call is made)."""
+    import numpy as np
+    from paper_2209_13711_gb300 import LstError, build_mini_doublets_static, lst
+    cfg = lst.default_config()
+    host = np.zeros(4, np.float32)
+    with pytest.raises(LstError, match="CUDA tensor"):
+        build_mini_doublets_static(cfg, host, 1, host, host, host, host, host, 4, 4, host, host, host, host, host,
+                                   host)
+    L = lst.library()
+    assert L.lst_build_mini_doublets_static(ctypes.byref(cfg), None, 1, *([None] * 5), 0, 0, *([None] * 7),
+                                            None) == -1
