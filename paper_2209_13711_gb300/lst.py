@@ -155,6 +155,57 @@ def _numel(a):
     return a.numel() if hasattr(a, "numel") else np.asarray(a).size
 
 
+_INPUT_DTYPES = (("x", "float32"), ("y", "float32"), ("z", "float32"), ("module", "int32"), ("side", "uint8"),
+                 ("seeds", "float32"))
+
+
+def _on_device(a):
+    return bool(getattr(a, "is_cuda", False))
+
+
+def _contiguous(a):
+    return a.is_contiguous() if hasattr(a, "is_contiguous") else bool(np.asarray(a).flags["C_CONTIGUOUS"])
+
+
+def _input_kind(d, n_hits, n_seeds):
+    """True when every input array of d (x, y, z, module, side, seeds) is a
+    CUDA tensor, False when none is (numpy arrays or CPU tensors). Raises
+    LstError, before anything is enqueued, for a mix of the two, a dtype other
+    than the one the library reads, a non-contiguous array, or an array
+    shorter than the n_hits hits (9 n_seeds floats for seeds) it must hold:
+    the library reads these pointers without knowing their sizes."""
+    kinds = set()
+    for k, dt in _INPUT_DTYPES:
+        a = d[k]
+        kinds.add(_on_device(a))
+        got = str(a.dtype).replace("torch.", "")
+        if got != dt:
+            raise LstError(f"{k}: dtype {got}, the library reads {dt}")
+        if not _contiguous(a):
+            raise LstError(f"{k}: not contiguous")
+        need = 9 * int(n_seeds) if k == "seeds" else int(n_hits)
+        if _numel(a) < need:
+            raise LstError(f"{k}: {_numel(a)} elements, {need} needed")
+    if len(kinds) > 1:
+        raise LstError("the inputs mix host arrays and CUDA tensors")
+    return kinds.pop()
+
+
+def _device_array(t, name, dtype, shape):
+    """Pointer of a contiguous CUDA tensor of the given dtype and shape;
+    LstError otherwise (the library would read it on the device)."""
+    if not _on_device(t):
+        raise LstError(f"{name}: a CUDA tensor is required")
+    got = str(t.dtype).replace("torch.", "")
+    if got != dtype:
+        raise LstError(f"{name}: dtype {got}, expected {dtype}")
+    if not _contiguous(t):
+        raise LstError(f"{name}: not contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise LstError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return _ptr(t)
+
+
 def _ptr(a):
     if a is None:
         return None
@@ -264,7 +315,7 @@ class Context:
     def run_packed(self, b, stream=None):
         """b: dict from pack_events (numpy) or the same keys as CUDA torch tensors
         (hit_off / seed_off stay numpy: they are host arrays)."""
-        dev = hasattr(b["x"], "is_cuda") and b["x"].is_cuda
+        dev = _input_kind(b, int(b["hit_off"][-1]), int(b["seed_off"][-1]))
         hits = LstHits(_ptr(b["x"]), _ptr(b["y"]), _ptr(b["z"]), _ptr(b["module"]), _ptr(b["side"]),
                        int(b["hit_off"][-1]))
         seeds = LstSeeds(_ptr(b["seeds"]), int(b["seed_off"][-1]))
@@ -286,9 +337,11 @@ class Context:
         n = len(events)
         hits = (LstHits * n)()
         seeds = (LstSeeds * n)()
-        dev = False
+        kinds = {_input_kind(e, _numel(e["x"]), _numel(e["seeds"]) // 9) for e in events}
+        if len(kinds) > 1:
+            raise LstError("the events mix host arrays and CUDA tensors")
+        dev = kinds.pop() if kinds else False
         for i, e in enumerate(events):
-            dev = hasattr(e["x"], "is_cuda") and e["x"].is_cuda
             hits[i] = LstHits(_ptr(e["x"]), _ptr(e["y"]), _ptr(e["z"]), _ptr(e["module"]), _ptr(e["side"]),
                               int(len(e["x"])))
             seeds[i] = LstSeeds(_ptr(e["seeds"]), int(_numel(e["seeds"]) // 9))
@@ -312,7 +365,7 @@ class Context:
         return off, out[:min(cap, int(off[-1]))]
 
     def _batch_args(self, b):
-        dev = hasattr(b["x"], "is_cuda") and b["x"].is_cuda
+        dev = _input_kind(b, int(b["hit_off"][-1]), int(b["seed_off"][-1]))
         hits = LstHits(_ptr(b["x"]), _ptr(b["y"]), _ptr(b["z"]), _ptr(b["module"]), _ptr(b["side"]),
                        int(b["hit_off"][-1]))
         seeds = LstSeeds(_ptr(b["seeds"]), int(b["seed_off"][-1]))
@@ -477,19 +530,26 @@ class Mlp:
 
     def forward(self, features, scores, stream=None):
         """features, scores: CUDA tensors ([n, 48] float32, [n] float32)."""
-        _check(library().lst_mlp_forward(self._h, _ptr(features), int(features.shape[0]), _ptr(scores),
-                                         C.c_void_p(stream) if stream is not None else None))
+        n = int(features.shape[0])
+        f = _device_array(features, "features", "float32", (n, N_MLP_INPUTS))
+        o = _device_array(scores, "scores", "float32", (n,))
+        _check(library().lst_mlp_forward(self._h, f, n, o, C.c_void_p(stream) if stream is not None else None))
 
     def gradient(self, features, labels, stream=None):
         g = np.zeros(N_MLP_PARAMS, np.float32)
         loss = C.c_float(0)
-        _check(library().lst_mlp_gradient(self._h, _ptr(features), _ptr(labels), int(features.shape[0]), _ptr(g),
-                                          C.byref(loss), C.c_void_p(stream) if stream is not None else None))
+        n = int(features.shape[0])
+        f = _device_array(features, "features", "float32", (n, N_MLP_INPUTS))
+        y = _device_array(labels, "labels", "float32", (n,))
+        _check(library().lst_mlp_gradient(self._h, f, y, n, _ptr(g), C.byref(loss),
+                                          C.c_void_p(stream) if stream is not None else None))
         return g, loss.value
 
     def train_step(self, features, labels, lr=1e-3, want_loss=False, stream=None):
         loss = C.c_float(0)
-        _check(library().lst_mlp_train_step(self._h, _ptr(features), _ptr(labels), int(features.shape[0]),
-                                            float(lr), C.byref(loss) if want_loss else None,
+        n = int(features.shape[0])
+        f = _device_array(features, "features", "float32", (n, N_MLP_INPUTS))
+        y = _device_array(labels, "labels", "float32", (n,))
+        _check(library().lst_mlp_train_step(self._h, f, y, n, float(lr), C.byref(loss) if want_loss else None,
                                             C.c_void_p(stream) if stream is not None else None))
         return loss.value if want_loss else None
