@@ -6,7 +6,6 @@ this module. It never imports the device package.
 from __future__ import annotations
 
 import ctypes as C
-import os
 
 import numpy as np
 

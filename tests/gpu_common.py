@@ -1,9 +1,5 @@
 """Shared set-up of the GPU tests: contexts, oracle runs, result dicts."""
-import numpy as np
-
 from oracle import oracle as O
-from synth import geometry as G
-from synth import maps as M
 from synth.config import DEFAULT_CUTS
 
 A_HALF = DEFAULT_CUTS["k_field"] * DEFAULT_CUTS["b_field"] / (200.0 * DEFAULT_CUTS["pt_min"])

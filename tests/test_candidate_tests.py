@@ -1,7 +1,6 @@
 """Candidate-test counts of the benchmark (CPU): the vectorised counts of
 metrics.candidate_tests equal a brute-force enumeration over the oracle's
 objects of small events."""
-import numpy as np
 import pytest
 
 from oracle import oracle as O

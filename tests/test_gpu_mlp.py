@@ -6,7 +6,7 @@ from oracle import mlp_oracle as R
 from synth import events as E
 from synth.config import DEFAULT_CUTS
 from synth.mlp_init import init_params
-from tests.gpu_common import make_context, oracle_result
+from tests.gpu_common import make_context
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")

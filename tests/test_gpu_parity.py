@@ -5,7 +5,7 @@ import pytest
 from synth import events as E
 from synth.config import DEFAULT_CUTS
 from tests.gpu_common import A_HALF, all_tuples as _all_tuples, gpu_result, make_context, oracle_result
-from tests.parity import chain_tuples, compare
+from tests.parity import compare
 
 pytestmark = pytest.mark.gpu
 
