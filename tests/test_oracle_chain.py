@@ -194,3 +194,35 @@ def test_noiseless_one_candidate_per_track(seed, geom_barrel, maps_barrel, cuts)
     assert sorted(pid_of_tc) == sorted(set(pid_of_tc))
     assert set(good) <= set(pid_of_tc)
     assert r["m_md"].shape[0] == 0 and r["m_t5"].shape[0] == 0
+
+
+@pytest.mark.parametrize("pu,seed", [(10, 5), (25, 7)])
+def test_cleaning_is_idempotent(pu, seed, geom_full, maps_full, cuts):
+    """Re-running the cross-cleaning on its own output removes nothing: no kept
+    pT3 is close to a kept pT5, no kept T5 to a kept pT5 or pT3, and no kept
+    pLS to any kept pT5, pT3 or T5 (close: eta-phi distance below dr_clean, or
+    a shared hit); no two kept objects share a hit or a seed."""
+    ev = E.pileup_event(pu, seed, geom_full)
+    tc = _setup(geom_full, maps_full, cuts, ev).run()["tc"]
+    n = tc["n"]
+    assert n > 20
+    hits = [frozenset(int(tc[f"h{j}"][i]) for j in range(10) if tc[f"h{j}"][i] >= 0) for i in range(n)]
+    kind = np.asarray(tc["type"])
+    thr2 = cuts["dr_clean"] ** 2
+
+    def close(i, j):
+        dphi = (tc["phi0"][i] - tc["phi0"][j] + np.pi) % (2 * np.pi) - np.pi
+        return bool(hits[i] & hits[j]) or (tc["eta"][i] - tc["eta"][j]) ** 2 + dphi ** 2 < thr2
+
+    higher = {1: (0,), 2: (0, 1), 3: (0, 1, 2)}        # pT3 | T5 | pLS against the categories cleaned first
+    by_kind = {k: np.flatnonzero(kind == k) for k in range(4)}
+    assert all(len(by_kind[k]) for k in (0, 1, 3))
+    for k, hs in higher.items():
+        for i in by_kind[k]:
+            for h in hs:
+                for j in by_kind[h]:
+                    assert not close(i, j), (k, i, h, j)
+    seeds = [int(s) for s in tc["seed"] if s >= 0]
+    assert len(seeds) == len(set(seeds))
+    for i, j in itertools.combinations(range(n), 2):
+        assert not (hits[i] & hits[j])
