@@ -226,3 +226,51 @@ def test_cleaning_is_idempotent(pu, seed, geom_full, maps_full, cuts):
     assert len(seeds) == len(set(seeds))
     for i, j in itertools.combinations(range(n), 2):
         assert not (hits[i] & hits[j])
+
+
+@pytest.mark.parametrize("pu,seed", [(10, 5), (25, 7)])
+def test_cleaning_drops_only_with_cause(pu, seed, geom_full, maps_full, cuts):
+    """Every candidate the cleaning drops has a reason in the output: a pT5 a
+    hit-sharing pT5 with no larger score; a pT3 such a pT3 or closeness to a
+    kept pT5; a T5 such a T5 or closeness to a kept pT5 or pT3; a passing pLS
+    a kept pT5/pT3 built on it or closeness to any kept pT5, pT3 or T5."""
+    ev = E.pileup_event(pu, seed, geom_full)
+    r = _setup(geom_full, maps_full, cuts, ev).run()
+    md, ls, t3, t5, pls, pt5, pt3, tc = (r[k] for k in ("md", "ls", "t3", "t5", "pls", "pt5", "pt3", "tc"))
+    nh = len(ev.x)
+    md_h = lambda m: {int(md["lo"][m]), int(md["up"][m])}
+    t3_mds = lambda i: (ls["md_in"][t3["ls_in"][i]], ls["md_out"][t3["ls_in"][i]], ls["md_out"][t3["ls_out"][i]])
+    t5_mds = lambda i: t3_mds(t5["t3_in"][i]) + t3_mds(t5["t3_out"][i])[1:]
+    pix = lambda s: {nh + 3 * int(s) + j for j in range(3)}
+    union = lambda ms: set().union(*(md_h(m) for m in ms))
+    H = {0: [union(t5_mds(pt5["t5"][i])) | pix(pt5["seed"][i]) for i in range(pt5["n"])],
+         1: [union(t3_mds(pt3["t3"][i])) | pix(pt3["seed"][i]) for i in range(pt3["n"])],
+         2: [union(t5_mds(i)) for i in range(t5["n"])],
+         3: [pix(pls["seed"][i]) for i in range(pls["n"])]}
+    ang = {0: [(pls["eta"][s], pls["phi0"][s]) for s in pt5["seed"]],
+           1: [(pls["eta"][s], pls["phi0"][s]) for s in pt3["seed"]],
+           2: list(zip(t5["eta"], t5["phi0"])), 3: list(zip(pls["eta"], pls["phi0"]))}
+    score = {0: pt5["score"], 1: pt3["score"], 2: t5["score"]}
+    kept = {k: set(int(o) for t, o in zip(tc["type"], tc["obj"]) if t == k) for k in range(4)}
+    thr2 = cuts["dr_clean"] ** 2
+
+    def close(c1, i, c2, j):
+        (e1, p1), (e2, p2) = ang[c1][i], ang[c2][j]
+        dphi = (p1 - p2 + np.pi) % (2 * np.pi) - np.pi
+        return bool(H[c1][i] & H[c2][j]) or (e1 - e2) ** 2 + dphi ** 2 < thr2
+
+    def beaten(c, i):
+        return any(j != i and H[c][i] & H[c][j] and score[c][j] <= score[c][i] for j in range(len(H[c])))
+
+    dropped = {k: [i for i in range(len(H[k])) if i not in kept[k]] for k in range(3)}
+    assert sum(len(v) for v in dropped.values()) > 0
+    for i in dropped[0]:
+        assert beaten(0, i), i
+    for i in dropped[1]:
+        assert beaten(1, i) or any(close(1, i, 0, j) for j in kept[0]), i
+    for i in dropped[2]:
+        assert beaten(2, i) or any(close(2, i, c, j) for c in (0, 1) for j in kept[c]), i
+    linked = {int(pt5["seed"][j]) for j in kept[0]} | {int(pt3["seed"][j]) for j in kept[1]}
+    for i in range(pls["n"]):
+        if pls["pass"][i] and i not in kept[3]:
+            assert int(pls["seed"][i]) in linked or any(close(3, i, c, j) for c in (0, 1, 2) for j in kept[c]), i
