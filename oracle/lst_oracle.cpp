@@ -297,10 +297,14 @@ bool t3_eval(const OCfg& c, const Pt& A, const Pt& B, const Pt& C, T3& o, bool& 
 // Frame: origin at the middle point P[n/2], x-axis along P[n-1] - P[0].
 // The circle g (xi^2 + eta^2) + h xi + k - eta = 0 is the least-squares
 // solution of eta_i ~ g rho_i^2 + h xi_i + k (an algebraic, Kasa-type fit
-// normalised on the transverse coordinate; exact on an exact circle).
-// Signed curvature kappa = 2g / S with S = sqrt(1 + h^2 - 4gk); residuals are
-// geometric distances to the circle; each point's error is projected on the
-// circle normal.
+// normalised on the transverse coordinate; exact on an exact circle; to first
+// order the unweighted geometric fit, since the algebraic residual of a point
+// near the circle is S times its distance). Signed curvature kappa = 2g / S
+// with S = sqrt(1 + h^2 - 4gk); residuals are geometric distances to the
+// circle; each point's error is projected on the circle normal. The fit does
+// not weight the points: where their projected errors differ (endcap strips,
+// pixel points with outer-tracker points) chi2 exceeds n - 3 on average, by
+// the factor its first-order expectation gives.
 // --------------------------------------------------------------------------
 struct Fit { double kappa, chi2_rphi, chi2_rz, tanl; };
 // circle and line parameters of a fit (for the scoring features)
@@ -325,6 +329,20 @@ bool solve3(double M[3][3], double b[3], double x[3]) {
         x[i] = s / A[i][i];
     }
     return true;
+}
+
+// Variance of point P's error along the circle normal whose (unnormalised)
+// components in the chord frame (x-hat = (xx, xy), y-hat = (-xy, xx)) are
+// (nl_x, nl_y): srphi along phi-hat and sr along r-hat, projected; floored at
+// (0.01 srphi)^2.
+double normal_variance(const Pt& P, double nl_x, double nl_y, double xx, double xy) {
+    double nx = nl_x * xx - nl_y * xy, ny = nl_x * xy + nl_y * xx;
+    double nn = std::hypot(nx, ny);
+    nx /= nn; ny /= nn;
+    double rx = P.x / P.r, ry = P.y / P.r;
+    double n_phi = -nx * ry + ny * rx;
+    double n_r = nx * rx + ny * ry;
+    return std::max(sq(P.srphi * n_phi) + sq(P.sr * n_r), sq(0.01 * P.srphi));
 }
 
 Fit fit_track(const Pt* P, int n, FitParams* fp = nullptr) {
@@ -360,16 +378,7 @@ Fit fit_track(const Pt* P, int n, FitParams* fp = nullptr) {
     for (int i = 0; i < n; ++i) {
         double u = gg * rho2[i] + hh * xi[i] + kk - et[i];
         double e = 2.0 * u / (S + std::sqrt(std::max(0.0, S * S + 4.0 * gg * u)));
-        double nl_x = 2.0 * gg * xi[i] + hh, nl_y = 2.0 * gg * et[i] - 1.0;
-        double nx = nl_x * xx + nl_y * yx, ny = nl_x * xy + nl_y * yy;
-        double nn = std::hypot(nx, ny);
-        nx /= nn; ny /= nn;
-        double rx = P[i].x / P[i].r, ry = P[i].y / P[i].r;
-        double n_phi = -nx * ry + ny * rx;
-        double n_r = nx * rx + ny * ry;
-        double s2 = sq(P[i].srphi * n_phi) + sq(P[i].sr * n_r);
-        s2 = std::max(s2, sq(0.01 * P[i].srphi));
-        chi2 += e * e / s2;
+        chi2 += e * e / normal_variance(P[i], 2.0 * gg * xi[i] + hh, 2.0 * gg * et[i] - 1.0, xx, xy);
     }
     f.chi2_rphi = chi2;
     // r-z: z linear in the transverse arc length s measured from P[0]
@@ -519,9 +528,10 @@ void pls_eval(const OCfg& c, const Pt* Q, PLS& o, bool& near) {
 // Step 6: pT5 / pT3 = pLS linked to a T5 / T3 (Figs. PixelQuintuplet, PixelTriplet).
 // --------------------------------------------------------------------------
 bool pt_eval(const OCfg& c, const Pt* P, int n, double kappa_pls, double sigk_pls, double kappa_t,
-             double sigk_t, double chi2_rphi_max, double chi2_rz_max, PT& o, bool& near) {
+             double sigk_t, double chi2_rphi_max, double chi2_rz_max, PT& o, bool& near, double* diag = nullptr) {
     const double a = half_curv_max(c);
     Cuts cut(c.margin_rel);
+    if (diag) { diag[0] = kappa_pls - kappa_t; diag[1] = c.n_pt * std::sqrt(sq(sigk_pls) + sq(sigk_t)); }
     bool ok = cut(std::fabs(kappa_pls - kappa_t), c.n_pt * std::sqrt(sq(sigk_pls) + sq(sigk_t)));
     Fit f = fit_track(P, n);
     if (!cut.fail) ok = cut(std::fabs(f.kappa), (1.0 + c.tol_r) * 2.0 * a) && ok;
@@ -1113,7 +1123,7 @@ int oracle_t3_d(const OCfg* c, const double* rows, double* out) {
     return ok;
 }
 
-// rows [5][6]; out = {dkappa, thr_dkappa, kappa, chi2_rphi, chi2_rz, eta, phi0, pt, score, near}
+// rows [5][6]; out = {dkappa, thr_dkappa, kappa, chi2_rphi, chi2_rz, eta, phi0, pt, score, near, sigk}
 int oracle_t5_d(const OCfg* c, const double* rows, double* out) {
     Pt P[5];
     for (int i = 0; i < 5; ++i) P[i] = pt_from_row(rows + 6 * i);
@@ -1121,7 +1131,7 @@ int oracle_t5_d(const OCfg* c, const double* rows, double* out) {
     bool near = false;
     bool ok = t5_eval(*c, P, o, near, out);
     out[2] = o.kappa; out[3] = o.chi2_rphi; out[4] = o.chi2_rz; out[5] = o.eta; out[6] = o.phi0; out[7] = o.pt;
-    out[8] = o.score; out[9] = near;
+    out[8] = o.score; out[9] = near; out[10] = o.sigk;
     return ok;
 }
 
@@ -1139,7 +1149,8 @@ void oracle_pls_d(const OCfg* c, const double* q, int32_t* iout, double* dout) {
     dout[0] = o.kappa; dout[1] = o.sigk; dout[2] = o.eta; dout[3] = o.phi0; dout[4] = o.z0; dout[5] = o.pt;
 }
 
-// pT3 (n = 6) / pT5 (n = 8) on rows [n][6] (3 pixel rows first); out = {kappa, chi2_rphi, chi2_rz, score, near}
+// pT3 (n = 6) / pT5 (n = 8) on rows [n][6] (3 pixel rows first);
+// out = {kappa, chi2_rphi, chi2_rz, score, near, dkappa, thr_dkappa}
 int oracle_pt_d(const OCfg* c, const double* rows, int n, double kappa_pls, double sigk_pls, double kappa_t,
                 double sigk_t, double* out) {
     Pt P[8];
@@ -1147,7 +1158,7 @@ int oracle_pt_d(const OCfg* c, const double* rows, int n, double kappa_pls, doub
     PT o;
     bool near = false;
     bool ok = pt_eval(*c, P, n, kappa_pls, sigk_pls, kappa_t, sigk_t, n == 8 ? c->chi2_rphi_pt5 : c->chi2_rphi_pt3,
-                      n == 8 ? c->chi2_rz_pt5 : c->chi2_rz_pt3, o, near);
+                      n == 8 ? c->chi2_rz_pt5 : c->chi2_rz_pt3, o, near, out + 5);
     out[0] = o.kappa; out[1] = o.chi2_rphi; out[2] = o.chi2_rz; out[3] = o.score; out[4] = near;
     return ok;
 }

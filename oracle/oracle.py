@@ -217,11 +217,11 @@ class Predicates:
                               near=bool(out[6]))
 
     def t5(self, rows):
-        out = np.zeros(10)
+        out = np.zeros(11)
         r = _d(rows)
         ok = lib().oracle_t5_d(C.byref(self.s.cfg), _ptr(r), _ptr(out))
         return bool(ok), dict(dkappa=out[0], thr_dkappa=out[1], kappa=out[2], chi2_rphi=out[3], chi2_rz=out[4],
-                              eta=out[5], phi0=out[6], pt=out[7], score=out[8], near=bool(out[9]))
+                              eta=out[5], phi0=out[6], pt=out[7], score=out[8], near=bool(out[9]), sigk=out[10])
 
     def pls(self, q):
         io = np.zeros(3, np.int32)
@@ -234,6 +234,7 @@ class Predicates:
     def pt(self, rows, kappa_pls, sigk_pls, kappa_t, sigk_t):
         r = _d(rows)
         n = len(r) // 6
-        out = np.zeros(5)
+        out = np.zeros(7)
         ok = lib().oracle_pt_d(C.byref(self.s.cfg), _ptr(r), n, kappa_pls, sigk_pls, kappa_t, sigk_t, _ptr(out))
-        return bool(ok), dict(kappa=out[0], chi2_rphi=out[1], chi2_rz=out[2], score=out[3], near=bool(out[4]))
+        return bool(ok), dict(kappa=out[0], chi2_rphi=out[1], chi2_rz=out[2], score=out[3], near=bool(out[4]),
+                              dkappa=out[5], thr_dkappa=out[6])
