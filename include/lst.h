@@ -262,18 +262,22 @@ lst_status lst_get_kernel_times(lst_ctx* ctx, int32_t capacity, int32_t* n_out, 
  * is a library service). For callers that cannot allocate device memory: a
  * host framework that owns the device budget through its own pool and forbids
  * its plugins from calling cudaMalloc, or a latency-critical loop that must
- * not pay for an allocation. It runs the hit binning and mini-doublet kernels
- * of lst_run_batch on one event and allocates nothing: its scratch (bucket
- * counters, sorted hits, module table in device layout, MD anchors) lives in
- * one file-scope device array of about 9 MB that every device loading the
- * library keeps until the process exits.
+ * not pay for an allocation. It runs the hit binning of lst_run_batch
+ * (including the per-sensor sort by input index) and a one-warp-per-module
+ * mini-doublet kernel with the same predicates on one event, and allocates
+ * nothing: its scratch (bucket counters, sorted hits, module table in device
+ * layout, MD anchors) lives in one file-scope device array of about 9 MB that
+ * every device loading the library keeps until the process exits.
  *   All pointers except cfg are DEVICE memory owned by the caller: modules
  *   (n_mod rows), the event's hits (x, y, z, module, side; n_hits), and the
  *   outputs md_lower / md_upper (hit indices), md_module, md_dphi, md_dlong
  *   with room for md_capacity rows, md_count (one int: rows written) and
  *   md_dropped (one int, may be NULL: MDs lost to the per-module bounds or to
- *   md_capacity). Rows match lst_get_objects(kind = 0) of the same event as a
- *   set (their order may differ).
+ *   md_capacity, plus hits ignored for a module id outside [0, n_mod) or a
+ *   side above 1; nonzero means the rows are not the complete set). Rows
+ *   match lst_get_objects(kind = 0) of the same event as a set (their order
+ *   may differ), truncation included: a sensor with more than 256 hits keeps
+ *   its 256 lowest input indices in both.
  *   Limits: n_hits <= 262144, n_mod <= 16384, md_capacity <= 131072; larger
  *   sizes return LST_ERR_CAPACITY before any work is enqueued.
  *   The first call on a device looks up the array's device address (on the

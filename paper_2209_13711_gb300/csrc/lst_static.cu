@@ -4,8 +4,11 @@
 // whole device budget through its own pool and forbids plugins from calling
 // cudaMalloc, or a latency-critical loop that must not pay for an allocation
 // (cudaMalloc / cudaFree can synchronize the device). For them this file
-// offers lst_build_mini_doublets_static: the hit binning and mini-doublet
-// kernels of the chain, with every scratch buffer (bucket counters and
+// offers lst_build_mini_doublets_static: the hit binning of the chain
+// (count, scan, scatter and the per-sensor sort by input index, so the same
+// hits are kept when a sensor holds more than 256) and a one-warp-per-module
+// mini-doublet kernel with the chain's predicates, with every scratch buffer
+// (bucket counters and
 // offsets, sorted hits, module table in device layout, per-module segments,
 // MD anchors) placed in one file-scope __device__ array of fixed size. The
 // caller passes device inputs and device outputs; nothing is allocated.
@@ -83,10 +86,13 @@ __global__ void k_static_prepare(MdScratch* S, const lst_module* mods, int n_mod
         S->mod[i] = make_float4(mods[i].dsep, mods[i].sig_rphi, mods[i].sig_long, float(mods[i].subdet));
 }
 
+// Rows written, and everything lost: MDs over the per-module bounds or over
+// the capacity, plus hits ignored for an invalid module id or side
+// (counters[16], counted by the binning).
 __global__ void k_static_finish(const MdScratch* S, int cap, int* count, int* dropped) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         *count = min(S->counters[0], cap);
-        if (dropped) *dropped = S->ev_drop[0];
+        if (dropped) *dropped = S->ev_drop[0] + S->counters[16];
     }
 }
 
@@ -184,6 +190,7 @@ extern "C" lst_status lst_build_mini_doublets_static(const lst_config* cfg, cons
     k_bin_count<<<hit_blocks, 256, 0, st>>>(A);
     k_bin_scan<<<1, 1024, 0, st>>>(A);
     k_bin_scatter<<<hit_blocks, 256, 0, st>>>(A);
+    k_bin_sort<<<4 * n_sm, 128, 0, st>>>(A);
     k_md<<<4 * n_sm, kMdWarps * 32, md_smem_bytes(), st>>>(A, dc);
     k_static_finish<<<1, 32, 0, st>>>(S, md_capacity, md_count, md_dropped);
     return cudaGetLastError() == cudaSuccess ? LST_OK : LST_ERR_CUDA;

@@ -241,24 +241,53 @@ def measure_peaks(device=0):
             "sm_count": p.sm_count, "clock_mhz": p.clock_khz / 1000.0}
 
 
+LST_MODULE_BYTES = C.sizeof(LstModule)
+
+
+def _device_min(t, name, dtype, n):
+    """Pointer of a contiguous CUDA tensor of the given dtype with at least n
+    elements; LstError otherwise (the library reads or writes n elements of
+    it on the device without knowing its size)."""
+    if not _on_device(t):
+        raise LstError(f"{name}: a CUDA tensor is required")
+    got = str(t.dtype).replace("torch.", "")
+    if got != dtype:
+        raise LstError(f"{name}: dtype {got}, expected {dtype}")
+    if not _contiguous(t):
+        raise LstError(f"{name}: not contiguous")
+    if _numel(t) < n:
+        raise LstError(f"{name}: {_numel(t)} elements, {n} needed")
+    return _ptr(t)
+
+
 def build_mini_doublets_static(cfg, modules, n_mod, x, y, z, module, side, n_hits, md_capacity, md_lower,
                                md_upper, md_module, md_dphi, md_dlong, md_count, md_dropped=None, stream=None):
     """lst_build_mini_doublets_static: the allocation-free MD builder of one
-    event. cfg is an LstConfig; every array is a CUDA tensor (modules: the
-    lst_module rows as bytes; x, y, z float32; module int32; side uint8;
-    outputs int32 / float32 with md_capacity rows, md_count and md_dropped one
-    int32 each, md_dropped optional). Asynchronous on `stream` (a
-    cudaStream_t handle; None: the legacy default stream)."""
-    arrays = (modules, x, y, z, module, side, md_lower, md_upper, md_module, md_dphi, md_dlong, md_count)
-    for t in arrays + ((md_dropped,) if md_dropped is not None else ()):
-        if t is not None and not (hasattr(t, "is_cuda") and t.is_cuda):
-            raise LstError("build_mini_doublets_static: every array must be a CUDA tensor")
-    p = _ptr
+    event. cfg is an LstConfig; every array is a contiguous CUDA tensor:
+    modules holds the lst_module rows as bytes (uint8, n_mod rows); x, y, z
+    float32, module int32 and side uint8 with n_hits elements; md_lower,
+    md_upper, md_module int32 and md_dphi, md_dlong float32 with md_capacity
+    elements; md_count and md_dropped (optional) one int32 each. Every array
+    is checked before the call (LstError): the library reads and writes them
+    by pointer. Asynchronous on `stream` (a cudaStream_t handle; None: the
+    legacy default stream)."""
+    n_mod, n_hits, md_capacity = int(n_mod), int(n_hits), int(md_capacity)
+    if n_mod <= 0 or n_hits < 0 or md_capacity < 0:
+        raise LstError("build_mini_doublets_static: n_mod > 0, n_hits >= 0 and md_capacity >= 0 are required")
+    ptrs = [_device_min(modules, "modules", "uint8", n_mod * LST_MODULE_BYTES)]
+    ptrs += [_device_min(a, k, dt, n_hits) for a, k, dt in ((x, "x", "float32"), (y, "y", "float32"),
+                                                               (z, "z", "float32"), (module, "module", "int32"),
+                                                               (side, "side", "uint8"))]
+    ptrs += [_device_min(a, k, dt, md_capacity) for a, k, dt in ((md_lower, "md_lower", "int32"),
+                                                                    (md_upper, "md_upper", "int32"),
+                                                                    (md_module, "md_module", "int32"),
+                                                                    (md_dphi, "md_dphi", "float32"),
+                                                                    (md_dlong, "md_dlong", "float32"))]
+    ptrs.append(_device_min(md_count, "md_count", "int32", 1))
+    ptrs.append(_device_min(md_dropped, "md_dropped", "int32", 1) if md_dropped is not None else None)
     s = C.c_void_p(stream) if stream is not None else None
-    _check(library().lst_build_mini_doublets_static(
-        C.byref(cfg), p(modules), int(n_mod), p(x), p(y), p(z), p(module), p(side), int(n_hits),
-        int(md_capacity), p(md_lower), p(md_upper), p(md_module), p(md_dphi), p(md_dlong), p(md_count),
-        p(md_dropped), s))
+    _check(library().lst_build_mini_doublets_static(C.byref(cfg), ptrs[0], n_mod, *ptrs[1:6], n_hits, md_capacity,
+                                                    *ptrs[6:], s))
 
 
 def pack_events(events):

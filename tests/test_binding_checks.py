@@ -82,3 +82,48 @@ def test_network_arrays_must_be_device_float32_of_the_right_shape():
         m.gradient(f, FakeCuda((7,), "torch.float64"))
     with pytest.raises(LstError, match="contiguous"):
         m.train_step(FakeCuda((7, 48), contiguous=False), s)
+
+
+def _static_args(n_mod=4, n_hits=5, cap=8):
+    return dict(modules=FakeCuda((n_mod * lst.LST_MODULE_BYTES,), "torch.uint8"),
+                x=FakeCuda((n_hits,)), y=FakeCuda((n_hits,)), z=FakeCuda((n_hits,)),
+                module=FakeCuda((n_hits,), "torch.int32"), side=FakeCuda((n_hits,), "torch.uint8"),
+                md_lower=FakeCuda((cap,), "torch.int32"), md_upper=FakeCuda((cap,), "torch.int32"),
+                md_module=FakeCuda((cap,), "torch.int32"), md_dphi=FakeCuda((cap,)), md_dlong=FakeCuda((cap,)),
+                md_count=FakeCuda((1,), "torch.int32"), md_dropped=FakeCuda((1,), "torch.int32"))
+
+
+@pytest.mark.parametrize("key,bad,match", [
+    ("modules", FakeCuda((4 * 20 - 1,), "torch.uint8"), "needed"),
+    ("modules", FakeCuda((80,), "torch.int32"), "dtype"),
+    ("x", np.zeros(5, np.float32), "CUDA tensor"),
+    ("y", FakeCuda((4,)), "needed"),
+    ("z", FakeCuda((5,), contiguous=False), "contiguous"),
+    ("module", FakeCuda((5,), "torch.int64"), "dtype"),
+    ("side", FakeCuda((5,), "torch.bool"), "dtype"),
+    ("md_lower", FakeCuda((7,), "torch.int32"), "needed"),
+    ("md_upper", FakeCuda((8,)), "dtype"),
+    ("md_module", FakeCuda((7,), "torch.int32"), "needed"),
+    ("md_dphi", FakeCuda((7,)), "needed"),
+    ("md_dlong", FakeCuda((8,), "torch.float64"), "dtype"),
+    ("md_count", FakeCuda((0,), "torch.int32"), "needed"),
+    ("md_dropped", FakeCuda((1,), "torch.float32"), "dtype"),
+])
+def test_static_builder_refuses_bad_arrays_before_calling_the_library(key, bad, match):
+    """Every array of the allocation-free MD builder is read or written by pointer on the device: a wrong dtype,
+    a strided view or an array shorter than n_mod rows / n_hits / md_capacity is refused on the host."""
+    assert lst.LST_MODULE_BYTES == 20
+    a = _static_args()
+    a[key] = bad
+    with pytest.raises(LstError, match=match):
+        lst.build_mini_doublets_static(None, a.pop("modules"), 4, a.pop("x"), a.pop("y"), a.pop("z"),
+                                       a.pop("module"), a.pop("side"), 5, 8, **a)
+
+
+def test_static_builder_refuses_negative_sizes():
+    a = _static_args()
+    for n_mod, n_hits, cap in ((0, 5, 8), (4, -1, 8), (4, 5, -1)):
+        b = dict(a)
+        with pytest.raises(LstError, match="required"):
+            lst.build_mini_doublets_static(None, b.pop("modules"), n_mod, b.pop("x"), b.pop("y"), b.pop("z"),
+                                           b.pop("module"), b.pop("side"), n_hits, cap, **b)
