@@ -24,7 +24,15 @@
  *   until the stream reaches the work (the copies are asynchronous). The
  *   library copies the geometry and keeps it until lst_destroy.
  *   Threading: one context per host thread; a context runs one batch at a
- *   time, and a new lst_run_batch call invalidates the previous results.
+ *   time (a new run waits on the host for the previous batch to finish).
+ *   Results: a run may return one lst_event_id per event (a handle). The
+ *   track candidates and statistics of a batch run with handles are kept in
+ *   one of LST_RESULT_SLOTS result slots until every event of the batch has
+ *   been released (lst_release_event), across later runs; a batch run
+ *   without handles gives its slot up to the next run. The intermediate
+ *   objects (lst_get_objects, lst_get_t5_candidates) belong to the last batch
+ *   only. Every getter takes an lst_event_id: a handle, or the index
+ *   (0 <= event < n_events) of an event in the last batch.
  */
 #ifndef LST_H
 #define LST_H
@@ -36,6 +44,12 @@ extern "C" {
 #endif
 
 typedef int32_t lst_status;
+
+/* An event handle: opaque, nonzero in its high 32 bits (a generation), so it
+ * never equals an event index. Stale or released handles are refused with
+ * LST_ERR_ARG. */
+typedef int64_t lst_event_id;
+#define LST_RESULT_SLOTS 4
 enum {
     LST_OK = 0,
     LST_WARN_TRUNCATED = 1,      /* an occupancy cap dropped objects (counted in lst_stats) */
@@ -44,7 +58,8 @@ enum {
     LST_ERR_OOM = -3,            /* device allocation failed at creation */
     LST_ERR_NO_GEOMETRY = -4,    /* lst_run_batch before lst_load_geometry */
     LST_ERR_TIMEOUT = -5,        /* reserved: a bounded device wait ran out */
-    LST_ERR_CAPACITY = -6        /* the batch exceeds the context's event / hit / seed capacity */
+    LST_ERR_CAPACITY = -6        /* the batch exceeds the context's event / hit / seed capacity, or every
+                                    result slot holds unreleased events */
 };
 
 /* Cut constants of the chain. The paper fixes only pt_min = 0.8 GeV (Section 2);
@@ -134,10 +149,15 @@ lst_status lst_load_geometry(lst_ctx* ctx, const lst_module* modules, int32_t n_
  * The chain is one CUDA graph per context, captured on the first call (and
  * again after a change of launch shapes, stage limits or T5 selection) and
  * replayed on `cuda_stream`; with profiling on, the kernels are launched
- * one by one instead. */
+ * one by one instead.
+ *   ids: NULL, or a HOST array of n_events that receives one handle per event
+ *   (the batch then holds its result slot until each event is released). With
+ *   every slot held, LST_ERR_CAPACITY is returned before anything is enqueued.
+ *   The chain's last stage writes the track candidates and statistics
+ *   straight into the slot: handles cost no copy. */
 lst_status lst_run_batch(lst_ctx* ctx, const lst_hits* hits, const int32_t* hit_offsets,
                          const lst_seeds* seeds, const int32_t* seed_offsets, int32_t n_events,
-                         int32_t mem_is_device, void* cuda_stream);
+                         int32_t mem_is_device, void* cuda_stream, lst_event_id* ids);
 
 /* A batch given event by event: hits[e] and seeds[e] (n_events entries, HOST
  * arrays of structs) point at each event's own arrays, host (mem_is_device =
@@ -145,23 +165,32 @@ lst_status lst_run_batch(lst_ctx* ctx, const lst_hits* hits, const int32_t* hit_
  * gathers them into its input staging with one copy per array and event on
  * `cuda_stream`, then runs the chain as lst_run_batch does. The event arrays
  * must stay valid until the stream reaches the copies. For serving loops whose
- * requests arrive with their own buffers. */
+ * requests arrive with their own buffers. ids as for lst_run_batch. */
 lst_status lst_run_events(lst_ctx* ctx, const lst_hits* hits, const lst_seeds* seeds, int32_t n_events,
-                          int32_t mem_is_device, void* cuda_stream);
+                          int32_t mem_is_device, void* cuda_stream, lst_event_id* ids);
 
-/* One event: lst_run_batch with n_events = 1. */
+/* One event (the call of the paper's per-event processing, Section 2.2): the
+ * chain of Section 2.1 / Fig. KernelFlow on one event's hits and pixel
+ * seeds, enqueued on cuda_stream; lst_run_batch with n_events = 1. id: NULL
+ * or a HOST lst_event_id that receives the event's handle. */
 lst_status lst_run_event(lst_ctx* ctx, const lst_hits* hits, const lst_seeds* seeds, int32_t mem_is_device,
-                         void* cuda_stream);
+                         void* cuda_stream, lst_event_id* id);
 
-/* Wait for the batch and copy the track candidates of event `event` (0-based
- * in the last batch) into caller-owned arrays (HOST memory): type[i] (0 pT5,
+/* Release one event of a batch run with handles; the batch's result slot is
+ * free again once all its events are released. LST_ERR_ARG for an index, a
+ * stale handle or one released before. Does not wait for the device. */
+lst_status lst_release_event(lst_ctx* ctx, lst_event_id id);
+
+/* Wait for the event's batch and copy the track candidates of `event` (a
+ * handle, or an index in the last batch) into caller-owned arrays (HOST
+ * memory): type[i] (0 pT5,
  * 1 pT3, 2 T5, 3 pLS), seed[i] (pixel seed index in the event, -1 for T5),
  * hits[10 i .. 10 i + 9] (outer-tracker hit indices in the event, -1 padded),
  * pt_eta_phi[3 i .. 3 i + 2]. Any output pointer may be NULL. At most
  * `capacity` rows are written; *n_out receives the true count and
  * LST_WARN_TRUNCATED is returned when it exceeds capacity. Candidate order is
  * unspecified. */
-lst_status lst_get_track_candidates(lst_ctx* ctx, int32_t event, int32_t capacity, int32_t* n_out,
+lst_status lst_get_track_candidates(lst_ctx* ctx, lst_event_id event, int32_t capacity, int32_t* n_out,
                                     int32_t* type, int32_t* seed, int32_t* hits, float* pt_eta_phi);
 
 /* One track candidate of a batch, as packed by the chain's last stage. */
@@ -173,7 +202,7 @@ typedef struct lst_tc {
     int32_t reserved;
 } lst_tc;
 
-/* Wait for the batch and copy every event's track candidates with two
+/* Wait for the last batch and copy every event's track candidates with two
  * copies: offsets[0 .. n_events] (HOST, caller-owned; event e owns records
  * offsets[e] .. offsets[e + 1] - 1) and at most `capacity` records into `out`
  * (HOST; may be NULL when capacity is 0). LST_WARN_TRUNCATED when the batch
@@ -182,7 +211,9 @@ typedef struct lst_tc {
 lst_status lst_get_batch_track_candidates(lst_ctx* ctx, int32_t capacity, int32_t* offsets, lst_tc* out);
 
 /* Wait for the batch and copy one intermediate collection of event `event`
- * (for parity tests). kind: 0 MD, 1 LS, 2 T3, 3 T5, 4 pLS, 5 pT5, 6 pT3.
+ * (for parity tests), which must belong to the last batch (LST_ERR_ARG
+ * otherwise: a later run has overwritten the objects). kind: 0 MD, 1 LS, 2
+ * T3, 3 T5, 4 pLS, 5 pT5, 6 pT3.
  * Rows are ints[ni * i ..] and floats[nf * i ..] (host memory) with
  *   MD : ints {lower hit, upper hit, module}              floats {dphi, dlong}
  *   LS : ints {inner MD row, outer MD row}                floats {dphi}
@@ -194,11 +225,12 @@ lst_status lst_get_batch_track_candidates(lst_ctx* ctx, int32_t capacity, int32_
  * where "row" indexes the rows returned for the same event and kind.
  * lst_object_columns gives ni and nf. Behaviour on capacity as above. */
 lst_status lst_object_columns(int32_t kind, int32_t* ni, int32_t* nf);
-lst_status lst_get_objects(lst_ctx* ctx, int32_t event, int32_t kind, int32_t capacity, int32_t* n_out,
+lst_status lst_get_objects(lst_ctx* ctx, lst_event_id event, int32_t kind, int32_t capacity, int32_t* n_out,
                            int32_t* ints, float* floats);
 
-/* Wait for the batch and copy the per-event statistics. */
-lst_status lst_get_stats(lst_ctx* ctx, int32_t event, lst_stats* out);
+/* Wait for the event's batch and copy its statistics (kept with the track
+ * candidates in the result slot). */
+lst_status lst_get_stats(lst_ctx* ctx, lst_event_id event, lst_stats* out);
 
 /* Non-blocking: 1 when the last batch has finished on the device, 0 while it
  * runs (or when no batch was run), < 0 on error. */
@@ -320,6 +352,13 @@ void lst_mlp_destroy(lst_mlp* m);
 /* Host parameter vector in / out (LST_MLP_PARAMS floats); set resets Adam. */
 lst_status lst_mlp_set_params(lst_mlp* m, const float* params);
 lst_status lst_mlp_get_params(lst_mlp* m, float* params);
+/* The whole training state, for checkpoints: parameters, Adam's first and
+ * second moments (HOST arrays of LST_MLP_PARAMS floats each) and its step
+ * count (the bias corrections depend on it). A network given the state of
+ * another continues its training exactly as the other would. Synchronous. */
+lst_status lst_mlp_get_state(lst_mlp* m, float* params, float* adam_m, float* adam_v, int64_t* step);
+lst_status lst_mlp_set_state(lst_mlp* m, const float* params, const float* adam_m, const float* adam_v,
+                             int64_t step);
 /* scores[i] = network(features[i]) for n samples (DEVICE pointers, features
  * [n][LST_MLP_INPUTS]); asynchronous on stream. */
 lst_status lst_mlp_forward(lst_mlp* m, const float* features, int32_t n, float* scores, void* stream);
@@ -342,11 +381,11 @@ lst_status lst_mlp_train_step(lst_mlp* m, const float* features, const float* la
  * training). The network must outlive its use by the context. */
 lst_status lst_set_t5_selection(lst_ctx* ctx, const lst_mlp* mlp, float threshold, float prefilter_scale,
                                 int32_t capture_features);
-/* All T5 candidates of an event (before the validity decision), HOST outputs:
+/* All T5 candidates of an event of the last batch (before the validity decision), HOST outputs:
  * features [n][LST_MLP_INPUTS] (when captured), hits [n][10] (lower, upper
  * of the five MDs), cut_pass [n] (the hand-set cut decision), score [n] (the
  * network score when attached). Any output may be NULL. */
-lst_status lst_get_t5_candidates(lst_ctx* ctx, int32_t event, int32_t capacity, int32_t* n_out, float* features,
+lst_status lst_get_t5_candidates(lst_ctx* ctx, lst_event_id event, int32_t capacity, int32_t* n_out, float* features,
                                  int32_t* hits, int32_t* cut_pass, float* score);
 
 /* ---- calibration (measurement support; not on the track-finding path) ----

@@ -688,14 +688,18 @@ __global__ void k_clean_pls(Arena A, DevCfg c) {
     }
 }
 
-// The batch's track candidates, event after event, into one record array:
-// one block per event (grid-stride over events) sums the counts of the
-// events before it for its offset, then copies its slab.
+// The batch's track candidates, event after event, into the record array of
+// the batch's result slot: one block per event (grid-stride over events)
+// sums the counts of the events before it for its offset, then copies its
+// slab and the event's statistics (every other stage has finished).
 __global__ void k_tc_pack(Arena A) {
     pdl_begin();
     __shared__ int red[32];
     __shared__ int s_off;
     const int n_ev = A.bd->n_ev;
+    TcRec* const out = A.bd->out_rec;
+    int* const out_off = A.bd->out_off;
+    int* const out_stats = A.bd->out_stats;
     const int nw = (blockDim.x + 31) >> 5, w = threadIdx.x >> 5;
     for (int e = blockIdx.x; e < n_ev; e += gridDim.x) {
         int part = 0;
@@ -711,9 +715,13 @@ __global__ void k_tc_pack(Arena A) {
         __syncthreads();
         const int off = s_off, n = min(A.tc_cnt[e], A.tc_cap);
         if (threadIdx.x == 0) {
-            A.tc_off[e] = off;
-            if (e == n_ev - 1) A.tc_off[n_ev] = off + n;
+            out_off[e] = off;
+            if (e == n_ev - 1) out_off[n_ev] = off + n;
         }
+        if (threadIdx.x < 16)
+            out_stats[kSlotStats * e + threadIdx.x] =
+                threadIdx.x < 8 ? A.ev_counts[8 * e + threadIdx.x] : A.ev_drop[8 * e + threadIdx.x - 8];
+        if (threadIdx.x == 16) out_stats[kSlotStats * e + 16] = n;
         const size_t src = (size_t)e * A.tc_cap;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             TcRec r;
@@ -726,7 +734,7 @@ __global__ void k_tc_pack(Arena A) {
             r.eta = A.tc_eta[src + i];
             r.phi = A.tc_phi[src + i];
             r.reserved = 0;
-            A.tc_rec[off + i] = r;
+            out[off + i] = r;
         }
         __syncthreads();
     }

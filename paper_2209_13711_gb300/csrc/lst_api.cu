@@ -113,6 +113,22 @@ struct lst_ctx {
     cudaEvent_t done = nullptr;
     bool ran = false;
     int n_ev = 0;
+    // Result slots: the packed track candidates, offsets and per-event
+    // statistics of a batch (written by the chain's last stage). A batch run
+    // with handles holds its slot until every event is released; a batch run
+    // without gives it up to the next run.
+    struct Slot {
+        TcRec* rec = nullptr;
+        int* off = nullptr;
+        int* stats = nullptr;
+        cudaEvent_t done = nullptr;
+        uint32_t gen = 0;              // generation of the batch in the slot (0: none)
+        int n_ev = 0;
+        int held = 0;                  // events not released (0: the slot is free)
+        std::vector<char> released;
+    } slot[LST_RESULT_SLOTS];
+    uint32_t next_gen = 1;
+    int last = -1;                     // slot of the last batch (its intermediate objects are in the arena)
     int launches = 0;
     std::vector<int> hit_off_host, seed_off_host;
     bool profiling = false;
@@ -251,6 +267,11 @@ lst_status lst_create(lst_ctx** out, const lst_config* cfg, const lst_capacity* 
         delete c;
         return LST_ERR_CUDA;
     }
+    for (auto& sl : c->slot)
+        if (cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            lst_destroy(c);
+            return LST_ERR_CUDA;
+        }
     *out = c;
     return LST_OK;
 }
@@ -267,6 +288,8 @@ void lst_destroy(lst_ctx* c) {
     if (c->side_stream) cudaStreamDestroy(c->side_stream);
     for (cudaEvent_t e : {c->ev_fork, c->ev_t3, c->ev_plan, c->ev_pt3})
         if (e) cudaEventDestroy(e);
+    for (auto& sl : c->slot)
+        if (sl.done) cudaEventDestroy(sl.done);
     if (c->dev_mem) cudaFree(c->dev_mem);
     if (c->h_offsets) cudaFreeHost(c->h_offsets);
     if (c->h_bd) cudaFreeHost(c->h_bd);
@@ -378,8 +401,11 @@ static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n
     A.tc_type = b.take<int>(TC); A.tc_seed = b.take<int>(TC); A.tc_obj = b.take<int>(TC);
     A.tc_hits = b.take<int>(10 * TC);
     A.tc_pt = b.take<float>(TC); A.tc_eta = b.take<float>(TC); A.tc_phi = b.take<float>(TC);
-    A.tc_rec = b.take<TcRec>(TC);
-    A.tc_off = b.take<int>(E + 1);
+    for (auto& sl : c->slot) {
+        sl.rec = b.take<TcRec>(TC);
+        sl.off = b.take<int>(E + 1);
+        sl.stats = b.take<int>(E * kSlotStats);
+    }
 }
 
 lst_status lst_load_geometry(lst_ctx* c, const lst_module* mods, int32_t n_mod, const int32_t* conn_off,
@@ -434,6 +460,13 @@ lst_status lst_load_geometry(lst_ctx* c, const lst_module* mods, int32_t n_mod, 
     }
     c->geometry = true;
     c->ran = false;
+    for (auto& sl : c->slot) {      // the results lived in the freed allocation
+        sl.gen = 0;
+        sl.n_ev = 0;
+        sl.held = 0;
+        sl.released.clear();
+    }
+    c->last = -1;
     return LST_OK;
 }
 
@@ -554,7 +587,24 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile, cudaStream_
 // Offsets and descriptor are in the pinned staging (h_offsets, h_bd); copy
 // them, launch the chain (captured graph, or direct launches when profiling)
 // and record the completion event.
-static lst_status launch_prepared(lst_ctx* c, cudaStream_t st, int n_ev) {
+// A slot for the next batch: the free one (no held events) that has gone
+// longest without a batch; -1 when every slot is held.
+static int free_slot(const lst_ctx* c) {
+    int best = -1;
+    for (int k = 0; k < LST_RESULT_SLOTS; ++k)
+        if (c->slot[k].held == 0 && (best < 0 || c->slot[k].gen < c->slot[best].gen)) best = k;
+    return best;
+}
+
+static lst_event_id make_id(uint32_t gen, int k, int e) {
+    return (lst_event_id)(((uint64_t)gen << 32) | ((uint64_t)k << 24) | (uint64_t)e);
+}
+
+static lst_status launch_prepared(lst_ctx* c, cudaStream_t st, int n_ev, int k, lst_event_id* ids) {
+    lst_ctx::Slot& sl = c->slot[k];
+    c->h_bd->out_rec = sl.rec;
+    c->h_bd->out_off = sl.off;
+    c->h_bd->out_stats = sl.stats;
     CK(cudaMemcpyAsync(c->d_hit_off, c->h_offsets, sizeof(int) * (n_ev + 1), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_seed_off, c->h_offsets + n_ev + 1, sizeof(int) * (n_ev + 1), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_bd, c->h_bd, sizeof(BatchDesc), cudaMemcpyHostToDevice, st));
@@ -578,7 +628,16 @@ static lst_status launch_prepared(lst_ctx* c, cudaStream_t st, int n_ev) {
         CK(cudaGraphLaunch(c->graph, st));
     }
     CK(cudaEventRecord(c->done, st));
+    CK(cudaEventRecord(sl.done, st));
     c->ran = true;
+    sl.gen = c->next_gen++;
+    if (c->next_gen == 0) c->next_gen = 1;
+    sl.n_ev = n_ev;
+    sl.held = ids ? n_ev : 0;
+    sl.released.assign(n_ev, 0);
+    c->last = k;
+    if (ids)
+        for (int e = 0; e < n_ev; ++e) ids[e] = make_id(sl.gen, k, e);
     return LST_OK;
 }
 
@@ -598,7 +657,8 @@ static void use_staging(lst_ctx* c, BatchDesc& d) {
 }
 
 lst_status lst_run_batch(lst_ctx* c, const lst_hits* hits, const int32_t* hit_off, const lst_seeds* seeds,
-                         const int32_t* seed_off, int32_t n_ev, int32_t mem_is_device, void* stream_) {
+                         const int32_t* seed_off, int32_t n_ev, int32_t mem_is_device, void* stream_,
+                         lst_event_id* ids) {
     if (!c) return LST_ERR_ARG;
     if (!c->geometry) return LST_ERR_NO_GEOMETRY;
     if (!hits || !hit_off || !seeds || !seed_off || n_ev <= 0) return LST_ERR_ARG;
@@ -610,6 +670,8 @@ lst_status lst_run_batch(lst_ctx* c, const lst_hits* hits, const int32_t* hit_of
         if (hit_off[e + 1] < hit_off[e] || seed_off[e + 1] < seed_off[e]) return LST_ERR_ARG;
     if ((hits->n && (!hits->x || !hits->y || !hits->z || !hits->module || !hits->side)) || (seeds->n && !seeds->xyz))
         return LST_ERR_ARG;
+    const int k = free_slot(c);
+    if (k < 0) return LST_ERR_CAPACITY;              // every result slot is held: release events first
     CK(cudaSetDevice(c->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream_);
     if (c->ran) CK(cudaEventSynchronize(c->done));   // the pinned staging is reused
@@ -633,11 +695,11 @@ lst_status lst_run_batch(lst_ctx* c, const lst_hits* hits, const int32_t* hit_of
         if (S) CK(cudaMemcpyAsync(c->in_seeds, seeds->xyz, 36 * S, cudaMemcpyHostToDevice, st));
         use_staging(c, d);
     }
-    return launch_prepared(c, st, n_ev);
+    return launch_prepared(c, st, n_ev, k, ids);
 }
 
 lst_status lst_run_events(lst_ctx* c, const lst_hits* hits, const lst_seeds* seeds, int32_t n_ev,
-                          int32_t mem_is_device, void* stream_) {
+                          int32_t mem_is_device, void* stream_, lst_event_id* ids) {
     if (!c) return LST_ERR_ARG;
     if (!c->geometry) return LST_ERR_NO_GEOMETRY;
     if (!hits || !seeds || n_ev <= 0) return LST_ERR_ARG;
@@ -652,6 +714,8 @@ lst_status lst_run_events(lst_ctx* c, const lst_hits* hits, const lst_seeds* see
         so[e + 1] = so[e] + q.n;
         if (ho[e + 1] > c->cap.max_hits || so[e + 1] > c->cap.max_seeds) return LST_ERR_CAPACITY;
     }
+    const int k = free_slot(c);
+    if (k < 0) return LST_ERR_CAPACITY;
     CK(cudaSetDevice(c->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream_);
     if (c->ran) CK(cudaEventSynchronize(c->done));
@@ -674,14 +738,26 @@ lst_status lst_run_events(lst_ctx* c, const lst_hits* hits, const lst_seeds* see
     d.n_hits = ho[n_ev];
     d.n_seeds = so[n_ev];
     use_staging(c, d);
-    return launch_prepared(c, st, n_ev);
+    return launch_prepared(c, st, n_ev, k, ids);
 }
 
 lst_status lst_run_event(lst_ctx* c, const lst_hits* hits, const lst_seeds* seeds, int32_t mem_is_device,
-                         void* stream) {
+                         void* stream, lst_event_id* id) {
     if (!hits || !seeds) return LST_ERR_ARG;
     int32_t ho[2] = {0, hits->n}, so[2] = {0, seeds->n};
-    return lst_run_batch(c, hits, ho, seeds, so, 1, mem_is_device, stream);
+    return lst_run_batch(c, hits, ho, seeds, so, 1, mem_is_device, stream, id);
+}
+
+lst_status lst_release_event(lst_ctx* c, lst_event_id id) {
+    if (!c || id < 0 || (id >> 32) == 0) return LST_ERR_ARG;
+    const uint32_t gen = (uint32_t)((uint64_t)id >> 32);
+    const int k = (int)(((uint64_t)id >> 24) & 0xff), e = (int)(id & 0xffffff);
+    if (k >= LST_RESULT_SLOTS) return LST_ERR_ARG;
+    lst_ctx::Slot& sl = c->slot[k];
+    if (sl.gen != gen || sl.held == 0 || e >= sl.n_ev || sl.released[e]) return LST_ERR_ARG;
+    sl.released[e] = 1;
+    --sl.held;
+    return LST_OK;
 }
 
 int32_t lst_last_launch_count(lst_ctx* c) { return c ? c->launches : 0; }
@@ -822,7 +898,7 @@ static lst_status time_stages(lst_ctx* c, const lst_hits* hits, const int32_t* h
     std::vector<float> t[kNumLaunch];
     float tot = 0.f;
     for (int r = 0; r < reps; ++r) {
-        lst_status s = lst_run_batch(c, hits, hit_off, seeds, seed_off, n_ev, mem_is_device, stream);
+        lst_status s = lst_run_batch(c, hits, hit_off, seeds, seed_off, n_ev, mem_is_device, stream, nullptr);
         if (s != LST_OK) return s;
         CK(cudaEventSynchronize(c->done));
         CK(cudaGetLastError());
@@ -900,13 +976,36 @@ lst_status lst_autotune(lst_ctx* c, const lst_hits* hits, const int32_t* hit_off
     return s2 != LST_OK ? s2 : s3;
 }
 
-static lst_status wait_batch(lst_ctx* c, int32_t event) {
-    if (!c) return LST_ERR_ARG;
-    if (!c->ran) return LST_ERR_ARG;
-    if (event < 0 || event >= c->n_ev) return LST_ERR_ARG;
+// The slot k and event e of `id`: a handle of a held batch, or an event index
+// (0 <= id < n_events) of the last batch. Waits for that batch.
+static lst_status resolve(lst_ctx* c, lst_event_id id, int& k, int& e) {
+    if (!c || !c->ran || c->last < 0 || id < 0) return LST_ERR_ARG;
+    if ((id >> 32) == 0) {
+        k = c->last;
+        e = (int)id;
+        if (e >= c->slot[k].n_ev) return LST_ERR_ARG;
+    } else {
+        const uint32_t gen = (uint32_t)((uint64_t)id >> 32);
+        k = (int)(((uint64_t)id >> 24) & 0xff);
+        e = (int)(id & 0xffffff);
+        if (k >= LST_RESULT_SLOTS) return LST_ERR_ARG;
+        const lst_ctx::Slot& sl = c->slot[k];
+        if (sl.gen != gen || sl.held == 0 || e >= sl.n_ev || sl.released[e]) return LST_ERR_ARG;
+    }
     CK(cudaSetDevice(c->device));
-    CK(cudaEventSynchronize(c->done));
+    CK(cudaEventSynchronize(c->slot[k].done));
     CK(cudaGetLastError());
+    return LST_OK;
+}
+
+// As resolve, for the intermediate objects: only the last batch has them.
+static lst_status wait_batch(lst_ctx* c, lst_event_id id, int32_t& event) {
+    int k = 0, e = 0;
+    lst_status s = resolve(c, id, k, e);
+    if (s != LST_OK) return s;
+    if (k != c->last) return LST_ERR_ARG;
+    CK(cudaEventSynchronize(c->done));
+    event = e;
     return LST_OK;
 }
 
@@ -934,9 +1033,10 @@ lst_status lst_set_t5_selection(lst_ctx* c, const lst_mlp* mlp, float threshold,
     return LST_OK;
 }
 
-lst_status lst_get_t5_candidates(lst_ctx* c, int32_t event, int32_t capacity, int32_t* n_out, float* features,
+lst_status lst_get_t5_candidates(lst_ctx* c, lst_event_id id, int32_t capacity, int32_t* n_out, float* features,
                                  int32_t* hits, int32_t* cut_pass, float* score) {
-    lst_status s = wait_batch(c, event);
+    int32_t event = 0;
+    lst_status s = wait_batch(c, id, event);
     if (s != LST_OK) return s;
     if (capacity < 0) return LST_ERR_ARG;
     const Arena& A = c->A;
@@ -992,57 +1092,55 @@ lst_status lst_get_counters(lst_ctx* c, int32_t* out, int32_t n) {
     return LST_OK;
 }
 
-lst_status lst_get_stats(lst_ctx* c, int32_t event, lst_stats* out) {
-    lst_status s = wait_batch(c, event);
+lst_status lst_get_stats(lst_ctx* c, lst_event_id id, lst_stats* out) {
+    int k = 0, e = 0;
+    lst_status s = resolve(c, id, k, e);
     if (s != LST_OK) return s;
     if (!out) return LST_ERR_ARG;
-    int cnt[8], drop[8], tc = 0;
-    CK(cudaMemcpy(cnt, c->A.ev_counts + 8 * event, sizeof cnt, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(drop, c->A.ev_drop + 8 * event, sizeof drop, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&tc, c->A.tc_cnt + event, sizeof(int), cudaMemcpyDeviceToHost));
-    for (int k = 0; k < 8; ++k) { out->counts[k] = cnt[k]; out->dropped[k] = drop[k]; }
-    out->counts[7] = std::min(tc, c->A.tc_cap);
+    int st[kSlotStats];
+    CK(cudaMemcpy(st, c->slot[k].stats + kSlotStats * (size_t)e, sizeof st, cudaMemcpyDeviceToHost));
+    for (int j = 0; j < 8; ++j) { out->counts[j] = st[j]; out->dropped[j] = st[8 + j]; }
+    out->counts[7] = st[16];
     return LST_OK;
 }
 
-lst_status lst_get_track_candidates(lst_ctx* c, int32_t event, int32_t capacity, int32_t* n_out, int32_t* type,
+static_assert(sizeof(lst_tc) == sizeof(TcRec), "lst_tc mirrors the packed record");
+
+lst_status lst_get_track_candidates(lst_ctx* c, lst_event_id id, int32_t capacity, int32_t* n_out, int32_t* type,
                                     int32_t* seed, int32_t* hits, float* pet) {
-    lst_status s = wait_batch(c, event);
+    int k = 0, e = 0;
+    lst_status s = resolve(c, id, k, e);
     if (s != LST_OK) return s;
     if (capacity < 0) return LST_ERR_ARG;
-    int n = 0;
-    CK(cudaMemcpy(&n, c->A.tc_cnt + event, sizeof(int), cudaMemcpyDeviceToHost));
-    n = std::min(n, c->A.tc_cap);
+    int off[2];
+    CK(cudaMemcpy(off, c->slot[k].off + e, sizeof off, cudaMemcpyDeviceToHost));
+    const int n = off[1] - off[0];
     if (n_out) *n_out = n;
-    const int k = std::min(n, (int)capacity);
-    const size_t o = (size_t)event * c->A.tc_cap;
-    if (k > 0) {
-        if (type) CK(cudaMemcpy(type, c->A.tc_type + o, 4 * k, cudaMemcpyDeviceToHost));
-        if (seed) CK(cudaMemcpy(seed, c->A.tc_seed + o, 4 * k, cudaMemcpyDeviceToHost));
-        if (hits) CK(cudaMemcpy(hits, c->A.tc_hits + 10 * o, 40 * (size_t)k, cudaMemcpyDeviceToHost));
-        if (pet) {
-            std::vector<float> a, b2, d;
-            FETCH(a, c->A.tc_pt + o, k);
-            FETCH(b2, c->A.tc_eta + o, k);
-            FETCH(d, c->A.tc_phi + o, k);
-            for (int i = 0; i < k; ++i) { pet[3 * i] = a[i]; pet[3 * i + 1] = b2[i]; pet[3 * i + 2] = d[i]; }
+    const int m = std::min(n, (int)capacity);
+    if (m > 0 && (type || seed || hits || pet)) {
+        std::vector<lst_tc> r(m);
+        CK(cudaMemcpy(r.data(), c->slot[k].rec + off[0], sizeof(lst_tc) * (size_t)m, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < m; ++i) {
+            if (type) type[i] = r[i].type;
+            if (seed) seed[i] = r[i].seed;
+            if (hits) std::memcpy(hits + 10 * (size_t)i, r[i].hits, sizeof r[i].hits);
+            if (pet) { pet[3 * i] = r[i].pt; pet[3 * i + 1] = r[i].eta; pet[3 * i + 2] = r[i].phi0; }
         }
     }
     return n > capacity ? LST_WARN_TRUNCATED : LST_OK;
 }
 
-static_assert(sizeof(lst_tc) == sizeof(TcRec), "lst_tc mirrors the packed record");
-
 lst_status lst_get_batch_track_candidates(lst_ctx* c, int32_t capacity, int32_t* offsets, lst_tc* out) {
     if (!c || !offsets || capacity < 0 || (capacity > 0 && !out)) return LST_ERR_ARG;
-    if (!c->ran) return LST_ERR_ARG;
+    if (!c->ran || c->last < 0) return LST_ERR_ARG;
+    const lst_ctx::Slot& sl = c->slot[c->last];
     CK(cudaSetDevice(c->device));
-    CK(cudaEventSynchronize(c->done));
+    CK(cudaEventSynchronize(sl.done));
     CK(cudaGetLastError());
-    CK(cudaMemcpy(offsets, c->A.tc_off, sizeof(int) * (c->n_ev + 1), cudaMemcpyDeviceToHost));
-    const int total = offsets[c->n_ev];
-    const int k = std::min(total, (int)capacity);
-    if (k > 0) CK(cudaMemcpy(out, c->A.tc_rec, sizeof(lst_tc) * (size_t)k, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(offsets, sl.off, sizeof(int) * (sl.n_ev + 1), cudaMemcpyDeviceToHost));
+    const int total = offsets[sl.n_ev];
+    const int m = std::min(total, (int)capacity);
+    if (m > 0) CK(cudaMemcpy(out, sl.rec, sizeof(lst_tc) * (size_t)m, cudaMemcpyDeviceToHost));
     return total > capacity ? LST_WARN_TRUNCATED : LST_OK;
 }
 
@@ -1055,9 +1153,10 @@ lst_status lst_object_columns(int32_t kind, int32_t* ni, int32_t* nf) {
     return LST_OK;
 }
 
-lst_status lst_get_objects(lst_ctx* c, int32_t event, int32_t kind, int32_t capacity, int32_t* n_out, int32_t* I,
+lst_status lst_get_objects(lst_ctx* c, lst_event_id id, int32_t kind, int32_t capacity, int32_t* n_out, int32_t* I,
                            float* F) {
-    lst_status s = wait_batch(c, event);
+    int32_t event = 0;
+    lst_status s = wait_batch(c, id, event);
     if (s != LST_OK) return s;
     if (kind < 0 || kind > 6 || capacity < 0) return LST_ERR_ARG;
     const Arena& A = c->A;

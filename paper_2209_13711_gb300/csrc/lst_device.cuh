@@ -72,6 +72,10 @@ template <> __device__ __forceinline__ float cval<float>(double, float f) { retu
 template <> __device__ __forceinline__ double cval<double>(double d, float) { return d; }
 
 // Shape and inputs of the batch being processed (device memory).
+// Per-event statistics a result slot keeps: counts[8], dropped[8], track
+// candidates (the lst_stats kinds).
+constexpr int kSlotStats = 17;
+
 struct BatchDesc {
     int n_ev, n_hits, n_seeds, pad;
     const float* hx;
@@ -80,6 +84,10 @@ struct BatchDesc {
     const int* hmod;
     const uint8_t* hside;
     const float* seeds;           // [n_seeds][9]
+    // the batch's result slot (chosen per run; the last stage writes it)
+    struct TcRec* out_rec;        // packed track candidates, event after event
+    int* out_off;                 // [n_ev + 1] record offsets
+    int* out_stats;               // [n_ev][kSlotStats]
 };
 
 // Device buffers of one context (all preallocated; flat object arenas with
@@ -228,8 +236,6 @@ struct Arena {
     float* tc_eta;
     float* tc_phi;
     // the batch's track candidates packed event after event (the last stage)
-    struct TcRec* tc_rec;         // [n_ev * tc_cap]
-    int* tc_off;                  // [n_ev + 1]
 };
 
 // One packed track candidate; the layout of lst_tc in the C ABI.

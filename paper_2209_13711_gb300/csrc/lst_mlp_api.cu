@@ -156,6 +156,31 @@ lst_status lst_mlp_get_params(lst_mlp* m, float* params) {
     return LST_OK;
 }
 
+lst_status lst_mlp_get_state(lst_mlp* m, float* params, float* adam_m, float* adam_v, int64_t* step) {
+    if (!m || !params || !adam_m || !adam_v || !step) return LST_ERR_ARG;
+    CKM(cudaSetDevice(m->device));
+    CKM(cudaDeviceSynchronize());
+    CKM(cudaMemcpy(params, m->theta, 4 * kParams, cudaMemcpyDeviceToHost));
+    CKM(cudaMemcpy(adam_m, m->m, 4 * kParams, cudaMemcpyDeviceToHost));
+    CKM(cudaMemcpy(adam_v, m->v, 4 * kParams, cudaMemcpyDeviceToHost));
+    *step = m->step;
+    return LST_OK;
+}
+
+lst_status lst_mlp_set_state(lst_mlp* m, const float* params, const float* adam_m, const float* adam_v,
+                             int64_t step) {
+    if (!m || !params || !adam_m || !adam_v || step < 0) return LST_ERR_ARG;
+    CKM(cudaSetDevice(m->device));
+    CKM(cudaDeviceSynchronize());
+    CKM(cudaMemcpy(m->theta, params, 4 * kParams, cudaMemcpyHostToDevice));
+    CKM(cudaMemcpy(m->m, adam_m, 4 * kParams, cudaMemcpyHostToDevice));
+    CKM(cudaMemcpy(m->v, adam_v, 4 * kParams, cudaMemcpyHostToDevice));
+    m->step = (long)step;
+    derive(m, nullptr);
+    CKM(cudaDeviceSynchronize());
+    return LST_OK;
+}
+
 lst_status lst_mlp_forward(lst_mlp* m, const float* X, int32_t n, float* scores, void* stream) {
     if (!m || n < 0 || (n && (!X || !scores))) return LST_ERR_ARG;
     if (n == 0) return LST_OK;

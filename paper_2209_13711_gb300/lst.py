@@ -43,6 +43,9 @@ class LstCapacity(C.Structure):
         "pt3_per_event", "pt5_per_event", "tc_per_event")]
 
 
+LST_RESULT_SLOTS = 4          # result slots of a context (include/lst.h)
+
+
 class LstModule(C.Structure):
     _fields_ = [("subdet", C.c_int32), ("layer", C.c_int32), ("dsep", C.c_float), ("sig_rphi", C.c_float),
                 ("sig_long", C.c_float)]
@@ -81,7 +84,7 @@ def library():
         if not os.path.exists(LIB_PATH):
             raise LstError(f"liblst.so is not built ({LIB_PATH}); run paper_2209_13711_gb300/build.py")
         L = C.CDLL(LIB_PATH)
-        vp, i32, p = C.c_void_p, C.c_int32, C.POINTER
+        vp, i32, i64, p = C.c_void_p, C.c_int32, C.c_int64, C.POINTER
         L.lst_status_str.restype = C.c_char_p
         L.lst_status_str.argtypes = [i32]
         L.lst_config_default.argtypes = [vp]
@@ -90,12 +93,13 @@ def library():
         L.lst_destroy.argtypes = [vp]
         L.lst_destroy.restype = None
         L.lst_load_geometry.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32]
-        L.lst_run_batch.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp]
-        L.lst_run_event.argtypes = [vp, vp, vp, i32, vp]
-        L.lst_get_track_candidates.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
+        L.lst_run_batch.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp, vp]
+        L.lst_run_event.argtypes = [vp, vp, vp, i32, vp, vp]
+        L.lst_release_event.argtypes = [vp, i64]
+        L.lst_get_track_candidates.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp]
         L.lst_object_columns.argtypes = [i32, vp, vp]
-        L.lst_get_objects.argtypes = [vp, i32, i32, i32, vp, vp, vp]
-        L.lst_get_stats.argtypes = [vp, i32, vp]
+        L.lst_get_objects.argtypes = [vp, i64, i32, i32, vp, vp, vp]
+        L.lst_get_stats.argtypes = [vp, i64, vp]
         L.lst_last_launch_count.argtypes = [vp]
         L.lst_set_profiling.argtypes = [vp, i32]
         L.lst_get_counters.argtypes = [vp, vp, i32]
@@ -105,7 +109,7 @@ def library():
         L.lst_get_launch_config.argtypes = [vp, i32, C.POINTER(C.c_char_p), vp, vp, vp]
         L.lst_set_launch_config.argtypes = [vp, i32, i32, i32]
         L.lst_autotune.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp, i32, vp, vp]
-        L.lst_run_events.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.lst_run_events.argtypes = [vp, vp, vp, i32, i32, vp, vp]
         L.lst_get_batch_track_candidates.argtypes = [vp, i32, vp, vp]
         L.lst_query.argtypes = [vp]
         L.lst_query.restype = i32
@@ -116,11 +120,13 @@ def library():
         L.lst_mlp_destroy.restype = None
         L.lst_mlp_set_params.argtypes = [vp, vp]
         L.lst_mlp_get_params.argtypes = [vp, vp]
+        L.lst_mlp_get_state.argtypes = [vp, vp, vp, vp, vp]
+        L.lst_mlp_set_state.argtypes = [vp, vp, vp, vp, i64]
         L.lst_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
         L.lst_mlp_gradient.argtypes = [vp, vp, vp, i32, vp, vp, vp]
         L.lst_mlp_train_step.argtypes = [vp, vp, vp, i32, C.c_float, vp, vp]
         L.lst_set_t5_selection.argtypes = [vp, vp, C.c_float, C.c_float, i32]
-        L.lst_get_t5_candidates.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
+        L.lst_get_t5_candidates.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp]
         L.lst_get_kernel_times.argtypes = [vp, i32, vp, vp, vp]
         L.lst_measure_peaks.argtypes = [i32, vp]
         L.lst_build_mini_doublets_static.argtypes = [vp, vp, i32] + [vp] * 5 + [i32, i32] + [vp] * 7 + [vp]
@@ -129,7 +135,9 @@ def library():
                   "lst_get_stats", "lst_last_launch_count", "lst_set_profiling", "lst_get_kernel_times",
                   "lst_get_counters", "lst_mlp_create", "lst_mlp_set_params", "lst_mlp_get_params",
                   "lst_mlp_forward", "lst_mlp_gradient", "lst_mlp_train_step", "lst_set_t5_selection",
-                  "lst_get_t5_candidates", "lst_measure_peaks", "lst_build_mini_doublets_static"):
+                  "lst_get_t5_candidates", "lst_measure_peaks", "lst_build_mini_doublets_static",
+                  "lst_release_event", "lst_run_events", "lst_get_batch_track_candidates", "lst_mlp_get_state",
+                  "lst_mlp_set_state"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -323,6 +331,7 @@ class Context:
         co, ct, so, st = [np.ascontiguousarray(a, np.int32) for a in maps]
         _check(L.lst_load_geometry(self._h, mods, n_mod, _ptr(co), _ptr(ct), _ptr(so), _ptr(st), len(so) - 1))
         self.n_events = 0
+        self.event_ids = None
         self._keep = None
 
     def close(self):
@@ -341,9 +350,12 @@ class Context:
         return self._cap
 
     # -- running ----------------------------------------------------------
-    def run_packed(self, b, stream=None):
+    def run_packed(self, b, stream=None, keep=False):
         """b: dict from pack_events (numpy) or the same keys as CUDA torch tensors
-        (hit_off / seed_off stay numpy: they are host arrays)."""
+        (hit_off / seed_off stay numpy: they are host arrays). keep=True asks
+        for event handles: the batch's track candidates and statistics stay
+        readable through them across later runs until release(); the handles
+        are returned (and kept in self.event_ids)."""
         dev = _input_kind(b, int(b["hit_off"][-1]), int(b["seed_off"][-1]))
         hits = LstHits(_ptr(b["x"]), _ptr(b["y"]), _ptr(b["z"]), _ptr(b["module"]), _ptr(b["side"]),
                        int(b["hit_off"][-1]))
@@ -352,14 +364,22 @@ class Context:
         so = np.ascontiguousarray(b["seed_off"], np.int32)
         self._keep = (b, ho, so)          # the library may read host inputs until the call returns
         s = C.c_void_p(stream) if stream is not None else None
+        ids = (C.c_int64 * (len(ho) - 1))() if keep else None
         _check(library().lst_run_batch(self._h, C.byref(hits), _ptr(ho), C.byref(seeds), _ptr(so), len(ho) - 1,
-                                       1 if dev else 0, s))
+                                       1 if dev else 0, s, ids))
         self.n_events = len(ho) - 1
+        self.event_ids = list(ids) if keep else None
+        return self.event_ids
 
-    def run(self, events, stream=None):
-        self.run_packed(pack_events(list(events)), stream)
+    def run(self, events, stream=None, keep=False):
+        return self.run_packed(pack_events(list(events)), stream, keep)
 
-    def run_events(self, events, stream=None):
+    def release(self, ids):
+        """Release event handles (lst_release_event)."""
+        for i in ids:
+            _check(library().lst_release_event(self._h, int(i)))
+
+    def run_events(self, events, stream=None, keep=False):
         """events: per-event dicts with x, y, z, module, side, seeds (numpy,
         pinned CPU tensors, or CUDA tensors; one kind for the whole batch).
         The library gathers them into its input staging (lst_run_events)."""
@@ -376,8 +396,11 @@ class Context:
             seeds[i] = LstSeeds(_ptr(e["seeds"]), int(_numel(e["seeds"]) // 9))
         self._keep = (events, hits, seeds)
         s = C.c_void_p(stream) if stream is not None else None
-        _check(library().lst_run_events(self._h, hits, seeds, n, 1 if dev else 0, s))
+        ids = (C.c_int64 * n)() if keep else None
+        _check(library().lst_run_events(self._h, hits, seeds, n, 1 if dev else 0, s, ids))
         self.n_events = n
+        self.event_ids = list(ids) if keep else None
+        return self.event_ids
 
     def batch_track_candidates(self, out=None):
         """(offsets [n_events + 1], records) of the whole batch in two copies;
@@ -556,6 +579,20 @@ class Mlp:
         p = np.zeros(N_MLP_PARAMS, np.float32)
         _check(library().lst_mlp_get_params(self._h, _ptr(p)))
         return p
+
+    def state(self):
+        """Training state for a checkpoint: params, Adam moments m and v, step."""
+        p, m, v = (np.zeros(N_MLP_PARAMS, np.float32) for _ in range(3))
+        step = C.c_int64(0)
+        _check(library().lst_mlp_get_state(self._h, _ptr(p), _ptr(m), _ptr(v), C.byref(step)))
+        return dict(params=p, m=m, v=v, step=int(step.value))
+
+    def set_state(self, st):
+        arr = [np.ascontiguousarray(st[k], np.float32) for k in ("params", "m", "v")]
+        for a in arr:
+            if a.size != N_MLP_PARAMS:
+                raise LstError(f"state arrays hold {N_MLP_PARAMS} floats, not {a.size}")
+        _check(library().lst_mlp_set_state(self._h, *[_ptr(a) for a in arr], int(st["step"])))
 
     def forward(self, features, scores, stream=None):
         """features, scores: CUDA tensors ([n, 48] float32, [n] float32)."""

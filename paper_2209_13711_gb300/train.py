@@ -68,15 +68,32 @@ def collect(ctx, events, batch=16, stream=None, device=False):
     return dict(X=Xc, y=cat(y), cut=cat(cut), particle=cat(part), event=cat(ev_idx))
 
 
-def train(mlp, X, y, epochs=4, batch=4096, lr=2e-3, seed=0, log=None):
+def save_checkpoint(path, mlp, epoch, hist):
+    """The network's whole training state (parameters, Adam moments and step) after `epoch` epochs."""
+    st = mlp.state()
+    np.savez(path, params=st["params"], m=st["m"], v=st["v"], step=st["step"], epoch=epoch,
+             hist=np.asarray(hist, np.float64))
+
+
+def load_checkpoint(path, mlp):
+    """Restore a checkpoint into mlp; returns (epochs done, loss history)."""
+    z = np.load(path)
+    mlp.set_state(dict(params=z["params"], m=z["m"], v=z["v"], step=int(z["step"])))
+    return int(z["epoch"]), [float(h) for h in z["hist"]]
+
+
+def train(mlp, X, y, epochs=4, batch=4096, lr=2e-3, seed=0, log=None, start_epoch=0, checkpoint=None,
+          hist=None):
+    """Adam over shuffled batches. Epoch ep shuffles with its own generator (seed, ep), so a run resumed
+    at start_epoch from a checkpoint continues exactly as the uninterrupted run; with `checkpoint` (a path)
+    the state is saved after every epoch."""
     import torch
-    rng = np.random.default_rng(seed)
     n = len(y)
     Xd = X if torch.is_tensor(X) else torch.from_numpy(np.ascontiguousarray(X)).cuda()
     yd = torch.from_numpy(np.ascontiguousarray(y)).cuda()
-    hist = []
-    for ep in range(epochs):
-        perm = torch.from_numpy(rng.permutation(n)).cuda()
+    hist = list(hist or [])
+    for ep in range(start_epoch, epochs):
+        perm = torch.from_numpy(np.random.default_rng([seed, ep]).permutation(n)).cuda()
         losses = []
         for b0 in range(0, n - batch + 1, batch):
             idx = perm[b0:b0 + batch]
@@ -89,6 +106,8 @@ def train(mlp, X, y, epochs=4, batch=4096, lr=2e-3, seed=0, log=None):
         hist.append(float(np.mean(losses)) if losses else float("nan"))
         if log:
             log(f"epoch {ep}: loss {hist[-1]:.4f}")
+        if checkpoint:
+            save_checkpoint(checkpoint, mlp, ep + 1, hist)
     return hist
 
 
@@ -140,6 +159,8 @@ def main(argv=None):
     ap.add_argument("--prefilter-scale", type=float, default=3.0)
     ap.add_argument("--out", default="t5_mlp.npy")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--checkpoint", default=None, help="save the training state here after every epoch")
+    ap.add_argument("--resume", action="store_true", help="continue from --checkpoint")
     args = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from synth import events as E, geometry as G, maps as M
@@ -155,8 +176,12 @@ def main(argv=None):
     print(f"samples: train {len(tr['y'])} ({tr['y'].mean():.3f} true), eval {len(va['y'])}; "
           f"{time.time() - t0:.1f} s", flush=True)
     mlp = L.Mlp(max_batch=4096, params=init_params(args.seed))
+    start, hist0 = 0, []
+    if args.resume and args.checkpoint and os.path.exists(args.checkpoint):
+        start, hist0 = load_checkpoint(args.checkpoint, mlp)
     t1 = time.time()
-    hist = train(mlp, tr["X"], tr["y"], epochs=args.epochs, log=lambda m: print(m, flush=True))
+    hist = train(mlp, tr["X"], tr["y"], epochs=args.epochs, seed=args.seed, log=lambda m: print(m, flush=True),
+                 start_epoch=start, checkpoint=args.checkpoint, hist=hist0)
     print(f"training: {time.time() - t1:.1f} s", flush=True)
     res = evaluate(mlp, va)
     res["loss_history"] = hist

@@ -17,8 +17,21 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for n in ("lst_load_geometry", "lst_run_event", "lst_run_batch", "lst_get_track_candidates", "lst_create",
-              "lst_destroy", "lst_get_objects", "lst_get_stats"):
+              "lst_destroy", "lst_get_objects", "lst_get_stats", "lst_release_event", "lst_status_str"):
         assert n in names
+
+
+def test_result_slot_count_matches_the_header():
+    from paper_2209_13711_gb300 import lst
+    src = open(os.path.join(ROOT, "include", "lst.h")).read()
+    assert int(re.search(r"#define LST_RESULT_SLOTS (\d+)", src).group(1)) == lst.LST_RESULT_SLOTS
+
+
+def test_release_refuses_indices_and_null_without_device():
+    from paper_2209_13711_gb300 import lst
+    L = lst.library()
+    assert L.lst_release_event(None, 1 << 40) == -1
+    assert L.lst_release_event(None, 0) == -1
 
 
 def test_library_exports_every_symbol():

@@ -138,3 +138,38 @@ def test_trained_network_beats_the_cuts(geom_full):
     assert res["network"]["fake_rate"] < 0.5 * res["cut"]["fake_rate"]
     ctx.close()
     m.close()
+
+
+def test_resume_from_checkpoint_matches_uninterrupted_training(tmp_path):
+    """Two epochs in one run against one epoch, a checkpoint (parameters, Adam moments and step) into a fresh
+    network, and the second epoch: identical parameters and moments. Resuming from the parameters alone (Adam
+    reset) ends elsewhere, so the moments are what the checkpoint must carry."""
+    torch = pytest.importorskip("torch")
+    import paper_2209_13711_gb300 as P
+    from paper_2209_13711_gb300 import train as T
+    rng = np.random.default_rng(3)
+    n = 4096 * 6
+    X = rng.normal(0.0, 1.0, (n, 48)).astype(np.float32)
+    X[:, 38:] = 0.0
+    y = (X[:, 0] + 0.5 * X[:, 3] - X[:, 7] > 0).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+
+    full = P.Mlp(max_batch=4096, params=init_params(2))
+    T.train(full, Xd, y, epochs=2, seed=5)
+    want = full.state()
+
+    first = P.Mlp(max_batch=4096, params=init_params(2))
+    ck = str(tmp_path / "ck.npz")
+    T.train(first, Xd, y, epochs=1, seed=5, checkpoint=ck)
+    resumed = P.Mlp(max_batch=4096)
+    done, hist = T.load_checkpoint(ck, resumed)
+    assert done == 1 and len(hist) == 1
+    T.train(resumed, Xd, y, epochs=2, seed=5, start_epoch=done, hist=hist)
+    got = resumed.state()
+    assert got["step"] == want["step"] == 12
+    for k in ("params", "m", "v"):
+        assert np.array_equal(got[k], want[k]), k
+
+    reset = P.Mlp(max_batch=4096, params=np.load(ck)["params"])
+    T.train(reset, Xd, y, epochs=2, seed=5, start_epoch=1)
+    assert not np.array_equal(reset.params(), want["params"])
