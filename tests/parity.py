@@ -70,11 +70,16 @@ def close(x32, x64, scale):
     return abs(float(x32) - float(x64)) <= REL * max(abs(float(x64)), scale)
 
 
+# eta and phi0 are cut only in the cleaning, against the eta-phi distance 0.02: that is their scale
+DIR_SCALE = 0.02
+
+
 def close_angle(x32, x64):
     """Angles in (-pi, pi]: compared modulo 2 pi (a value within rounding of
-    +-pi may be wrapped to the other end on one side)."""
+    +-pi may be wrapped to the other end on one side), within REL of the
+    value, at least of the cleaning's eta-phi scale."""
     d = (float(x32) - float(x64) + math.pi) % (2 * math.pi) - math.pi
-    return abs(d) <= REL * math.pi
+    return abs(d) <= REL * max(abs(float(x64)), DIR_SCALE)
 
 
 def compare(gpu, orc, a_half, cuts, check_tc=True):
@@ -125,7 +130,7 @@ def compare(gpu, orc, a_half, cuts, check_tc=True):
         assert close(g5["kappa"][i], o5["kappa"][j], two_a), ("t5 kappa", t)
         assert close(g5["chi2_rphi"][i], o5["chi2_rphi"][j], cuts["chi2_rphi_t5"]), ("t5 chi2", t)
         assert close(g5["chi2_rz"][i], o5["chi2_rz"][j], cuts["chi2_rz_t5"]), ("t5 chi2z", t)
-        assert close(g5["eta"][i], o5["eta"][j], 1.0) and close_angle(g5["phi0"][i], o5["phi0"][j]), ("t5 dir", t)
+        assert close(g5["eta"][i], o5["eta"][j], DIR_SCALE) and close_angle(g5["phi0"][i], o5["phi0"][j]), ("t5 dir", t)
         assert close(g5["pt"][i], o5["pt"][j], 0.0), ("t5 pt", t)
     gp, op = gpu["pls"], orc["pls"]
     assert gp["n"] == op["n"]
@@ -134,7 +139,7 @@ def compare(gpu, orc, a_half, cuts, check_tc=True):
             continue
         assert gp["pass"][s] == op["pass"][s] and gp["sb"][s] == op["sb"][s], ("pls", s)
         assert close(gp["kappa"][s], op["kappa"][s], two_a), ("pls kappa", s)
-        assert close(gp["eta"][s], op["eta"][s], 1.0) and close_angle(gp["phi0"][s], op["phi0"][s]), ("pls dir", s)
+        assert close(gp["eta"][s], op["eta"][s], DIR_SCALE) and close_angle(gp["phi0"][s], op["phi0"][s]), ("pls dir", s)
         assert close(gp["z0"][s], op["z0"][s], cuts["z_lumi"]), ("pls z0", s)
     for lvl, cr, cz in (("pt5", "chi2_rphi_pt5", "chi2_rz_pt5"), ("pt3", "chi2_rphi_pt3", "chi2_rz_pt3")):
         gi, oi = idx(G[lvl]), idx(O[lvl])
@@ -261,7 +266,7 @@ def compare_tc(gpu, orc, G, O, M, cuts):
     assert g == o, f"tc: {len(g - o)} GPU-only {sorted(g - o)[:2]}, {len(o - g)} oracle-only {sorted(o - g)[:2]}"
     for t in g:
         i, j = g_tc[t], o_tc[t]
-        assert close(gpu["tc"]["eta"][i], orc["tc"]["eta"][j], 1.0)
+        assert close(gpu["tc"]["eta"][i], orc["tc"]["eta"][j], DIR_SCALE)
         assert close_angle(gpu["tc"]["phi0"][i], orc["tc"]["phi0"][j])
         assert close(gpu["tc"]["pt"][i], orc["tc"]["pt"][j], 0.0)
     return (len(g), len(g_tc) - len(g))
