@@ -116,7 +116,7 @@ def whole_job_rate(ws, steps, seconds):
     return ws * steps / seconds
 
 
-def measured_counters(kernel):
+def measured_counters(kernel, workload="pu200"):
     """Per-launch ncu counters of `kernel` from the committed profile
     summaries (their machine-readable blocks), merged; a block whose kernel
     sources changed since its capture is skipped."""
@@ -130,7 +130,7 @@ def measured_counters(kernel):
                 if ":" in line and not line.startswith(("|", "#", "`", " ", "*")):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("kernel") != kernel or "sources_sha256" not in kv:
+        if kv.get("kernel") != kernel or "sources_sha256" not in kv or kv.get("workload", "pu200") != workload:
             continue
         h = hashlib.sha256()
         try:
@@ -147,10 +147,11 @@ def measured_counters(kernel):
     return out
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+def measured_traffic(kernel, workload="pu200"):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of the
+    workload (pu200: one PU200 event; pu200xN: N of them in one batch), or None
     when there is none or the kernel's sources changed since it was taken."""
-    v = measured_counters(kernel).get("dram_bytes_per_launch")
+    v = measured_counters(kernel, workload).get("dram_bytes_per_launch")
     return None if v is None else int(v)
 
 
@@ -164,7 +165,8 @@ def _peaks():
 
 
 def algorithmic_bytes(kernel, st, n_hits, n_seeds, n_mod):
-    """Compulsory bytes of one launch: its inputs read once and outputs written once (from object counts)."""
+    """Compulsory bytes of one launch: its inputs read once and outputs written once (from object counts;
+    for a batch, st holds the counts summed over its events and n_mod the modules times the events)."""
     c = st["counts"]
     md, ls, t3, t5, pls, p5, p3 = (c[k] for k in ("md", "ls", "t3", "t5", "pls", "pt5", "pt3"))
     table = {
@@ -331,6 +333,8 @@ def run_ours(args):
     out["physics"] = measure_physics(P, ctx, dev, events, st)
     out["streams"] = measure_streams(P, geom, maps, DEFAULT_CUTS, dev, st)
     out["batched"] = measure_batched(P, E, geom, maps, DEFAULT_CUTS, flush, st, steps=max(2, min(args.steps, 5)))
+    out["batched_pu200"] = measure_batched_pu200(P, E, geom, maps, DEFAULT_CUTS, flush, st,
+                                                 steps=max(2, min(args.steps, 5)), events=events)
     out["mlp"] = measure_mlp(P, E, geom, maps, DEFAULT_CUTS, flush, st, dev)
     out["serving"] = measure_serving(E, geom, maps, DEFAULT_CUTS)
     if ws == 1 and not args.no_cpu_baseline:
@@ -458,6 +462,69 @@ def measure_batched(P, E, geom, maps, cuts, flush, st, steps, n_batch=64):
             "launch": "one CUDA graph per batch", "dropped_objects": int(dropped), "autotune": tune,
             "plain_same_events": {"value": round(n_batch / (ms1 / 1e3), 2), "unit": "events/s",
                                   "launch": "one graph per event"}}
+
+
+def measure_batched_pu200(P, E, geom, maps, cuts, flush, st, steps, events, sizes=(16, 64)):
+    """PU200 events batched into one graph launch (16 and 64 per batch): events/s, and the batch's dominant
+    kernel against the HBM roofline (algorithmic bytes of the whole batch over its live time, ncu traffic of
+    the same launch from the committed summary when its sources are unchanged)."""
+    import torch
+    evs = list(events) + [E.pu200_event(s, geom) for s in range(len(events), max(sizes))]
+    hbm_peak, peak_kind = _peaks()
+    out = {}
+    for n in sizes:
+        ctx = P.Context(geom.module_table(), maps, cfg=cuts, capacity=P.default_capacity(n))
+        b = P.pack_events(evs[:n])
+        bd = {k: (torch.from_numpy(v).cuda() if k not in ("hit_off", "seed_off") else v) for k, v in b.items()}
+        tune = autotune(ctx, bd, st, reps=2)
+        for _ in range(2):
+            ctx.run_packed(bd, stream=st.cuda_stream)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for i in range(steps):
+            flush.fill_(i & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ctx.run_packed(bd, stream=st.cuda_stream)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        tot = {"counts": {}, "dropped": 0}
+        for e in range(n):
+            s_ = ctx.stats(e)
+            for k, v in s_["counts"].items():
+                tot["counts"][k] = tot["counts"].get(k, 0) + v
+            tot["dropped"] += sum(s_["dropped"].values())
+        ctx.set_profiling(True)
+        per = {}
+        for i in range(2):
+            flush.fill_(i & 0xff)
+            ctx.run_packed(bd, stream=st.cuda_stream)
+            for name, kms in ctx.kernel_times():
+                per.setdefault(name, []).append(kms)
+        ctx.set_profiling(False)
+        ctx.close()
+        kavg = {k: sum(v) / len(v) for k, v in per.items()}
+        top = max(kavg, key=kavg.get)
+        wl = f"pu200x{n}"
+        rec = {"value": round(n * steps / (ms / 1e3), 2), "unit": "events/s", "ms_per_batch": round(ms / steps, 3),
+               "launch": "one CUDA graph per batch", "dropped_objects": int(tot["dropped"]),
+               "stage_sum_ms": round(sum(kavg.values()), 4),
+               "kernel_ms": {k: round(v, 4) for k, v in sorted(kavg.items(), key=lambda kv: -kv[1])[:8]},
+               "autotune_stage_sum_ms": [tune.get("stage_sum_ms_default"), tune.get("stage_sum_ms_tuned")]}
+        b_alg = algorithmic_bytes(top, tot, int(b["hit_off"][-1]), int(b["seed_off"][-1]), geom.n_mod * n)
+        if b_alg is not None:
+            achieved = b_alg / (kavg[top] / 1e3) / 1e9
+            traffic = measured_traffic(top, wl)
+            rec["roofline"] = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
+                               "unit": "GB/s", "frac": round(achieved / hbm_peak, 5), "traffic": traffic,
+                               "traffic_over_algorithmic": None if traffic is None else round(traffic / b_alg, 3),
+                               "peak_source": peak_kind, "algorithmic_bytes": int(b_alg),
+                               "kernel_ms": round(kavg[top], 4)}
+        out[f"{n}_events"] = rec
+    out["workload"] = "PU200 events (the headline event recipe, seeds 0..63), one batch per launch sequence"
+    out["l2"] = "flushed between batches (256 MiB write, outside the timed spans)"
+    return out
 
 
 def measure_mlp(P, E, geom, maps, cuts, flush, st, dev_events):
