@@ -131,6 +131,42 @@ def curves(per_event, pt_min=1.0, eta_max=2.4, frac=0.75, pt_edges=PT_EDGES, eta
                          for t, v in by_type.items()})
 
 
+D0_EDGES = (0.0, 0.25, 0.5, 1.0, 1.5, 2.0, 2.5, 3.6)
+
+
+def efficiency_vs_d0(per_event, edges=D0_EDGES, pt_min=1.0, eta_max=2.4, frac=0.75):
+    """Efficiency against the generated transverse impact parameter d0 (cm), overall and by the type of the
+    TC that finds the particle (the displaced-track study of Section 2.2: the T5 has no d0 cut).
+
+    per_event: (tc, pid, seed_pid, tracks) per event, tracks with a d0 property. Per d0 bin: findable
+    particles (pT >= pt_min, |eta| <= eta_max), found by any TC, and found by a TC of each type (a particle
+    found by TCs of several types counts for each)."""
+    e = np.asarray(edges, float)
+    nb = len(e) - 1
+    findable = np.zeros(nb, np.int64)
+    found = np.zeros(nb, np.int64)
+    by_type = {t: np.zeros(nb, np.int64) for t in TC_TYPES}
+    for tc, pid, seed_pid, tracks in per_event:
+        m = match(tc, pid, seed_pid, frac)
+        d0 = np.asarray(tracks.d0, float)
+        ok = (np.asarray(tracks.pt) >= pt_min) & (np.abs(np.asarray(tracks.eta)) <= eta_max)
+        b = np.searchsorted(e, d0, side="right") - 1
+        ok &= (b >= 0) & (b < nb)
+        any_found = np.zeros(len(d0), bool)
+        any_found[m[m >= 0]] = True
+        np.add.at(findable, b[ok], 1)
+        np.add.at(found, b[ok], any_found[ok].astype(np.int64))
+        types = np.asarray(tc["type"])
+        for t, name in enumerate(TC_TYPES):
+            f = np.zeros(len(d0), bool)
+            sel = (types == t) & (m >= 0)
+            f[m[sel]] = True
+            np.add.at(by_type[name], b[ok], f[ok].astype(np.int64))
+    eff = lambda num: [round(float(a) / max(1, int(d)), 4) for a, d in zip(num, findable)]
+    return dict(d0_edges=list(e), findable=findable.tolist(), efficiency=eff(found),
+                efficiency_by_type={t: eff(v) for t, v in by_type.items()})
+
+
 def combine(per_event):
     """Pool the counts of several events' rates() results."""
     tcs = sum(r["tcs"] for r in per_event)

@@ -31,7 +31,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import geometry as G
-from .helix import cross_cylinder, cross_plane
+from .helix import cross_cylinder, cross_cylinder_from, cross_plane, cross_plane_from
 
 PIXEL_R = (5.0, 10.0, 15.0)
 PIXEL_SIGMA = 0.001   # 10 um
@@ -41,13 +41,33 @@ PIXEL_SIGMA = 0.001   # 10 um
 class Tracks:
     pt: np.ndarray
     eta: np.ndarray
-    phi0: np.ndarray
+    phi0: np.ndarray        # transverse direction at the production vertex
     q: np.ndarray
     z0: np.ndarray
+    x0: np.ndarray = None   # transverse production vertex (None: the beam line)
+    y0: np.ndarray = None
 
     @property
     def n(self):
         return len(self.pt)
+
+    @property
+    def displaced(self):
+        return self.x0 is not None and (np.any(self.x0 != 0) or np.any(self.y0 != 0))
+
+    @property
+    def d0(self):
+        """Unsigned transverse distance of closest approach of each track's circle to the beam line."""
+        if self.x0 is None:
+            return np.zeros(self.n)
+        ks = self.kappa_s
+        ka = np.abs(ks)
+        R = 1.0 / np.where(ka > 0, ka, 1.0)
+        sg = np.where(ks >= 0, 1.0, -1.0)
+        cx = self.x0 - sg * R * np.sin(self.phi0)
+        cy = self.y0 + sg * R * np.cos(self.phi0)
+        straight = np.abs(self.x0 * np.sin(self.phi0) - self.y0 * np.cos(self.phi0))
+        return np.where(ka > 0, np.abs(np.hypot(cx, cy) - R), straight)
 
     @property
     def kappa_s(self):
@@ -59,7 +79,11 @@ class Tracks:
 
     @staticmethod
     def concat(parts):
-        return Tracks(*[np.concatenate([getattr(p, f) for p in parts]) for f in ("pt", "eta", "phi0", "q", "z0")])
+        t = Tracks(*[np.concatenate([getattr(p, f) for p in parts]) for f in ("pt", "eta", "phi0", "q", "z0")])
+        if any(p.x0 is not None for p in parts):
+            t.x0 = np.concatenate([p.x0 if p.x0 is not None else np.zeros(p.n) for p in parts])
+            t.y0 = np.concatenate([p.y0 if p.y0 is not None else np.zeros(p.n) for p in parts])
+        return t
 
 
 @dataclass
@@ -143,13 +167,16 @@ def true_crossings(geom, tr: Tracks):
     ks, tl = tr.kappa_s, tr.tanl
     cols = {k: [] for k in ("tid", "module", "side", "r", "phi", "z", "kind")}
     tids = np.arange(tr.n)
+    disp = tr.displaced
     for kind, val, li, sgn, sensor in sensor_surfaces(geom):
         if kind == 0:
-            ok, s, phi, z = cross_cylinder(ks, tr.phi0, tl, tr.z0, val)
+            ok, s, phi, z = (cross_cylinder_from(ks, tr.phi0, tl, tr.x0, tr.y0, tr.z0, val) if disp
+                             else cross_cylinder(ks, tr.phi0, tl, tr.z0, val))
             r = np.full_like(s, val)
             mid = geom.locate_barrel(np.full(tr.n, li), phi, z)
         else:
-            ok, s, phi, r = cross_plane(ks, tr.phi0, tl, tr.z0, val)
+            ok, s, phi, r = (cross_plane_from(ks, tr.phi0, tl, tr.x0, tr.y0, tr.z0, val) if disp
+                             else cross_plane(ks, tr.phi0, tl, tr.z0, val))
             z = np.full_like(s, val)
             mid = geom.locate_endcap(np.full(tr.n, sgn), li, phi, r)
         ok = ok & (mid >= 0)
@@ -222,7 +249,8 @@ def make_seeds(tracks: Tracks, rng, smear=True):
     pts = []
     ok_all = np.ones(tracks.n, dtype=bool)
     for r in PIXEL_R:
-        ok, s, phi, z = cross_cylinder(ks, tracks.phi0, tl, tracks.z0, r)
+        ok, s, phi, z = (cross_cylinder_from(ks, tracks.phi0, tl, tracks.x0, tracks.y0, tracks.z0, r)
+                         if tracks.displaced else cross_cylinder(ks, tracks.phi0, tl, tracks.z0, r))
         ok_all &= ok
         if smear:
             phi = phi + rng.normal(0.0, PIXEL_SIGMA, tracks.n) / r
@@ -247,6 +275,29 @@ def pu200_event(seed=0, geom=None, n_tracks=8000, n_jet=12):
     rng = np.random.default_rng(seed)
     tr = sample_pileup_tracks(rng, n_tracks, n_jet=n_jet)
     return make_event(geom, tr, rng, noise_frac=0.02)
+
+
+def sample_muon_gun(rng, n, pt_range=(2.0, 10.0), eta_max=2.4, cube=5.0):
+    """Muons from vertices uniform in a cube of side `cube` cm centred on the interaction point (the
+    displaced-track sample of Section 2.2): pT uniform in pt_range, |eta| < eta_max, phi uniform."""
+    h = 0.5 * cube
+    return Tracks(
+        pt=rng.uniform(pt_range[0], pt_range[1], n),
+        eta=rng.uniform(-eta_max, eta_max, n),
+        phi0=rng.uniform(-math.pi, math.pi, n),
+        q=rng.choice([-1.0, 1.0], n),
+        z0=rng.uniform(-h, h, n),
+        x0=rng.uniform(-h, h, n),
+        y0=rng.uniform(-h, h, n),
+    )
+
+
+def muon_gun_event(seed, geom=None, n=20, pt_range=(2.0, 10.0), cube=5.0):
+    """Zero-pileup event of n displaced muons (sample_muon_gun), one pixel seed per muon, no noise."""
+    geom = geom or G.make_geometry(barrel_only=False)
+    rng = np.random.default_rng(seed)
+    tr = sample_muon_gun(rng, n, pt_range, cube=cube)
+    return make_event(geom, tr, rng, n_noise=0)
 
 
 def pileup_event(pu, seed, geom=None):

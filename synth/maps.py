@@ -30,7 +30,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import geometry as G
-from .helix import cross_cylinder, cross_plane, wrap_phi
+from .helix import cross_cylinder, cross_cylinder_from, cross_plane, cross_plane_from, wrap_phi
 
 
 @dataclass
@@ -43,6 +43,7 @@ class MapParams:
     pt_tol: float = 0.05      # pLS keep pT >= pt_min (1 - pt_tol)
     margin_cm: float = 1.0    # widening of every bounding box (cm)
     sim_events: int = 4       # generated events whose true transitions are added
+    d0_max: float = 0.0       # transverse vertex displacement the connection map also covers (cm)
 
     @property
     def kappa_max(self):
@@ -84,6 +85,31 @@ def _crossings_all(geom, ks, phi0, tanl, z0):
             ell = z
         else:
             ok, s, phi, r = cross_plane(ks, phi0, tanl, z0, val)
+            mid = geom.locate_endcap(np.full(n, sgn), li, phi, r)
+            ell = r
+        ok = ok & (mid >= 0)
+        S[j] = np.where(ok, s, np.inf)
+        PHI[j] = phi
+        ELL[j] = ell
+        MOD[j] = np.where(ok, mid, -1)
+    return surfs, S, PHI, ELL, MOD
+
+
+def _crossings_from(geom, tr):
+    """As _crossings_all, for tracks with transverse production vertices (tr.x0, tr.y0)."""
+    surfs = lower_surfaces(geom)
+    n = tr.n
+    S = np.full((len(surfs), n), np.inf)
+    PHI = np.zeros((len(surfs), n))
+    ELL = np.zeros((len(surfs), n))
+    MOD = np.full((len(surfs), n), -1, dtype=np.int64)
+    for j, (kind, val, li, sgn) in enumerate(surfs):
+        if kind == 0:
+            ok, s, phi, z = cross_cylinder_from(tr.kappa_s, tr.phi0, tr.tanl, tr.x0, tr.y0, tr.z0, val)
+            mid = geom.locate_barrel(np.full(n, li), phi, z)
+            ell = z
+        else:
+            ok, s, phi, r = cross_plane_from(tr.kappa_s, tr.phi0, tr.tanl, tr.x0, tr.y0, tr.z0, val)
             mid = geom.locate_endcap(np.full(n, sgn), li, phi, r)
             ell = r
         ok = ok & (mid >= 0)
@@ -178,6 +204,42 @@ def _to_csr(lists):
     return off.astype(np.int32), tgt.astype(np.int32)
 
 
+def _displaced_next(geom, M, ks, phi1, r1, z1, tanl, p: MapParams, turns=(-1.0, -0.5, 0.5, 1.0)):
+    """Next-surface crossings of helices through the module points (phi1, r1, z1) whose direction there is
+    turned from the prompt helix's by up to asin(d0_max / r1): a vertex displaced by d0 <= d0_max turns a
+    track's direction at radius r by at most that angle. Returns (module, surface index, phi, ell)."""
+    x1, y1 = r1 * np.cos(phi1), r1 * np.sin(phi1)
+    ka = np.abs(ks)
+    s1 = np.where(ka > 0, 2.0 * np.arcsin(np.minimum(r1 * ka / 2.0, 1.0)) / np.where(ka > 0, ka, 1.0), r1)
+    theta_prompt = phi1 + ks * s1 / 2.0
+    dmax = np.arcsin(np.minimum(1.0, p.d0_max / r1))
+    surfs = lower_surfaces(geom)
+    outs = []
+    for f in turns:
+        th = theta_prompt + f * dmax
+        best = np.full(len(M), np.inf)
+        best_j = np.full(len(M), -1)
+        best_phi = np.zeros(len(M))
+        best_ell = np.zeros(len(M))
+        for j, (kind, val, li, sgn) in enumerate(surfs):
+            if kind == 0:
+                ok, s, phi, z = cross_cylinder_from(ks, th, tanl, x1, y1, z1, val)
+                mid = geom.locate_barrel(np.full(len(M), li), phi, z)
+                ell = z
+            else:
+                ok, s, phi, r = cross_plane_from(ks, th, tanl, x1, y1, z1, val)
+                mid = geom.locate_endcap(np.full(len(M), sgn), li, phi, r)
+                ell = r
+            take = ok & (mid >= 0) & (s > 1e-6) & (s < best)
+            best = np.where(take, s, best)
+            best_j = np.where(take, j, best_j)
+            best_phi = np.where(take, phi, best_phi)
+            best_ell = np.where(take, ell, best_ell)
+        good = best_j >= 0
+        outs.append((M[good], best_j[good], best_phi[good], best_ell[good]))
+    return [np.concatenate(c) for c in zip(*outs)]
+
+
 def _module_samples(geom, p: MapParams, mods, n_grid=5, kappas=(-1.0, -0.5, 0.0, 0.5, 1.0)):
     """Helices through a grid of points of the lower sensor of modules `mods`."""
     kmax = p.kappa_max
@@ -201,7 +263,9 @@ def _module_samples(geom, p: MapParams, mods, n_grid=5, kappas=(-1.0, -0.5, 0.0,
     ok = (r1 * ka / 2.0 < 1.0) & (ka * s1 <= math.pi) & (z1 != z0)
     phi0 = phi1 - ks * s1 / 2.0
     tanl = (z1 - z0) / s1
-    return M[ok], ks[ok], phi0[ok], tanl[ok], z0[ok], s1[ok]
+    if p.d0_max > 0:
+        return M[ok], ks[ok], phi0[ok], tanl[ok], z0[ok], s1[ok], (phi1[ok], r1[ok], z1[ok])
+    return M[ok], ks[ok], phi0[ok], tanl[ok], z0[ok], s1[ok], None
 
 
 def _next_after(S, s1):
@@ -218,13 +282,16 @@ def build_connection_map(geom, p: MapParams | None = None, sim_events=None, chun
     boxes = _Boxes(geom.n_mod, ns, 0.5 * (geom.phi_lo + geom.phi_hi))
     for c0 in range(0, geom.n_mod, chunk):
         mods = np.arange(c0, min(geom.n_mod, c0 + chunk))
-        M, ks, phi0, tanl, z0, s1 = _module_samples(geom, p, mods)
+        M, ks, phi0, tanl, z0, s1, pts = _module_samples(geom, p, mods)
         _, S, PHI, ELL, MOD = _crossings_all(geom, ks, phi0, tanl, z0)
         j = _next_after(S, s1)
         ok = j >= 0
         cols = np.arange(len(M))[ok]
         jj = j[ok]
         boxes.add(M[ok], jj, PHI[jj, cols], ELL[jj, cols])
+        if pts is not None:
+            Md, jd, phid, elld = _displaced_next(geom, M, ks, pts[0], pts[1], pts[2], tanl, p)
+            boxes.add(Md, jd, phid, elld)
     lists = boxes.lists(geom, p.margin_cm)
     # transitions of the true tracks of generated events
     n_sim = p.sim_events if sim_events is None else sim_events
@@ -235,6 +302,13 @@ def build_connection_map(geom, p: MapParams | None = None, sim_events=None, chun
             tr = (sample_tiny_tracks(rng, 2000) if geom.barrel_only
                   else sample_pileup_tracks(rng, 8000, n_jet=12))
             _, S2, _, _, MOD2 = _crossings_all(geom, tr.kappa_s, tr.phi0, tr.tanl, tr.z0)
+            if p.d0_max > 0 and not geom.barrel_only:
+                from .events import sample_muon_gun
+                mu = sample_muon_gun(np.random.default_rng(2000 + e), 8000, pt_range=(p.pt_min, 20.0),
+                                     cube=2.0 * p.d0_max / math.sqrt(2.0))
+                _, S3, _, _, MOD3 = _crossings_from(geom, mu)
+                S2 = np.concatenate([S2, S3], axis=1)
+                MOD2 = np.concatenate([MOD2, MOD3], axis=1)
             order = np.argsort(S2, axis=0)
             Ms = np.take_along_axis(MOD2, order, axis=0)
             Ss = np.take_along_axis(S2, order, axis=0)

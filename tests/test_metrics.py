@@ -92,3 +92,22 @@ def test_efficiency_without_bare_seeds():
     r = rates(tc, pid, np.array([1], np.int32), tr)
     assert r["efficiency"] == pytest.approx(1.0) and r["efficiency_ot"] == pytest.approx(0.5)
     assert combine([r, r])["efficiency_ot"] == pytest.approx(0.5)
+
+
+def test_efficiency_vs_d0_by_type():
+    from paper_2209_13711_gb300 import metrics as MT
+    from synth.events import Tracks
+    tr = Tracks(pt=np.full(4, 3.0), eta=np.zeros(4), phi0=np.zeros(4), q=np.ones(4), z0=np.zeros(4),
+                x0=np.array([0.0, 0.0, 0.0, 0.0]), y0=np.array([0.1, 0.7, 1.7, 3.0]))
+    # straight-line d0 = |y0| for phi0 = 0 up to the curvature; particle i owns hits 2i, 2i+1
+    pid = np.repeat(np.arange(4), 10)
+    hits = np.full((3, 10), -1)
+    hits[0, :] = np.arange(0, 10)          # particle 0 by a pT5
+    hits[1, :] = np.arange(20, 30)         # particle 2 by a T5
+    hits[2, :] = np.arange(30, 40)         # particle 3 by a T5
+    tc = dict(n=3, hits=hits, seed=np.array([-1, -1, -1]), type=np.array([0, 2, 2]))
+    r = MT.efficiency_vs_d0([(tc, pid, np.zeros(0, np.int64), tr)], edges=(0.0, 0.5, 1.0, 2.0, 3.6))
+    assert r["findable"] == [1, 1, 1, 1]
+    assert r["efficiency"] == [1.0, 0.0, 1.0, 1.0]
+    assert r["efficiency_by_type"]["T5"] == [0.0, 0.0, 1.0, 1.0]
+    assert r["efficiency_by_type"]["pT5"] == [1.0, 0.0, 0.0, 0.0]
