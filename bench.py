@@ -331,10 +331,12 @@ def run_ours(args):
         "dropped_per_event": stats0["dropped"],
     }
     out["physics"] = measure_physics(P, ctx, dev, events, st)
+    out["physics"]["d0_scan"] = measure_d0_scan(P, E, geom, maps, DEFAULT_CUTS, st)
     out["streams"] = measure_streams(P, geom, maps, DEFAULT_CUTS, dev, st)
     out["batched"] = measure_batched(P, E, geom, maps, DEFAULT_CUTS, flush, st, steps=max(2, min(args.steps, 5)))
     out["batched_pu200"] = measure_batched_pu200(P, E, geom, maps, DEFAULT_CUTS, flush, st,
                                                  steps=max(2, min(args.steps, 5)), events=events)
+    out["compact_storage"] = measure_compact(P, geom, maps, DEFAULT_CUTS, flush, st, events)
     out["mlp"] = measure_mlp(P, E, geom, maps, DEFAULT_CUTS, flush, st, dev)
     out["serving"] = measure_serving(E, geom, maps, DEFAULT_CUTS)
     if ws == 1 and not args.no_cpu_baseline:
@@ -524,6 +526,77 @@ def measure_batched_pu200(P, E, geom, maps, cuts, flush, st, steps, events, size
         out[f"{n}_events"] = rec
     out["workload"] = "PU200 events (the headline event recipe, seeds 0..63), one batch per launch sequence"
     out["l2"] = "flushed between batches (256 MiB write, outside the timed spans)"
+    return out
+
+
+def measure_d0_scan(P, E, geom, maps, cuts, st, n_events=32, n_muons=40):
+    """Efficiency against the transverse impact parameter for displaced muons (vertices uniform in a 5 cm
+    cube, zero pileup; the study of Section 2.2), by the type of the TC that finds each muon: with the
+    connection map that covers vertices up to the cube's corner (2.5 sqrt(2) cm), and with the prompt maps."""
+    import math
+    from paper_2209_13711_gb300.metrics import efficiency_vs_d0
+    from synth import maps as M
+    evs = [E.muon_gun_event(9000 + i, geom, n=n_muons) for i in range(n_events)]
+    out = {"events": n_events, "muons_per_event": n_muons, "muon_pt": "uniform 2-10 GeV", "eta": "|eta| < 2.4",
+           "vertex": "uniform in a 5 cm cube"}
+    for name, mp in (("displaced_map", M.load_maps(geom, M.MapParams(d0_max=2.5 * math.sqrt(2.0)))),
+                     ("prompt_map", maps)):
+        ctx = P.Context(geom.module_table(), mp, cfg=cuts, capacity=P.default_capacity(n_events))
+        ctx.run(evs, stream=st.cuda_stream)
+        per_event = [(ctx.track_candidates(e), ev.pid, ev.seed_pid, ev.tracks) for e, ev in enumerate(evs)]
+        ctx.close()
+        out[name] = efficiency_vs_d0(per_event)
+    out["connections"] = {"displaced_map": int(len(M.load_maps(geom, M.MapParams(d0_max=2.5 * math.sqrt(2.0)))[1])),
+                          "prompt_map": int(len(maps[1]))}
+    return out
+
+
+def measure_compact(P, geom, maps, cuts, flush, st, events, sizes=(1, 64), reps=3):
+    """Compact (16-bit) storage against the default, at 1 and 64 PU200 events per batch: device time per
+    batch and the stage times of the kernels that read the 16-bit copies (default launch shapes for both, so
+    that only the storage differs). Objects are identical by construction (tested on the GPU)."""
+    import torch
+    from synth import events as E
+    evs = list(events) + [E.pu200_event(s, geom) for s in range(len(events), max(sizes))]
+    touched = ("t5", "pt3", "clean_pt3_cross", "clean_t5", "clean_pls")
+    out = {}
+    for n in sizes:
+        b = P.pack_events(evs[:n])
+        bd = {k: (torch.from_numpy(v).cuda() if k not in ("hit_off", "seed_off") else v) for k, v in b.items()}
+        rec = {}
+        for mode in ("default", "compact"):
+            ctx = P.Context(geom.module_table(), maps, cfg=cuts, capacity=P.default_capacity(n))
+            ctx.set_compact_storage(mode == "compact")
+            for _ in range(2):
+                ctx.run_packed(bd, stream=st.cuda_stream)
+            torch.cuda.synchronize()
+            ms = 0.0
+            for i in range(reps):
+                flush.fill_(i & 0xff)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                ctx.run_packed(bd, stream=st.cuda_stream)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+            t3 = sum(ctx.stats(e)["counts"]["t3"] for e in range(n))
+            ctx.set_profiling(True)
+            per = {}
+            for i in range(reps):
+                flush.fill_(i & 0xff)
+                ctx.run_packed(bd, stream=st.cuda_stream)
+                for name, kms in ctx.kernel_times():
+                    per.setdefault(name, []).append(kms)
+            ctx.set_profiling(False)
+            ctx.close()
+            rec[mode] = {"ms_per_batch": round(ms / reps, 4),
+                         "stage_ms": {k: round(sum(per[k]) / len(per[k]), 4) for k in touched if k in per},
+                         "triplet_curvature_bytes": int(t3 * (8 if mode == "default" else 12))}
+        rec["speedup"] = round(rec["default"]["ms_per_batch"] / rec["compact"]["ms_per_batch"], 3)
+        out[f"{n}_events"] = rec
+    out["note"] = ("compact keeps the FP32 (kappa, sigma) for the exact decisions and adds a 4-byte FP16 copy per "
+                   "triplet that the searches read instead of the 8-byte pair; the eta-phi list entries shrink "
+                   "from 8 to 4 bytes")
     return out
 
 

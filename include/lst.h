@@ -271,6 +271,16 @@ int64_t lst_device_bytes(lst_ctx* ctx);
  * restores 256). Results do not depend on them; small limits exercise the
  * fallback. Waits for the running batch; the next batch captures a new graph. */
 lst_status lst_set_stage_limits(lst_ctx* ctx, int32_t t5, int32_t pt);
+/* Compact (16-bit) storage, off by default (half-precision object
+ * properties are the paper's future work, Section 3). On: the triplets'
+ * (curvature, sigma) pair is also stored in FP16 (scaled by 1/(2a)) and the
+ * T5 and pT3 searches read that copy, with their FP32 prefilter slack widened
+ * by the FP16 rounding; the cleaning's eta-phi lists hold 16-bit fixed-point
+ * (eta, phi) pairs instead of FP32 ones, with the FP64 re-test band widened to
+ * cover their rounding. Every decision is still taken by the FP32 / FP64
+ * values, so the objects are those of the default storage. Waits for the
+ * running batch; the next run captures a new graph. */
+lst_status lst_set_compact_storage(lst_ctx* ctx, int32_t enable);
 int32_t lst_launch_stage_count(void);
 lst_status lst_get_launch_config(lst_ctx* ctx, int32_t stage, const char** name, int32_t* blocks_per_sm,
                                  int32_t* block, int32_t* flags);
@@ -381,6 +391,22 @@ lst_status lst_mlp_train_step(lst_mlp* m, const float* features, const float* la
  * training). The network must outlive its use by the context. */
 lst_status lst_set_t5_selection(lst_ctx* ctx, const lst_mlp* mlp, float threshold, float prefilter_scale,
                                 int32_t capture_features);
+/* Learned triplet selection (optional; the default keeps every T3 that passes
+ * the hand-set cuts). mlp = NULL: no network; otherwise every T3 is scored
+ * (LST_MLP_FEATURES features of the triplet in the T5's slots, the missing
+ * ones zero) and the T5 and pT3 searches skip the T3s whose score is below
+ * threshold, which saves their combinatorics. capture_features = 1 computes
+ * the features without a network (for training). The first call that needs
+ * them allocates the feature buffer (t3_per_event x max_events x 197 bytes;
+ * LST_ERR_OOM if that fails). The network must outlive its use. Waits for the
+ * running batch; the next run captures a new graph. */
+lst_status lst_set_t3_selection(lst_ctx* ctx, const lst_mlp* mlp, float threshold, int32_t capture_features);
+/* All T3s of an event of the last batch, HOST outputs (any may be NULL):
+ * features [n][LST_MLP_INPUTS] (only when computed), hits [n][6] (lower,
+ * upper of the three MDs), score [n] (with a network), kept [n] (1 when the
+ * searches use the T3). */
+lst_status lst_get_t3_candidates(lst_ctx* ctx, lst_event_id event, int32_t capacity, int32_t* n_out,
+                                 float* features, int32_t* hits, float* score, int32_t* kept);
 /* All T5 candidates of an event of the last batch (before the validity decision), HOST outputs:
  * features [n][LST_MLP_INPUTS] (when captured), hits [n][10] (lower, upper
  * of the five MDs), cut_pass [n] (the hand-set cut decision), score [n] (the

@@ -455,6 +455,52 @@ void t5_features(const OCfg& c, const Pt* P, const Pt* H, const int* code, doubl
     for (int j = 38; j < 48; ++j) f[j] = 0.0;
 }
 
+// ----------------------------------------------------------------------------
+// Scoring features of a T3, in the T5's slots with the missing ones zero
+// (the optional learned selection scores triplets too). Hits H[0..5] =
+// (lower, upper) of the three MDs, anchors P = the lower hits.
+//   f[0..5]   r-phi pulls of the six hits to the circle fitted to the three
+//             anchors (exact through them), f[6..9] = 0
+//   f[10..15] r-z pulls of the six hits to the weighted line of the fit,
+//             f[16..19] = 0
+//   f[20..22] anchor radius / 100, f[23..24] = 0
+//   f[25]     triplet curvature over 2a, f[26] = 0, f[27] fitted curvature / 2a
+//   f[28..29] log(1 + chi2_rphi), log(1 + chi2_rz)
+//   f[30]     10 x beta, f[31] = 0
+//   f[32]     eta of the r-z fit
+//   f[33..35] layer code / 11; f[36..47] = 0
+// ----------------------------------------------------------------------------
+void t3_features(const OCfg& c, const Pt* P, const Pt* H, const int* code, double* f) {
+    FitParams F;
+    Fit fit = fit_track(P, 3, &F);
+    Tri t = tri(P[0], P[1], P[2]);
+    const double ka = std::fabs(fit.kappa);
+    const double yx = -F.xy, yy = F.xx;
+    auto clip = [](double v) { return std::min(50.0, std::max(-50.0, v)); };
+    for (int j = 0; j < 48; ++j) f[j] = 0.0;
+    for (int j = 0; j < 6; ++j) {
+        const Pt& Q = H[j];
+        double dx = Q.x - F.ox, dy = Q.y - F.oy;
+        double xi = dx * F.xx + dy * F.xy, et = dx * yx + dy * yy;
+        double u = F.gg * (xi * xi + et * et) + F.hh * xi + F.kk - et;
+        double e = 2.0 * u / (F.S + std::sqrt(std::max(0.0, F.S * F.S + 4.0 * F.gg * u)));
+        double s2 = normal_variance(Q, 2.0 * F.gg * xi + F.hh, 2.0 * F.gg * et - 1.0, F.xx, F.xy);
+        f[j] = clip(e / std::sqrt(s2));
+        double sj = arc(std::hypot(Q.x - P[0].x, Q.y - P[0].y), ka);
+        double w = 1.0 / std::max(1e-12, sq(Q.sz) + sq(F.t_hat * Q.sr));
+        f[10 + j] = clip((Q.z - F.c0 - F.t * sj) * std::sqrt(w));
+    }
+    for (int j = 0; j < 3; ++j) f[20 + j] = P[j].r / 100.0;
+    const double two_a = 2.0 * half_curv_max(c);
+    f[25] = t.kappa / two_a;
+    f[27] = fit.kappa / two_a;
+    f[28] = std::log1p(std::min(fit.chi2_rphi, 1e30));
+    f[29] = std::log1p(std::min(fit.chi2_rz, 1e30));
+    f[30] = 10.0 * t.beta;
+    f[32] = std::asinh(fit.tanl);
+    for (int j = 0; j < 3; ++j) f[33 + j] = code[j] / 11.0;
+}
+
 // Direction at the point of closest approach to the beam line, assuming a
 // prompt track through P: phi0 = phi(P) + q asin(r |kappa| / 2), q = -sgn(kappa).
 double phi0_of(const Pt& P, double kappa) {
@@ -1178,6 +1224,22 @@ void oracle_t5_features(const OGeom* g, const OCfg* c, const OEvent* e, const in
         code[j] = g->layer[m] + (g->subdet[m] ? 6 : 0);
     }
     t5_features(*c, P, H, code, out);
+}
+
+// Features of the T3 formed by three MDs given as (lower, upper) hit pairs
+// of the event: out[48].
+void oracle_t3_features(const OGeom* g, const OCfg* c, const OEvent* e, const int32_t* md_hits, double* out) {
+    Pt P[3], H[6];
+    int code[3];
+    for (int j = 0; j < 3; ++j) {
+        int hl = md_hits[2 * j], hu = md_hits[2 * j + 1];
+        P[j] = make_hit_point(*g, *e, hl);
+        H[2 * j] = P[j];
+        H[2 * j + 1] = make_hit_point(*g, *e, hu);
+        int m = e->module[hl];
+        code[j] = g->layer[m] + (g->subdet[m] ? 6 : 0);
+    }
+    t3_features(*c, P, H, code, out);
 }
 
 }  // extern "C"

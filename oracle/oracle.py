@@ -66,6 +66,7 @@ def lib():
         L.oracle_fit.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
         L.oracle_tri.argtypes = [C.c_void_p, C.c_void_p]
         L.oracle_t5_features.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.oracle_t3_features.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_md_d.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_ls_d.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                   C.c_void_p, C.c_void_p]
@@ -148,6 +149,13 @@ class Setup:
         h = np.ascontiguousarray(np.asarray(md_hits, np.int32).ravel())
         out = np.zeros(48)
         lib().oracle_t5_features(C.byref(self.geom), C.byref(self.cfg), C.byref(self.event), _ptr(h), _ptr(out))
+        return out
+
+    def t3_features(self, md_hits):
+        """Scoring features (48) of the T3 formed by three (lower, upper) hit pairs."""
+        h = np.ascontiguousarray(np.asarray(md_hits, np.int32).ravel())
+        out = np.zeros(48)
+        lib().oracle_t3_features(C.byref(self.geom), C.byref(self.cfg), C.byref(self.event), _ptr(h), _ptr(out))
         return out
 
     def pred_chain(self, md_hits, kind):

@@ -665,6 +665,10 @@ __global__ void __launch_bounds__(kT3Warps * 32, 4) k_t3(Arena A, DevCfg c) {
             A.t3_md[o] = make_int4(i, B_, C_, 0);
             A.t3_beta[o] = beta;
             A.t3_ks[o] = make_float2(kap, sk);
+            if (A.compact) {
+                const float inv = 1.f / A.two_a;
+                A.t3_ksh[o] = __floats2half2_rn(kap * inv, sk * inv);
+            }
         }
         if (lane == 0) {
             A.t3_off[i] = base;
@@ -741,25 +745,25 @@ __device__ __forceinline__ void t5_enumerate(const Arena& A, const DevCfg& c, Sm
         int t1 = cb + lane;
         int off = 0, len = 0;
         float2 ks = make_float2(0.f, 0.f);
-        if (t1 < t_end) {
+        if (t1 < t_end && (!A.t3_sel || A.t3_ok[t1])) {
             int C_ = A.t3_md[t1].z;
             off = A.t3_off[C_];
             len = A.t3_cnt[C_];
-            ks = A.t3_ks[t1];
+            ks = t3_ks_search(A, t1);
         }
         S.t1[lane] = t1;
         S.ks1[lane] = ks;
         for_each_flat(off, len, S.pre, S.off, [&](bool valid, int seg, int t2) {
             bool pass = false;
             int t1_ = 0;
-            if (valid) {
+            if (valid && (!A.t3_sel || A.t3_ok[t2])) {
                 t1_ = S.t1[seg];
-                const float2 a = S.ks1[seg], b = A.t3_ks[t2];
+                const float2 a = S.ks1[seg], b = t3_ks_search(A, t2);
                 float k1 = a.x, k2 = b.x;
                 float s1_ = a.y, s2_ = b.y;
                 float thr = nk * fast_sqrtf(s1_ * s1_ + s2_ * s2_);
-                // slack covers the FP32 rounding of the stored curvatures
-                pass = fabsf(k1 - k2) <= thr * 1.01f + 1e-5f * (fabsf(k1) + fabsf(k2)) + 1e-7f;
+                // slack covers the rounding of the stored curvatures (FP32, or FP16 in compact storage)
+                pass = fabsf(k1 - k2) <= thr * 1.01f + ks_slack(A) * (fabsf(k1) + fabsf(k2)) + 1e-7f;
             }
             int tot;
             int r = warp_rank(pass, tot);
@@ -964,6 +968,45 @@ __global__ void k_t5_refine(Arena A, DevCfg c) {
             if (pass) atomicAdd(&A.ev_counts[e * 8 + 3], 1);
         }
     }
+}
+
+// Scoring features of every T3 of the batch (the optional learned triplet
+// selection): one thread per T3; the upper hits come from the input arrays.
+__global__ void k_t3_features(Arena A, DevCfg c) {
+    pdl_begin();
+    const int n = min(A.counters[2], A.t3_cap);
+    const BatchDesc* B = A.bd;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int4 q = A.t3_md[i];
+        const int m[3] = {q.x, q.y, q.z};
+        const int e = A.md_gmod[m[0]] / A.n_mod;
+        const int h0 = A.hit_off[e];
+        Pt<float> P[3], H[6];
+        int code[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            P[j] = md_point<float>(A, m[j]);
+            H[2 * j] = P[j];
+            Pt<float> U = P[j];
+            const int hu = h0 + A.md_up[m[j]];
+            U.x = B->hx[hu];
+            U.y = B->hy[hu];
+            U.z = B->hz[hu];
+            U.r = sqrtf(U.x * U.x + U.y * U.y);
+            H[2 * j + 1] = U;
+            const int mod = A.md_gmod[m[j]] % A.n_mod;
+            code[j] = A.mod_layer[mod] + (A.mod[mod].w > 0.5f ? 6 : 0);
+        }
+        t3_features(c, P, H, code, A.t3_feat + (size_t)48 * i);
+    }
+}
+
+// Triplets the network keeps: the T5 and pT3 searches skip the others.
+__global__ void k_t3_mlp_select(Arena A, DevCfg c) {
+    pdl_begin();
+    const int n = min(A.counters[2], A.t3_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        A.t3_ok[i] = A.t3_mlp[i] >= c.t3_threshold;
 }
 
 // Validity from the network score (the hand-set cut decision stays in t5_cut).

@@ -134,11 +134,12 @@ __device__ __forceinline__ void pt_enumerate(const Arena& A, const DevCfg& c, Pt
         }
         for_each_flat(oo, on, S.pre2, S.off2, [&](bool valid, int, int obj) {
             bool pass = false;
-            if (valid && (NT == 3 || A.t5_valid[obj])) {
-                const float2 ks = NT == 5 ? A.t5_ks[obj] : A.t3_ks[obj];
+            if (valid && (NT == 3 ? (!A.t3_sel || A.t3_ok[obj]) : A.t5_valid[obj] != 0)) {
+                const float2 ks = NT == 5 ? A.t5_ks[obj] : t3_ks_search(A, obj);
                 const float kt = ks.x, st = ks.y;
                 float thr = nk * fast_sqrtf(sp * sp + st * st);
-                pass = fabsf(kp - kt) <= thr * 1.01f + 1e-5f * (fabsf(kp) + fabsf(kt)) + 1e-7f;
+                const float rel = NT == 5 ? 1e-5f : ks_slack(A);
+                pass = fabsf(kp - kt) <= thr * 1.01f + rel * (fabsf(kp) + fabsf(kt)) + 1e-7f;
             }
             int tot;
             int r = warp_rank(pass, tot);
@@ -543,7 +544,10 @@ __device__ __forceinline__ void list_append(const Arena& A, int e, int list, flo
     int k = atomicAdd(&A.list_cnt[e * 2 + list], 1);
     if (k < A.list_cap) {
         size_t o = ((size_t)e * 2 + list) * A.list_cap + k;
-        A.list_ef[o] = make_float2(eta, phi);
+        if (A.compact)
+            A.list_q[o] = pack_eta_phi(eta, phi);
+        else
+            A.list_ef[o] = make_float2(eta, phi);
         A.list_ref[o] = ref;
     }
 }
@@ -559,8 +563,10 @@ __device__ __forceinline__ void ref_eta_phi(const Arena& A, int ref, double& eta
 
 // Is (eta, phi) within dr_clean of any entry of the event's list? Called by
 // all 32 lanes of a warp with the same query; the lanes stride over the list.
-// FP32 test with an FP64 re-test inside a 1e-3 relative band around the
-// threshold.
+// FP32 test with an FP64 re-test inside a band around the threshold: 1e-3
+// relative for FP32 entries; 2e-2 for the compact fixed-point entries, whose
+// rounding (<= 5e-5 per coordinate) moves d^2 by at most 4e-6 = 1 % of the
+// threshold's square wherever d is near the threshold.
 __device__ __forceinline__ bool dr_close_warp(const Arena& A, const DevCfg& c, int e, int list, double eta,
                                               double phi) {
     constexpr int kU = 8;                 // list entries per lane per round: 8 loads in flight
@@ -568,14 +574,20 @@ __device__ __forceinline__ bool dr_close_warp(const Arena& A, const DevCfg& c, i
     const size_t base = ((size_t)e * 2 + list) * A.list_cap;
     const double thr2 = c.dr_clean * c.dr_clean;
     const float thr2f = float(thr2);
+    const float band = A.compact ? 2e-2f : 1e-3f;
     const float ef = float(eta), pf = float(phi);
     const float two_pi = float(2 * kPi);
     for (int j0 = 0; j0 < n; j0 += 32 * kU) {
         float2 v[kU];
+        bool sent[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int j = j0 + 32 * u + lane_id();
-            v[u] = j < n ? A.list_ef[base + j] : make_float2(1e30f, 0.f);
+            sent[u] = false;
+            if (A.compact)
+                v[u] = j < n ? unpack_eta_phi(A.list_q[base + j], sent[u]) : make_float2(1e30f, 0.f);
+            else
+                v[u] = j < n ? A.list_ef[base + j] : make_float2(1e30f, 0.f);
         }
         bool hit = false;
 #pragma unroll
@@ -585,9 +597,9 @@ __device__ __forceinline__ bool dr_close_warp(const Arena& A, const DevCfg& c, i
             if (dp > float(kPi)) dp -= two_pi;
             if (dp <= -float(kPi)) dp += two_pi;
             float d2 = de * de + dp * dp;
-            if (d2 < thr2f * (1.0f - 1e-3f)) {
+            if (!sent[u] && d2 < thr2f * (1.0f - band)) {
                 hit = true;
-            } else if (d2 <= thr2f * (1.0f + 1e-3f)) {
+            } else if (sent[u] || d2 <= thr2f * (1.0f + band)) {
                 double e2, p2;
                 ref_eta_phi(A, A.list_ref[base + j0 + 32 * u + lane_id()], e2, p2);
                 double dd = eta - e2, dq = wrap_pi(phi - p2);

@@ -37,7 +37,8 @@ struct Buffer {
 // their shared-memory stages by a compile-time warp count and keep their block.
 // `tunable` stages are grid-stride over their units, so any grid is valid.
 enum LaunchId {
-    L_RESET, L_BIN_COUNT, L_BIN_SCAN, L_BIN_SCATTER, L_BIN_SORT, L_MD_PLAN, L_MD, L_MD_WRITE, L_LS, L_T3, L_T5_PLAN, L_T5, L_T5_GATHER, L_T5_REFINE,
+    L_RESET, L_BIN_COUNT, L_BIN_SCAN, L_BIN_SCATTER, L_BIN_SORT, L_MD_PLAN, L_MD, L_MD_WRITE, L_LS, L_T3,
+    L_T3_FEAT, L_T3_MLP, L_T3_SELECT, L_T5_PLAN, L_T5, L_T5_GATHER, L_T5_REFINE,
     L_T5_MLP, L_T5_MLP_SELECT, L_PLS, L_PT_PLAN, L_PT5, L_PT5_REFINE, L_PT3, L_PT3_REFINE, L_CLEAN_KEYS, L_CLEAN_KEEP,
     L_CLEAN_PT5, L_CLEAN_PT3_CROSS, L_CLEAN_PT3_MARK, L_CLEAN_T5, L_CLEAN_PLS, L_TC_PACK, kNumLaunch
 };
@@ -61,6 +62,9 @@ const LaunchInfo kLaunch[kNumLaunch] = {
     {"md_write", 4, 128, true, false},
     {"ls", 8, kLsWarps * 32, true, false},
     {"t3", 8, kT3Warps * 32, true, false},
+    {"t3_features", 4, 128, true, true},
+    {"t3_mlp", 4, 128, true, false},
+    {"t3_mlp_select", 4, 256, true, true},
     {"t5_plan", 4, 256, true, true},
     {"t5", 6, kT5Warps * 32, true, false},
     {"t5_gather", 4, 128, true, false},
@@ -134,6 +138,9 @@ struct lst_ctx {
     bool profiling = false;
     bool use_graph = true;
     const lst_mlp* mlp = nullptr;     // network deciding T5 validity (NULL: the hand-set cuts)
+    const lst_mlp* mlp3 = nullptr;    // network pruning triplets (NULL: every T3 that passes the cuts)
+    bool t3_features = false;         // compute the T3 scoring features (network attached or capture)
+    void* t3_mem = nullptr;           // features, scores and flags of the learned triplet selection
     BatchDesc* d_bd = nullptr;        // device batch descriptor
     BatchDesc* h_bd = nullptr;        // pinned staging of the descriptor
     cudaStream_t cap_stream = nullptr;
@@ -291,6 +298,7 @@ void lst_destroy(lst_ctx* c) {
     for (auto& sl : c->slot)
         if (sl.done) cudaEventDestroy(sl.done);
     if (c->dev_mem) cudaFree(c->dev_mem);
+    if (c->t3_mem) cudaFree(c->t3_mem);
     if (c->h_offsets) cudaFreeHost(c->h_offsets);
     if (c->h_bd) cudaFreeHost(c->h_bd);
     for (cudaEvent_t& e : c->prof_ev)
@@ -353,6 +361,8 @@ static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n
     A.t3_cap = (int)T3;
     A.t3_lsin = b.take<int>(T3); A.t3_lsout = b.take<int>(T3);
     A.t3_beta = b.take<float>(T3); A.t3_ks = b.take<float2>(T3);
+    A.t3_ksh = b.take<__half2>(T3);
+    A.two_a = float(2.0 * c->dc.a);
     A.t3_md = b.take<int4>(T3);
     A.t3_off = b.take<int>(MD); A.t3_cnt = b.take<int>(MD);
     const size_t T5 = E * K.t5_per_event;
@@ -395,6 +405,7 @@ static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n
     A.list_cnt = b.take<int>(E * 2);
     A.list_ef = b.take<float2>(E * 2 * A.list_cap);
     A.list_ref = b.take<int>(E * 2 * A.list_cap);
+    A.list_q = b.take<unsigned>(E * 2 * A.list_cap);
     A.tc_cap = K.tc_per_event;
     A.tc_cnt = b.take<int>(E);
     const size_t TC = E * K.tc_per_event;
@@ -541,6 +552,12 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile, cudaStream_
     LAUNCH(L_MD_WRITE, run_k(k_md_write, GB(L_MD_WRITE), 0, st, pdl, A, dc));
     LAUNCH(L_LS, run_k(k_ls, GB(L_LS), 0, st, pdl, A, dc));
     LAUNCH(L_T3, run_k(k_t3, GB(L_T3), 0, st, pdl, A, dc));
+    if (c->t3_features) LAUNCH(L_T3_FEAT, run_k(k_t3_features, GB(L_T3_FEAT), 0, st, pdl, A, dc));
+    if (c->mlp3) {
+        LAUNCH(L_T3_MLP, run_k(k_mlp_forward, GB(L_T3_MLP), 0, st, pdl, lst_mlp_device_params(c->mlp3), A.t3_feat,
+                               A.t3_cap, A.counters + 2, A.t3_mlp, MlpSaved{}));
+        LAUNCH(L_T3_SELECT, run_k(k_t3_mlp_select, GB(L_T3_SELECT), 0, st, pdl, A, dc));
+    }
     if (side) {
         cudaEventRecord(c->ev_t3, st);
         cudaStreamWaitEvent(side, c->ev_t3, 0);
@@ -814,6 +831,9 @@ static const void* launch_fn(int id) {
         case L_T5_PLAN: return (const void*)k_t5_plan;
         case L_T5_GATHER: return (const void*)k_t5_gather;
         case L_T5_REFINE: return (const void*)k_t5_refine;
+        case L_T3_FEAT: return (const void*)k_t3_features;
+        case L_T3_MLP: return (const void*)k_mlp_forward;
+        case L_T3_SELECT: return (const void*)k_t3_mlp_select;
         case L_T5_MLP: return (const void*)k_mlp_forward;
         case L_T5_MLP_SELECT: return (const void*)k_t5_mlp_select;
         case L_PLS: return (const void*)k_pls;
@@ -854,6 +874,13 @@ static lst_status drop_graph(lst_ctx* c) {
         c->graph = nullptr;
     }
     return LST_OK;
+}
+
+lst_status lst_set_compact_storage(lst_ctx* c, int32_t enable) {
+    if (!c || enable < 0 || enable > 1) return LST_ERR_ARG;
+    lst_status s = drop_graph(c);
+    c->A.compact = enable;
+    return s;
 }
 
 lst_status lst_set_stage_limits(lst_ctx* c, int32_t t5, int32_t pt) {
@@ -1031,6 +1058,83 @@ lst_status lst_set_t5_selection(lst_ctx* c, const lst_mlp* mlp, float threshold,
         c->graph = nullptr;
     }
     return LST_OK;
+}
+
+lst_status lst_set_t3_selection(lst_ctx* c, const lst_mlp* mlp, float threshold, int32_t capture_features) {
+    if (!c) return LST_ERR_ARG;
+    if (!c->geometry) return LST_ERR_NO_GEOMETRY;
+    if (c->ran) CK(cudaEventSynchronize(c->done));
+    const bool feat = mlp || capture_features;
+    if (feat && !c->t3_mem) {
+        const size_t T3 = (size_t)c->A.t3_cap;
+        const size_t bytes = T3 * (48 * sizeof(float) + sizeof(float) + 1) + 512;
+        CK(cudaSetDevice(c->device));
+        if (cudaMalloc(&c->t3_mem, bytes) != cudaSuccess) {
+            c->t3_mem = nullptr;
+            return LST_ERR_OOM;
+        }
+        char* p = static_cast<char*>(c->t3_mem);
+        c->A.t3_feat = reinterpret_cast<float*>(p);
+        c->A.t3_mlp = reinterpret_cast<float*>(p + T3 * 48 * sizeof(float));
+        c->A.t3_ok = reinterpret_cast<uint8_t*>(p + T3 * 49 * sizeof(float));
+    }
+    c->mlp3 = mlp;
+    c->t3_features = feat;
+    c->A.t3_sel = mlp ? 1 : 0;
+    c->dc.t3_threshold = threshold;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return LST_OK;
+}
+
+lst_status lst_get_t3_candidates(lst_ctx* c, lst_event_id id, int32_t capacity, int32_t* n_out, float* features,
+                                 int32_t* hits, float* score, int32_t* kept) {
+    int32_t event = 0;
+    lst_status s = wait_batch(c, id, event);
+    if (s != LST_OK) return s;
+    if (capacity < 0) return LST_ERR_ARG;
+    const Arena& A = c->A;
+    int cnt[32];
+    CK(cudaMemcpy(cnt, A.counters, sizeof cnt, cudaMemcpyDeviceToHost));
+    const int n = std::min(cnt[2], A.t3_cap), n_md = std::min(cnt[0], A.md_cap);
+    std::vector<int4> t3md;
+    std::vector<int> gm, lo, up;
+    FETCH(t3md, A.t3_md, n);
+    FETCH(gm, A.md_gmod, n_md); FETCH(lo, A.md_lo, n_md); FETCH(up, A.md_up, n_md);
+    std::vector<int> rows;
+    for (int i = 0; i < n; ++i)
+        if (gm[t3md[i].x] / A.n_mod == event) rows.push_back(i);
+    const int k = std::min((int)rows.size(), (int)capacity);
+    if (n_out) *n_out = (int)rows.size();
+    if (features && k) {
+        if (!c->t3_features) return LST_ERR_ARG;
+        std::vector<float> f;
+        FETCH(f, A.t3_feat, (size_t)48 * n);
+        for (int r = 0; r < k; ++r) std::memcpy(features + 48 * (size_t)r, f.data() + 48 * (size_t)rows[r], 48 * 4);
+    }
+    if (score && k) {
+        if (!c->mlp3) return LST_ERR_ARG;
+        std::vector<float> sc;
+        FETCH(sc, A.t3_mlp, n);
+        for (int r = 0; r < k; ++r) score[r] = sc[rows[r]];
+    }
+    if (kept && k) {
+        std::vector<uint8_t> ok;
+        if (c->mlp3) FETCH(ok, A.t3_ok, n);
+        for (int r = 0; r < k; ++r) kept[r] = c->mlp3 ? ok[rows[r]] : 1;
+    }
+    if (hits)
+        for (int r = 0; r < k; ++r) {
+            const int4 q = t3md[rows[r]];
+            const int md[3] = {q.x, q.y, q.z};
+            for (int j = 0; j < 3; ++j) {
+                hits[6 * r + 2 * j] = lo[md[j]];
+                hits[6 * r + 2 * j + 1] = up[md[j]];
+            }
+        }
+    return (int)rows.size() > capacity ? LST_WARN_TRUNCATED : LST_OK;
 }
 
 lst_status lst_get_t5_candidates(lst_ctx* c, lst_event_id id, int32_t capacity, int32_t* n_out, float* features,

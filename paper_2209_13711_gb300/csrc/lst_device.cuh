@@ -25,6 +25,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "lst_pdl.cuh"
@@ -60,6 +61,7 @@ struct DevCfg {
     int use_mlp;           // T5 validity from the network score instead of the cuts
     float prefit_scale;    // widening of the T5 FP32 prefilter (1: conservative for the cuts)
     float mlp_threshold;
+    float t3_threshold;    // learned triplet selection: keep a T3 when its score reaches this
     int t5_stage;          // T5 survivors staged per work item before the re-enumeration path
     int pt_stage;          // the same for the pT5 / pT3 search
     CfgF f;
@@ -151,6 +153,16 @@ struct Arena {
     int* t3_lsout;
     float* t3_beta;
     float2* t3_ks;                // {curvature, its sigma} (FP32)
+    __half2* t3_ksh;              // the same over 2a in FP16 (compact storage: the searches' copy)
+    float two_a;                  // 2a in FP32 (the FP16 copy's scale)
+    int compact;                  // 16-bit storage: FP16 triplet curvatures for the T5 / pT3 searches and
+                                  // fixed-point eta-phi lists for the cleaning (decisions unchanged)
+    // optional learned triplet selection (a network scores every T3; the T5 and pT3 searches skip the
+    // T3s it rejects)
+    int t3_sel;                   // 1: t3_ok gates the searches
+    float* t3_feat;               // [T3][48] scoring features (allocated when enabled)
+    float* t3_mlp;                // [T3] network score
+    uint8_t* t3_ok;               // [T3] score >= threshold
     int4* t3_md;                  // the three MDs {inner, middle, outer, 0}
     int* t3_off;                  // [md_cap] by inner MD
     int* t3_cnt;
@@ -225,6 +237,7 @@ struct Arena {
     int* list_cnt;                // [n_ev][2]: list 0 = kept pT5 + pT3, list 1 = kept T5
     float2* list_ef;              // [n_ev][2][list_cap] (eta, phi) float
     int* list_ref;                // [n_ev][2][list_cap] (category << 28) | index
+    unsigned* list_q;             // compact storage: (eta, phi) as two 16-bit fixed-point halves
     // track candidates, per-event slabs
     int tc_cap;
     int* tc_cnt;                  // [n_ev]
@@ -910,6 +923,133 @@ __device__ inline void t5_features(const DevCfg& c, const Pt<double>* P, const P
     for (int j = 38; j < 48; ++j) f[j] = 0.f;
 }
 
+// FP32 chord-frame fit of N points with every output (the same algebra as
+// fit_track, no early exit): the triplet features' fit. IEEE division and
+// square root; FP32 is ample for features the network reads in BF16.
+struct FitF {
+    float gg, hh, kk, S, xx, xy, ox, oy, c0, t, t_hat, kappa, chi2, chi2z;
+};
+template <int N> __device__ inline FitF fit_f32(const Pt<float>* P) {
+    FitF F;
+    const Pt<float>& O = P[N / 2];
+    const float ex = P[N - 1].x - P[0].x, ey = P[N - 1].y - P[0].y;
+    const float il = 1.f / sqrtf(ex * ex + ey * ey);
+    const float xx = ex * il, xy = ey * il;
+    float xi[N], et[N], rho2[N], mr = 0.f, mx = 0.f, me = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const float dx = P[i].x - O.x, dy = P[i].y - O.y;
+        xi[i] = dx * xx + dy * xy;
+        et[i] = dy * xx - dx * xy;
+        rho2[i] = xi[i] * xi[i] + et[i] * et[i];
+        mr += rho2[i]; mx += xi[i]; me += et[i];
+    }
+    mr *= 1.f / N; mx *= 1.f / N; me *= 1.f / N;
+    float saa = 0.f, sab = 0.f, sbb = 0.f, sac = 0.f, sbc = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const float a = rho2[i] - mr, b = xi[i] - mx, cc = et[i] - me;
+        saa += a * a; sab += a * b; sbb += b * b; sac += a * cc; sbc += b * cc;
+    }
+    const float det = saa * sbb - sab * sab;
+    F.xx = xx; F.xy = xy; F.ox = O.x; F.oy = O.y;
+    if (!(det > 0.f)) {
+        F.gg = F.hh = F.kk = 0.f; F.S = 1.f; F.kappa = 0.f; F.chi2 = F.chi2z = 1e30f; F.c0 = F.t = F.t_hat = 0.f;
+        return F;
+    }
+    F.gg = (sac * sbb - sab * sbc) / det;
+    F.hh = (saa * sbc - sab * sac) / det;
+    F.kk = me - F.gg * mr - F.hh * mx;
+    F.S = sqrtf(fmaxf(0.f, 1.f + F.hh * F.hh - 4.f * F.gg * F.kk));
+    F.kappa = 2.f * F.gg / F.S;
+    float chi2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const float u = F.gg * rho2[i] + F.hh * xi[i] + F.kk - et[i];
+        const float e = 2.f * u / (F.S + sqrtf(fmaxf(0.f, F.S * F.S + 4.f * F.gg * u)));
+        const float nlx = 2.f * F.gg * xi[i] + F.hh, nly = 2.f * F.gg * et[i] - 1.f;
+        const float nx = nlx * xx - nly * xy, ny = nlx * xy + nly * xx;
+        const float nn2 = nx * nx + ny * ny;
+        const float rx = P[i].x / P[i].r, ry = P[i].y / P[i].r;
+        const float n_phi = ny * rx - nx * ry, n_r = nx * rx + ny * ry;
+        const float s2 = fmaxf(sq(P[i].srphi * n_phi) + sq(P[i].sr * n_r), sq(0.01f * P[i].srphi) * nn2);
+        chi2 += e * e * nn2 / s2;
+    }
+    F.chi2 = chi2;
+    const float ka = fabsf(F.kappa);
+    float s[N], w[N], W = 0.f, Ws = 0.f, Wz = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) s[i] = arc(sqrtf(sq(P[i].x - P[0].x) + sq(P[i].y - P[0].y)), ka);
+    F.t_hat = (P[N - 1].z - P[0].z) / s[N - 1];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        w[i] = 1.f / fmaxf(1e-12f, sq(P[i].sz) + sq(F.t_hat * P[i].sr));
+        W += w[i]; Ws += w[i] * s[i]; Wz += w[i] * P[i].z;
+    }
+    const float sbar = Ws / W, zbar = Wz / W;
+    float Sss = 0.f, Ssz = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        Sss += w[i] * sq(s[i] - sbar);
+        Ssz += w[i] * (s[i] - sbar) * (P[i].z - zbar);
+    }
+    F.t = Ssz / Sss;
+    F.c0 = zbar - F.t * sbar;
+    float cz = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) cz += w[i] * sq(P[i].z - F.c0 - F.t * s[i]);
+    F.chi2z = cz;
+    return F;
+}
+
+// Scoring features of a T3 (FP32), in the T5's slots with the missing ones
+// zero: hits H[0..5] = (lower, upper) of the three MDs, anchors P = the lower
+// hits. f[0..5] r-phi pulls of the six hits to the anchors' circle, f[10..15]
+// r-z pulls to the fitted line (both clipped to +-50), f[20..22] anchor
+// radius / 100, f[25] the triplet's curvature / 2a, f[27] the fit's,
+// f[28..29] log(1 + chi2_rphi), log(1 + chi2_rz), f[30] 10 x beta, f[32] eta,
+// f[33..35] layer code / 11; every other slot 0.
+__device__ inline void t3_features(const DevCfg& c, const Pt<float>* P, const Pt<float>* H, const int* code,
+                                   float* f) {
+    const FitF F = fit_f32<3>(P);
+    const Tri<float> t = tri(P[0], P[1], P[2]);
+    const float ka = fabsf(F.kappa);
+    float v[48];
+#pragma unroll
+    for (int j = 0; j < 48; ++j) v[j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const Pt<float>& Q = H[j];
+        const float dx = Q.x - F.ox, dy = Q.y - F.oy;
+        const float xi = dx * F.xx + dy * F.xy, et = dy * F.xx - dx * F.xy;
+        const float u = F.gg * (xi * xi + et * et) + F.hh * xi + F.kk - et;
+        const float e = 2.f * u / (F.S + sqrtf(fmaxf(0.f, F.S * F.S + 4.f * F.gg * u)));
+        const float nlx = 2.f * F.gg * xi + F.hh, nly = 2.f * F.gg * et - 1.f;
+        const float nx = nlx * F.xx - nly * F.xy, ny = nlx * F.xy + nly * F.xx;
+        const float nn2 = nx * nx + ny * ny;
+        const float rx = Q.x / Q.r, ry = Q.y / Q.r;
+        const float n_phi = ny * rx - nx * ry, n_r = nx * rx + ny * ry;
+        const float s2 = fmaxf(sq(Q.srphi * n_phi) + sq(Q.sr * n_r), sq(0.01f * Q.srphi) * nn2) / nn2;
+        v[j] = fminf(50.f, fmaxf(-50.f, e / sqrtf(s2)));
+        const float sj = arc(sqrtf(sq(Q.x - P[0].x) + sq(Q.y - P[0].y)), ka);
+        const float w = 1.f / fmaxf(1e-12f, sq(Q.sz) + sq(F.t_hat * Q.sr));
+        v[10 + j] = fminf(50.f, fmaxf(-50.f, (Q.z - F.c0 - F.t * sj) * sqrtf(w)));
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v[20 + j] = P[j].r / 100.f;
+    const float two_a = 2.f * c.f.a;
+    v[25] = t.kappa / two_a;
+    v[27] = F.kappa / two_a;
+    v[28] = log1pf(fminf(F.chi2, 1e30f));
+    v[29] = log1pf(fminf(F.chi2z, 1e30f));
+    v[30] = 10.f * t.beta;
+    v[32] = asinhf(F.t);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v[33 + j] = code[j] / 11.f;
+#pragma unroll
+    for (int j = 0; j < 48; j += 4) *reinterpret_cast<float4*>(f + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+}
+
 // T5 on anchors P[0..4]; outputs in double
 struct T5Out {
     double kappa, chi2_rphi, chi2_rz, eta, phi0, pt, score, sigk;
@@ -989,6 +1129,37 @@ __device__ inline bool pt_eval(const DevCfg& c, const Pt<double>* P, const Pt<fl
 // ---------------------------------------------------------------------------
 // small device utilities
 // ---------------------------------------------------------------------------
+// ---- compact (16-bit) storage ---------------------------------------------
+// A triplet's stored (curvature, sigma) as the T5 and pT3 searches read it:
+// FP32, or the FP16 copy scaled by 1/(2a) (|kappa| / 2a <= 1 + tol for a
+// triplet, so the copy stays in FP16's normal range). A search prefilter that
+// reads the copy widens its slack by ks_slack: each FP16 value is within
+// 2^-11 of its FP32 value (relative), subnormals within 1e-9 absolute after
+// rescaling, both far inside 1e-3 relative plus the 1e-7 absolute term.
+__device__ __forceinline__ float2 t3_ks_search(const Arena& A, int t) {
+    if (!A.compact) return A.t3_ks[t];
+    const float2 v = __half22float2(A.t3_ksh[t]);
+    return make_float2(v.x * A.two_a, v.y * A.two_a);
+}
+__device__ __forceinline__ float ks_slack(const Arena& A) { return A.compact ? 1e-3f : 1e-5f; }
+
+// Fixed-point eta-phi: 1e-4 per step in eta (|eta| < 3.2767) and pi / 32767
+// in phi; an eta outside that range is stored as the sentinel -32768, which
+// the list scan always re-tests in FP64.
+constexpr float kEtaQ = 1e-4f;
+constexpr float kPhiQ = 3.14159265358979f / 32767.f;
+__device__ __forceinline__ unsigned pack_eta_phi(float eta, float phi) {
+    const float qe = eta / kEtaQ;
+    const int ie = fabsf(qe) < 32767.f ? __float2int_rn(qe) : -32768;
+    const int ip = max(-32767, min(32767, __float2int_rn(phi / kPhiQ)));
+    return (unsigned(ie) & 0xffffu) | (unsigned(ip) << 16);
+}
+__device__ __forceinline__ float2 unpack_eta_phi(unsigned q, bool& sentinel) {
+    const int ie = int(short(q & 0xffffu)), ip = int(short(q >> 16));
+    sentinel = ie == -32768;
+    return make_float2(float(ie) * kEtaQ, float(ip) * kPhiQ);
+}
+
 __device__ __forceinline__ int event_of(const int* off, int n_ev, int i) {
     int lo = 0, hi = n_ev;            // off[lo] <= i < off[hi]
     while (hi - lo > 1) {

@@ -48,6 +48,8 @@ __global__ void k_pt3(Arena A, DevCfg c);
 __global__ void k_pt5_refine(Arena A, DevCfg c);
 __global__ void k_pt3_refine(Arena A, DevCfg c);
 __global__ void k_clean_keys(Arena A, int pass);
+__global__ void k_t3_features(Arena A, DevCfg c);
+__global__ void k_t3_mlp_select(Arena A, DevCfg c);
 __global__ void k_clean_pt5(Arena A);
 __global__ void k_clean_pt3_cross(Arena A, DevCfg c);
 __global__ void k_clean_pt3_mark(Arena A);

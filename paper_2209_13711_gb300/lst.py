@@ -104,6 +104,7 @@ def library():
         L.lst_set_profiling.argtypes = [vp, i32]
         L.lst_get_counters.argtypes = [vp, vp, i32]
         L.lst_set_stage_limits.argtypes = [vp, i32, i32]
+        L.lst_set_compact_storage.argtypes = [vp, i32]
         L.lst_launch_stage_count.argtypes = []
         L.lst_launch_stage_count.restype = i32
         L.lst_get_launch_config.argtypes = [vp, i32, C.POINTER(C.c_char_p), vp, vp, vp]
@@ -127,6 +128,8 @@ def library():
         L.lst_mlp_train_step.argtypes = [vp, vp, vp, i32, C.c_float, vp, vp]
         L.lst_set_t5_selection.argtypes = [vp, vp, C.c_float, C.c_float, i32]
         L.lst_get_t5_candidates.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp]
+        L.lst_set_t3_selection.argtypes = [vp, vp, C.c_float, i32]
+        L.lst_get_t3_candidates.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp]
         L.lst_get_kernel_times.argtypes = [vp, i32, vp, vp, vp]
         L.lst_measure_peaks.argtypes = [i32, vp]
         L.lst_build_mini_doublets_static.argtypes = [vp, vp, i32] + [vp] * 5 + [i32, i32] + [vp] * 7 + [vp]
@@ -137,7 +140,8 @@ def library():
                   "lst_mlp_forward", "lst_mlp_gradient", "lst_mlp_train_step", "lst_set_t5_selection",
                   "lst_get_t5_candidates", "lst_measure_peaks", "lst_build_mini_doublets_static",
                   "lst_release_event", "lst_run_events", "lst_get_batch_track_candidates", "lst_mlp_get_state",
-                  "lst_mlp_set_state"):
+                  "lst_mlp_set_state", "lst_set_compact_storage", "lst_set_t3_selection",
+                  "lst_get_t3_candidates"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -438,6 +442,11 @@ class Context:
                             tunable=bool(f.value & 1), generic=bool(f.value & 2)))
         return out
 
+    def set_compact_storage(self, enable=True):
+        """16-bit copies for the searches' curvature prefilters and the cleaning's eta-phi lists
+        (lst_set_compact_storage); the objects do not change."""
+        _check(library().lst_set_compact_storage(self._h, 1 if enable else 0))
+
     def set_stage_limits(self, t5=0, pt=0):
         """Survivors a T5 / pT work item stages before re-enumerating (0: the defaults 512 / 256)."""
         _check(library().lst_set_stage_limits(self._h, int(t5), int(pt)))
@@ -490,6 +499,28 @@ class Context:
         self._mlp = mlp
         _check(library().lst_set_t5_selection(self._h, mlp._h if mlp is not None else None, float(threshold),
                                               float(prefilter_scale), 1 if capture_features else 0))
+
+    def set_t3_selection(self, mlp=None, threshold=0.5, capture_features=False):
+        """Network pruning of triplets before the T5 and pT3 searches (mlp: an Mlp), or none (mlp=None);
+        capture_features computes the triplet features without a network (training)."""
+        self._mlp3 = mlp
+        _check(library().lst_set_t3_selection(self._h, mlp._h if mlp is not None else None, float(threshold),
+                                              1 if capture_features else 0))
+
+    def t3_candidates(self, event=0, features=True):
+        """Every T3 of an event: features [n, 48] (when computed), hits [n, 6], score [n] (with a network),
+        kept [n]."""
+        L = library()
+        n = C.c_int32(0)
+        _check(L.lst_get_t3_candidates(self._h, int(event), 0, C.byref(n), None, None, None, None))
+        k = n.value
+        f = np.zeros((k, 48), np.float32) if features else None
+        h = np.zeros((k, 6), np.int32)
+        has_net = getattr(self, "_mlp3", None) is not None
+        sc = np.zeros(k, np.float32) if has_net else None
+        kept = np.zeros(k, np.int32)
+        _check(L.lst_get_t3_candidates(self._h, int(event), k, C.byref(n), _ptr(f), _ptr(h), _ptr(sc), _ptr(kept)))
+        return dict(features=f, hits=h, score=sc, kept=kept.astype(bool))
 
     def t5_candidates(self, event=0):
         """Every T5 candidate of an event: features [n, 48], hits [n, 10], cut_pass [n], score [n]."""

@@ -176,3 +176,53 @@ def test_grouped_and_per_thread_refine_agree(geom_full, maps_full):
         assert _all_tuples(one, 0) == batched[i]
     ctx.close()
     one.close()
+
+
+def test_compact_storage_gives_the_same_objects(geom_full, maps_full):
+    """16-bit copies for the searches' curvature prefilters and the cleaning's eta-phi lists: every object
+    level and the track candidates equal those of the default storage, and the oracle's."""
+    ev = E.pu200_event(7, geom_full)
+    plain = make_context(geom_full, maps_full, max_events=1)
+    plain.run([ev])
+    want = _all_tuples(plain, 0)
+    plain.close()
+    ctx = make_context(geom_full, maps_full, max_events=1)
+    ctx.set_compact_storage(True)
+    ctx.run([ev])
+    assert _all_tuples(ctx, 0) == want
+    g = gpu_result(ctx)
+    _no_drops(g)
+    compare(g, oracle_result(geom_full, maps_full, ev), A_HALF, DEFAULT_CUTS)
+    ctx.close()
+
+
+def test_compact_storage_batch_equals_default(geom_full, maps_full):
+    evs = [E.pileup_event(60 + 20 * i, 70 + i, geom_full) for i in range(6)]
+    res = []
+    for compact in (False, True):
+        ctx = make_context(geom_full, maps_full, max_events=6)
+        ctx.set_compact_storage(compact)
+        ctx.run(evs)
+        res.append([_all_tuples(ctx, e) for e in range(6)])
+        ctx.close()
+    assert res[0] == res[1]
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_displaced_muon_gun_parity(geom_full, seed):
+    """Muons from vertices in a 5 cm cube, with the connection map that covers them: every object level and
+    the track candidates against the oracle; T5s are built for muons with d0 above 1 cm."""
+    import math
+    from synth import maps as M
+    maps = M.load_maps(geom_full, M.MapParams(d0_max=2.5 * math.sqrt(2.0)))
+    ev = E.muon_gun_event(seed, geom_full, n=60)
+    ctx = make_context(geom_full, maps, max_events=1)
+    ctx.run([ev])
+    g = gpu_result(ctx)
+    _no_drops(g)
+    s = compare(g, oracle_result(geom_full, maps, ev), A_HALF, DEFAULT_CUTS)
+    assert s["t5"][0] > 0
+    d0 = ev.tracks.d0
+    t5_tc = [h[h >= 0] for t, h in zip(g["tc"]["type"], g["tc"]["hits"]) if t == 2]
+    assert any(d0[np.bincount(ev.pid[h]).argmax()] > 1.0 for h in t5_tc if len(h))
+    ctx.close()

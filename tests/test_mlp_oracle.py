@@ -7,6 +7,7 @@ import pytest
 from oracle import mlp_oracle as R
 from oracle import oracle as O
 from synth.mlp_init import init_params
+from synth import geometry as G
 from tests.helix_points import on_cylinder
 
 
@@ -104,3 +105,56 @@ def test_features_of_a_helix():
         assert np.all(f[38:] == 0)
         # beta of each triplet has the bending sign
         assert np.sign(f[30]) == np.sign(ks) and np.sign(f[31]) == np.sign(ks)
+
+
+def _t3_event(geom, pt, q, eta, phi0, layers, shift=0.0):
+    """Three barrel MDs of one noiseless helix (lower and upper hits); the middle upper hit moved by `shift`
+    along phi-hat."""
+    import math
+    from types import SimpleNamespace
+    from tests.helix_points import barrel_module, on_cylinder
+    xs, mods, sides = [], [], []
+    for li in layers:
+        r = G.BARREL_R[li]
+        for side, rr in ((0, r), (1, r + float(np.float32(G.DSEP)))):
+            p, _ = on_cylinder(pt, q, eta, phi0, 0.0, rr)
+            if side == 1 and li == layers[1]:
+                ph = math.atan2(p[1], p[0]) + shift / rr
+                p = np.array([rr * math.cos(ph), rr * math.sin(ph), p[2]])
+            xs.append(p)
+            mods.append(barrel_module(geom, li, xs[-2] if side == 1 else p))
+            sides.append(side)
+    xs = np.array(xs)
+    return SimpleNamespace(x=xs[:, 0], y=xs[:, 1], z=xs[:, 2], module=np.array(mods, np.int32),
+                           side=np.array(sides, np.uint8), seeds=np.zeros((0, 3, 3), np.float32))
+
+
+def test_t3_features_closed_forms(geom_full, maps_full, cuts):
+    """Noiseless helix: every pull 0, curvature and eta of the helix, the anchors' radii, beta of the circle,
+    and zeros in the slots a triplet does not fill. One upper hit moved by delta in r-phi: its pull is
+    delta / sigma_rphi (hits are stored in FP32, hence the tolerances)."""
+    import math
+    from oracle import oracle as O
+    from synth import geometry as G_
+    pt, q, eta = 2.5, -1.0, 0.4
+    ev = _t3_event(geom_full, pt, q, eta, 0.9, (1, 2, 3))
+    S = O.Setup(geom_full.module_table(), maps_full, cuts, ev)
+    f = S.t3_features([0, 1, 2, 3, 4, 5])
+    two_a = 2 * 0.3 * 3.8 / (200 * 0.8)
+    ks = -q * float(G_.curvature_of_pt(pt))
+    assert np.all(np.abs(f[0:6]) < 0.05) and np.all(np.abs(f[10:16]) < 0.05)
+    assert abs(f[25] - ks / two_a) < 1e-4 * abs(ks / two_a) and abs(f[27] - f[25]) < 1e-6
+    assert abs(f[32] - eta) < 1e-5
+    assert np.allclose(f[20:23], np.array([G_.BARREL_R[1], G_.BARREL_R[2], G_.BARREL_R[3]]) / 100, atol=1e-6)
+    R = 1 / abs(ks)
+    a, b, c = (np.array([ev.x[i], ev.y[i]], float) for i in (0, 2, 4))
+    beta = math.copysign(math.asin(np.linalg.norm(b - a) / (2 * R)) + math.asin(np.linalg.norm(c - b) / (2 * R)), ks)
+    assert abs(f[30] - 10 * beta) < 1e-4
+    assert np.allclose(f[33:36], np.array([2, 3, 4]) / 11.0)
+    zero = [6, 7, 8, 9, 16, 17, 18, 19, 23, 24, 26, 31] + list(range(36, 48))
+    assert np.all(f[zero] == 0.0)
+    delta = 3 * 0.009 / math.sqrt(12)
+    g = S.__class__(geom_full.module_table(), maps_full, cuts, _t3_event(geom_full, pt, q, eta, 0.9, (1, 2, 3),
+                                                                          shift=delta)).t3_features(range(6))
+    assert abs(abs(g[3]) - 3.0) < 0.05
+    assert np.all(np.abs(np.delete(g[0:6], 3)) < 0.05)
