@@ -77,7 +77,7 @@ typedef struct lst_config {
 
 /* Capacities, fixed at creation; all device memory is allocated once. */
 typedef struct lst_capacity {
-    int32_t max_events;          /* events per batch */
+    int32_t max_events;          /* events per batch, 1 .. 8192 */
     int32_t max_hits;            /* outer-tracker hits per batch */
     int32_t max_seeds;           /* pixel seeds per batch */
     int32_t md_per_event, ls_per_event, t3_per_event, t5_per_event;
@@ -338,9 +338,11 @@ lst_status lst_build_mini_doublets_static(const lst_config* cfg, const lst_modul
  * reserved (MD, LS, T3, T5 candidates, pT5 candidates, pT3 candidates), [16]
  * hits with an invalid module or side, [20] T5 search work items (chunks of 8, 16
  * or 32 T3 of one inner MD, by batch size) whose survivors exceeded the shared-memory stage
- * and were enumerated a second time, [22] + [23] T5 work items, [25] pT work
- * items (seed, superbin module), [28] pT work items enumerated a second time.
- * At most n (<= 32) values. */
+ * and were enumerated a second time, [21] T5 search survivors, [22] + [23] T5
+ * work items, [24] the T5 search's event pointer (items are taken event by
+ * event; n_events once done), [25] pT work items (seed, superbin module),
+ * [26] / [27] the pT5 / pT3 searches' item cursors, [28] pT work items
+ * enumerated a second time. At most n (<= 32) values. */
 lst_status lst_get_counters(lst_ctx* ctx, int32_t* out, int32_t n);
 
 /* ---- learned T5 selection (an optional scoring network; the paper's own
@@ -394,8 +396,9 @@ lst_status lst_set_t5_selection(lst_ctx* ctx, const lst_mlp* mlp, float threshol
 /* Learned triplet selection (optional; the default keeps every T3 that passes
  * the hand-set cuts). mlp = NULL: no network; otherwise every T3 is scored
  * (LST_MLP_FEATURES features of the triplet in the T5's slots, the missing
- * ones zero) and the T5 and pT3 searches skip the T3s whose score is below
- * threshold, which saves their combinatorics. capture_features = 1 computes
+ * ones zero) and the T5 search skips the T3s whose score is below threshold,
+ * which saves its combinatorics (the pT3 search, on its own branch of the
+ * graph, keeps every T3 and starts without waiting for the scores). capture_features = 1 computes
  * the features without a network (for training). The first call that needs
  * them allocates the feature buffer (t3_per_event x max_events x 197 bytes;
  * LST_ERR_OOM if that fails). The network must outlive its use. Waits for the

@@ -40,6 +40,9 @@ __global__ void k_reset(Arena A) {
         A.list_cnt[2 * i] = 0;
         A.list_cnt[2 * i + 1] = 0;
         A.tc_cnt[i] = 0;
+        A.t5_evf[i] = 0;
+        A.t5_evb[i] = 0;
+        A.t5_evc[i] = 0;
     }
     if (t < 32) A.counters[t] = 0;
 }
@@ -686,6 +689,7 @@ __global__ void __launch_bounds__(kT3Warps * 32, 4) k_t3(Arena A, DevCfg c) {
 // then the full test in FP64 for the survivors (k_t5_refine).
 // ---------------------------------------------------------------------------
 struct T5Smem {
+    int cur[5];                // the warp's item cursor (t5_next_item): event, front count, total, region
     int pre[32], off[32], t1[32];
     float2 ks1[32];            // curvature and sigma of each lane's T3_1
     int2 cand[kT5Pre];
@@ -788,25 +792,81 @@ __device__ __forceinline__ int t5_chunk_len(const Arena& A) {
     return n_t3 < (1 << 21) ? 8 : (n_t3 < (1 << 23) ? 16 : 32);
 }
 
-// T5 work items: the T3_1 of each inner MD in chunks of t5_chunk_len. Chunks of
-// units with more than one chunk go to the front of the item list (they are
-// the heavy units and start first), single-chunk units to the back.
+// T5 work items: the T3_1 of each inner MD in chunks of t5_chunk_len, event
+// by event. Event e owns the region [base_e, base_e+1) of the item list, as
+// long as its T3 count (every item holds at least one T3_1), so no second pass
+// is needed: chunks of units with more than one chunk go to the front of the
+// region (they are the heavy units and start first), single-chunk units to
+// the back. The bases are written for the search (t5_evbase[0..n_ev]).
 __global__ void k_t5_plan(Arena A) {
     pdl_begin();
+    extern __shared__ int s_base[];
+    const int n_ev = A.bd->n_ev;
+    if (threadIdx.x == 0) {
+        int b = 0;
+        for (int e = 0; e < n_ev; ++e) {
+            s_base[e] = b;
+            b += A.ev_counts[8 * e + 2];
+        }
+        s_base[n_ev] = b;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int e = threadIdx.x; e <= n_ev; e += blockDim.x) A.t5_evbase[e] = s_base[e];
     const int n_md = min(A.counters[0], A.md_cap);
     const int clen = t5_chunk_len(A);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_md; i += gridDim.x * blockDim.x) {
         const int n = A.t3_cnt[i];
         if (n == 0) continue;
+        const int e = A.md_gmod[i] / A.n_mod;
         const int s0 = A.t3_off[i], nch = (n + clen - 1) / clen;
         if (nch > 1) {
-            const int k = atomicAdd(&A.counters[22], nch);
-            for (int j = 0; j < nch; ++j) A.t5_items[k + j] = s0 + j * clen;
+            const int k = atomicAdd(&A.t5_evf[e], nch);
+            for (int j = 0; j < nch; ++j) A.t5_items[s_base[e] + k + j] = s0 + j * clen;
+            atomicAdd(&A.counters[22], nch);
         } else {
-            const int k = atomicAdd(&A.counters[23], 1);
-            A.t5_items[A.t3_cap - 1 - k] = s0;
+            const int k = atomicAdd(&A.t5_evb[e], 1);
+            A.t5_items[s_base[e + 1] - 1 - k] = s0;
+            atomicAdd(&A.counters[23], 1);
         }
     }
+}
+
+size_t t5_plan_smem_bytes(int max_events) { return sizeof(int) * (size_t)(max_events + 1); }
+
+// Next T5 work item of a warp (lane 0 claims, all lanes receive it): the
+// events are taken in order, so the warps of the grid work on one or two
+// events at a time and the records they gather stay in L2 at batch size.
+// counters[24] is the first event whose items may remain. The warp keeps its
+// current event's item counts and region in its shared-memory slot (cur: event
+// or -1, front count, total, region start and end; registers are scarce in the
+// search), so a claim is one atomic and one load; a warp that finds its event's
+// cursor past the end moves the pointer on and loads the next event. Every
+// pass either claims an item or advances the event, so the loop ends within
+// n_ev passes. Returns the item's first T3_1, or -1 when none is left.
+__device__ __noinline__ int t5_next_item(const Arena& A, int n_ev, int* cur) {
+    int t0 = -1;
+    if (lane_id() == 0) {
+        for (int pass = 0; pass <= n_ev; ++pass) {
+            if (cur[0] < 0) {
+                const int e = *reinterpret_cast<volatile const int*>(&A.counters[24]);
+                if (e >= n_ev) break;
+                cur[0] = e;
+                cur[1] = A.t5_evf[e];
+                cur[2] = cur[1] + A.t5_evb[e];
+                cur[3] = A.t5_evbase[e];
+                cur[4] = A.t5_evbase[e + 1];
+            }
+            const int k = atomicAdd(&A.t5_evc[cur[0]], 1);
+            if (k < cur[2]) {
+                t0 = k < cur[1] ? A.t5_items[cur[3] + k] : A.t5_items[cur[4] - 1 - (k - cur[1])];
+                break;
+            }
+            atomicMax(&A.counters[24], cur[0] + 1);
+            cur[0] = -1;
+        }
+    }
+    return __shfl_sync(kFull, t0, 0);
 }
 
 // T5 search (FP32 only): each warp takes work items from a shared cursor
@@ -820,15 +880,14 @@ __global__ void __launch_bounds__(kT5Warps * 32, 6) k_t5(Arena A, DevCfg c) {
     __shared__ T5Smem sm[kT5Warps];
     T5Smem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
-    const int n_front = A.counters[22], n_items = n_front + A.counters[23];
+    const int n_ev = A.bd->n_ev;
     const int stage = min(max(c.t5_stage, 1), kT5Stage);
     const int clen = t5_chunk_len(A);
+    if (lane == 0) S.cur[0] = -1;
+    __syncwarp();
     for (;;) {
-        int k = 0;
-        if (lane == 0) k = atomicAdd(&A.counters[24], 1);
-        k = __shfl_sync(kFull, k, 0);
-        if (k >= n_items) break;
-        const int t0 = k < n_front ? A.t5_items[k] : A.t5_items[A.t3_cap - 1 - (k - n_front)];
+        const int t0 = t5_next_item(A, n_ev, S.cur);
+        if (t0 < 0) break;
         const int i = A.t3_md[t0].x;
         const int t_end = min(t0 + clen, A.t3_off[i] + A.t3_cnt[i]);
         int cnt = 0;
@@ -970,8 +1029,9 @@ __global__ void k_t5_refine(Arena A, DevCfg c) {
     }
 }
 
-// Scoring features of every T3 of the batch (the optional learned triplet
-// selection): one thread per T3; the upper hits come from the input arrays.
+// Scoring features of every T3 of the batch, written out (the learned triplet
+// selection's training set; k_t3_score computes them in place for the
+// network): one thread per T3; the upper hits come from the input arrays.
 __global__ void k_t3_features(Arena A, DevCfg c) {
     pdl_begin();
     const int n = min(A.counters[2], A.t3_cap);
@@ -999,14 +1059,6 @@ __global__ void k_t3_features(Arena A, DevCfg c) {
         }
         t3_features(c, P, H, code, A.t3_feat + (size_t)48 * i);
     }
-}
-
-// Triplets the network keeps: the T5 and pT3 searches skip the others.
-__global__ void k_t3_mlp_select(Arena A, DevCfg c) {
-    pdl_begin();
-    const int n = min(A.counters[2], A.t3_cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        A.t3_ok[i] = A.t3_mlp[i] >= c.t3_threshold;
 }
 
 // Validity from the network score (the hand-set cut decision stays in t5_cut).

@@ -18,6 +18,7 @@
 #include <cstdint>
 
 #include "../../include/lst.h"
+#include "lst_kernels.cuh"
 #include "lst_mlp.cuh"
 
 namespace lst {
@@ -50,14 +51,145 @@ __device__ __forceinline__ void bfrag(const __nv_bfloat16* W, int n_in, int s, i
     b1 = *reinterpret_cast<const uint32_t*>(row + 8);
 }
 
-// Forward pass over n samples. scores[i] = sigmoid(z4); when save != nullptr
-// the BF16-rounded layer inputs x1, x2 (as float), h3 and the score are kept
-// for the backward pass.
-__global__ void __launch_bounds__(128) k_mlp_forward(MlpParams P, const float* __restrict__ X, int n,
-                                                     const int* n_dev, float* __restrict__ scores, MlpSaved save) {
-    pdl_begin();
-    __shared__ MlpSmem S;
-    if (n_dev) n = min(*n_dev, n);      // in the chain the candidate count lives on the device
+// One warp's 16 rows base .. base + 15 (rows >= n skipped) through every
+// layer: row r's features come from load(r, c) (two adjacent inputs c, c + 1
+// as a float2). scores[r] = sigmoid(z4); keep (optional) receives
+// scores[r] >= thr; save (optional) keeps the BF16-rounded layer inputs, h3 and
+// z4 for the backward pass. All 32 lanes must call.
+template <typename Load>
+__device__ __forceinline__ void mlp_rows16(const MlpSmem& S, Load load, int n, int base, float* __restrict__ scores,
+                                           MlpSaved save, uint8_t* keep, float thr) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int r0 = base + g, r1 = base + g + 8;
+    // layer 1: A fragments straight from the FP32 features
+    uint32_t a[3][4];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int c = 16 * s + 2 * t;
+        float2 v00 = r0 < n ? load(r0, c) : make_float2(0.f, 0.f);
+        float2 v10 = r1 < n ? load(r1, c) : make_float2(0.f, 0.f);
+        float2 v01 = r0 < n ? load(r0, c + 8) : make_float2(0.f, 0.f);
+        float2 v11 = r1 < n ? load(r1, c + 8) : make_float2(0.f, 0.f);
+        a[s][0] = pack_bf16(v00.x, v00.y);
+        a[s][1] = pack_bf16(v10.x, v10.y);
+        a[s][2] = pack_bf16(v01.x, v01.y);
+        a[s][3] = pack_bf16(v11.x, v11.y);
+    }
+    float h1[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float bb0 = S.b1[8 * j + 2 * t], bb1 = S.b1[8 * j + 2 * t + 1];
+        h1[j][0] = bb0; h1[j][1] = bb1; h1[j][2] = bb0; h1[j][3] = bb1;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            uint32_t b0, b1;
+            bfrag(S.w1, kIn, s, j, g, t, b0, b1);
+            mma_bf16(h1[j], a[s], b0, b1);
+        }
+    }
+    // ReLU, BF16, and the layer-2 A fragments from the layer-1 accumulators
+    uint32_t a2[4][4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        a2[s][0] = pack_bf16(fmaxf(h1[2 * s][0], 0.f), fmaxf(h1[2 * s][1], 0.f));
+        a2[s][1] = pack_bf16(fmaxf(h1[2 * s][2], 0.f), fmaxf(h1[2 * s][3], 0.f));
+        a2[s][2] = pack_bf16(fmaxf(h1[2 * s + 1][0], 0.f), fmaxf(h1[2 * s + 1][1], 0.f));
+        a2[s][3] = pack_bf16(fmaxf(h1[2 * s + 1][2], 0.f), fmaxf(h1[2 * s + 1][3], 0.f));
+    }
+    if (save.x1) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162*>(&a2[s][q]);
+                const int row = (q & 1) ? r1 : r0;
+                const int col = 16 * s + 8 * (q >> 1) + 2 * t;
+                if (row < n)
+                    *reinterpret_cast<float2*>(save.x1 + (size_t)row * kH1 + col) =
+                        make_float2(__bfloat162float(v.x), __bfloat162float(v.y));
+            }
+        }
+    }
+    float h2[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float bb0 = S.b2[8 * j + 2 * t], bb1 = S.b2[8 * j + 2 * t + 1];
+        h2[j][0] = bb0; h2[j][1] = bb1; h2[j][2] = bb0; h2[j][3] = bb1;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            uint32_t b0, b1;
+            bfrag(S.w2, kH1, s, j, g, t, b0, b1);
+            mma_bf16(h2[j], a2[s], b0, b1);
+        }
+    }
+    uint32_t a3[4][4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        a3[s][0] = pack_bf16(fmaxf(h2[2 * s][0], 0.f), fmaxf(h2[2 * s][1], 0.f));
+        a3[s][1] = pack_bf16(fmaxf(h2[2 * s][2], 0.f), fmaxf(h2[2 * s][3], 0.f));
+        a3[s][2] = pack_bf16(fmaxf(h2[2 * s + 1][0], 0.f), fmaxf(h2[2 * s + 1][1], 0.f));
+        a3[s][3] = pack_bf16(fmaxf(h2[2 * s + 1][2], 0.f), fmaxf(h2[2 * s + 1][3], 0.f));
+    }
+    if (save.x2) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162*>(&a3[s][q]);
+                const int row = (q & 1) ? r1 : r0;
+                const int col = 16 * s + 8 * (q >> 1) + 2 * t;
+                if (row < n)
+                    *reinterpret_cast<float2*>(save.x2 + (size_t)row * kH2 + col) =
+                        make_float2(__bfloat162float(v.x), __bfloat162float(v.y));
+            }
+        }
+    }
+    float h3[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float bb0 = S.b3[8 * j + 2 * t], bb1 = S.b3[8 * j + 2 * t + 1];
+        h3[j][0] = bb0; h3[j][1] = bb1; h3[j][2] = bb0; h3[j][3] = bb1;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            uint32_t b0, b1;
+            bfrag(S.w3, kH2, s, j, g, t, b0, b1);
+            mma_bf16(h3[j], a3[s], b0, b1);
+        }
+    }
+    // layer 4 (FP32): rows g and g+8, reduced over the 4 lanes of the group
+    float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = 8 * j + 2 * t;
+        const float p0 = fmaxf(h3[j][0], 0.f), p1 = fmaxf(h3[j][1], 0.f);
+        const float q0 = fmaxf(h3[j][2], 0.f), q1 = fmaxf(h3[j][3], 0.f);
+        z0 += p0 * S.w4[c] + p1 * S.w4[c + 1];
+        z1 += q0 * S.w4[c] + q1 * S.w4[c + 1];
+        if (save.h3) {
+            if (r0 < n) *reinterpret_cast<float2*>(save.h3 + (size_t)r0 * kH3 + c) = make_float2(p0, p1);
+            if (r1 < n) *reinterpret_cast<float2*>(save.h3 + (size_t)r1 * kH3 + c) = make_float2(q0, q1);
+        }
+    }
+    z0 += __shfl_xor_sync(0xffffffffu, z0, 1);
+    z0 += __shfl_xor_sync(0xffffffffu, z0, 2);
+    z1 += __shfl_xor_sync(0xffffffffu, z1, 1);
+    z1 += __shfl_xor_sync(0xffffffffu, z1, 2);
+    if (t == 0) {
+        const float s0 = 1.f / (1.f + expf(-(z0 + S.b4))), s1 = 1.f / (1.f + expf(-(z1 + S.b4)));
+        if (r0 < n) scores[r0] = s0;
+        if (r1 < n) scores[r1] = s1;
+        if (keep) {
+            if (r0 < n) keep[r0] = s0 >= thr;
+            if (r1 < n) keep[r1] = s1 >= thr;
+        }
+        if (save.z4) {
+            if (r0 < n) save.z4[r0] = z0 + S.b4;
+            if (r1 < n) save.z4[r1] = z1 + S.b4;
+        }
+    }
+}
+
+__device__ __forceinline__ void mlp_load_weights(MlpSmem& S, const MlpParams& P) {
     for (int i = threadIdx.x; i < kH1 * kIn; i += blockDim.x) S.w1[i] = P.w1_bf[i];
     for (int i = threadIdx.x; i < kH2 * kH1; i += blockDim.x) S.w2[i] = P.w2_bf[i];
     for (int i = threadIdx.x; i < kH3 * kH2; i += blockDim.x) S.w3[i] = P.w3_bf[i];
@@ -65,131 +197,71 @@ __global__ void __launch_bounds__(128) k_mlp_forward(MlpParams P, const float* _
     for (int i = threadIdx.x; i < kH3; i += blockDim.x) { S.b3[i] = P.b3[i]; S.w4[i] = P.w4[i]; }
     if (threadIdx.x == 0) S.b4 = P.b4[0];
     __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+}
+
+// Forward pass over n samples X [n][48]. scores[i] = sigmoid(z4); when save
+// != nullptr the BF16-rounded layer inputs x1, x2 (as float), h3 and the
+// score are kept for the backward pass.
+__global__ void __launch_bounds__(128) k_mlp_forward(MlpParams P, const float* __restrict__ X, int n,
+                                                     const int* n_dev, float* __restrict__ scores, MlpSaved save) {
+    pdl_begin();
+    __shared__ MlpSmem S;
+    if (n_dev) n = min(*n_dev, n);      // in the chain the candidate count lives on the device
+    mlp_load_weights(S, P);
     const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 16; base < n; base += warps * 16) {
-        const int r0 = base + g, r1 = base + g + 8;
-        // layer 1: A fragments straight from the FP32 features
-        uint32_t a[3][4];
+    auto load = [&](int r, int c) { return *reinterpret_cast<const float2*>(X + (size_t)r * kIn + c); };
+    for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 16; base < n; base += warps * 16)
+        mlp_rows16(S, load, n, base, scores, save, nullptr, 0.f);
+}
+
+// Learned triplet selection, fused: each warp computes the scoring features
+// of 32 T3s (one per lane) into a shared-memory tile, runs the network over
+// its two 16-row halves and writes the score and the keep flag (score >=
+// threshold) of each T3. The features never go to global memory.
+constexpr int kFeatPad = 52;          // tile row stride (floats): 16-byte rows, fewer bank conflicts
+__global__ void __launch_bounds__(128) k_t3_score(Arena A, DevCfg c, MlpParams P) {
+    pdl_begin();
+    __shared__ MlpSmem S;
+    __shared__ __align__(16) float F[4][32][kFeatPad];
+    mlp_load_weights(S, P);
+    const int n = min(A.counters[2], A.t3_cap);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const BatchDesc* B = A.bd;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int base = (blockIdx.x * (blockDim.x >> 5) + w) * 32; base < n; base += warps * 32) {
+        const int i = base + lane;
+        float* f = &F[w][lane][0];
+        if (i < n) {
+            const int4 q = A.t3_md[i];
+            const int m[3] = {q.x, q.y, q.z};
+            const int e = A.md_gmod[m[0]] / A.n_mod;
+            const int h0 = A.hit_off[e];
+            Pt<float> Pp[3], H[6];
+            int code[3];
 #pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            const int c = 16 * s + 2 * t;
-            float2 v00 = r0 < n ? *reinterpret_cast<const float2*>(X + (size_t)r0 * kIn + c) : make_float2(0.f, 0.f);
-            float2 v10 = r1 < n ? *reinterpret_cast<const float2*>(X + (size_t)r1 * kIn + c) : make_float2(0.f, 0.f);
-            float2 v01 = r0 < n ? *reinterpret_cast<const float2*>(X + (size_t)r0 * kIn + c + 8) : make_float2(0.f, 0.f);
-            float2 v11 = r1 < n ? *reinterpret_cast<const float2*>(X + (size_t)r1 * kIn + c + 8) : make_float2(0.f, 0.f);
-            a[s][0] = pack_bf16(v00.x, v00.y);
-            a[s][1] = pack_bf16(v10.x, v10.y);
-            a[s][2] = pack_bf16(v01.x, v01.y);
-            a[s][3] = pack_bf16(v11.x, v11.y);
-        }
-        float h1[8][4];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float bb0 = S.b1[8 * j + 2 * t], bb1 = S.b1[8 * j + 2 * t + 1];
-            h1[j][0] = bb0; h1[j][1] = bb1; h1[j][2] = bb0; h1[j][3] = bb1;
-#pragma unroll
-            for (int s = 0; s < 3; ++s) {
-                uint32_t b0, b1;
-                bfrag(S.w1, kIn, s, j, g, t, b0, b1);
-                mma_bf16(h1[j], a[s], b0, b1);
+            for (int j = 0; j < 3; ++j) {
+                Pp[j] = md_point<float>(A, m[j]);
+                H[2 * j] = Pp[j];
+                Pt<float> U = Pp[j];
+                const int hu = h0 + A.md_up[m[j]];
+                U.x = B->hx[hu];
+                U.y = B->hy[hu];
+                U.z = B->hz[hu];
+                U.r = sqrtf(U.x * U.x + U.y * U.y);
+                H[2 * j + 1] = U;
+                const int mod = A.md_gmod[m[j]] % A.n_mod;
+                code[j] = A.mod_layer[mod] + (A.mod[mod].w > 0.5f ? 6 : 0);
             }
+            t3_features(c, Pp, H, code, f);
         }
-        // ReLU, BF16, and the layer-2 A fragments from the layer-1 accumulators
-        uint32_t a2[4][4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            a2[s][0] = pack_bf16(fmaxf(h1[2 * s][0], 0.f), fmaxf(h1[2 * s][1], 0.f));
-            a2[s][1] = pack_bf16(fmaxf(h1[2 * s][2], 0.f), fmaxf(h1[2 * s][3], 0.f));
-            a2[s][2] = pack_bf16(fmaxf(h1[2 * s + 1][0], 0.f), fmaxf(h1[2 * s + 1][1], 0.f));
-            a2[s][3] = pack_bf16(fmaxf(h1[2 * s + 1][2], 0.f), fmaxf(h1[2 * s + 1][3], 0.f));
-        }
-        if (save.x1) {
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162*>(&a2[s][q]);
-                    const int row = (q & 1) ? r1 : r0;
-                    const int col = 16 * s + 8 * (q >> 1) + 2 * t;
-                    if (row < n)
-                        *reinterpret_cast<float2*>(save.x1 + (size_t)row * kH1 + col) =
-                            make_float2(__bfloat162float(v.x), __bfloat162float(v.y));
-                }
-            }
-        }
-        float h2[8][4];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float bb0 = S.b2[8 * j + 2 * t], bb1 = S.b2[8 * j + 2 * t + 1];
-            h2[j][0] = bb0; h2[j][1] = bb1; h2[j][2] = bb0; h2[j][3] = bb1;
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                uint32_t b0, b1;
-                bfrag(S.w2, kH1, s, j, g, t, b0, b1);
-                mma_bf16(h2[j], a2[s], b0, b1);
-            }
-        }
-        uint32_t a3[4][4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            a3[s][0] = pack_bf16(fmaxf(h2[2 * s][0], 0.f), fmaxf(h2[2 * s][1], 0.f));
-            a3[s][1] = pack_bf16(fmaxf(h2[2 * s][2], 0.f), fmaxf(h2[2 * s][3], 0.f));
-            a3[s][2] = pack_bf16(fmaxf(h2[2 * s + 1][0], 0.f), fmaxf(h2[2 * s + 1][1], 0.f));
-            a3[s][3] = pack_bf16(fmaxf(h2[2 * s + 1][2], 0.f), fmaxf(h2[2 * s + 1][3], 0.f));
-        }
-        if (save.x2) {
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162*>(&a3[s][q]);
-                    const int row = (q & 1) ? r1 : r0;
-                    const int col = 16 * s + 8 * (q >> 1) + 2 * t;
-                    if (row < n)
-                        *reinterpret_cast<float2*>(save.x2 + (size_t)row * kH2 + col) =
-                            make_float2(__bfloat162float(v.x), __bfloat162float(v.y));
-                }
-            }
-        }
-        float h3[4][4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float bb0 = S.b3[8 * j + 2 * t], bb1 = S.b3[8 * j + 2 * t + 1];
-            h3[j][0] = bb0; h3[j][1] = bb1; h3[j][2] = bb0; h3[j][3] = bb1;
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                uint32_t b0, b1;
-                bfrag(S.w3, kH2, s, j, g, t, b0, b1);
-                mma_bf16(h3[j], a3[s], b0, b1);
-            }
-        }
-        // layer 4 (FP32): rows g and g+8, reduced over the 4 lanes of the group
-        float z0 = 0.f, z1 = 0.f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = 8 * j + 2 * t;
-            const float p0 = fmaxf(h3[j][0], 0.f), p1 = fmaxf(h3[j][1], 0.f);
-            const float q0 = fmaxf(h3[j][2], 0.f), q1 = fmaxf(h3[j][3], 0.f);
-            z0 += p0 * S.w4[c] + p1 * S.w4[c + 1];
-            z1 += q0 * S.w4[c] + q1 * S.w4[c + 1];
-            if (save.h3) {
-                if (r0 < n) *reinterpret_cast<float2*>(save.h3 + (size_t)r0 * kH3 + c) = make_float2(p0, p1);
-                if (r1 < n) *reinterpret_cast<float2*>(save.h3 + (size_t)r1 * kH3 + c) = make_float2(q0, q1);
-            }
-        }
-        z0 += __shfl_xor_sync(0xffffffffu, z0, 1);
-        z0 += __shfl_xor_sync(0xffffffffu, z0, 2);
-        z1 += __shfl_xor_sync(0xffffffffu, z1, 1);
-        z1 += __shfl_xor_sync(0xffffffffu, z1, 2);
-        if (t == 0) {
-            if (r0 < n) scores[r0] = 1.f / (1.f + expf(-(z0 + S.b4)));
-            if (r1 < n) scores[r1] = 1.f / (1.f + expf(-(z1 + S.b4)));
-            if (save.z4) {
-                if (r0 < n) save.z4[r0] = z0 + S.b4;
-                if (r1 < n) save.z4[r1] = z1 + S.b4;
-            }
-        }
+        __syncwarp();
+        const float* tile = &F[w][0][0];
+        auto load = [&](int r, int col) {
+            return *reinterpret_cast<const float2*>(tile + (size_t)(r - base) * kFeatPad + col);
+        };
+        mlp_rows16(S, load, n, base, A.t3_mlp, MlpSaved{}, A.t3_ok, c.t3_threshold);
+        mlp_rows16(S, load, n, base + 16, A.t3_mlp, MlpSaved{}, A.t3_ok, c.t3_threshold);
+        __syncwarp();
     }
 }
 

@@ -134,7 +134,7 @@ __device__ __forceinline__ void pt_enumerate(const Arena& A, const DevCfg& c, Pt
         }
         for_each_flat(oo, on, S.pre2, S.off2, [&](bool valid, int, int obj) {
             bool pass = false;
-            if (valid && (NT == 3 ? (!A.t3_sel || A.t3_ok[obj]) : A.t5_valid[obj] != 0)) {
+            if (valid && (NT == 3 || A.t5_valid[obj])) {
                 const float2 ks = NT == 5 ? A.t5_ks[obj] : t3_ks_search(A, obj);
                 const float kt = ks.x, st = ks.y;
                 float thr = nk * fast_sqrtf(sp * sp + st * st);

@@ -38,7 +38,7 @@ struct Buffer {
 // `tunable` stages are grid-stride over their units, so any grid is valid.
 enum LaunchId {
     L_RESET, L_BIN_COUNT, L_BIN_SCAN, L_BIN_SCATTER, L_BIN_SORT, L_MD_PLAN, L_MD, L_MD_WRITE, L_LS, L_T3,
-    L_T3_FEAT, L_T3_MLP, L_T3_SELECT, L_T5_PLAN, L_T5, L_T5_GATHER, L_T5_REFINE,
+    L_T3_FEAT, L_T3_SCORE, L_T5_PLAN, L_T5, L_T5_GATHER, L_T5_REFINE,
     L_T5_MLP, L_T5_MLP_SELECT, L_PLS, L_PT_PLAN, L_PT5, L_PT5_REFINE, L_PT3, L_PT3_REFINE, L_CLEAN_KEYS, L_CLEAN_KEEP,
     L_CLEAN_PT5, L_CLEAN_PT3_CROSS, L_CLEAN_PT3_MARK, L_CLEAN_T5, L_CLEAN_PLS, L_TC_PACK, kNumLaunch
 };
@@ -63,8 +63,7 @@ const LaunchInfo kLaunch[kNumLaunch] = {
     {"ls", 8, kLsWarps * 32, true, false},
     {"t3", 8, kT3Warps * 32, true, false},
     {"t3_features", 4, 128, true, true},
-    {"t3_mlp", 4, 128, true, false},
-    {"t3_mlp_select", 4, 256, true, true},
+    {"t3_score", 4, 128, true, false},
     {"t5_plan", 4, 256, true, true},
     {"t5", 6, kT5Warps * 32, true, false},
     {"t5_gather", 4, 128, true, false},
@@ -139,7 +138,8 @@ struct lst_ctx {
     bool use_graph = true;
     const lst_mlp* mlp = nullptr;     // network deciding T5 validity (NULL: the hand-set cuts)
     const lst_mlp* mlp3 = nullptr;    // network pruning triplets (NULL: every T3 that passes the cuts)
-    bool t3_features = false;         // compute the T3 scoring features (network attached or capture)
+    bool t3_features = false;         // the T3 buffers exist (network attached or features captured)
+    bool t3_capture = false;          // write the T3 scoring features out (training)
     void* t3_mem = nullptr;           // features, scores and flags of the learned triplet selection
     BatchDesc* d_bd = nullptr;        // device batch descriptor
     BatchDesc* h_bd = nullptr;        // pinned staging of the descriptor
@@ -253,7 +253,8 @@ lst_status lst_capacity_default(lst_capacity* c, int32_t max_events) {
 lst_status lst_create(lst_ctx** out, const lst_config* cfg, const lst_capacity* cap, int32_t device) {
     if (!out) return LST_ERR_ARG;
     *out = nullptr;
-    if (!cfg || !cap || cap->max_events <= 0 || cap->max_hits < 0 || cap->max_seeds < 0) return LST_ERR_ARG;
+    if (!cfg || !cap || cap->max_events <= 0 || cap->max_events > 8192 || cap->max_hits < 0 || cap->max_seeds < 0)
+        return LST_ERR_ARG;
     lst_ctx* c = new (std::nothrow) lst_ctx();
     if (!c) return LST_ERR_OOM;
     c->device = device;
@@ -375,6 +376,10 @@ static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n
     A.t5_feat = b.take<float>(48 * T5); A.t5_mlp = b.take<float>(T5);
     A.t5_off = b.take<int>(MD); A.t5_cnt = b.take<int>(MD);
     A.t5_ks = b.take<float2>(T5);
+    A.t5_evf = b.take<int>(E);
+    A.t5_evb = b.take<int>(E);
+    A.t5_evc = b.take<int>(E);
+    A.t5_evbase = b.take<int>(E + 1);
     A.t5_items = b.take<int>(T3); A.t5_chunk_off = b.take<int>(T3); A.t5_chunk_cnt = b.take<int>(T3);
     A.t5_tmp = b.take<int2>(T5);
     A.pls_pass = b.take<int>(S); A.pls_sb = b.take<int>(S);
@@ -552,12 +557,6 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile, cudaStream_
     LAUNCH(L_MD_WRITE, run_k(k_md_write, GB(L_MD_WRITE), 0, st, pdl, A, dc));
     LAUNCH(L_LS, run_k(k_ls, GB(L_LS), 0, st, pdl, A, dc));
     LAUNCH(L_T3, run_k(k_t3, GB(L_T3), 0, st, pdl, A, dc));
-    if (c->t3_features) LAUNCH(L_T3_FEAT, run_k(k_t3_features, GB(L_T3_FEAT), 0, st, pdl, A, dc));
-    if (c->mlp3) {
-        LAUNCH(L_T3_MLP, run_k(k_mlp_forward, GB(L_T3_MLP), 0, st, pdl, lst_mlp_device_params(c->mlp3), A.t3_feat,
-                               A.t3_cap, A.counters + 2, A.t3_mlp, MlpSaved{}));
-        LAUNCH(L_T3_SELECT, run_k(k_t3_mlp_select, GB(L_T3_SELECT), 0, st, pdl, A, dc));
-    }
     if (side) {
         cudaEventRecord(c->ev_t3, st);
         cudaStreamWaitEvent(side, c->ev_t3, 0);
@@ -565,7 +564,12 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile, cudaStream_
         LAUNCH(L_PT3_REFINE, run_k(k_pt3_refine, GB(L_PT3_REFINE), 0, side, pdl, A, dc));
         cudaEventRecord(c->ev_pt3, side);
     }
-    LAUNCH(L_T5_PLAN, run_k(k_t5_plan, GB(L_T5_PLAN), 0, st, pdl, A));
+    // the learned triplet selection gates the T5 search only, so the pT3 branch starts at once
+    if (c->t3_capture) LAUNCH(L_T3_FEAT, run_k(k_t3_features, GB(L_T3_FEAT), 0, st, side ? false : pdl, A, dc));
+    if (c->mlp3)
+        LAUNCH(L_T3_SCORE, run_k(k_t3_score, GB(L_T3_SCORE), 0, st, side && !c->t3_capture ? false : pdl, A, dc,
+                                 lst_mlp_device_params(c->mlp3)));
+    LAUNCH(L_T5_PLAN, run_k(k_t5_plan, GB(L_T5_PLAN), t5_plan_smem_bytes(A.max_events), st, pdl, A));
     LAUNCH(L_T5, run_k(k_t5, GB(L_T5), 0, st, pdl, A, dc));
     LAUNCH(L_T5_GATHER, run_k(k_t5_gather, GB(L_T5_GATHER), 0, st, pdl, A));
     LAUNCH(L_T5_REFINE, run_k(k_t5_refine, GB(L_T5_REFINE), 0, st, pdl, A, dc));
@@ -832,8 +836,7 @@ static const void* launch_fn(int id) {
         case L_T5_GATHER: return (const void*)k_t5_gather;
         case L_T5_REFINE: return (const void*)k_t5_refine;
         case L_T3_FEAT: return (const void*)k_t3_features;
-        case L_T3_MLP: return (const void*)k_mlp_forward;
-        case L_T3_SELECT: return (const void*)k_t3_mlp_select;
+        case L_T3_SCORE: return (const void*)k_t3_score;
         case L_T5_MLP: return (const void*)k_mlp_forward;
         case L_T5_MLP_SELECT: return (const void*)k_t5_mlp_select;
         case L_PLS: return (const void*)k_pls;
@@ -1079,7 +1082,8 @@ lst_status lst_set_t3_selection(lst_ctx* c, const lst_mlp* mlp, float threshold,
         c->A.t3_ok = reinterpret_cast<uint8_t*>(p + T3 * 49 * sizeof(float));
     }
     c->mlp3 = mlp;
-    c->t3_features = feat;
+    c->t3_features = c->t3_features || feat;
+    c->t3_capture = capture_features != 0;
     c->A.t3_sel = mlp ? 1 : 0;
     c->dc.t3_threshold = threshold;
     if (c->graph) {
@@ -1109,7 +1113,7 @@ lst_status lst_get_t3_candidates(lst_ctx* c, lst_event_id id, int32_t capacity, 
     const int k = std::min((int)rows.size(), (int)capacity);
     if (n_out) *n_out = (int)rows.size();
     if (features && k) {
-        if (!c->t3_features) return LST_ERR_ARG;
+        if (!c->t3_capture) return LST_ERR_ARG;
         std::vector<float> f;
         FETCH(f, A.t3_feat, (size_t)48 * n);
         for (int r = 0; r < k; ++r) std::memcpy(features + 48 * (size_t)r, f.data() + 48 * (size_t)rows[r], 48 * 4);

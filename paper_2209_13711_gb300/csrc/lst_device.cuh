@@ -183,6 +183,10 @@ struct Arena {
     float* t5_feat;               // [t5_cap][48] scoring features
     float* t5_mlp;                // network score
     float2* t5_ks;                // FP32 {curvature, sigma} of each T5 (the pT5 search's prefilter)
+    int* t5_evf;                  // [n_ev] T5 work items at the front of each event's region (split units)
+    int* t5_evb;                  // [n_ev] ... at its back (single-chunk units)
+    int* t5_evc;                  // [n_ev] claim cursor of each event's items
+    int* t5_evbase;               // [n_ev + 1] first item slot of each event's region
     int* t5_off;                  // [md_cap] by inner MD
     int* t5_cnt;
     // T5 search work items: chunks of 8, 16 or 32 T3_1 of one inner MD,

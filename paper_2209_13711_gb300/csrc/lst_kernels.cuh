@@ -2,6 +2,7 @@
 #pragma once
 
 #include "lst_device.cuh"
+#include "lst_mlp.cuh"
 
 namespace lst {
 
@@ -48,8 +49,9 @@ __global__ void k_pt3(Arena A, DevCfg c);
 __global__ void k_pt5_refine(Arena A, DevCfg c);
 __global__ void k_pt3_refine(Arena A, DevCfg c);
 __global__ void k_clean_keys(Arena A, int pass);
+size_t t5_plan_smem_bytes(int max_events);
 __global__ void k_t3_features(Arena A, DevCfg c);
-__global__ void k_t3_mlp_select(Arena A, DevCfg c);
+__global__ void k_t3_score(Arena A, DevCfg c, MlpParams P);
 __global__ void k_clean_pt5(Arena A);
 __global__ void k_clean_pt3_cross(Arena A, DevCfg c);
 __global__ void k_clean_pt3_mark(Arena A);

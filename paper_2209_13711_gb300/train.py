@@ -68,6 +68,48 @@ def collect(ctx, events, batch=16, stream=None, device=False):
     return dict(X=Xc, y=cat(y), cut=cat(cut), particle=cat(part), event=cat(ev_idx))
 
 
+def collect_t3(ctx, events, batch=8, stream=None, device=True, max_per_event=None, seed=0):
+    """Features and labels of the T3s of some events (the learned triplet selection's training set): label 1
+    when all six hits come from one generated particle. max_per_event keeps a random subset of each event's
+    T3s (a PU200 event holds about 4e5)."""
+    import itertools
+    rng = np.random.default_rng(seed)
+    X, y = [], []
+    it = iter(events)
+    while True:
+        chunk = list(itertools.islice(it, batch))
+        if not chunk:
+            break
+        ctx.run(chunk, stream=stream)
+        for j, ev in enumerate(chunk):
+            c = ctx.t3_candidates(j)
+            p = ev.pid[c["hits"]]
+            true = (p[:, 0] >= 0) & np.all(p == p[:, :1], axis=1)
+            f = c["features"]
+            if max_per_event and len(true) > max_per_event:
+                k = rng.choice(len(true), max_per_event, replace=False)
+                f, true = f[k], true[k]
+            if device:
+                import torch
+                X.append(torch.from_numpy(f).cuda())
+            else:
+                X.append(f)
+            y.append(true.astype(np.float32))
+    if device:
+        import torch
+        return dict(X=torch.cat(X), y=np.concatenate(y))
+    return dict(X=np.concatenate(X), y=np.concatenate(y))
+
+
+def threshold_keeping(scores, y, keep=0.99):
+    """Largest threshold that keeps at least `keep` of the true candidates."""
+    s = np.sort(np.asarray(scores)[np.asarray(y) > 0.5])
+    if len(s) == 0:
+        return 0.0
+    k = int(np.floor((1.0 - keep) * len(s)))
+    return float(s[k]) if k < len(s) else 0.0
+
+
 def save_checkpoint(path, mlp, epoch, hist):
     """The network's whole training state (parameters, Adam moments and step) after `epoch` epochs."""
     st = mlp.state()

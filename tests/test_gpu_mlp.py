@@ -173,3 +173,52 @@ def test_resume_from_checkpoint_matches_uninterrupted_training(tmp_path):
     reset = P.Mlp(max_batch=4096, params=np.load(ck)["params"])
     T.train(reset, Xd, y, epochs=2, seed=5, start_epoch=1)
     assert not np.array_equal(reset.params(), want["params"])
+
+
+def test_t3_features_match_the_oracle(geom_full, maps_full):
+    """FP32 triplet features on the device against the FP64 oracle's, for a sample of an event's T3s."""
+    from oracle import oracle as O
+    ev = E.pileup_event(60, 8, geom_full)
+    ctx = make_context(geom_full, maps_full, max_events=1)
+    ctx.set_t3_selection(None, capture_features=True)
+    ctx.run([ev])
+    c = ctx.t3_candidates(0)
+    assert len(c["hits"]) > 10000 and c["kept"].all()
+    S = O.Setup(geom_full.module_table(), maps_full, DEFAULT_CUTS, ev)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(len(c["hits"]), 400, replace=False):
+        want = S.t3_features(c["hits"][i])
+        got = c["features"][i]
+        assert np.all(np.abs(got - want) <= 0.02 + 2e-3 * np.abs(want)), (i, np.nonzero(
+            np.abs(got - want) > 0.02 + 2e-3 * np.abs(want))[0])
+    ctx.close()
+
+
+def test_t3_network_prunes_triplets_and_keeps_the_track_candidates(geom_full, maps_full):
+    """A network trained on 6 PU200 events' triplets, at the threshold that keeps 99 % of true T3s, prunes
+    most of the fake ones; the T5 searches then see fewer candidates and the track-candidate efficiency on
+    other events stays within 1 % of the hand-set cuts' alone."""
+    import paper_2209_13711_gb300 as P
+    from paper_2209_13711_gb300 import metrics as MT
+    from paper_2209_13711_gb300 import train as T
+    ctx = make_context(geom_full, maps_full, max_events=2)
+    ctx.set_t3_selection(None, capture_features=True)
+    tr = T.collect_t3(ctx, [E.pu200_event(40000 + i, geom_full) for i in range(6)], batch=2, max_per_event=150000)
+    va = T.collect_t3(ctx, [E.pu200_event(41000 + i, geom_full) for i in range(2)], batch=2, device=False)
+    m = P.Mlp(max_batch=4096, params=init_params(4))
+    T.train(m, tr["X"], tr["y"], epochs=3)
+    s = T.scores_of(m, va["X"])
+    thr = T.threshold_keeping(s, va["y"], 0.99)
+    fake = va["y"] < 0.5
+    pruned = float(np.mean(s[fake] < thr))
+    assert pruned > 0.5, pruned
+    evs = [E.pu200_event(42000 + i, geom_full) for i in range(2)]
+    res = {}
+    for mode in ("cuts", "network"):
+        ctx.set_t3_selection(m if mode == "network" else None, threshold=thr)
+        ctx.run(evs)
+        rates = [MT.rates(ctx.track_candidates(e), ev.pid, ev.seed_pid, ev.tracks) for e, ev in enumerate(evs)]
+        res[mode] = (MT.combine(rates), int(ctx.counters()[21]))
+    assert res["network"][0]["efficiency"] >= res["cuts"][0]["efficiency"] - 0.01
+    assert res["network"][1] < 0.8 * res["cuts"][1]           # T5 search survivors
+    ctx.close()
