@@ -1035,29 +1035,15 @@ __global__ void k_t5_refine(Arena A, DevCfg c) {
 __global__ void k_t3_features(Arena A, DevCfg c) {
     pdl_begin();
     const int n = min(A.counters[2], A.t3_cap);
-    const BatchDesc* B = A.bd;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int4 q = A.t3_md[i];
-        const int m[3] = {q.x, q.y, q.z};
-        const int e = A.md_gmod[m[0]] / A.n_mod;
-        const int h0 = A.hit_off[e];
         Pt<float> P[3], H[6];
         int code[3];
+        t3_feature_inputs(A, i, P, H, code);
+        float v[48];
+        t3_features(c, P, H, code, v);
+        float4* f = reinterpret_cast<float4*>(A.t3_feat + (size_t)48 * i);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            P[j] = md_point<float>(A, m[j]);
-            H[2 * j] = P[j];
-            Pt<float> U = P[j];
-            const int hu = h0 + A.md_up[m[j]];
-            U.x = B->hx[hu];
-            U.y = B->hy[hu];
-            U.z = B->hz[hu];
-            U.r = sqrtf(U.x * U.x + U.y * U.y);
-            H[2 * j + 1] = U;
-            const int mod = A.md_gmod[m[j]] % A.n_mod;
-            code[j] = A.mod_layer[mod] + (A.mod[mod].w > 0.5f ? 6 : 0);
-        }
-        t3_features(c, P, H, code, A.t3_feat + (size_t)48 * i);
+        for (int j = 0; j < 12; ++j) f[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
     }
 }
 

@@ -215,49 +215,40 @@ __global__ void __launch_bounds__(128) k_mlp_forward(MlpParams P, const float* _
 }
 
 // Learned triplet selection, fused: each warp computes the scoring features
-// of 32 T3s (one per lane) into a shared-memory tile, runs the network over
-// its two 16-row halves and writes the score and the keep flag (score >=
-// threshold) of each T3. The features never go to global memory.
-constexpr int kFeatPad = 52;          // tile row stride (floats): 16-byte rows, fewer bank conflicts
-__global__ void __launch_bounds__(128) k_t3_score(Arena A, DevCfg c, MlpParams P) {
+// of 32 T3s (one per lane) into a BF16 shared-memory tile, runs the network
+// over its two 16-row halves and writes the score and the keep flag (score >=
+// threshold) of each T3. The features never go to global memory. The tile
+// holds the BF16 values the first layer's fragments take anyway, so the scores
+// equal those of an FP32 tile; at half its shared memory, four blocks of eight
+// warps fit on an SM.
+constexpr int kScoreWarps = 8;
+constexpr int kTileStride = 56;       // BF16 per tile row: 112-byte rows, conflict-free fragment loads
+__global__ void __launch_bounds__(kScoreWarps * 32, 4) k_t3_score(Arena A, DevCfg c, MlpParams P) {
     pdl_begin();
     __shared__ MlpSmem S;
-    __shared__ __align__(16) float F[4][32][kFeatPad];
+    __shared__ __align__(16) __nv_bfloat16 F[kScoreWarps][32][kTileStride];
     mlp_load_weights(S, P);
     const int n = min(A.counters[2], A.t3_cap);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const BatchDesc* B = A.bd;
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int base = (blockIdx.x * (blockDim.x >> 5) + w) * 32; base < n; base += warps * 32) {
         const int i = base + lane;
-        float* f = &F[w][lane][0];
         if (i < n) {
-            const int4 q = A.t3_md[i];
-            const int m[3] = {q.x, q.y, q.z};
-            const int e = A.md_gmod[m[0]] / A.n_mod;
-            const int h0 = A.hit_off[e];
             Pt<float> Pp[3], H[6];
             int code[3];
+            t3_feature_inputs(A, i, Pp, H, code);
+            float v[48];
+            t3_features(c, Pp, H, code, v);
+            uint4* f = reinterpret_cast<uint4*>(&F[w][lane][0]);
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                Pp[j] = md_point<float>(A, m[j]);
-                H[2 * j] = Pp[j];
-                Pt<float> U = Pp[j];
-                const int hu = h0 + A.md_up[m[j]];
-                U.x = B->hx[hu];
-                U.y = B->hy[hu];
-                U.z = B->hz[hu];
-                U.r = sqrtf(U.x * U.x + U.y * U.y);
-                H[2 * j + 1] = U;
-                const int mod = A.md_gmod[m[j]] % A.n_mod;
-                code[j] = A.mod_layer[mod] + (A.mod[mod].w > 0.5f ? 6 : 0);
-            }
-            t3_features(c, Pp, H, code, f);
+            for (int j = 0; j < 6; ++j)
+                f[j] = make_uint4(pack_bf16(v[8 * j], v[8 * j + 1]), pack_bf16(v[8 * j + 2], v[8 * j + 3]),
+                                  pack_bf16(v[8 * j + 4], v[8 * j + 5]), pack_bf16(v[8 * j + 6], v[8 * j + 7]));
         }
         __syncwarp();
-        const float* tile = &F[w][0][0];
+        const __nv_bfloat16* tile = &F[w][0][0];
         auto load = [&](int r, int col) {
-            return *reinterpret_cast<const float2*>(tile + (size_t)(r - base) * kFeatPad + col);
+            return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(tile + (r - base) * kTileStride + col));
         };
         mlp_rows16(S, load, n, base, A.t3_mlp, MlpSaved{}, A.t3_ok, c.t3_threshold);
         mlp_rows16(S, load, n, base + 16, A.t3_mlp, MlpSaved{}, A.t3_ok, c.t3_threshold);

@@ -63,7 +63,7 @@ const LaunchInfo kLaunch[kNumLaunch] = {
     {"ls", 8, kLsWarps * 32, true, false},
     {"t3", 8, kT3Warps * 32, true, false},
     {"t3_features", 4, 128, true, true},
-    {"t3_score", 4, 128, true, false},
+    {"t3_score", 4, 256, true, false},
     {"t5_plan", 4, 256, true, true},
     {"t5", 6, kT5Warps * 32, true, false},
     {"t5_gather", 4, 128, true, false},

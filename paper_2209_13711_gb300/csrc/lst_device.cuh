@@ -1014,11 +1014,10 @@ template <int N> __device__ inline FitF fit_f32(const Pt<float>* P) {
 // f[28..29] log(1 + chi2_rphi), log(1 + chi2_rz), f[30] 10 x beta, f[32] eta,
 // f[33..35] layer code / 11; every other slot 0.
 __device__ inline void t3_features(const DevCfg& c, const Pt<float>* P, const Pt<float>* H, const int* code,
-                                   float* f) {
+                                   float (&v)[48]) {
     const FitF F = fit_f32<3>(P);
     const Tri<float> t = tri(P[0], P[1], P[2]);
     const float ka = fabsf(F.kappa);
-    float v[48];
 #pragma unroll
     for (int j = 0; j < 48; ++j) v[j] = 0.f;
 #pragma unroll
@@ -1050,8 +1049,29 @@ __device__ inline void t3_features(const DevCfg& c, const Pt<float>* P, const Pt
     v[32] = asinhf(F.t);
 #pragma unroll
     for (int j = 0; j < 3; ++j) v[33 + j] = code[j] / 11.f;
+}
+
+// Inputs of the scoring features of T3 i: anchors P (the MDs' lower hits),
+// hits H (lower, upper of each MD) and layer codes (layer, +6 on a 2S module).
+__device__ inline void t3_feature_inputs(const Arena& A, int i, Pt<float>* P, Pt<float>* H, int* code) {
+    const int4 q = A.t3_md[i];
+    const int m[3] = {q.x, q.y, q.z};
+    const int h0 = A.hit_off[A.md_gmod[m[0]] / A.n_mod];
+    const BatchDesc* B = A.bd;
 #pragma unroll
-    for (int j = 0; j < 48; j += 4) *reinterpret_cast<float4*>(f + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    for (int j = 0; j < 3; ++j) {
+        P[j] = md_point<float>(A, m[j]);
+        H[2 * j] = P[j];
+        Pt<float> U = P[j];
+        const int hu = h0 + A.md_up[m[j]];
+        U.x = B->hx[hu];
+        U.y = B->hy[hu];
+        U.z = B->hz[hu];
+        U.r = sqrtf(U.x * U.x + U.y * U.y);
+        H[2 * j + 1] = U;
+        const int mod = A.md_gmod[m[j]] % A.n_mod;
+        code[j] = A.mod_layer[mod] + (A.mod[mod].w > 0.5f ? 6 : 0);
+    }
 }
 
 // T5 on anchors P[0..4]; outputs in double

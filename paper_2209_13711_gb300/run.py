@@ -29,6 +29,8 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--profile", action="store_true")
+    ap.add_argument("--t3-net", default=None, help="learned triplet selection saved by train --kind t3")
+    ap.add_argument("--t5-net", default=None, help="network-scored T5 selection saved by train --kind t5")
     args = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
@@ -49,6 +51,16 @@ def main(argv=None):
         else:
             evs.append(E.pileup_event(args.pileup, args.seed * 1000 + i, geom))
     ctx = L.Context(geom.module_table(), maps, cfg=DEFAULT_CUTS, capacity=L.default_capacity(args.events))
+    nets = []
+    if args.t3_net:
+        z = np.load(args.t3_net)
+        nets.append(L.Mlp(params=z["params"]))
+        ctx.set_t3_selection(nets[-1], threshold=float(z["threshold"]))
+    if args.t5_net:
+        z = np.load(args.t5_net)
+        nets.append(L.Mlp(params=z["params"]))
+        ctx.set_t5_selection(nets[-1], threshold=float(z["threshold"]),
+                             prefilter_scale=float(z["prefilter_scale"]) if "prefilter_scale" in z.files else 1.0)
     b = L.pack_events(evs)
     bd = {k: (torch.from_numpy(v).cuda() if k not in ("hit_off", "seed_off") else v) for k, v in b.items()}
     st = torch.cuda.current_stream()
@@ -75,6 +87,8 @@ def main(argv=None):
         out["stage_ms"] = {n: round(t, 4) for n, t in ctx.kernel_times()}
         ctx.set_profiling(False)
     ctx.close()
+    for m in nets:
+        m.close()
     print(json.dumps(out))
 
 

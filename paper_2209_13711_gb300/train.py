@@ -7,7 +7,15 @@ The network is trained with the library's own forward, backward and Adam
 kernels. Evaluation compares, on separate events, the hand-set cut selection
 with the network at the threshold that matches the cut efficiency.
 
-    python -m paper_2209_13711_gb300.train --train-events 100 --eval-events 8 --out t5_mlp.npy
+    python -m paper_2209_13711_gb300.train --train-events 100 --eval-events 8 --out t5_mlp.npz
+    python -m paper_2209_13711_gb300.train --kind t3 --train-events 16 --eval-events 4 --out t3_mlp.npz
+
+A T5 file holds the parameters and the threshold that matches the cut
+efficiency (`run --t5-net` attaches it). --kind t3 trains the learned triplet
+selection instead: every T3 of the training events is a sample (label 1 when
+its six hits come from one particle), and the saved file holds the parameters
+and the threshold that keeps 99 % of the true T3s of the evaluation events
+(`run --t3-net` attaches it).
 """
 from __future__ import annotations
 
@@ -193,8 +201,36 @@ def evaluate(mlp, data):
     return dict(cut=cut, network=net, threshold=thr)
 
 
+def main_t3(args):
+    """Train and save the learned triplet selection (parameters and threshold)."""
+    from synth import events as E, geometry as G, maps as M
+    from synth.config import DEFAULT_CUTS
+    from synth.mlp_init import init_params
+    geom = G.make_geometry(barrel_only=False)
+    maps = M.load_maps(geom)
+    ctx = L.Context(geom.module_table(), maps, cfg=DEFAULT_CUTS, capacity=L.default_capacity(4))
+    ctx.set_t3_selection(None, capture_features=True)
+    t0 = time.time()
+    tr = collect_t3(ctx, (E.pu200_event(43000 + i, geom) for i in range(args.train_events)), batch=4,
+                    max_per_event=200000)
+    va = collect_t3(ctx, [E.pu200_event(44000 + i, geom) for i in range(args.eval_events)], batch=4, device=False)
+    ctx.close()
+    mlp = L.Mlp(max_batch=4096, params=init_params(args.seed))
+    hist = train(mlp, tr["X"], tr["y"], epochs=args.epochs, seed=args.seed)
+    s = scores_of(mlp, va["X"])
+    thr = threshold_keeping(s, va["y"], args.keep)
+    fake = va["y"] < 0.5
+    np.savez(args.out, params=mlp.params(), threshold=thr)
+    mlp.close()
+    print(json.dumps(dict(samples_train=int(len(tr["y"])), loss_history=hist, threshold=thr,
+                          true_kept=float(np.mean(s[~fake] >= thr)), fake_pruned=float(np.mean(s[fake] < thr)),
+                          seconds=round(time.time() - t0, 1))))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
+    ap.add_argument("--kind", choices=("t5", "t3"), default="t5")
+    ap.add_argument("--keep", type=float, default=0.99, help="t3: fraction of true T3s the threshold keeps")
     ap.add_argument("--train-events", type=int, default=100)
     ap.add_argument("--eval-events", type=int, default=8)
     ap.add_argument("--epochs", type=int, default=4)
@@ -205,6 +241,8 @@ def main(argv=None):
     ap.add_argument("--resume", action="store_true", help="continue from --checkpoint")
     args = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    if args.kind == "t3":
+        return main_t3(args)
     from synth import events as E, geometry as G, maps as M
     from synth.config import DEFAULT_CUTS
     from synth.mlp_init import init_params
@@ -229,7 +267,8 @@ def main(argv=None):
     res["loss_history"] = hist
     res["train_events"], res["eval_events"] = args.train_events, args.eval_events
     res["samples_train"], res["samples_eval"] = int(len(tr["y"])), int(len(va["y"]))
-    np.save(args.out, mlp.params())
+    np.savez(args.out, params=mlp.params(), threshold=res["threshold"], prefilter_scale=args.prefilter_scale)
+    mlp.close()
     print(json.dumps(res))
 
 
