@@ -337,6 +337,7 @@ def run_ours(args):
     out["batched_pu200"] = measure_batched_pu200(P, E, geom, maps, DEFAULT_CUTS, flush, st,
                                                  steps=max(2, min(args.steps, 5)), events=events)
     out["compact_storage"] = measure_compact(P, geom, maps, DEFAULT_CUTS, flush, st, events)
+    out["fit_precision"] = measure_fit_precision(P, geom, maps, DEFAULT_CUTS, flush, st, events)
     out["mlp"] = measure_mlp(P, E, geom, maps, DEFAULT_CUTS, flush, st, dev)
     out["mlp_t3"] = measure_mlp_t3(P, E, geom, maps, DEFAULT_CUTS, flush, st, dev, events)
     out["serving"] = measure_serving(E, geom, maps, DEFAULT_CUTS)
@@ -552,52 +553,83 @@ def measure_d0_scan(P, E, geom, maps, cuts, st, n_events=32, n_muons=40):
     return out
 
 
+def _time_modes(P, geom, maps, cuts, flush, st, evs, modes, touched, reps=3):
+    """Device time per batch of `evs` and the stage times of `touched` for each context set-up in `modes`
+    (name -> function of the context), default launch shapes, L2 flushed before every run."""
+    import torch
+    b = P.pack_events(evs)
+    bd = {k: (torch.from_numpy(v).cuda() if k not in ("hit_off", "seed_off") else v) for k, v in b.items()}
+    rec = {}
+    for mode, setup in modes.items():
+        ctx = P.Context(geom.module_table(), maps, cfg=cuts, capacity=P.default_capacity(len(evs)))
+        setup(ctx)
+        for _ in range(2):
+            ctx.run_packed(bd, stream=st.cuda_stream)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for i in range(reps):
+            flush.fill_(i & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ctx.run_packed(bd, stream=st.cuda_stream)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        counts = [ctx.stats(e)["counts"] for e in range(len(evs))]
+        ctx.set_profiling(True)
+        per = {}
+        for i in range(reps):
+            flush.fill_(i & 0xff)
+            ctx.run_packed(bd, stream=st.cuda_stream)
+            for name, kms in ctx.kernel_times():
+                per.setdefault(name, []).append(kms)
+        ctx.set_profiling(False)
+        ctx.close()
+        rec[mode] = {"ms_per_batch": round(ms / reps, 4), "events_per_s": round(1e3 * len(evs) * reps / ms, 2),
+                     "stage_ms": {k: round(sum(per[k]) / len(per[k]), 4) for k in touched if k in per},
+                     "counts": counts}
+    return rec
+
+
 def measure_compact(P, geom, maps, cuts, flush, st, events, sizes=(1, 64), reps=3):
     """Compact (16-bit) storage against the default, at 1 and 64 PU200 events per batch: device time per
     batch and the stage times of the kernels that read the 16-bit copies (default launch shapes for both, so
     that only the storage differs). Objects are identical by construction (tested on the GPU)."""
-    import torch
     from synth import events as E
     evs = list(events) + [E.pu200_event(s, geom) for s in range(len(events), max(sizes))]
     touched = ("t5", "pt3", "clean_pt3_cross", "clean_t5", "clean_pls")
     out = {}
     for n in sizes:
-        b = P.pack_events(evs[:n])
-        bd = {k: (torch.from_numpy(v).cuda() if k not in ("hit_off", "seed_off") else v) for k, v in b.items()}
-        rec = {}
+        rec = _time_modes(P, geom, maps, cuts, flush, st, evs[:n],
+                          {"default": lambda c: None, "compact": lambda c: c.set_compact_storage(True)}, touched, reps)
         for mode in ("default", "compact"):
-            ctx = P.Context(geom.module_table(), maps, cfg=cuts, capacity=P.default_capacity(n))
-            ctx.set_compact_storage(mode == "compact")
-            for _ in range(2):
-                ctx.run_packed(bd, stream=st.cuda_stream)
-            torch.cuda.synchronize()
-            ms = 0.0
-            for i in range(reps):
-                flush.fill_(i & 0xff)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                ctx.run_packed(bd, stream=st.cuda_stream)
-                e1.record(st)
-                torch.cuda.synchronize()
-                ms += e0.elapsed_time(e1)
-            t3 = sum(ctx.stats(e)["counts"]["t3"] for e in range(n))
-            ctx.set_profiling(True)
-            per = {}
-            for i in range(reps):
-                flush.fill_(i & 0xff)
-                ctx.run_packed(bd, stream=st.cuda_stream)
-                for name, kms in ctx.kernel_times():
-                    per.setdefault(name, []).append(kms)
-            ctx.set_profiling(False)
-            ctx.close()
-            rec[mode] = {"ms_per_batch": round(ms / reps, 4),
-                         "stage_ms": {k: round(sum(per[k]) / len(per[k]), 4) for k in touched if k in per},
-                         "triplet_curvature_bytes": int(t3 * (8 if mode == "default" else 12))}
+            counts = rec[mode].pop("counts")
+            t3 = sum(c["t3"] for c in counts)
+            rec[mode].pop("events_per_s")
+            rec[mode]["triplet_curvature_bytes"] = int(t3 * (8 if mode == "default" else 12))
         rec["speedup"] = round(rec["default"]["ms_per_batch"] / rec["compact"]["ms_per_batch"], 3)
         out[f"{n}_events"] = rec
     out["note"] = ("compact keeps the FP32 (kappa, sigma) for the exact decisions and adds a 4-byte FP16 copy per "
                    "triplet that the searches read instead of the 8-byte pair; the eta-phi list entries shrink "
                    "from 8 to 4 bytes")
+    return out
+
+
+def measure_fit_precision(P, geom, maps, cuts, flush, st, events, sizes=(1, 64), reps=3):
+    """The refine fits in float-float on the FP32 pipe (the default) against FP64, at 1 and 64 PU200 events per
+    batch: device time per batch and the refine stage times (default launch shapes for both). The objects
+    agree (tested on the GPU); the counts are reported as a check."""
+    from synth import events as E
+    evs = list(events) + [E.pu200_event(s, geom) for s in range(len(events), max(sizes))]
+    touched = ("t5_refine", "pt5_refine", "pt3_refine")
+    out = {}
+    for n in sizes:
+        rec = _time_modes(P, geom, maps, cuts, flush, st, evs[:n],
+                          {"float_float": lambda c: None, "fp64": lambda c: c.set_fp64_fit(True)}, touched, reps)
+        same = rec["float_float"].pop("counts") == rec["fp64"].pop("counts")
+        rec["speedup"] = round(rec["fp64"]["ms_per_batch"] / rec["float_float"]["ms_per_batch"], 3)
+        rec["same_object_counts"] = same
+        out[f"{n}_events"] = rec
     return out
 
 

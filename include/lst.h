@@ -281,6 +281,14 @@ lst_status lst_set_stage_limits(lst_ctx* ctx, int32_t t5, int32_t pt);
  * values, so the objects are those of the default storage. Waits for the
  * running batch; the next run captures a new graph. */
 lst_status lst_set_compact_storage(lst_ctx* ctx, int32_t enable);
+/* Precision of the refine fits (the five-point T5 fit, Section 2.1, and the
+ * pT5 / pT3 fits, Section 2.2: the chord-frame circle fit, the residual chi2
+ * and the r-z line fit). 0 (the default): float-float arithmetic (pairs of
+ * FP32 numbers, about 48 significant bits) on the FP32 pipe from the FP32
+ * hit coordinates; 1: FP64 as before. The two agree to about 1e-10 relative,
+ * far inside the 1e-5 parity tolerance, so the objects are the same. Waits
+ * for the running batch; the next run captures a new graph. */
+lst_status lst_set_fp64_fit(lst_ctx* ctx, int32_t enable);
 int32_t lst_launch_stage_count(void);
 lst_status lst_get_launch_config(lst_ctx* ctx, int32_t stage, const char** name, int32_t* blocks_per_sm,
                                  int32_t* block, int32_t* flags);

@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblst.so")
 SOURCES = ["k_chain.cu", "k_pixel_clean.cu", "k_mlp.cu", "lst_api.cu", "lst_mlp_api.cu", "lst_static.cu", "lst_peaks.cu"]
-HEADERS = ["lst_device.cuh", "lst_kernels.cuh", "lst_warp.cuh", "lst_mlp.cuh", "lst_pdl.cuh"]
+HEADERS = ["lst_device.cuh", "lst_kernels.cuh", "lst_warp.cuh", "lst_mlp.cuh", "lst_pdl.cuh", "lst_ff.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xptxas", "-v"]

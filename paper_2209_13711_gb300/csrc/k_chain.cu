@@ -972,9 +972,29 @@ __global__ void __launch_bounds__(128) k_t5_gather(Arena A) {
     }
 }
 
-// T5 refine (FP64): one thread per searched candidate, lane-dense. Decides
-// the hand-set cuts, writes the T5 outputs and, when enabled, the scoring
-// features; without the network the cut decision is the validity.
+// The T5 outputs of candidate i (event e)
+__device__ __forceinline__ void t5_store(Arena& A, int i, int e, bool pass, const T5Out& o, bool use_mlp) {
+    A.t5_cut[i] = pass;
+    A.t5_kappa[i] = o.kappa;
+    A.t5_sigk[i] = o.sigk;
+    A.t5_ks[i] = make_float2(float(o.kappa), float(o.sigk));
+    A.t5_eta[i] = o.eta;
+    A.t5_phi[i] = o.phi0;
+    A.t5_chi2[i] = float(o.chi2_rphi);
+    A.t5_chi2z[i] = float(o.chi2_rz);
+    A.t5_score[i] = float(o.score);
+    A.t5_pt[i] = float(o.pt);
+    if (!use_mlp) {
+        A.t5_valid[i] = pass;
+        if (pass) atomicAdd(&A.ev_counts[e * 8 + 3], 1);
+    }
+}
+
+// T5 refine, one thread per searched candidate (lane-dense): decides the
+// hand-set cuts, writes the T5 outputs and, when enabled, the scoring
+// features; without the network the cut decision is the validity. (A group
+// of 8 lanes per candidate, as in the pT refines, measured slower here: the
+// shuffled float-float sums cost more than the latency they hide.)
 __global__ void k_t5_refine(Arena A, DevCfg c) {
     pdl_begin();
     const int n = min(A.counters[3], A.t5_cap);
@@ -983,32 +1003,20 @@ __global__ void k_t5_refine(Arena A, DevCfg c) {
         int m[5];
         const int2 pr = make_int2(A.t5_in[i], A.t5_out[i]);
         t5_mds(A, pr, m);
-        Pt<double> P[5];
         Pt<float> Pf[5];
 #pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            P[j] = md_point<double>(A, m[j]);
-            Pf[j] = md_point<float>(A, m[j]);
-        }
+        for (int j = 0; j < 5; ++j) Pf[j] = md_point<float>(A, m[j]);
         T5Out o;
         const float2 ka = A.t3_ks[pr.x], kb = A.t3_ks[pr.y];
-        bool pass = t5_eval(c, P, Pf, ka.x, ka.y, kb.x, kb.y, c.use_mlp != 0, o);
+        bool pass = t5_eval(c, Pf, ka.x, ka.y, kb.x, kb.y, c.use_mlp != 0, o);
         const int e = A.md_gmod[m[0]] / A.n_mod;
-        A.t5_cut[i] = pass;
-        A.t5_kappa[i] = o.kappa;
-        A.t5_sigk[i] = o.sigk;
-        A.t5_ks[i] = make_float2(float(o.kappa), float(o.sigk));
-        A.t5_eta[i] = o.eta;
-        A.t5_phi[i] = o.phi0;
-        A.t5_chi2[i] = float(o.chi2_rphi);
-        A.t5_chi2z[i] = float(o.chi2_rz);
-        A.t5_score[i] = float(o.score);
-        A.t5_pt[i] = float(o.pt);
+        t5_store(A, i, e, pass, o, c.use_mlp != 0);
         if (c.features_on) {
-            Pt<double> H[10];
+            Pt<double> P[5], H[10];
             int code[5];
             const int h0 = A.hit_off[e];
             for (int j = 0; j < 5; ++j) {
+                P[j] = pt_f64(Pf[j]);
                 H[2 * j] = P[j];
                 Pt<double> U = P[j];
                 const int hu = h0 + A.md_up[m[j]];
@@ -1021,10 +1029,6 @@ __global__ void k_t5_refine(Arena A, DevCfg c) {
                 code[j] = A.mod_layer[mod] + (A.mod[mod].w > 0.5f ? 6 : 0);
             }
             t5_features(c, P, H, code, A.t5_feat + (size_t)48 * i);
-        }
-        if (!c.use_mlp) {
-            A.t5_valid[i] = pass;
-            if (pass) atomicAdd(&A.ev_counts[e * 8 + 3], 1);
         }
     }
 }

@@ -252,8 +252,8 @@ __device__ __forceinline__ Pt<double> shfl_pt8(const Pt<double>& q, int src) {
 }
 
 // pT5 / pT3 refine, one candidate per group of 8 lanes, one point per lane
-// (fit_track_group): for few candidates (one event), where a thread per
-// candidate would leave the FP64 latency exposed.
+// (fit_track_group_ff, or fit_track_group in FP64): for few candidates (one
+// event), where a thread per candidate would leave the fit's latency exposed.
 template <int NT> __device__ __forceinline__ void pt_refine_group(Arena& A, const DevCfg& c, int n) {
     constexpr int N = NT + 3;
     const int lane = lane_id(), j = lane & 7;
@@ -271,12 +271,12 @@ template <int NT> __device__ __forceinline__ void pt_refine_group(Arena& A, cons
         if (j >= 3 && j < N) {
             int m[NT];
             pt_mds<NT>(A, obj, m);
-            Q = md_point<double>(A, m[j - 3]);
             Qf = md_point<float>(A, m[j - 3]);
+            Q = pt_f64(Qf);
         } else {
             const int k = j < 3 ? j : 0;      // lanes past the last point repeat pixel point 0 (unused)
-            Q = pix_pt<double>(sd + 3 * k, c.sig_pix);
             Qf = pix_pt<float>(sd + 3 * k, c.f.sig_pix);
+            Q = pix_pt<double>(sd + 3 * k, c.sig_pix);
         }
         const double kp = A.pls_kappa[g], sp = A.pls_sigk[g];
         // the triplet's points for an undecided pT3 curvature test (all lanes shuffle)
@@ -294,7 +294,7 @@ template <int NT> __device__ __forceinline__ void pt_refine_group(Arena& A, cons
             }
             kc = k != 0;
         }
-        const Fit f = fit_track_group<N>(Q, Qf, j);
+        const Fit f = c.fp64_fit ? fit_track_group<N>(Q, Qf, j) : fit_track_group_ff<N>(Qf, j);
         const double chi2_max = NT == 5 ? c.chi2_rphi_pt5 : c.chi2_rphi_pt3;
         const double chi2z_max = NT == 5 ? c.chi2_rz_pt5 : c.chi2_rz_pt3;
         const bool pass = kc && fabs(f.kappa) <= (1.0 + c.tol_r) * 2.0 * c.a && f.chi2_rphi <= chi2_max &&
@@ -330,16 +330,17 @@ template <int NT> __device__ __forceinline__ void pt_refine_thread(Arena& A, con
         Pt<float> Pf[NT + 3];
         const float* sd = A.bd->seeds + 9 * (size_t)g;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            P[j] = pix_pt<double>(sd + 3 * j, c.sig_pix);
-            Pf[j] = pix_pt<float>(sd + 3 * j, c.f.sig_pix);
-        }
+        for (int j = 0; j < 3; ++j) Pf[j] = pix_pt<float>(sd + 3 * j, c.f.sig_pix);
         int m[NT];
         pt_mds<NT>(A, obj, m);
 #pragma unroll
-        for (int j = 0; j < NT; ++j) {
-            P[3 + j] = md_point<double>(A, m[j]);
-            Pf[3 + j] = md_point<float>(A, m[j]);
+        for (int j = 0; j < NT; ++j) Pf[3 + j] = md_point<float>(A, m[j]);
+        if (c.fp64_fit) {
+            // the FP64 fit's own points (the pixel errors from the FP64 configuration)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) P[j] = pix_pt<double>(sd + 3 * j, c.sig_pix);
+#pragma unroll
+            for (int j = 0; j < NT; ++j) P[3 + j] = pt_f64(Pf[3 + j]);
         }
         const double kp = A.pls_kappa[g], sp = A.pls_sigk[g];
         bool kc;
@@ -350,7 +351,7 @@ template <int NT> __device__ __forceinline__ void pt_refine_thread(Arena& A, con
             const float2 ks = A.t3_ks[obj];
             int k = kappa_test_f32(float(kp), float(sp), ks.x, ks.y, c.f.n_pt);
             if (k < 0) {
-                Tri<double> tt = tri(P[3], P[4], P[5]);
+                Tri<double> tt = tri(pt_f64(Pf[3]), pt_f64(Pf[4]), pt_f64(Pf[5]));
                 k = fabs(kp - tt.kappa) <= c.n_pt * sqrt(sq(sp) + sq(tt.sigk));
             }
             kc = k != 0;

@@ -193,6 +193,7 @@ static DevCfg make_devcfg(const lst_config& c) {
     d.dr_clean = c.dr_clean; d.k_field = c.k_field; d.b_field = c.b_field;
     d.features_on = 0;
     d.use_mlp = 0;
+    d.fp64_fit = 0;
     d.prefit_scale = 1.0f;
     d.mlp_threshold = 0.5f;
     d.t5_stage = kT5Stage;
@@ -883,6 +884,13 @@ lst_status lst_set_compact_storage(lst_ctx* c, int32_t enable) {
     if (!c || enable < 0 || enable > 1) return LST_ERR_ARG;
     lst_status s = drop_graph(c);
     c->A.compact = enable;
+    return s;
+}
+
+lst_status lst_set_fp64_fit(lst_ctx* c, int32_t enable) {
+    if (!c || enable < 0 || enable > 1) return LST_ERR_ARG;
+    lst_status s = drop_graph(c);
+    c->dc.fp64_fit = enable;
     return s;
 }
 

@@ -28,6 +28,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "lst_ff.cuh"
 #include "lst_pdl.cuh"
 
 namespace lst {
@@ -59,6 +60,7 @@ struct DevCfg {
     double dr_clean, k_field, b_field;
     int features_on;       // the T5 refine also writes the 38 scoring features
     int use_mlp;           // T5 validity from the network score instead of the cuts
+    int fp64_fit;          // refine fits in FP64 (default: float-float on the FP32 pipe)
     float prefit_scale;    // widening of the T5 FP32 prefilter (1: conservative for the cuts)
     float mlp_threshold;
     float t3_threshold;    // learned triplet selection: keep a T3 when its score reaches this
@@ -694,6 +696,124 @@ template <int N> __device__ inline Fit fit_track(const Pt<double>* P, FitFull* f
     return f;
 }
 
+// r-phi chi2 term of point Q (scaled-frame coordinates xi, et, rho2) for the
+// circle (gg, hh, kk) of fit_track_ff: the geometric residual from u and the
+// error projected on the circle normal, as in fit_track with FP32 points, with
+// the radial component of the normal at a strip point in float-float.
+__device__ __forceinline__ float ff_rphi_term(const Pt<float>& Q, ff xi, ff et, ff rho2, ff gg, ff hh, ff kk, ff ex,
+                                              ff ey, float Sf, float iLf) {
+    const float gf = gg.hi, hf = hh.hi, exf = ex.hi, eyf = ey.hi;
+    const float u = (gg * rho2 + hh * xi + kk - et).hi;
+    const float e = 2.f * u / (Sf + sqrtf(fmaxf(0.f, Sf * Sf + 4.f * gf * u))) * iLf;
+    // the normal (nlx, nly) in the chord frame; n_phi, n_r against the radial direction
+    const float nlx = 2.f * gf * xi.hi + hf, nly = 2.f * gf * et.hi - 1.f;
+    const float nn2 = nlx * nlx + nly * nly;
+    const float ilr = iLf / Q.r;
+    const float n_phi = ((nlx * eyf + nly * exf) * Q.x - (nlx * exf - nly * eyf) * Q.y) * ilr;
+    float s2;
+    if (Q.sr > 0.f) {
+        const ff lx = gg * xi * 2.f + hh, ly = gg * et * 2.f - 1.f;
+        const float n_r = ((lx * ex - ly * ey) * Q.x + (lx * ey + ly * ex) * Q.y).hi * ilr;
+        s2 = fmaxf(sq(Q.srphi * n_phi) + sq(Q.sr * n_r), sq(0.01f * Q.srphi) * nn2);
+    } else {
+        s2 = fmaxf(sq(Q.srphi * n_phi), sq(0.01f * Q.srphi) * nn2);
+    }
+    return e * e * nn2 / s2;
+}
+
+// fit_track in float-float on the FP32 pipe, from the FP32 points (the
+// coordinates are FP32 in memory, so the FP64 fit sees the same numbers).
+// The frame axis is the exact chord (the differences of the end points as
+// float-float), left unnormalised: the chord frame scaled by the chord length
+// L, to which the algebraic circle fit is invariant (curvature and residuals
+// scale by L and 1/L). The axis must be exact: the fit is not invariant under
+// a turn of the frame, and a turn by the FP32 rounding of the chord (~1e-7
+// rad) moves the curvature of a nearly straight candidate by ~2e-11 /cm, 1e-4
+// of a curvature of 2e-7 /cm. The residuals, the arc lengths and the r-z line
+// fit are float-float; the geometric residual from u, the error projection on
+// the circle normal and the r-z weights are FP32, as in fit_track with FP32
+// points, except the radial component of the normal at strip points (a
+// cancelling dot product), which is float-float. The point loops stay rolled:
+// unrolled, the float-float code outgrows the instruction cache (measured:
+// instruction-fetch stalls dominated the refine).
+template <int N> __device__ inline Fit fit_track_ff(const Pt<float>* P) {
+    Fit f;
+    const float ox = P[N / 2].x, oy = P[N / 2].y;
+    const ff ex = two_sum(P[N - 1].x, -P[0].x), ey = two_sum(P[N - 1].y, -P[0].y);
+    const ff L2 = ex * ex + ey * ey;
+    ff xi[N], et[N], rho2[N];
+    ff mr{0.f, 0.f}, mx{0.f, 0.f}, me{0.f, 0.f};
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+        const ff dx = two_sum(P[i].x, -ox), dy = two_sum(P[i].y, -oy);
+        xi[i] = dx * ex + dy * ey;
+        et[i] = dy * ex - dx * ey;
+        rho2[i] = (dx * dx + dy * dy) * L2;
+        mr = mr + rho2[i]; mx = mx + xi[i]; me = me + et[i];
+    }
+    mr = mr / float(N); mx = mx / float(N); me = me / float(N);
+    ff saa{0.f, 0.f}, sab{0.f, 0.f}, sbb{0.f, 0.f}, sac{0.f, 0.f}, sbc{0.f, 0.f};
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+        const ff a = rho2[i] - mr, b = xi[i] - mx, cc = et[i] - me;
+        saa = saa + a * a; sab = sab + a * b; sbb = sbb + b * b; sac = sac + a * cc; sbc = sbc + b * cc;
+    }
+    const ff det = saa * sbb - sab * sab;
+    if (!(det.hi > 0.f)) {
+        f.kappa = 1e30; f.chi2_rphi = 1e30; f.chi2_rz = 1e30; f.tanl = 0;
+        return f;
+    }
+    // the circle in the scaled frame; curvature and residuals scale by L, 1/L
+    const ff gg = (sac * sbb - sab * sbc) / det, hh = (saa * sbc - sab * sac) / det;
+    const ff kk = me - gg * mr - hh * mx;
+    const ff S = ff_sqrt(hh * hh + 1.f - gg * kk * 4.f);
+    const ff L = ff_sqrt(L2);
+    const ff kappa = gg * L * 2.f / S;
+    f.kappa = ff_d(kappa);
+    const float iLf = 1.f / L.hi;
+    float chi2 = 0.f;
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) chi2 += ff_rphi_term(P[i], xi[i], et[i], rho2[i], gg, hh, kk, ex, ey, S.hi, iLf);
+    f.chi2_rphi = chi2;
+    // r-z: arc lengths from the first point, weighted line z = c0 + t s
+    const ff ka = ff_abs(kappa);
+    ff s[N];
+    s[0] = ff{0.f, 0.f};
+#pragma unroll 1
+    for (int i = 1; i < N; ++i) {
+        const ff cx = two_sum(P[i].x, -P[0].x), cy = two_sum(P[i].y, -P[0].y);
+        s[i] = ff_arc(ff_sqrt(cx * cx + cy * cy), ka);
+    }
+    const float t_hat = (P[N - 1].z - P[0].z) / s[N - 1].hi;
+    float w[N];
+    ff W{0.f, 0.f}, Ws{0.f, 0.f}, Wz{0.f, 0.f};
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+        w[i] = 1.f / fmaxf(1e-12f, sq(P[i].sz) + sq(t_hat * P[i].sr));
+        W = W + w[i];
+        Ws = Ws + s[i] * w[i];
+        Wz = Wz + two_prod(w[i], P[i].z);
+    }
+    const ff sbar = Ws / W, zbar = Wz / W;
+    ff Sss{0.f, 0.f}, Ssz{0.f, 0.f};
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+        const ff ds = s[i] - sbar, dz = ff_of(P[i].z) - zbar;
+        Sss = Sss + ds * ds * w[i];
+        Ssz = Ssz + ds * dz * w[i];
+    }
+    const ff t = Ssz / Sss, c0 = zbar - t * sbar;
+    float chi2z = 0.f;
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+        const float r = (ff_of(P[i].z) - c0 - t * s[i]).hi;
+        chi2z += w[i] * r * r;
+    }
+    f.chi2_rz = chi2z;
+    f.tanl = ff_d(t);
+    return f;
+}
+
 // The same fit with one candidate per group of 8 lanes: lane j of the group
 // holds point j (j < N) in FP64 (Q) and FP32 (Qf); the per-point work runs in
 // parallel, the sums are taken with shuffles and every lane of the group
@@ -780,6 +900,72 @@ template <int N> __device__ inline Fit fit_track_group(const Pt<double>& Q, cons
     const double t = Ssz / Sss, c0 = zbar - t * sbar;
     f.chi2_rz = grp_sum8(w * sq(Q.z - c0 - t * sj));
     f.tanl = t;
+    return f;
+}
+
+// Sum over a group of 8 lanes (float-float)
+__device__ __forceinline__ ff grp_sum8(ff v) {
+#pragma unroll
+    for (int d = 4; d; d >>= 1)
+        v = v + ff{__shfl_xor_sync(0xffffffffu, v.hi, d, 8), __shfl_xor_sync(0xffffffffu, v.lo, d, 8)};
+    return v;
+}
+__device__ __forceinline__ float grp_sum8(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
+    return v;
+}
+
+// fit_track_ff with one candidate per group of 8 lanes, lane j holding point j
+// (j < N); every lane of the group returns the fit. For kernels with few
+// candidates, where a thread per candidate leaves the dependent float-float
+// chain exposed. All 32 lanes must call.
+template <int N> __device__ inline Fit fit_track_group_ff(const Pt<float>& Q, int j) {
+    static_assert(N <= 8, "one point per lane of a group of 8");
+    const unsigned F = 0xffffffffu;
+    const bool act = j < N;
+    const ff zero{0.f, 0.f};
+    Fit f;
+    const float x0 = __shfl_sync(F, Q.x, 0, 8), y0 = __shfl_sync(F, Q.y, 0, 8), z0 = __shfl_sync(F, Q.z, 0, 8);
+    const float xn = __shfl_sync(F, Q.x, N - 1, 8), yn = __shfl_sync(F, Q.y, N - 1, 8);
+    const float zn = __shfl_sync(F, Q.z, N - 1, 8);
+    const float ox = __shfl_sync(F, Q.x, N / 2, 8), oy = __shfl_sync(F, Q.y, N / 2, 8);
+    const ff ex = two_sum(xn, -x0), ey = two_sum(yn, -y0);
+    const ff L2 = ex * ex + ey * ey;
+    const ff dx = two_sum(Q.x, -ox), dy = two_sum(Q.y, -oy);
+    const ff xi = dx * ex + dy * ey, et = dy * ex - dx * ey, rho2 = (dx * dx + dy * dy) * L2;
+    const ff mr = grp_sum8(act ? rho2 : zero) / float(N), mx = grp_sum8(act ? xi : zero) / float(N);
+    const ff me = grp_sum8(act ? et : zero) / float(N);
+    const ff ca = act ? rho2 - mr : zero, cb = act ? xi - mx : zero, cc = act ? et - me : zero;
+    const ff saa = grp_sum8(ca * ca), sab = grp_sum8(ca * cb), sbb = grp_sum8(cb * cb);
+    const ff sac = grp_sum8(ca * cc), sbc = grp_sum8(cb * cc);
+    const ff det = saa * sbb - sab * sab;
+    if (!(det.hi > 0.f)) {
+        f.kappa = 1e30; f.chi2_rphi = 1e30; f.chi2_rz = 1e30; f.tanl = 0;
+        return f;
+    }
+    const ff gg = (sac * sbb - sab * sbc) / det, hh = (saa * sbc - sab * sac) / det;
+    const ff kk = me - gg * mr - hh * mx;
+    const ff S = ff_sqrt(hh * hh + 1.f - gg * kk * 4.f);
+    const ff L = ff_sqrt(L2);
+    const ff kappa = gg * L * 2.f / S;
+    f.kappa = ff_d(kappa);
+    const float term = act ? ff_rphi_term(Q, xi, et, rho2, gg, hh, kk, ex, ey, S.hi, 1.f / L.hi) : 0.f;
+    f.chi2_rphi = grp_sum8(term);
+    const ff cx = two_sum(Q.x, -x0), cy = two_sum(Q.y, -y0);
+    const ff sj = ff_arc(ff_sqrt(cx * cx + cy * cy), ff_abs(kappa));
+    const float sn = __shfl_sync(F, sj.hi, N - 1, 8);
+    const float t_hat = (zn - z0) / sn;
+    const float w = act ? 1.f / fmaxf(1e-12f, sq(Q.sz) + sq(t_hat * Q.sr)) : 0.f;
+    const ff W = grp_sum8(ff{w, 0.f}), Ws = grp_sum8(sj * w), Wz = grp_sum8(two_prod(w, Q.z));
+    const ff sbar = Ws / W, zbar = Wz / W;
+    const ff ds = sj - sbar, dz = ff_of(Q.z) - zbar;
+    const ff Sss = grp_sum8(ds * ds * w), Ssz = grp_sum8(ds * dz * w);
+    const ff t = Ssz / Sss, c0 = zbar - t * sbar;
+    const float r = (ff_of(Q.z) - c0 - t * sj).hi;
+    f.chi2_rz = grp_sum8(w * r * r);
+    f.tanl = ff_d(t);
     return f;
 }
 
@@ -1090,23 +1276,34 @@ __device__ __forceinline__ int kappa_test_f32(float k1, float s1, float k2, floa
     return -1;
 }
 
-// T5 on anchors P[0..4]; the two triplets' curvatures (k, s) come from the T3
-// arrays (FP32) and decide the consistency test unless it is undecided, in
-// which case both triplets are recomputed in FP64. all_outputs = false skips
-// eta, phi0 and pT of a rejected candidate.
-__device__ inline bool t5_eval(const DevCfg& c, const Pt<double>* P, const Pt<float>* Pf, float k1, float s1,
-                               float k2, float s2, bool all_outputs, T5Out& o) {
-    o = T5Out{};
-    o.sigk = 0.5 * sqrt(sq(double(s1)) + sq(double(s2)));
-    int kc = kappa_test_f32(k1, s1, k2, s2, c.f.n_t5);
-    if (kc < 0) {
-        Tri<double> ti = tri(P[0], P[1], P[2]);
-        Tri<double> to = tri(P[2], P[3], P[4]);
-        o.sigk = 0.5 * sqrt(sq(ti.sigk) + sq(to.sigk));
-        kc = fabs(ti.kappa - to.kappa) <= c.n_t5 * sqrt(sq(ti.sigk) + sq(to.sigk));
-    }
+// The FP64 twin of an FP32 point: the coordinates convert exactly and r is
+// recomputed in FP64, as md_point<double> does.
+__device__ __forceinline__ Pt<double> pt_f64(const Pt<float>& q) {
+    Pt<double> p;
+    p.x = q.x; p.y = q.y; p.z = q.z;
+    p.r = m_hypot(p.x, p.y);
+    p.srphi = q.srphi; p.sz = q.sz; p.sr = q.sr;
+    return p;
+}
+
+// FP64 curvature consistency of a T5's two triplets, recomputed from the
+// anchors Pf[0..4] (for a test the stored FP32 curvatures leave undecided);
+// sigk receives the T5's curvature error.
+__device__ inline bool t5_kc_fp64(const DevCfg& c, const Pt<float>* Pf, double& sigk) {
+    const Pt<double> P0 = pt_f64(Pf[0]), P1 = pt_f64(Pf[1]), P2 = pt_f64(Pf[2]);
+    const Pt<double> P3 = pt_f64(Pf[3]), P4 = pt_f64(Pf[4]);
+    const Tri<double> ti = tri(P0, P1, P2), to = tri(P2, P3, P4);
+    sigk = 0.5 * sqrt(sq(ti.sigk) + sq(to.sigk));
+    return fabs(ti.kappa - to.kappa) <= c.n_t5 * sqrt(sq(ti.sigk) + sq(to.sigk));
+}
+
+// A T5's verdict and outputs from its fit f, its curvature consistency kc and
+// its first anchor P0 (o.sigk already set). all_outputs = false leaves the
+// outputs of a candidate that fails kc at zero and skips eta, phi0 and pT of
+// a rejected one.
+__device__ inline bool t5_finish(const DevCfg& c, const Pt<float>& P0, const Fit& f, bool kc, bool all_outputs,
+                                 T5Out& o) {
     if (!kc && !all_outputs) return false;
-    Fit f = fit_track<5>(P, nullptr, Pf);
     o.kappa = f.kappa;
     o.chi2_rphi = f.chi2_rphi;
     o.chi2_rz = f.chi2_rz;
@@ -1114,12 +1311,12 @@ __device__ inline bool t5_eval(const DevCfg& c, const Pt<double>* P, const Pt<fl
     const bool pass = kc && fabs(f.kappa) <= (1.0 + c.tol_r) * 2.0 * c.a && f.chi2_rphi <= c.chi2_rphi_t5 &&
                       f.chi2_rz <= c.chi2_rz_t5;
     if (pass || all_outputs) {
-        // direction in FP32 (well conditioned; ~1e-7 rad): eta from the FP64
-        // r-z slope, phi0 from the first anchor and the FP64 curvature
+        // direction in FP32 (well conditioned; ~1e-7 rad): eta from the fitted
+        // r-z slope, phi0 from the first anchor and the fitted curvature
         o.eta = double(asinhf(float(f.tanl)));
         const float kf = float(f.kappa);
-        const float turn = asinf(fminf(1.f, fmaxf(0.f, Pf[0].r * fabsf(kf) * 0.5f)));
-        float ph = atan2f(Pf[0].y, Pf[0].x) - (kf < 0.f ? -turn : turn);
+        const float turn = asinf(fminf(1.f, fmaxf(0.f, P0.r * fabsf(kf) * 0.5f)));
+        float ph = atan2f(P0.y, P0.x) - (kf < 0.f ? -turn : turn);
         if (ph > float(kPi)) ph -= float(2 * kPi);
         if (ph <= -float(kPi)) ph += float(2 * kPi);
         o.phi0 = double(ph);
@@ -1128,17 +1325,41 @@ __device__ inline bool t5_eval(const DevCfg& c, const Pt<double>* P, const Pt<fl
     return pass;
 }
 
+// T5 on anchors Pf[0..4]; the two triplets' curvatures (k, s) come from the
+// T3 arrays (FP32) and decide the consistency test unless it is undecided, in
+// which case both triplets are recomputed in FP64. The fit is float-float, or
+// FP64 with c.fp64_fit.
+__device__ inline bool t5_eval(const DevCfg& c, const Pt<float>* Pf, float k1, float s1, float k2, float s2,
+                               bool all_outputs, T5Out& o) {
+    o = T5Out{};
+    o.sigk = 0.5 * sqrt(sq(double(s1)) + sq(double(s2)));
+    int kc = kappa_test_f32(k1, s1, k2, s2, c.f.n_t5);
+    if (kc < 0) kc = t5_kc_fp64(c, Pf, o.sigk);
+    if (!kc && !all_outputs) return false;
+    Fit f;
+    if (c.fp64_fit) {
+        Pt<double> P[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) P[j] = pt_f64(Pf[j]);
+        f = fit_track<5>(P, nullptr, Pf);
+    } else {
+        f = fit_track_ff<5>(Pf);
+    }
+    return t5_finish(c, Pf[0], f, kc != 0, all_outputs, o);
+}
+
 struct PTOut {
     double kappa, chi2_rphi, chi2_rz, score, pt;
 };
 
-// pT5 / pT3 with the curvature-consistency verdict kc decided by the caller.
+// pT5 / pT3 with the curvature-consistency verdict kc decided by the caller;
+// the fit is float-float, or FP64 on P with c.fp64_fit (P is read only then).
 template <int N>
 __device__ inline bool pt_eval(const DevCfg& c, const Pt<double>* P, const Pt<float>* Pf, bool kc,
                                double chi2_rphi_max, double chi2_rz_max, PTOut& o) {
     o = PTOut{};
     if (!kc) return false;
-    Fit f = fit_track<N>(P, nullptr, Pf);
+    const Fit f = c.fp64_fit ? fit_track<N>(P, nullptr, Pf) : fit_track_ff<N>(Pf);
     o.kappa = f.kappa;
     o.chi2_rphi = f.chi2_rphi;
     o.chi2_rz = f.chi2_rz;

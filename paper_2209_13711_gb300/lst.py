@@ -105,6 +105,7 @@ def library():
         L.lst_get_counters.argtypes = [vp, vp, i32]
         L.lst_set_stage_limits.argtypes = [vp, i32, i32]
         L.lst_set_compact_storage.argtypes = [vp, i32]
+        L.lst_set_fp64_fit.argtypes = [vp, i32]
         L.lst_launch_stage_count.argtypes = []
         L.lst_launch_stage_count.restype = i32
         L.lst_get_launch_config.argtypes = [vp, i32, C.POINTER(C.c_char_p), vp, vp, vp]
@@ -140,7 +141,7 @@ def library():
                   "lst_mlp_forward", "lst_mlp_gradient", "lst_mlp_train_step", "lst_set_t5_selection",
                   "lst_get_t5_candidates", "lst_measure_peaks", "lst_build_mini_doublets_static",
                   "lst_release_event", "lst_run_events", "lst_get_batch_track_candidates", "lst_mlp_get_state",
-                  "lst_mlp_set_state", "lst_set_compact_storage", "lst_set_t3_selection",
+                  "lst_mlp_set_state", "lst_set_compact_storage", "lst_set_t3_selection", "lst_set_fp64_fit",
                   "lst_get_t3_candidates"):
             getattr(L, f).restype = i32
         _lib = L
@@ -446,6 +447,10 @@ class Context:
         """16-bit copies for the searches' curvature prefilters and the cleaning's eta-phi lists
         (lst_set_compact_storage); the objects do not change."""
         _check(library().lst_set_compact_storage(self._h, 1 if enable else 0))
+
+    def set_fp64_fit(self, enable=True):
+        """Refine fits in FP64 instead of float-float on the FP32 pipe (lst_set_fp64_fit)."""
+        _check(library().lst_set_fp64_fit(self._h, 1 if enable else 0))
 
     def set_stage_limits(self, t5=0, pt=0):
         """Survivors a T5 / pT work item stages before re-enumerating (0: the defaults 512 / 256)."""

@@ -31,6 +31,7 @@ def main(argv=None):
     ap.add_argument("--profile", action="store_true")
     ap.add_argument("--t3-net", default=None, help="learned triplet selection saved by train --kind t3")
     ap.add_argument("--t5-net", default=None, help="network-scored T5 selection saved by train --kind t5")
+    ap.add_argument("--fp64-fit", action="store_true", help="refine fits in FP64 instead of float-float")
     args = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
@@ -51,6 +52,8 @@ def main(argv=None):
         else:
             evs.append(E.pileup_event(args.pileup, args.seed * 1000 + i, geom))
     ctx = L.Context(geom.module_table(), maps, cfg=DEFAULT_CUTS, capacity=L.default_capacity(args.events))
+    if args.fp64_fit:
+        ctx.set_fp64_fit(True)
     nets = []
     if args.t3_net:
         z = np.load(args.t3_net)

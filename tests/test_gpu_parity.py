@@ -226,3 +226,41 @@ def test_displaced_muon_gun_parity(geom_full, seed):
     t5_tc = [h[h >= 0] for t, h in zip(g["tc"]["type"], g["tc"]["hits"]) if t == 2]
     assert any(d0[np.bincount(ev.pid[h]).argmax()] > 1.0 for h in t5_tc if len(h))
     ctx.close()
+
+
+def _fit_rows(ctx, event):
+    """T5 / pT5 / pT3 fit outputs keyed by the object's hit tuple (object indices depend on the run)."""
+    from tests.parity import chain_tuples
+    g = gpu_result(ctx, event)
+    T = chain_tuples(g)
+    out = {}
+    for kind, vals in (("t5", ("kappa", "chi2_rphi", "chi2_rz", "eta", "phi0", "pt")),
+                       ("pt5", ("kappa", "chi2_rphi", "chi2_rz", "pt")), ("pt3", ("kappa", "chi2_rphi", "chi2_rz", "pt"))):
+        v = np.stack([g[kind][c] for c in vals], 1).astype(np.float64)
+        out[kind] = dict(zip(T[kind], v))
+    return out
+
+
+@pytest.mark.parametrize("n_ev", [1, 4])
+def test_float_float_and_fp64_fits_agree(geom_full, maps_full, n_ev):
+    """The refine fits in float-float (the default) and in FP64 give the same objects at every level, and fit
+    outputs within 2e-6 relative (the FP32 storage of the outputs; the fits themselves agree to ~1e-10).
+    One event takes the grouped pT refines, four events the per-thread ones."""
+    evs = [E.pu200_event(90 + i, geom_full) for i in range(n_ev)]
+    res = []
+    for fp64 in (False, True):
+        ctx = make_context(geom_full, maps_full, max_events=n_ev)
+        ctx.set_fp64_fit(fp64)
+        ctx.run(evs)
+        res.append([(_all_tuples(ctx, i), _fit_rows(ctx, i)) for i in range(n_ev)])
+        ctx.close()
+    for (t_ff, f_ff), (t_64, f_64) in zip(*res):
+        assert t_ff == t_64
+        for kind in f_ff:
+            assert f_ff[kind].keys() == f_64[kind].keys() and len(f_ff[kind]) > 100
+            a = np.array([f_ff[kind][k] for k in f_64[kind]])
+            b = np.array(list(f_64[kind].values()))
+            d = np.abs(a - b)
+            if kind == "t5":
+                d[:, 4] = np.abs(np.angle(np.exp(1j * (a[:, 4] - b[:, 4]))))     # phi0 across the +-pi cut
+            assert np.all(d <= 2e-6 * np.abs(b) + 1e-7), kind
