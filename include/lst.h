@@ -343,7 +343,8 @@ lst_status lst_build_mini_doublets_static(const lst_config* cfg, const lst_modul
                                           void* cuda_stream);
 
 /* Wait for the batch and copy the batch-wide device counters: [0..5] objects
- * reserved (MD, LS, T3, T5 candidates, pT5 candidates, pT3 candidates), [16]
+ * reserved (MD, LS, T3, T5 candidates, pT5 candidates, pT3 candidates), [10]
+ * / [11] the LS / T3 searches' inner-MD cursors, [16]
  * hits with an invalid module or side, [20] T5 search work items (chunks of 8, 16
  * or 32 T3 of one inner MD, by batch size) whose survivors exceeded the shared-memory stage
  * and were enumerated a second time, [21] T5 search survivors, [22] + [23] T5

@@ -36,9 +36,13 @@ __global__ void k_reset(Arena A) {
         A.ev_counts[i] = 0;
         A.ev_drop[i] = 0;
     }
+    const size_t n_cells = (size_t)B.n_ev * 2 * A.cell_ne * A.cell_np;
+    for (size_t i = t; i < n_cells; i += stride) A.cell_cnt[i] = 0;
     for (size_t i = t; i < (size_t)B.n_ev; i += stride) {
         A.list_cnt[2 * i] = 0;
         A.list_cnt[2 * i + 1] = 0;
+        A.ovf_cnt[2 * i] = 0;
+        A.ovf_cnt[2 * i + 1] = 0;
         A.tc_cnt[i] = 0;
         A.t5_evf[i] = 0;
         A.t5_evb[i] = 0;
@@ -532,6 +536,17 @@ __global__ void __launch_bounds__(128) k_md_write(Arena A, DevCfg c) {
     }
 }
 
+// Inner MDs for the LS and T3 searches are taken kMdChunk at a time from a
+// shared cursor (lane 0 claims, all lanes receive): a warp that drew light MDs
+// takes more, so the kernel's tail is one chunk's work instead of the heaviest
+// warp's share of a fixed stride.
+constexpr int kMdChunk = 2;
+__device__ __forceinline__ int next_md_chunk(int* cursor) {
+    int i = 0;
+    if (lane_id() == 0) i = atomicAdd(cursor, kMdChunk);
+    return __shfl_sync(kFull, i, 0);
+}
+
 // ---------------------------------------------------------------------------
 // LS: one warp per inner MD A, candidates = MDs of the connected modules
 // ---------------------------------------------------------------------------
@@ -547,7 +562,8 @@ __global__ void __launch_bounds__(kLsWarps * 32, 4) k_ls(Arena A, DevCfg c) {
     LsSmem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
     const int n_md = min(A.counters[0], A.md_cap);
-    for (int i = blockIdx.x * kLsWarps + (threadIdx.x >> 5); i < n_md; i += gridDim.x * kLsWarps) {
+    for (int i0 = next_md_chunk(&A.counters[10]); i0 < n_md; i0 = next_md_chunk(&A.counters[10]))
+    for (int i = i0; i < min(i0 + kMdChunk, n_md); ++i) {
         const int gm = A.md_gmod[i];
         const int e = gm / A.n_mod, m1 = gm - e * A.n_mod;
         const float4 miA = A.mod[m1];
@@ -618,7 +634,8 @@ __global__ void __launch_bounds__(kT3Warps * 32, 4) k_t3(Arena A, DevCfg c) {
     T3Smem& S = sm[threadIdx.x >> 5];
     const int lane = lane_id();
     const int n_md = min(A.counters[0], A.md_cap);
-    for (int i = blockIdx.x * kT3Warps + (threadIdx.x >> 5); i < n_md; i += gridDim.x * kT3Warps) {
+    for (int i0 = next_md_chunk(&A.counters[11]); i0 < n_md; i0 = next_md_chunk(&A.counters[11]))
+    for (int i = i0; i < min(i0 + kMdChunk, n_md); ++i) {
         const int s0 = A.ls_off[i], s1 = s0 + A.ls_cnt[i];
         if (s1 == s0) {
             if (lane == 0) { A.t3_off[i] = 0; A.t3_cnt[i] = 0; }

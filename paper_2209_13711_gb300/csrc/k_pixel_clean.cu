@@ -541,15 +541,31 @@ __device__ __forceinline__ void tc_append_pls(const Arena& A, int e, int seed_lo
     A.tc_phi[t] = phi;
 }
 
+// eta-phi cell of a list entry, or -1 (the overflow) outside |eta| < kCellEta
+__device__ __forceinline__ int cell_of(const Arena& A, float eta, float phi) {
+    if (!(fabsf(eta) < kCellEta) || !(fabsf(phi) <= 4.f)) return -1;
+    const int ie = min(A.cell_ne - 1, int(floorf((eta + kCellEta) / A.cell_we)));
+    const int ip = (int(floorf((phi + float(kPi)) / A.cell_wp)) % A.cell_np + A.cell_np) % A.cell_np;
+    return ie * A.cell_np + ip;
+}
+
 __device__ __forceinline__ void list_append(const Arena& A, int e, int list, float eta, float phi, int ref) {
     int k = atomicAdd(&A.list_cnt[e * 2 + list], 1);
     if (k < A.list_cap) {
-        size_t o = ((size_t)e * 2 + list) * A.list_cap + k;
+        const size_t L = (size_t)e * 2 + list;
+        size_t o = L * A.list_cap + k;
         if (A.compact)
             A.list_q[o] = pack_eta_phi(eta, phi);
         else
             A.list_ef[o] = make_float2(eta, phi);
         A.list_ref[o] = ref;
+        const size_t NC = (size_t)A.cell_ne * A.cell_np;
+        const int cell = cell_of(A, eta, phi);
+        const int slot = cell >= 0 ? atomicAdd(&A.cell_cnt[L * NC + cell], 1) : kCellSlots;
+        if (slot < kCellSlots)
+            A.cell_idx[(L * NC + cell) * kCellSlots + slot] = k;
+        else
+            A.ovf_idx[L * A.list_cap + atomicAdd(&A.ovf_cnt[L], 1)] = k;
     }
 }
 
@@ -562,52 +578,68 @@ __device__ __forceinline__ void ref_eta_phi(const Arena& A, int ref, double& eta
     else { eta = A.t5_eta[idx]; phi = A.t5_phi[idx]; }
 }
 
-// Is (eta, phi) within dr_clean of any entry of the event's list? Called by
-// all 32 lanes of a warp with the same query; the lanes stride over the list.
-// FP32 test with an FP64 re-test inside a band around the threshold: 1e-3
-// relative for FP32 entries; 2e-2 for the compact fixed-point entries, whose
-// rounding (<= 5e-5 per coordinate) moves d^2 by at most 4e-6 = 1 % of the
-// threshold's square wherever d is near the threshold.
-__device__ __forceinline__ bool dr_close_warp(const Arena& A, const DevCfg& c, int e, int list, double eta,
-                                              double phi) {
-    constexpr int kU = 8;                 // list entries per lane per round: 8 loads in flight
-    const int n = min(A.list_cnt[e * 2 + list], A.list_cap);
-    const size_t base = ((size_t)e * 2 + list) * A.list_cap;
+// Is list entry j (position in the event's list at base) within dr_clean of
+// (eta, phi)? FP32 test with an FP64 re-test inside a band around the
+// threshold: 1e-3 relative for FP32 entries; 2e-2 for the compact fixed-point
+// entries, whose rounding (<= 5e-5 per coordinate) moves d^2 by at most
+// 4e-6 = 1 % of the threshold's square wherever d is near the threshold.
+__device__ __forceinline__ bool entry_close(const Arena& A, const DevCfg& c, size_t base, int j, double eta,
+                                           double phi) {
     const double thr2 = c.dr_clean * c.dr_clean;
     const float thr2f = float(thr2);
     const float band = A.compact ? 2e-2f : 1e-3f;
+    bool sent = false;
+    const float2 v = A.compact ? unpack_eta_phi(A.list_q[base + j], sent) : A.list_ef[base + j];
+    const float de = v.x - float(eta);
+    float dp = v.y - float(phi);
+    if (dp > float(kPi)) dp -= float(2 * kPi);
+    if (dp <= -float(kPi)) dp += float(2 * kPi);
+    const float d2 = de * de + dp * dp;
+    if (!sent && d2 < thr2f * (1.0f - band)) return true;
+    if (sent || d2 <= thr2f * (1.0f + band)) {
+        double e2, p2;
+        ref_eta_phi(A, A.list_ref[base + j], e2, p2);
+        const double dd = eta - e2, dq = wrap_pi(phi - p2);
+        return dd * dd + dq * dq < thr2;
+    }
+    return false;
+}
+
+// Is (eta, phi) within dr_clean of any entry of the event's list? Called by
+// all 32 lanes of a warp with the same query. The entries within reach lie in
+// at most 2 x 2 eta-phi cells (cell sides >= 2 (dr_clean + 1e-3), the 1e-3
+// covering the FP32 rounding of either side): lane (d, s) reads slot s of
+// cell d, one round for the whole query; then the lanes stride over the
+// list's overflow (entries beyond a cell's slots, or outside the cells'
+// eta range).
+__device__ __forceinline__ bool dr_close_warp(const Arena& A, const DevCfg& c, int e, int list, double eta,
+                                              double phi) {
+    static_assert(4 * kCellSlots == 32, "one lane per slot of 2 x 2 cells");
+    const int lane = lane_id();
+    const size_t L = (size_t)e * 2 + list;
+    const size_t base = L * A.list_cap;
+    const size_t NC = (size_t)A.cell_ne * A.cell_np;
+    const float reach = float(c.dr_clean) + 1e-3f;
     const float ef = float(eta), pf = float(phi);
-    const float two_pi = float(2 * kPi);
-    for (int j0 = 0; j0 < n; j0 += 32 * kU) {
-        float2 v[kU];
-        bool sent[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int j = j0 + 32 * u + lane_id();
-            sent[u] = false;
-            if (A.compact)
-                v[u] = j < n ? unpack_eta_phi(A.list_q[base + j], sent[u]) : make_float2(1e30f, 0.f);
-            else
-                v[u] = j < n ? A.list_ef[base + j] : make_float2(1e30f, 0.f);
-        }
-        bool hit = false;
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            float de = v[u].x - ef;
-            float dp = v[u].y - pf;
-            if (dp > float(kPi)) dp -= two_pi;
-            if (dp <= -float(kPi)) dp += two_pi;
-            float d2 = de * de + dp * dp;
-            if (!sent[u] && d2 < thr2f * (1.0f - band)) {
-                hit = true;
-            } else if (sent[u] || d2 <= thr2f * (1.0f + band)) {
-                double e2, p2;
-                ref_eta_phi(A, A.list_ref[base + j0 + 32 * u + lane_id()], e2, p2);
-                double dd = eta - e2, dq = wrap_pi(phi - p2);
-                hit = hit || dd * dd + dq * dq < thr2;
-            }
-        }
-        if (__any_sync(kFull, hit)) return true;
+    const int ie0 = int(floorf((ef - reach + kCellEta) / A.cell_we));
+    const int ie1 = int(floorf((ef + reach + kCellEta) / A.cell_we));
+    const int jp0 = int(floorf((pf - reach + float(kPi)) / A.cell_wp));
+    const int jp1 = int(floorf((pf + reach + float(kPi)) / A.cell_wp));
+    const int ip0 = (jp0 % A.cell_np + A.cell_np) % A.cell_np, ip1 = (jp1 % A.cell_np + A.cell_np) % A.cell_np;
+    const int d = lane / kCellSlots, s = lane % kCellSlots;
+    const int ie = (d & 1) ? ie1 : ie0, ip = (d & 2) ? ip1 : ip0;
+    const bool own = !((d & 1) && ie1 == ie0) && !((d & 2) && ip1 == ip0) && ie >= 0 && ie < A.cell_ne;
+    bool hit = false;
+    if (own) {
+        const size_t cell = L * NC + (size_t)ie * A.cell_np + ip;
+        if (s < min(A.cell_cnt[cell], kCellSlots)) hit = entry_close(A, c, base, A.cell_idx[cell * kCellSlots + s], eta, phi);
+    }
+    if (__any_sync(kFull, hit)) return true;
+    const int n_ovf = min(A.ovf_cnt[L], A.list_cap);
+    for (int k0 = 0; k0 < n_ovf; k0 += 32) {
+        const int k = k0 + lane;
+        const bool h = k < n_ovf && entry_close(A, c, base, A.ovf_idx[L * A.list_cap + k], eta, phi);
+        if (__any_sync(kFull, h)) return true;
     }
     return false;
 }

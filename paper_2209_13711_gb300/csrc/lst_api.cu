@@ -412,6 +412,18 @@ static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n
     A.list_ef = b.take<float2>(E * 2 * A.list_cap);
     A.list_ref = b.take<int>(E * 2 * A.list_cap);
     A.list_q = b.take<unsigned>(E * 2 * A.list_cap);
+    {
+        const double w = std::max(0.1, 2.0 * (c->dc.dr_clean + 1e-3));
+        A.cell_ne = int(std::ceil(2.0 * kCellEta / w));
+        A.cell_np = std::max(1, int(std::floor(2.0 * kPi / w)));
+        A.cell_we = float(w);
+        A.cell_wp = float(2.0 * kPi / A.cell_np);
+    }
+    const size_t NC = (size_t)A.cell_ne * A.cell_np;
+    A.cell_cnt = b.take<int>(E * 2 * NC);
+    A.cell_idx = b.take<int>(E * 2 * NC * kCellSlots);
+    A.ovf_cnt = b.take<int>(E * 2);
+    A.ovf_idx = b.take<int>(E * 2 * A.list_cap);
     A.tc_cap = K.tc_per_event;
     A.tc_cnt = b.take<int>(E);
     const size_t TC = E * K.tc_per_event;

@@ -79,6 +79,8 @@ template <> __device__ __forceinline__ double cval<double>(double d, float) { re
 // Per-event statistics a result slot keeps: counts[8], dropped[8], track
 // candidates (the lst_stats kinds).
 constexpr int kSlotStats = 17;
+constexpr int kCellSlots = 8;      // list positions held per eta-phi cell
+constexpr float kCellEta = 4.f;    // the cells cover |eta| < kCellEta
 
 struct BatchDesc {
     int n_ev, n_hits, n_seeds, pad;
@@ -244,6 +246,15 @@ struct Arena {
     float2* list_ef;              // [n_ev][2][list_cap] (eta, phi) float
     int* list_ref;                // [n_ev][2][list_cap] (category << 28) | index
     unsigned* list_q;             // compact storage: (eta, phi) as two 16-bit fixed-point halves
+    // eta-phi cells over each list (|eta| < kCellEta, cell sides >= 2 (dr_clean + 1e-3)), so that a
+    // query reads the entries of at most 2 x 2 cells; entries past kCellSlots in a cell, or outside the
+    // eta range, go to the list's overflow, which every query scans
+    int cell_ne, cell_np;         // cells in eta and in phi
+    float cell_we, cell_wp;       // cell widths
+    int* cell_cnt;                // [n_ev][2][cell_ne * cell_np]
+    int* cell_idx;                // [n_ev][2][cells][kCellSlots]: list positions
+    int* ovf_cnt;                 // [n_ev][2]
+    int* ovf_idx;                 // [n_ev][2][list_cap]
     // track candidates, per-event slabs
     int tc_cap;
     int* tc_cnt;                  // [n_ev]
