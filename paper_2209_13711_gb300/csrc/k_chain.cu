@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(kT3Warps * 32, 4) k_t3(Arena A, DevCfg c) {
 // ---------------------------------------------------------------------------
 // T5: candidates = (T3_1 from inner MD A) x (T3_2 from T3_1's outer MD), in
 // work items of 8-32 T3_1. FP32 curvature and fit prefilters (conservative),
-// then the full test in FP64 for the survivors (k_t5_refine).
+// then the full test for the survivors (k_t5_refine, float-float fit).
 // ---------------------------------------------------------------------------
 struct T5Smem {
     int cur[5];                // the warp's item cursor (t5_next_item): event, front count, total, region

@@ -176,7 +176,7 @@ __global__ void k_pt_plan(Arena A) {
 // items from a shared cursor; a seed's candidates are the T objects whose
 // inner MD sits in one of the chunk's modules. An item's survivors are staged and written as one
 // segment; an item with more survivors than the stage holds is enumerated a
-// second time and written directly. k_pt_refine decides in FP64.
+// second time and written directly. The pT refines decide (float-float fit).
 template <int NT>
 __device__ __forceinline__ void pt_kernel_body(Arena& A, const DevCfg& c) {
     __shared__ PtSmem sm[kPtWarps];
