@@ -734,9 +734,12 @@ __global__ void k_clean_pls(Arena A, DevCfg c) {
 }
 
 // The batch's track candidates, event after event, into the record array of
-// the batch's result slot: one block per event (grid-stride over events)
-// sums the counts of the events before it for its offset, then copies its
-// slab and the event's statistics (every other stage has finished).
+// the batch's result slot. Blocks take (event, slice) pairs, grid-stride, with
+// as many slices per event as the grid has blocks per event (at most 16): for
+// one event the copy spreads over 16 blocks, for a batch it stays one or two
+// blocks per event. Each block sums the counts of the events before its event
+// for the offset and copies its slice; the first slice of an event also
+// writes the event's offset and statistics (every other stage has finished).
 __global__ void k_tc_pack(Arena A) {
     pdl_begin();
     __shared__ int red[32];
@@ -746,9 +749,15 @@ __global__ void k_tc_pack(Arena A) {
     int* const out_off = A.bd->out_off;
     int* const out_stats = A.bd->out_stats;
     const int nw = (blockDim.x + 31) >> 5, w = threadIdx.x >> 5;
-    for (int e = blockIdx.x; e < n_ev; e += gridDim.x) {
+    const int slices = max(1, min(16, int(gridDim.x) / max(1, n_ev)));
+    for (long long v = blockIdx.x; v < (long long)n_ev * slices; v += gridDim.x) {
+        const int e = int(v / slices), j = int(v % slices);
+        const int n = min(A.tc_cnt[e], A.tc_cap);
+        const int len = (n + slices - 1) / slices;
+        const int i0 = j * len;
+        if (i0 >= n && j > 0) continue;           // block-uniform: nothing of this event in the slice
         int part = 0;
-        for (int j = threadIdx.x; j < e; j += blockDim.x) part += min(A.tc_cnt[j], A.tc_cap);
+        for (int k = threadIdx.x; k < e; k += blockDim.x) part += min(A.tc_cnt[k], A.tc_cap);
         for (int d = 16; d; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
         if (lane_id() == 0) red[w] = part;
         __syncthreads();
@@ -758,17 +767,19 @@ __global__ void k_tc_pack(Arena A) {
             s_off = t;
         }
         __syncthreads();
-        const int off = s_off, n = min(A.tc_cnt[e], A.tc_cap);
-        if (threadIdx.x == 0) {
-            out_off[e] = off;
-            if (e == n_ev - 1) out_off[n_ev] = off + n;
+        const int off = s_off;
+        if (j == 0) {
+            if (threadIdx.x == 0) {
+                out_off[e] = off;
+                if (e == n_ev - 1) out_off[n_ev] = off + n;
+            }
+            if (threadIdx.x < 16)
+                out_stats[kSlotStats * e + threadIdx.x] =
+                    threadIdx.x < 8 ? A.ev_counts[8 * e + threadIdx.x] : A.ev_drop[8 * e + threadIdx.x - 8];
+            if (threadIdx.x == 16) out_stats[kSlotStats * e + 16] = n;
         }
-        if (threadIdx.x < 16)
-            out_stats[kSlotStats * e + threadIdx.x] =
-                threadIdx.x < 8 ? A.ev_counts[8 * e + threadIdx.x] : A.ev_drop[8 * e + threadIdx.x - 8];
-        if (threadIdx.x == 16) out_stats[kSlotStats * e + 16] = n;
         const size_t src = (size_t)e * A.tc_cap;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = i0 + threadIdx.x; i < min(n, i0 + len); i += blockDim.x) {
             TcRec r;
             r.type = A.tc_type[src + i];
             r.seed = A.tc_seed[src + i];
