@@ -264,3 +264,20 @@ def test_float_float_and_fp64_fits_agree(geom_full, maps_full, n_ev):
             if kind == "t5":
                 d[:, 4] = np.abs(np.angle(np.exp(1j * (a[:, 4] - b[:, 4]))))     # phi0 across the +-pi cut
             assert np.all(d <= 2e-6 * np.abs(b) + 1e-7), kind
+
+
+def test_cleaning_cells_overflow_matches_the_oracle(geom_full, maps_full):
+    """A cleaning distance of 0.3 makes the eta-phi cells 0.6 wide, so busy cells hold more entries than their
+    8 slots and the lists' overflow path runs; the track candidates still match the oracle's."""
+    import paper_2209_13711_gb300 as P
+    from oracle import oracle as O
+    cuts = dict(DEFAULT_CUTS, dr_clean=0.3)
+    ev = E.pileup_event(60, 31, geom_full)
+    ctx = P.Context(geom_full.module_table(), maps_full, cfg=cuts, capacity=P.default_capacity(1))
+    ctx.run([ev])
+    g = gpu_result(ctx)
+    _no_drops(g)
+    o = O.Setup(geom_full.module_table(), maps_full, cuts, ev).run()
+    s = compare(g, o, A_HALF, cuts)
+    assert s["tc"][0] >= 100
+    ctx.close()
