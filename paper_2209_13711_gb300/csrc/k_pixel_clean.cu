@@ -228,11 +228,11 @@ __device__ __forceinline__ void pt_kernel_body(Arena& A, const DevCfg& c) {
     }
 }
 
-__global__ void __launch_bounds__(kPtWarps * 32, 6) k_pt5(Arena A, DevCfg c) {
+__global__ void __launch_bounds__(kPtWarps * 32, 8) k_pt5(Arena A, DevCfg c) {
     pdl_begin();
     pt_kernel_body<5>(A, c);
 }
-__global__ void __launch_bounds__(kPtWarps * 32, 6) k_pt3(Arena A, DevCfg c) {
+__global__ void __launch_bounds__(kPtWarps * 32, 8) k_pt3(Arena A, DevCfg c) {
     pdl_begin();
     pt_kernel_body<3>(A, c);
 }
