@@ -378,10 +378,10 @@ __global__ void k_md_plan(Arena A) {
         if (nl == 0 || nu == 0) continue;
         const int len = md_chunk_len(nl, nu), nch = (nl + len - 1) / len;
         if (nch > 1) {
-            const int k = atomicAdd(&A.counters[8], nch);
+            const int k = atomic_add_agg(&A.counters[8], nch);
             for (int j = 0; j < nch; ++j) A.md_items[k + j] = make_int2(u, (j * len) | (len << 16));
         } else {
-            const int k = atomicAdd(&A.counters[9], 1);
+            const int k = atomic_add_agg(&A.counters[9], 1);
             A.md_items[A.md_item_cap - 1 - k] = make_int2(u, len << 16);
         }
     }
@@ -838,13 +838,13 @@ __global__ void k_t5_plan(Arena A) {
         const int e = A.md_gmod[i] / A.n_mod;
         const int s0 = A.t3_off[i], nch = (n + clen - 1) / clen;
         if (nch > 1) {
-            const int k = atomicAdd(&A.t5_evf[e], nch);
+            const int k = atomic_add_agg(&A.t5_evf[e], nch);
             for (int j = 0; j < nch; ++j) A.t5_items[s_base[e] + k + j] = s0 + j * clen;
-            atomicAdd(&A.counters[22], nch);
+            atomic_add_agg(&A.counters[22], nch);
         } else {
-            const int k = atomicAdd(&A.t5_evb[e], 1);
+            const int k = atomic_add_agg(&A.t5_evb[e], 1);
             A.t5_items[s_base[e + 1] - 1 - k] = s0;
-            atomicAdd(&A.counters[23], 1);
+            atomic_add_agg(&A.counters[23], 1);
         }
     }
 }
@@ -1003,7 +1003,7 @@ __device__ __forceinline__ void t5_store(Arena& A, int i, int e, bool pass, cons
     A.t5_pt[i] = float(o.pt);
     if (!use_mlp) {
         A.t5_valid[i] = pass;
-        if (pass) atomicAdd(&A.ev_counts[e * 8 + 3], 1);
+        if (pass) atomic_add_agg(&A.ev_counts[e * 8 + 3], 1);
     }
 }
 

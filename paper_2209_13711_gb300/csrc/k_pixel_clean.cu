@@ -46,7 +46,7 @@ __global__ void k_pls(Arena A, DevCfg c) {
         A.pls_phi[g] = phi0;
         if (pass) {
             int e = event_of(A.seed_off, B.n_ev, g);
-            atomicAdd(&A.ev_counts[e * 8 + 4], 1);
+            atomic_add_agg(&A.ev_counts[e * 8 + 4], 1);
         }
     }
 }
@@ -167,7 +167,7 @@ __global__ void k_pt_plan(Arena A) {
         const int j0 = A.sb_off[sb], n = A.sb_off[sb + 1] - j0;
         if (n <= 0) continue;
         const int nch = (n + kPtChunk - 1) / kPtChunk;
-        const int k = atomicAdd(&A.counters[25], nch);
+        const int k = atomic_add_agg(&A.counters[25], nch);
         for (int j = 0; j < nch && k + j < A.pt_item_cap; ++j) A.pt_items[k + j] = make_int2(g, j0 + j * kPtChunk);
     }
 }
@@ -315,7 +315,7 @@ template <int NT> __device__ __forceinline__ void pt_refine_group(Arena& A, cons
                 A.pt3_valid[i] = pass; A.pt3_kappa[i] = float(o.kappa); A.pt3_chi2[i] = float(o.chi2_rphi);
                 A.pt3_chi2z[i] = float(o.chi2_rz); A.pt3_score[i] = float(o.score); A.pt3_pt[i] = float(o.pt);
             }
-            if (pass) atomicAdd(&A.ev_counts[event_of(A.seed_off, A.bd->n_ev, g) * 8 + (NT == 5 ? 5 : 6)], 1);
+            if (pass) atomic_add_agg(&A.ev_counts[event_of(A.seed_off, A.bd->n_ev, g) * 8 + (NT == 5 ? 5 : 6)], 1);
         }
     }
 }
@@ -366,7 +366,7 @@ template <int NT> __device__ __forceinline__ void pt_refine_thread(Arena& A, con
             A.pt3_valid[i] = pass; A.pt3_kappa[i] = float(o.kappa); A.pt3_chi2[i] = float(o.chi2_rphi);
             A.pt3_chi2z[i] = float(o.chi2_rz); A.pt3_score[i] = float(o.score); A.pt3_pt[i] = float(o.pt);
         }
-        if (pass) atomicAdd(&A.ev_counts[event_of(A.seed_off, A.bd->n_ev, g) * 8 + (NT == 5 ? 5 : 6)], 1);
+        if (pass) atomic_add_agg(&A.ev_counts[event_of(A.seed_off, A.bd->n_ev, g) * 8 + (NT == 5 ? 5 : 6)], 1);
     }
 }
 

@@ -45,6 +45,26 @@ __device__ __forceinline__ void for_each_flat(int off, int len, int* sm_pre, int
     __syncwarp();
 }
 
+// atomicAdd(p, v) for the lanes that call it together, one atomic per
+// distinct address among them: each lane receives what its own atomicAdd would
+// have returned had the lanes of its address gone in lane order. Planning
+// kernels add to a handful of per-event or global cursors from every thread;
+// unaggregated, those same-address atomics serialise at the L2.
+__device__ __forceinline__ int atomic_add_agg(int* p, int v) {
+    const unsigned peers = __match_any_sync(__activemask(), reinterpret_cast<unsigned long long>(p));
+    const int lane = lane_id(), leader = __ffs(peers) - 1;
+    int prefix = 0, total = 0;
+    for (unsigned m = peers; m; m &= m - 1) {
+        const int l = __ffs(m) - 1;
+        const int vl = __shfl_sync(peers, v, l);
+        if (l < lane) prefix += vl;
+        total += vl;
+    }
+    int base = 0;
+    if (lane == leader) base = atomicAdd(p, total);
+    return __shfl_sync(peers, base, leader) + prefix;
+}
+
 // Reserve n slots of a flat arena with one atomic per warp; returns the
 // base (broadcast) and clips n to the arena capacity (the clipped part is
 // added to dropped).
