@@ -266,7 +266,10 @@ class DeviceSlot:
         self.capacity = SlotCapacity(cap.max_events, cap.max_hits, cap.max_seeds)
         self.stream = torch.cuda.Stream(device=torch.device("cuda", device))
         self.device_bytes = self.ctx.device_bytes
-        self.records = np.empty(cap.max_events * cap.tc_per_event, L.TC_DTYPE)
+        # results land in pinned host memory (a direct copy, not one staged through a driver buffer)
+        self._rec_buf = torch.empty(cap.max_events * cap.tc_per_event * L.TC_DTYPE.itemsize,
+                                    dtype=torch.uint8).pin_memory()
+        self.records = self._rec_buf.numpy().view(L.TC_DTYPE)
 
     def launch(self, batch):
         self.ctx.run_events([self.pool.views[r.event] for r in batch], stream=self.stream.cuda_stream)
