@@ -131,11 +131,23 @@ __device__ __forceinline__ void pt_enumerate(const Arena& A, const DevCfg& c, Pt
         if (mvalid) {
             oo = NT == 5 ? A.t5_off[md] : A.t3_off[md];
             on = NT == 5 ? A.t5_cnt[md] : A.t3_cnt[md];
+            if (NT == 3) {
+                const float smax = A.t3_smax[md];
+                if (smax >= 0.f) {
+                    // the view is curvature-ordered: only the T3s inside the seed's window can pass
+                    const float w = ks_window(kp, sp, smax, nk, ks_slack(A));
+                    const int lo = ks_bound(A.t3_kord, oo, oo + on, kp - w, false);
+                    on = ks_bound(A.t3_kord, lo, oo + on, kp + w, true) - lo;
+                    oo = lo;
+                }
+            }
         }
-        for_each_flat(oo, on, S.pre2, S.off2, [&](bool valid, int, int obj) {
+        for_each_flat(oo, on, S.pre2, S.off2, [&](bool valid, int, int p) {
             bool pass = false;
+            // pT3: p is a position of the ordered view, the T3 its permutation entry
+            const int obj = NT == 5 ? p : (valid ? A.t3_perm[p] : 0);
             if (valid && (NT == 3 || A.t5_valid[obj])) {
-                const float2 ks = NT == 5 ? A.t5_ks[obj] : t3_ks_search(A, obj);
+                const float2 ks = NT == 5 ? A.t5_ks[obj] : A.t3_kord[p];
                 const float kt = ks.x, st = ks.y;
                 float thr = nk * fast_sqrtf(sp * sp + st * st);
                 const float rel = NT == 5 ? 1e-5f : ks_slack(A);
@@ -154,6 +166,60 @@ __device__ __forceinline__ void pt_enumerate(const Arena& A, const DevCfg& c, Pt
     });
     __syncwarp();
     if (ncand) pt_flush<NT>(A, c, S, g, ncand, sink);
+}
+
+// The pT3 search's curvature-ordered view of each inner MD's T3s, one warp
+// per MD: the permutation, the (curvature, sigma) pairs in that order and the
+// largest sigma, so that the search bounds the T3s that can pass its curvature
+// prefilter by binary search (on a PU200 event 95 % of the (seed, T3) pairs
+// fail it). An MD with more than kT3Order T3s keeps the identity order (its
+// t3_smax < 0: no window). The T3 arrays themselves are not reordered: the T5
+// search reads them at the same time on the graph's other branch.
+constexpr int kT3Order = 128;
+constexpr int kOrderWarps = 8;
+__device__ __forceinline__ unsigned float_order_key(float v) {
+    const unsigned u = __float_as_uint(v);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);   // the FP32 order (NaNs at the ends)
+}
+__global__ void __launch_bounds__(kOrderWarps * 32) k_t3_order(Arena A) {
+    pdl_begin();
+    __shared__ unsigned key[kOrderWarps][kT3Order];
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    const int n_md = min(A.counters[0], A.md_cap);
+    const int warps = gridDim.x * kOrderWarps;
+    for (int i = blockIdx.x * kOrderWarps + w; i < n_md; i += warps) {
+        const int off = A.t3_off[i], n = A.t3_cnt[i];
+        if (n == 0) continue;                        // the search never reads an empty MD's view
+        if (n > kT3Order) {
+            for (int k = lane; k < n; k += 32) {
+                A.t3_perm[off + k] = off + k;
+                A.t3_kord[off + k] = t3_ks_search(A, off + k);
+            }
+            if (lane == 0) A.t3_smax[i] = -1.f;
+            continue;
+        }
+        float smax = 0.f;
+        for (int k = lane; k < n; k += 32) {
+            const float2 v = t3_ks_search(A, off + k);
+            key[w][k] = float_order_key(v.x);
+            smax = fmaxf(smax, v.y);
+        }
+        __syncwarp();
+        for (int k = lane; k < n; k += 32) {
+            const unsigned kk = key[w][k];
+            int rank = 0;
+            for (int j = 0; j < n; ++j) {
+                const unsigned kj = key[w][j];
+                rank += (kj < kk) || (kj == kk && j < k);
+            }
+            A.t3_perm[off + rank] = off + k;
+            A.t3_kord[off + rank] = t3_ks_search(A, off + k);
+        }
+#pragma unroll
+        for (int d = 16; d; d >>= 1) smax = fmaxf(smax, __shfl_xor_sync(kFull, smax, d));
+        if (lane == 0) A.t3_smax[i] = smax;
+        __syncwarp();
+    }
 }
 
 // pT work items: (passing seed, a chunk of up to kPtChunk modules of its

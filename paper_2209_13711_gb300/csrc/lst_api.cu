@@ -39,7 +39,7 @@ struct Buffer {
 enum LaunchId {
     L_RESET, L_BIN_COUNT, L_BIN_SCAN, L_BIN_SCATTER, L_BIN_SORT, L_MD_PLAN, L_MD, L_MD_WRITE, L_LS, L_T3,
     L_T3_FEAT, L_T3_SCORE, L_T5_PLAN, L_T5, L_T5_GATHER, L_T5_REFINE,
-    L_T5_MLP, L_T5_MLP_SELECT, L_PLS, L_PT_PLAN, L_PT5, L_PT5_REFINE, L_PT3, L_PT3_REFINE, L_CLEAN_KEYS, L_CLEAN_KEEP,
+    L_T5_MLP, L_T5_MLP_SELECT, L_PLS, L_PT_PLAN, L_T3_ORDER, L_PT5, L_PT5_REFINE, L_PT3, L_PT3_REFINE, L_CLEAN_KEYS, L_CLEAN_KEEP,
     L_CLEAN_PT5, L_CLEAN_PT3_CROSS, L_CLEAN_PT3_MARK, L_CLEAN_T5, L_CLEAN_PLS, L_TC_PACK, kNumLaunch
 };
 
@@ -72,6 +72,7 @@ const LaunchInfo kLaunch[kNumLaunch] = {
     {"t5_mlp_select", 4, 128, true, true},
     {"pls", 4, 128, true, true},
     {"pt_plan", 4, 256, true, true},
+    {"t3_order", 8, 256, true, false},
     {"pt5", 8, kPtWarps * 32, true, false},
     {"pt5_refine", 2, 128, true, true},
     {"pt3", 8, kPtWarps * 32, true, false},
@@ -367,6 +368,7 @@ static void layout(lst_ctx* c, Buffer& b, int n_mod, int n_conn, int n_sb, int n
     A.two_a = float(2.0 * c->dc.a);
     A.t3_md = b.take<int4>(T3);
     A.t3_off = b.take<int>(MD); A.t3_cnt = b.take<int>(MD);
+    A.t3_perm = b.take<int>(T3); A.t3_kord = b.take<float2>(T3); A.t3_smax = b.take<float>(MD);
     const size_t T5 = E * K.t5_per_event;
     A.t5_cap = (int)T5;
     A.t5_in = b.take<int>(T5); A.t5_out = b.take<int>(T5);
@@ -573,7 +575,8 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile, cudaStream_
     if (side) {
         cudaEventRecord(c->ev_t3, st);
         cudaStreamWaitEvent(side, c->ev_t3, 0);
-        LAUNCH(L_PT3, run_k(k_pt3, GB(L_PT3), 0, side, false, A, dc));
+        LAUNCH(L_T3_ORDER, run_k(k_t3_order, GB(L_T3_ORDER), 0, side, false, A));
+        LAUNCH(L_PT3, run_k(k_pt3, GB(L_PT3), 0, side, pdl, A, dc));
         LAUNCH(L_PT3_REFINE, run_k(k_pt3_refine, GB(L_PT3_REFINE), 0, side, pdl, A, dc));
         cudaEventRecord(c->ev_pt3, side);
     }
@@ -602,6 +605,7 @@ static void enqueue_chain(lst_ctx* c, cudaStream_t st, bool profile, cudaStream_
     if (side) {
         cudaStreamWaitEvent(st, c->ev_pt3, 0);
     } else {
+        LAUNCH(L_T3_ORDER, run_k(k_t3_order, GB(L_T3_ORDER), 0, st, pdl, A));
         LAUNCH(L_PT3, run_k(k_pt3, GB(L_PT3), 0, st, pdl, A, dc));
         LAUNCH(L_PT3_REFINE, run_k(k_pt3_refine, GB(L_PT3_REFINE), 0, st, pdl, A, dc));
     }
@@ -854,6 +858,7 @@ static const void* launch_fn(int id) {
         case L_T5_MLP_SELECT: return (const void*)k_t5_mlp_select;
         case L_PLS: return (const void*)k_pls;
         case L_PT_PLAN: return (const void*)k_pt_plan;
+        case L_T3_ORDER: return (const void*)k_t3_order;
         case L_PT5: return (const void*)k_pt5;
         case L_PT5_REFINE: return (const void*)k_pt5_refine;
         case L_PT3: return (const void*)k_pt3;

@@ -170,6 +170,9 @@ struct Arena {
     int4* t3_md;                  // the three MDs {inner, middle, outer, 0}
     int* t3_off;                  // [md_cap] by inner MD
     int* t3_cnt;
+    int* t3_perm;                 // [t3_cap] the pT3 search's view: each inner MD's T3s in curvature order
+    float2* t3_kord;              // [t3_cap] their (curvature, sigma) as the searches read them, in that order
+    float* t3_smax;               // [md_cap] the largest such sigma of the MD's T3s; < 0: view not ordered
     // T5
     int t5_cap;
     int* t5_in;
@@ -1398,6 +1401,26 @@ __device__ __forceinline__ float2 t3_ks_search(const Arena& A, int t) {
     return make_float2(v.x * A.two_a, v.y * A.two_a);
 }
 __device__ __forceinline__ float ks_slack(const Arena& A) { return A.compact ? 1e-3f : 1e-5f; }
+
+// Curvature window of the searches' prefilter |k - kt| <= 1.01 n sqrt(s^2 + st^2) + rel (|k| + |kt|) + 1e-7
+// against objects whose sigma st is at most smax: with sqrt(s^2 + st^2) <= s + st and |kt| <= |k| + |k - kt|,
+// every kt that can pass lies within the returned w of k (the factors 1.001 and 1e-7 cover the FP32 rounding
+// of both sides).
+__device__ __forceinline__ float ks_window(float k, float s, float smax, float n, float rel) {
+    return (1.01f * n * (s + smax) + 2.f * rel * fabsf(k) + 1e-7f) / (1.f - rel) * 1.001f + 1e-7f;
+}
+
+// First position in [lo, hi) of curvature-ordered (curvature, sigma) pairs whose curvature is >= x (> x with
+// upper).
+__device__ __forceinline__ int ks_bound(const float2* ks, int lo, int hi, float x, bool upper) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const float v = ks[mid].x;
+        if (upper ? !(v > x) : (v < x)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
 
 // Fixed-point eta-phi: 1e-4 per step in eta (|eta| < 3.2767) and pi / 32767
 // in phi; an eta outside that range is stored as the sentinel -32768, which

@@ -44,6 +44,7 @@ __global__ void k_t5_refine(Arena A, DevCfg c);
 __global__ void k_t5_mlp_select(Arena A, DevCfg c);
 __global__ void k_pls(Arena A, DevCfg c);
 __global__ void k_pt_plan(Arena A);
+__global__ void k_t3_order(Arena A);
 __global__ void k_pt5(Arena A, DevCfg c);
 __global__ void k_pt3(Arena A, DevCfg c);
 __global__ void k_pt5_refine(Arena A, DevCfg c);
