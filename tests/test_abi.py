@@ -27,6 +27,14 @@ def test_result_slot_count_matches_the_header():
     assert int(re.search(r"#define LST_RESULT_SLOTS (\d+)", src).group(1)) == lst.LST_RESULT_SLOTS
 
 
+def test_setters_refuse_a_null_context_without_device():
+    """The context setters answer LST_ERR_ARG for a missing context before touching a device."""
+    from paper_2209_13711_gb300 import lst
+    L = lst.library()
+    assert L.lst_set_fp64_fit(None, 1) == -1
+    assert L.lst_set_compact_storage(None, 1) == -1
+
+
 def test_release_refuses_indices_and_null_without_device():
     from paper_2209_13711_gb300 import lst
     L = lst.library()
